@@ -1,0 +1,192 @@
+"""Seeded synthetic inputs: octree leaf lists, density fields and weights.
+
+This module holds no arithmetic of the gravity solve.  It builds the inputs
+that both the GPU library and the CPU oracle are run on: binary-star density
+fields on octrees of 8x8x8-cell subgrids (the paper's workloads are double
+white dwarf binaries with the AMR refined on the stars and the region between
+them, Sec. 1 and Sec. 3.1, Fig. 2; the production restart files are not
+available, so polytrope-like spheres stand in for the stars).
+
+Leaves are int32 ``[n_leaf, 4]`` = (level, ix, iy, iz); densities are float64
+``[n_leaf, 512]`` with cell (i, j, k) of a leaf at ``i + 8 j + 64 k``.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+ATMOSPHERE = 1e-10
+
+# (centre, central density, radius) of the stars of each workload
+SPHERE = [((0.5, 0.5, 0.5), 1.0, 0.4)]                              # R^2 = 0.16
+BINARY = [((0.25, 0.5, 0.5), 1.0, 0.18), ((0.75, 0.5, 0.5), 0.6, 0.12)]
+# mass ratio 0.7 with the same radii: rho_c2 = 0.7 (0.18 / 0.12)^3
+BINARY_Q07 = [((0.25, 0.5, 0.5), 1.0, 0.18), ((0.75, 0.5, 0.5), 0.7 * (0.18 / 0.12) ** 3, 0.12)]
+
+
+def uniform_leaves(level: int, order: str = "zyx", seed: int | None = None) -> np.ndarray:
+    """All 8**level nodes of one level as leaves (lexicographic, z slowest),
+    optionally shuffled with a seeded permutation."""
+    n = 1 << level
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    leaves = np.stack([np.full(x.size, level), x.ravel(), y.ravel(), z.ravel()], 1)
+    leaves = leaves.astype(np.int32)
+    if seed is not None:
+        leaves = leaves[np.random.default_rng(seed).permutation(leaves.shape[0])]
+    return np.ascontiguousarray(leaves)
+
+
+def cell_centres(leaves, origin=(0.0, 0.0, 0.0), size=1.0) -> np.ndarray:
+    """Cell centres [n_leaf, 512, 3] of every leaf's 8^3 cells."""
+    leaves = np.asarray(leaves)
+    L = leaves[:, 0].astype(np.float64)
+    h = size / (8.0 * 2.0 ** L)
+    l = np.arange(512)
+    loc = np.stack([l & 7, (l >> 3) & 7, l >> 6], 1).astype(np.float64)  # [512, 3]
+    base = 8.0 * leaves[:, 1:4].astype(np.float64)                        # [n, 3]
+    return np.asarray(origin) + (base[:, None, :] + loc[None] + 0.5) * h[:, None, None]
+
+
+def star_density(x: np.ndarray, stars) -> np.ndarray:
+    """max(atmosphere, sum_s rho_s (1 - |x - c_s|^2 / R_s^2)_+^1.5) at points x [..., 3]."""
+    rho = np.zeros(x.shape[:-1])
+    for c, rc, R in stars:
+        q = 1.0 - np.sum((x - np.asarray(c)) ** 2, -1) / (R * R)
+        rho += rc * np.clip(q, 0.0, None) ** 1.5
+    return np.maximum(rho, ATMOSPHERE)
+
+
+def density(leaves, stars, seed: int = 0, noise: float = 1e-3, origin=(0.0, 0.0, 0.0),
+            size=1.0) -> np.ndarray:
+    """Star densities at cell centres times (1 + noise * u), u ~ U[-1, 1] drawn
+    from PCG64(seed) in leaf order."""
+    rho = star_density(cell_centres(leaves, origin, size), stars)
+    u = np.random.Generator(np.random.PCG64(seed)).uniform(-1.0, 1.0, size=rho.shape)
+    return np.ascontiguousarray(rho * (1.0 + noise * u))
+
+
+def _node_mass(nodes: np.ndarray, stars) -> np.ndarray:
+    """Sum of rho h^3 over the 8^3 cells of each node (no noise): the
+    refinement indicator of the synthetic AMR trees."""
+    rho = star_density(cell_centres(nodes), stars)
+    h = 1.0 / (8.0 * 2.0 ** nodes[:, 0].astype(np.float64))
+    return rho.sum(1) * h ** 3
+
+
+def _covering_level(leafset: set, L: int, x: int, y: int, z: int) -> int:
+    """Level of the leaf that covers node position (L, x, y, z), or L+1 if the
+    region is refined below L."""
+    for q in range(L, -1, -1):
+        s = L - q
+        if (q, x >> s, y >> s, z >> s) in leafset:
+            return q
+    return L + 1
+
+
+def balance(leaves) -> np.ndarray:
+    """Refine leaves until every pair of face/edge/corner-adjacent leaves
+    differs by at most one level (2:1 balance)."""
+    leafset = set(map(tuple, np.asarray(leaves).tolist()))
+    changed = True
+    while changed:
+        changed = False
+        for (L, x, y, z) in sorted(leafset, key=lambda t: -t[0]):
+            if (L, x, y, z) not in leafset:
+                continue
+            n = 1 << L
+            for dz in (-1, 0, 1):
+                for dy in (-1, 0, 1):
+                    for dx in (-1, 0, 1):
+                        qx, qy, qz = x + dx, y + dy, z + dz
+                        if (dx | dy | dz) == 0 or min(qx, qy, qz) < 0 or max(qx, qy, qz) >= n:
+                            continue
+                        cl = _covering_level(leafset, L, qx, qy, qz)
+                        if cl < L - 1:
+                            s = L - cl
+                            cx, cy, cz = qx >> s, qy >> s, qz >> s
+                            leafset.discard((cl, cx, cy, cz))
+                            for c in range(8):
+                                leafset.add((cl + 1, 2 * cx + (c & 1), 2 * cy + ((c >> 1) & 1),
+                                             2 * cz + (c >> 2)))
+                            changed = True
+    out = np.array(sorted(leafset), dtype=np.int32)
+    return np.ascontiguousarray(out)
+
+
+def is_balanced(leaves) -> bool:
+    leafset = set(map(tuple, np.asarray(leaves).tolist()))
+    for (L, x, y, z) in leafset:
+        n = 1 << L
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    qx, qy, qz = x + dx, y + dy, z + dz
+                    if (dx | dy | dz) == 0 or min(qx, qy, qz) < 0 or max(qx, qy, qz) >= n:
+                        continue
+                    if _covering_level(leafset, L, qx, qy, qz) < L - 1:
+                        return False
+    return True
+
+
+def amr_leaves(lmax: int, m_thr: float, stars, lmin: int = 1, do_balance: bool = True):
+    """Refine from the root: a node below lmax is split iff its mass exceeds
+    m_thr (nodes above lmin are always split), then 2:1 balance."""
+    leaves = []
+    front = np.array([[0, 0, 0, 0]], dtype=np.int64)
+    while front.shape[0]:
+        L = front[:, 0]
+        split = L < lmin
+        can = (L < lmax) & ~split
+        if np.any(can):
+            split[can] = _node_mass(front[can], stars) > m_thr
+        leaves.append(front[~split])
+        par = front[split]
+        kids = []
+        for c in range(8):
+            k = par.copy()
+            k[:, 0] += 1
+            k[:, 1] = 2 * par[:, 1] + (c & 1)
+            k[:, 2] = 2 * par[:, 2] + ((c >> 1) & 1)
+            k[:, 3] = 2 * par[:, 3] + (c >> 2)
+            kids.append(k)
+        front = np.concatenate(kids) if par.shape[0] else np.zeros((0, 4), np.int64)
+    out = np.concatenate(leaves).astype(np.int32)
+    if do_balance:
+        out = balance(out)
+    return np.ascontiguousarray(out)
+
+
+def weights(n_leaf: int, seed_w1: int = 1, seed_w2: int = 2):
+    """Gaussian weights w1 [n_leaf, 512] and w2 [n_leaf, 3, 512] of the
+    functional J = sum(w1 phi + w2 . g)."""
+    w1 = np.random.Generator(np.random.PCG64(seed_w1)).standard_normal((n_leaf, 512))
+    w2 = np.random.Generator(np.random.PCG64(seed_w2)).standard_normal((n_leaf, 3, 512))
+    return w1, w2
+
+
+# Named workloads (sizes as in the project's configuration list).
+WORKLOADS = {
+    "sphere_l1": "uniform level-1 octree, 8 leaves of 8^3 (16^3 = 4,096 cells), one sphere",
+    "binary_l3": "uniform level-3 octree, 512 leaves of 8^3 (64^3 = 262,144 cells), binary",
+    "binary_amr6": "AMR octree to level 6 refined on the binary, ~4,000 leaves (~2M cells)",
+    "binary_amr8": "AMR octree to level 8, mass ratio 0.7 binary, ~40,000 leaves (~20M cells)",
+}
+
+AMR6_MTHR = 1e-5
+AMR8_MTHR = 1e-6
+
+
+def workload(name: str, seed: int = 0):
+    """(leaves, rho) of a named workload."""
+    if name == "sphere_l1":
+        lv = uniform_leaves(1)
+        return lv, density(lv, SPHERE, seed)
+    if name == "binary_l3":
+        lv = uniform_leaves(3)
+        return lv, density(lv, BINARY, seed)
+    if name == "binary_amr6":
+        lv = amr_leaves(6, AMR6_MTHR, BINARY)
+        return lv, density(lv, BINARY, seed)
+    if name == "binary_amr8":
+        lv = amr_leaves(8, AMR8_MTHR, BINARY_Q07)
+        return lv, density(lv, BINARY_Q07, seed)
+    raise KeyError(name)
