@@ -1,0 +1,185 @@
+/*
+ * octofmm.h -- C ABI of the GB300 fast-multipole self-gravity solve.
+ *
+ * The solve is the gravity half of Octo-Tiger (arXiv 2412.15518): a fast
+ * multipole method on an adaptive octree whose every node holds an 8x8x8
+ * sub-grid of cells (Sec. 4.3.2), conserving linear momentum and, through a
+ * correction term, angular momentum (Sec. 4.3.1), with cell-to-cell
+ * interactions taken from a fixed stencil (Sec. 5.5).  The paper states the
+ * method in prose only; the operations below are the reading documented with
+ * each entry point:
+ *
+ *   * a leaf cell is a point mass m = rho h^3 at its centre (h = cell side);
+ *     phi(x) = -G sum_b m_b / |x - x_b| in free space, self pair excluded;
+ *   * moments up to order 3 about each cell's centre of mass;
+ *   * two level-L cells at integer offset d are "near" iff |d| <= 1/theta;
+ *     a non-near pair interacts at level L iff L = 0 or the parents are near
+ *     (multipole-to-local, order 3, plus the angular-momentum correction);
+ *     near pairs of two leaf cells interact exactly, near pairs with one
+ *     leaf cell interact by multipole at level L, near pairs of two interior
+ *     cells descend one level;
+ *   * exact degree-3 local-to-local shifts down the tree, then at each leaf
+ *     cell phi = L0 + near terms, g = -L1 + a_c + near terms.
+ *
+ * Conventions for every call:
+ *   * return 0 (OT_OK) or a negative OT_ERR_* code; nothing is thrown, no
+ *     call traps the GPU; ot_error_string() names each code;
+ *   * device buffers are owned by the caller (for instance torch tensors),
+ *     must live on the tree's device, hold float64, be 8-byte aligned and
+ *     contiguous in the layouts stated below;
+ *   * the library owns the tree workspace (moments, expansions, tables,
+ *     work lists, CUDA graphs); it allocates device memory only in
+ *     ot_build_tree and when a solve first meets a new (theta, precision)
+ *     plan; a solve with a known plan allocates nothing;
+ *   * work is enqueued asynchronously on the caller's CUDA stream
+ *     (cudaStream_t passed as void*, NULL = legacy default stream); the
+ *     caller synchronises before reading outputs;
+ *   * leaf order is the caller's order; cell (i, j, k) of a leaf's 8^3
+ *     sub-grid is at index i + 8 j + 64 k (x fastest);
+ *   * calls on one tree must not overlap in time (one stream at a time).
+ */
+#ifndef OCTOFMM_H
+#define OCTOFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OT_OK 0
+#define OT_ERR_INVALID_ARG -1    /* bad size, option or theta out of range        */
+#define OT_ERR_INVALID_TREE -2   /* leaf out of range, duplicate, overlap, holes  */
+#define OT_ERR_NOT_BALANCED -3   /* adjacent leaves differ by more than one level */
+#define OT_ERR_BAD_POINTER -4    /* NULL, or not device memory where required     */
+#define OT_ERR_BAD_ALIGNMENT -5  /* buffer not 8-byte aligned                     */
+#define OT_ERR_CUDA -6           /* a CUDA runtime call failed                    */
+#define OT_ERR_TIMEOUT -7        /* a bounded device wait gave up                 */
+#define OT_ERR_DEVICE_STATUS -8  /* a kernel latched an error in the status word  */
+#define OT_ERR_NO_MEMORY -9      /* host or device allocation failed              */
+#define OT_ERR_WRONG_DEVICE -10  /* buffer on another device than the tree        */
+
+#define OT_PRECISION_FP64 0      /* every step in FP64                           */
+#define OT_PRECISION_FP32_BULK 1 /* cell-to-cell multipole interactions in FP32,
+                                    FP64 accumulation; FP64 near field, moments,
+                                    expansions and correction assembly          */
+
+typedef struct ot_tree ot_tree; /* opaque, library-owned */
+
+/* Octree description (Sec. 4.3.2).  leaves: host int32 [n_leaf][4] =
+ * (L, ix, iy, iz), 0 <= ix, iy, iz < 2^L, 0 <= L <= 15; a level-L node covers
+ * origin + [ix, ix+1) * size / 2^L per axis and holds 8^3 cells of side
+ * size / (8 * 2^L).  The leaves must tile the cube exactly (a complete octree)
+ * and be 2:1 balanced across faces, edges and corners. */
+typedef struct {
+    double origin[3];
+    double size;
+    int32_t n_leaf;
+    const int32_t* leaves;
+} ot_tree_desc;
+
+/* Solve options.  theta: opening parameter of the near test |d| <= 1/theta,
+ * 0.3 <= theta <= 1 (default 0.5).  G: gravitational constant (default 1).
+ * precision: OT_PRECISION_*.  am_correction: 1 adds the angular-momentum
+ * correction (Sec. 4.3.1), 0 leaves it out.  self_term: 1 adds each leaf
+ * cell's own uniform-cube self potential -G rho h^2 C at its centre
+ * (C = 3 (ln(2 + sqrt 3) - pi/6)); 0 excludes the self pair entirely. */
+typedef struct {
+    double theta;
+    double G;
+    int32_t precision;
+    int32_t am_correction;
+    int32_t self_term;
+    int32_t reserved;
+} ot_solve_opts;
+
+#define OT_MAX_LEVELS 16
+
+/* Counts of a tree and of its current plan (theta, precision). */
+typedef struct {
+    int32_t n_levels;                          /* Lmax + 1                          */
+    int32_t n_leaf;
+    int64_t n_nodes[OT_MAX_LEVELS];            /* nodes per level                   */
+    int64_t n_leaf_nodes[OT_MAX_LEVELS];       /* leaf nodes per level              */
+    int64_t n_m2l;                             /* directed far multipole pairs      */
+    int64_t n_p2p;                             /* directed exact near leaf pairs    */
+    int64_t n_seam;                            /* directed near leaf/interior pairs */
+    int64_t n_lattice;                         /* far pairs of two leaf cells       */
+    int64_t n_m2p;                             /* pairs: interior source, leaf target */
+    int64_t n_p2m;                             /* pairs: leaf source, interior target */
+    int64_t n_mm;                              /* pairs: two interior cells         */
+    double flops_am;                           /* algorithmic flops of one interaction
+                                                  launch with the correction (fma = 2) */
+    double flops_noam;                         /* the same without the correction    */
+    double flops_near;                         /* part of either kept in FP64 by the
+                                                  FP32-bulk form (exact near pairs)  */
+    int64_t n_work_items;                      /* items of the persistent launch    */
+    int32_t tuned_chunk;                       /* stencil entries per work item     */
+    int32_t tuned_ctas_per_sm;                 /* persistent CTAs per SM            */
+    int32_t tuned_warps_per_cta;
+    int32_t device_status;                     /* latched device error, 0 = none    */
+    int64_t workspace_bytes;                   /* device memory held by the tree    */
+} ot_tree_stats;
+
+/* Builds the octree, its level tables, neighbour tables, stencils and work
+ * lists (host), and uploads them to `device`.  device = -1 validates and
+ * counts on the host only (no CUDA call; solves then fail with
+ * OT_ERR_INVALID_ARG).  On success *out owns the workspace until
+ * ot_destroy_tree. */
+int ot_build_tree(const ot_tree_desc* desc, int device, ot_tree** out);
+
+/* Upward pass: leaf moments (m = rho h^3 at the cell centre) and exact M2M
+ * to every interior cell's centre of mass.  rho: device float64
+ * [n_leaf][512].  The moments stay in the tree workspace. */
+int ot_compute_moments(ot_tree* tree, const double* rho, void* stream);
+
+/* Full solve: moments, every cell-to-cell interaction of every level in one
+ * persistent launch, L2L shifts and evaluation.  rho: device float64
+ * [n_leaf][512]; phi: device float64 [n_leaf][512]; g: device float64
+ * [n_leaf][3][512] (component-major per leaf).  opts may be NULL
+ * (defaults).  The first solve of a plan captures a CUDA graph that later
+ * solves with the same buffers replay. */
+int ot_solve_gravity(ot_tree* tree, const double* rho, double* phi, double* g,
+                     const ot_solve_opts* opts, void* stream);
+
+/* Same as ot_solve_gravity with HOST buffers (pageable or pinned):
+ * copies rho in, solves, copies phi and g out, all on `stream`; the outputs
+ * are valid after the stream is synchronised. */
+int ot_solve_gravity_host(ot_tree* tree, const double* rho_host, double* phi_host,
+                          double* g_host, const ot_solve_opts* opts, void* stream);
+
+/* Adjoint of the solve: drho = dJ/drho for J = sum_c (w1_c phi_c + w2_c . g_c),
+ * the exact derivative of the discrete solve (through the centres of mass
+ * and the correction's mass ratio).  w1: device float64 [n_leaf][512];
+ * w2: device float64 [n_leaf][3][512]; drho: device float64 [n_leaf][512]
+ * (overwritten).  Runs the upward pass itself. */
+int ot_gravity_backward(ot_tree* tree, const double* rho, const double* w1, const double* w2,
+                        double* drho, const ot_solve_opts* opts, void* stream);
+
+/* Times the candidate work-item shapes of the persistent launch for this
+ * plan on `stream` (synchronises it) and keeps the fastest.  rho/phi/g as in
+ * ot_solve_gravity (their contents are overwritten by the timing runs). */
+int ot_autotune(ot_tree* tree, const double* rho, double* phi, double* g,
+                const ot_solve_opts* opts, void* stream);
+
+/* Device time in milliseconds of the interaction launch (all levels) and of
+ * the whole solve in the most recent ot_solve_gravity(_host) on this tree,
+ * from CUDA events recorded around them inside the solve's CUDA graph.
+ * Waits for those events.  Either pointer may be NULL. */
+int ot_last_solve_times(ot_tree* tree, float* interact_ms, float* solve_ms);
+
+/* Counts of the tree and of the current plan; synchronises the tree's last
+ * stream to read the device status word. */
+int ot_tree_info(ot_tree* tree, ot_tree_stats* stats);
+
+/* Releases the workspace; NULL is ignored. */
+void ot_destroy_tree(ot_tree* tree);
+
+/* Static string for an OT_* code. */
+const char* ot_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OCTOFMM_H */

@@ -54,7 +54,7 @@ def _load():
                               ctypes.c_double, ctypes.c_int, ctypes.c_int, _D, _D, _I64]
     lib.orc_solve_sample.argtypes = [ctypes.c_int, _I32, _D, ctypes.c_double, _D,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_int,
-                                     ctypes.c_int, ctypes.c_long, _I64, _D, _D]
+                                     ctypes.c_int, ctypes.c_long, _I64, _D, _D, _I64]
     lib.orc_solve_jvp.argtypes = [ctypes.c_int, _I32, _D, ctypes.c_double, _D, _D,
                                   ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                   _D, _D, _D, _D]
@@ -122,17 +122,21 @@ def solve(leaves, rho, theta=0.5, G=1.0, am_correction=True, self_term=False,
 
 
 def solve_sample(leaves, rho, sample, theta=0.5, G=1.0, am_correction=True, self_term=False,
-                 origin=(0.0, 0.0, 0.0), size=1.0):
+                 origin=(0.0, 0.0, 0.0), size=1.0, return_counts=False):
     """Solve for sampled leaf cells only (sample = leaf * 512 + cell); returns
-    (phi [n_sample], g [n_sample, 3])."""
+    (phi [n_sample], g [n_sample, 3][, counts of the pairs evaluated])."""
     lib = _load()
     leaves, rho, org = _prep(leaves, rho, origin)
     sample = np.ascontiguousarray(sample, dtype=np.int64)
     phi = np.empty(sample.shape[0])
     g = np.empty((sample.shape[0], 3))
+    cnt = np.zeros(3, dtype=np.int64)
     _check(lib.orc_solve_sample(leaves.shape[0], _p(leaves, _I32), _p(org), size, _p(rho),
                                 theta, G, int(bool(am_correction)), int(bool(self_term)),
-                                sample.shape[0], _p(sample, _I64), _p(phi), _p(g)))
+                                sample.shape[0], _p(sample, _I64), _p(phi), _p(g),
+                                _p(cnt, _I64)))
+    if return_counts:
+        return phi, g, dict(m2l=int(cnt[0]), p2p=int(cnt[1]), seam=int(cnt[2]))
     return phi, g
 
 

@@ -691,14 +691,16 @@ int orc_solve(int n_leaf, const int32_t* leaves, const double* origin, double si
 }
 
 // Solve for a sample of leaf cells only: sample[s] = leaf * 512 + cell;
-// phi_s [n_sample], g_s [n_sample][3].
+// phi_s [n_sample], g_s [n_sample][3]; counts (optional) as in orc_solve,
+// restricted to the pairs evaluated for the sampled cells and their ancestors.
 int orc_solve_sample(int n_leaf, const int32_t* leaves, const double* origin, double size,
                      const double* rho, double theta, double G, int am, int self_term,
-                     long n_sample, const int64_t* sample, double* phi_s, double* g_s) {
+                     long n_sample, const int64_t* sample, double* phi_s, double* g_s,
+                     int64_t* counts) {
     Tree t;
     int e = build_tree(n_leaf, leaves, origin, size, t);
     if (e) return e;
-    return solve<double>(t, rho, theta, G, am, self_term, phi_s, g_s, sample, n_sample, nullptr);
+    return solve<double>(t, rho, theta, G, am, self_term, phi_s, g_s, sample, n_sample, counts);
 }
 
 // Forward-mode directional derivative of (phi, g) along v (same layout as rho).

@@ -1,0 +1,562 @@
+// C ABI of the GB300 FMM gravity library (declared in include/octofmm.h).
+//
+// Owns the tree workspace on the device, the interaction plan for the
+// current opening parameter, the CUDA graphs of the solve and the autotuned
+// shape of the persistent interaction launch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/octofmm.h"
+#include "kernels.hpp"
+#include "tree_host.hpp"
+
+using namespace otfmm;
+
+namespace {
+
+struct GraphEntry {
+    const double* rho;
+    double* phi;
+    double* g;
+    int precision, am, self_term;
+    double G;
+    cudaGraphExec_t exec;
+};
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+struct ot_tree {
+    HostTree h;
+    HostPlan plan;
+    int device = -1;
+    int num_sms = 0;
+    bool have_plan = false;
+    int plan_precision = -1;
+    // device arrays of the tree
+    int *d_level = nullptr, *d_leaf = nullptr, *d_parent = nullptr, *d_child = nullptr;
+    int *d_xyz = nullptr, *d_nbr = nullptr, *d_level_first = nullptr, *d_leaf_node = nullptr;
+    double* d_mom64 = nullptr;
+    float* d_mom32 = nullptr;
+    double* d_loc = nullptr;
+    int* d_status = nullptr;
+    // device arrays of the plan
+    int* d_entries = nullptr;
+    double2* d_tab64 = nullptr;
+    float4* d_tab32 = nullptr;
+    int* d_list_first = nullptr;
+    int* d_list_len = nullptr;
+    int4* d_items = nullptr;
+    size_t items_cap = 0;
+    size_t entries_cap = 0;
+    int* d_counter = nullptr;
+    // staging of the host-buffer solve
+    double *d_rho_in = nullptr, *d_phi_out = nullptr, *d_g_out = nullptr;
+    // tuning of the persistent launch
+    int chunk = 64;
+    int ctas_per_sm = 4;
+    int warps_per_cta = 4;
+    bool tuned = false;
+    // graphs
+    cudaStream_t cap_stream = nullptr;
+    std::vector<GraphEntry> graphs;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // solve start, interact start/end, solve end
+    int64_t workspace_bytes = 0;
+    cudaStream_t last_stream = nullptr;
+};
+
+namespace {
+
+template <class T> int dalloc(ot_tree* t, T** p, size_t count) {
+    if (count == 0) count = 1;
+    if (cudaMalloc((void**)p, count * sizeof(T)) != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return OT_ERR_NO_MEMORY;
+    }
+    t->workspace_bytes += (int64_t)(count * sizeof(T));
+    return OT_OK;
+}
+
+template <class T> int upload(T* d, const std::vector<T>& v) {
+    if (v.empty()) return OT_OK;
+    return cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) == cudaSuccess
+               ? OT_OK
+               : OT_ERR_CUDA;
+}
+
+#define TRY(x)                   \
+    do {                         \
+        int _e = (x);            \
+        if (_e != OT_OK) return _e; \
+    } while (0)
+#define TRYC(x)                                    \
+    do {                                           \
+        if ((x) != cudaSuccess) {                  \
+            cudaGetLastError();                    \
+            return OT_ERR_CUDA;                    \
+        }                                          \
+    } while (0)
+
+DevTree dev_tree(const ot_tree* t) {
+    DevTree d;
+    d.n_levels = t->h.n_levels;
+    d.n_nodes = t->h.n_nodes();
+    d.n_leaf = t->h.n_leaf;
+    d.n_cells = (long long)t->h.n_nodes() * kCells;
+    d.size = t->h.size;
+    d.node_level = t->d_level;
+    d.node_leaf = t->d_leaf;
+    d.node_parent = t->d_parent;
+    d.node_child = t->d_child;
+    d.node_xyz = t->d_xyz;
+    d.nbr = t->d_nbr;
+    d.level_first = t->d_level_first;
+    d.mom64 = t->d_mom64;
+    d.mom32 = t->d_mom32;
+    d.loc = t->d_loc;
+    d.status = t->d_status;
+    return d;
+}
+
+DevPlan dev_plan(const ot_tree* t) {
+    DevPlan p;
+    p.entries = t->d_entries;
+    p.tab64 = t->d_tab64;
+    p.tab32 = t->d_tab32;
+    p.list_first = t->d_list_first;
+    p.list_len = t->d_list_len;
+    p.items = t->d_items;
+    p.n_items = (int)t->plan.items.size();
+    p.counter = t->d_counter;
+    return p;
+}
+
+void destroy_graphs(ot_tree* t) {
+    for (auto& g : t->graphs) cudaGraphExecDestroy(g.exec);
+    t->graphs.clear();
+}
+
+// Stencil lists and work items for theta (allocates when they grow).
+int ensure_plan(ot_tree* t, double theta) {
+    if (t->have_plan && t->plan.theta == theta && t->plan.chunk == t->chunk) return OT_OK;
+    HostPlan p;
+    TRY(build_stencil(t->h, theta, p));
+    build_items(t->h, t->chunk, p);
+    if (p.entries.size() > t->entries_cap) {
+        cudaFree(t->d_entries);
+        cudaFree(t->d_tab64);
+        cudaFree(t->d_tab32);
+        t->entries_cap = p.entries.size();
+        TRY(dalloc(t, &t->d_entries, t->entries_cap));
+        TRY(dalloc(t, &t->d_tab64, 2 * t->entries_cap));
+        TRY(dalloc(t, &t->d_tab32, t->entries_cap));
+    }
+    if (p.items.size() > t->items_cap) {
+        cudaFree(t->d_items);
+        t->items_cap = p.items.size();
+        TRY(dalloc(t, &t->d_items, t->items_cap));
+    }
+    TRY(upload(t->d_entries, p.entries));
+    TRYC(cudaMemcpy(t->d_tab64, p.tab64.data(), p.tab64.size() * 2 * sizeof(double2),
+                    cudaMemcpyHostToDevice));
+    TRYC(cudaMemcpy(t->d_tab32, p.tab32.data(), p.tab32.size() * sizeof(float4),
+                    cudaMemcpyHostToDevice));
+    TRYC(cudaMemcpy(t->d_list_first, p.list_first, sizeof(p.list_first), cudaMemcpyHostToDevice));
+    TRYC(cudaMemcpy(t->d_list_len, p.list_len, sizeof(p.list_len), cudaMemcpyHostToDevice));
+    TRYC(cudaMemcpy(t->d_items, p.items.data(), p.items.size() * sizeof(Item),
+                    cudaMemcpyHostToDevice));
+    t->plan = std::move(p);
+    t->have_plan = true;
+    destroy_graphs(t);
+    return OT_OK;
+}
+
+void fill_opts(const ot_solve_opts* o, ot_solve_opts& out) {
+    out.theta = 0.5;
+    out.G = 1.0;
+    out.precision = OT_PRECISION_FP64;
+    out.am_correction = 1;
+    out.self_term = 0;
+    out.reserved = 0;
+    if (o) out = *o;
+}
+
+int check_opts(const ot_solve_opts& o) {
+    if (!(o.theta >= 0.3 && o.theta <= 1.0)) return OT_ERR_INVALID_ARG;
+    if (o.precision != OT_PRECISION_FP64 && o.precision != OT_PRECISION_FP32_BULK)
+        return OT_ERR_INVALID_ARG;
+    if (!(o.G == o.G)) return OT_ERR_INVALID_ARG;
+    return OT_OK;
+}
+
+int check_dev_ptr(const ot_tree* t, const void* p) {
+    if (!p) return OT_ERR_BAD_POINTER;
+    if (((uintptr_t)p) & 7) return OT_ERR_BAD_ALIGNMENT;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return OT_ERR_BAD_POINTER;
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return OT_ERR_BAD_POINTER;
+    if (a.device != t->device) return OT_ERR_WRONG_DEVICE;
+    return OT_OK;
+}
+
+// Enqueues the upward pass.
+void enqueue_moments(ot_tree* t, const double* rho, cudaStream_t s) {
+    DevTree d = dev_tree(t);
+    launch_leaf_moments(d, t->d_leaf_node, rho, s);
+    for (int L = t->h.n_levels - 2; L >= 0; L--)
+        launch_m2m(d, L, t->h.level_first[L], t->h.level_first[L + 1] - t->h.level_first[L], s);
+}
+
+// Enqueues the interaction launch (expansions zeroed first).
+int enqueue_interact(ot_tree* t, const ot_solve_opts& o, cudaStream_t s) {
+    DevTree d = dev_tree(t);
+    TRYC(cudaMemsetAsync(t->d_loc, 0, sizeof(double) * kLoc * (size_t)d.n_cells, s));
+    TRYC(cudaMemsetAsync(t->d_counter, 0, sizeof(int), s));
+    int ctas = std::max(1, t->num_sms * t->ctas_per_sm);
+    launch_interact(d, dev_plan(t), o.precision, o.G, o.am_correction ? 1 : 0, ctas,
+                    t->warps_per_cta, s);
+    TRYC(cudaGetLastError());
+    return OT_OK;
+}
+
+void enqueue_downward(ot_tree* t, const double* rho, double* phi, double* g,
+                      const ot_solve_opts& o, cudaStream_t s) {
+    DevTree d = dev_tree(t);
+    for (int L = 0; L < t->h.n_levels; L++)
+        launch_l2l(d, L, t->h.level_first[L], t->h.level_first[L + 1] - t->h.level_first[L], rho,
+                   phi, g, o.G, o.self_term ? 1 : 0, s);
+}
+
+int enqueue_solve(ot_tree* t, const double* rho, double* phi, double* g, const ot_solve_opts& o,
+                  cudaStream_t s) {
+    TRYC(cudaEventRecord(t->ev[0], s));
+    enqueue_moments(t, rho, s);
+    TRYC(cudaGetLastError());
+    TRYC(cudaEventRecord(t->ev[1], s));
+    TRY(enqueue_interact(t, o, s));
+    TRYC(cudaEventRecord(t->ev[2], s));
+    enqueue_downward(t, rho, phi, g, o, s);
+    TRYC(cudaGetLastError());
+    TRYC(cudaEventRecord(t->ev[3], s));
+    return OT_OK;
+}
+
+cudaGraphExec_t find_graph(ot_tree* t, const double* rho, double* phi, double* g,
+                           const ot_solve_opts& o) {
+    for (auto& e : t->graphs)
+        if (e.rho == rho && e.phi == phi && e.g == g && e.precision == o.precision &&
+            e.am == o.am_correction && e.self_term == o.self_term && e.G == o.G)
+            return e.exec;
+    return nullptr;
+}
+
+int solve_graph(ot_tree* t, const double* rho, double* phi, double* g, const ot_solve_opts& o,
+                cudaStream_t s) {
+    cudaGraphExec_t ex = find_graph(t, rho, phi, g, o);
+    if (!ex) {
+        if (t->graphs.size() >= 8) destroy_graphs(t);
+        cudaGraph_t graph;
+        TRYC(cudaStreamBeginCapture(t->cap_stream, cudaStreamCaptureModeThreadLocal));
+        int e = enqueue_solve(t, rho, phi, g, o, t->cap_stream);
+        cudaError_t ce = cudaStreamEndCapture(t->cap_stream, &graph);
+        if (e != OT_OK) {
+            if (ce == cudaSuccess) cudaGraphDestroy(graph);
+            return e;
+        }
+        TRYC(ce);
+        cudaError_t ie = cudaGraphInstantiate(&ex, graph, 0);
+        cudaGraphDestroy(graph);
+        TRYC(ie);
+        t->graphs.push_back({rho, phi, g, o.precision, o.am_correction, o.self_term, o.G, ex});
+    }
+    TRYC(cudaGraphLaunch(ex, s));
+    return OT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ot_error_string(int code) {
+    switch (code) {
+        case OT_OK: return "ok";
+        case OT_ERR_INVALID_ARG: return "invalid argument";
+        case OT_ERR_INVALID_TREE: return "invalid tree (leaf out of range, duplicate, overlap or hole)";
+        case OT_ERR_NOT_BALANCED: return "tree is not 2:1 balanced";
+        case OT_ERR_BAD_POINTER: return "null pointer or not device memory";
+        case OT_ERR_BAD_ALIGNMENT: return "buffer not 8-byte aligned";
+        case OT_ERR_CUDA: return "CUDA runtime error";
+        case OT_ERR_TIMEOUT: return "bounded device wait gave up";
+        case OT_ERR_DEVICE_STATUS: return "device status word latched an error";
+        case OT_ERR_NO_MEMORY: return "out of memory";
+        case OT_ERR_WRONG_DEVICE: return "buffer lives on another device";
+        default: return "unknown error";
+    }
+}
+
+int ot_build_tree(const ot_tree_desc* desc, int device, ot_tree** out) {
+    if (!desc || !out) return OT_ERR_BAD_POINTER;
+    *out = nullptr;
+    ot_tree* t = new (std::nothrow) ot_tree();
+    if (!t) return OT_ERR_NO_MEMORY;
+    int e = build_host_tree(*desc, t->h);
+    if (e == OT_OK) e = build_stencil(t->h, 0.5, t->plan);
+    if (e != OT_OK) {
+        delete t;
+        return e;
+    }
+    t->device = device;
+    if (device < 0) {
+        *out = t;
+        return OT_OK;
+    }
+    DeviceGuard guard(device);
+    if (!guard.ok) {
+        delete t;
+        return OT_ERR_CUDA;
+    }
+    auto fail = [&](int code) {
+        ot_destroy_tree(t);
+        return code;
+    };
+    cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, device);
+    const HostTree& h = t->h;
+    const size_t N = (size_t)h.n_nodes(), C = N * kCells;
+    if ((e = dalloc(t, &t->d_level, N)) || (e = dalloc(t, &t->d_leaf, N)) ||
+        (e = dalloc(t, &t->d_parent, N)) || (e = dalloc(t, &t->d_child, N)) ||
+        (e = dalloc(t, &t->d_xyz, 3 * N)) || (e = dalloc(t, &t->d_nbr, 27 * N)) ||
+        (e = dalloc(t, &t->d_level_first, h.level_first.size())) ||
+        (e = dalloc(t, &t->d_leaf_node, (size_t)h.n_leaf)) || (e = dalloc(t, &t->d_mom64, kMom * C)) ||
+        (e = dalloc(t, &t->d_mom32, kMom * C)) || (e = dalloc(t, &t->d_loc, kLoc * C)) ||
+        (e = dalloc(t, &t->d_status, 1)) || (e = dalloc(t, &t->d_list_first, kNumLists)) ||
+        (e = dalloc(t, &t->d_list_len, kNumLists)) || (e = dalloc(t, &t->d_counter, 1)) ||
+        (e = dalloc(t, &t->d_rho_in, (size_t)h.n_leaf * kCells)) ||
+        (e = dalloc(t, &t->d_phi_out, (size_t)h.n_leaf * kCells)) ||
+        (e = dalloc(t, &t->d_g_out, (size_t)h.n_leaf * 3 * kCells)))
+        return fail(e);
+    if ((e = upload(t->d_level, h.node_level)) || (e = upload(t->d_leaf, h.node_leaf)) ||
+        (e = upload(t->d_parent, h.node_parent)) || (e = upload(t->d_child, h.node_child)) ||
+        (e = upload(t->d_xyz, h.node_xyz)) || (e = upload(t->d_nbr, h.nbr)) ||
+        (e = upload(t->d_level_first, h.level_first)) || (e = upload(t->d_leaf_node, h.leaf_node)))
+        return fail(e);
+    // leaf cells keep dX = M2 = M3 = 0 for the life of the tree
+    if (cudaMemset(t->d_mom64, 0, sizeof(double) * kMom * C) != cudaSuccess ||
+        cudaMemset(t->d_mom32, 0, sizeof(float) * kMom * C) != cudaSuccess ||
+        cudaMemset(t->d_status, 0, sizeof(int)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&t->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&t->ev[0]) != cudaSuccess || cudaEventCreate(&t->ev[1]) != cudaSuccess ||
+        cudaEventCreate(&t->ev[2]) != cudaSuccess || cudaEventCreate(&t->ev[3]) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(OT_ERR_CUDA);
+    }
+    t->have_plan = false;
+    if ((e = ensure_plan(t, 0.5))) return fail(e);
+    *out = t;
+    return OT_OK;
+}
+
+void ot_destroy_tree(ot_tree* t) {
+    if (!t) return;
+    if (t->device >= 0) {
+        DeviceGuard guard(t->device);
+        destroy_graphs(t);
+        if (t->cap_stream) cudaStreamDestroy(t->cap_stream);
+        for (cudaEvent_t e : t->ev)
+            if (e) cudaEventDestroy(e);
+        void* ptrs[] = {t->d_level, t->d_leaf, t->d_parent, t->d_child, t->d_xyz, t->d_nbr,
+                        t->d_level_first, t->d_leaf_node, t->d_mom64, t->d_mom32, t->d_loc,
+                        t->d_status, t->d_entries, t->d_tab64, t->d_tab32, t->d_list_first,
+                        t->d_list_len, t->d_items, t->d_counter, t->d_rho_in, t->d_phi_out,
+                        t->d_g_out};
+        for (void* p : ptrs)
+            if (p) cudaFree(p);
+    }
+    delete t;
+}
+
+int ot_compute_moments(ot_tree* t, const double* rho, void* stream) {
+    if (!t) return OT_ERR_BAD_POINTER;
+    if (t->device < 0) return OT_ERR_INVALID_ARG;
+    DeviceGuard guard(t->device);
+    TRY(check_dev_ptr(t, rho));
+    cudaStream_t s = (cudaStream_t)stream;
+    enqueue_moments(t, rho, s);
+    TRYC(cudaGetLastError());
+    t->last_stream = s;
+    return OT_OK;
+}
+
+int ot_solve_gravity(ot_tree* t, const double* rho, double* phi, double* g,
+                     const ot_solve_opts* opts, void* stream) {
+    if (!t) return OT_ERR_BAD_POINTER;
+    if (t->device < 0) return OT_ERR_INVALID_ARG;
+    ot_solve_opts o;
+    fill_opts(opts, o);
+    TRY(check_opts(o));
+    DeviceGuard guard(t->device);
+    TRY(check_dev_ptr(t, rho));
+    TRY(check_dev_ptr(t, phi));
+    TRY(check_dev_ptr(t, g));
+    TRY(ensure_plan(t, o.theta));
+    cudaStream_t s = (cudaStream_t)stream;
+    t->last_stream = s;
+    return solve_graph(t, rho, phi, g, o, s);
+}
+
+int ot_solve_gravity_host(ot_tree* t, const double* rho_host, double* phi_host, double* g_host,
+                          const ot_solve_opts* opts, void* stream) {
+    if (!t) return OT_ERR_BAD_POINTER;
+    if (t->device < 0) return OT_ERR_INVALID_ARG;
+    if (!rho_host || !phi_host || !g_host) return OT_ERR_BAD_POINTER;
+    ot_solve_opts o;
+    fill_opts(opts, o);
+    TRY(check_opts(o));
+    DeviceGuard guard(t->device);
+    TRY(ensure_plan(t, o.theta));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)t->h.n_leaf * kCells;
+    TRYC(cudaMemcpyAsync(t->d_rho_in, rho_host, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    TRY(solve_graph(t, t->d_rho_in, t->d_phi_out, t->d_g_out, o, s));
+    TRYC(cudaMemcpyAsync(phi_host, t->d_phi_out, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TRYC(cudaMemcpyAsync(g_host, t->d_g_out, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    t->last_stream = s;
+    return OT_OK;
+}
+
+int ot_gravity_backward(ot_tree* t, const double* rho, const double* w1, const double* w2,
+                        double* drho, const ot_solve_opts* opts, void* stream) {
+    (void)rho; (void)w1; (void)w2; (void)drho; (void)opts; (void)stream;
+    if (!t) return OT_ERR_BAD_POINTER;
+    return OT_ERR_INVALID_ARG;
+}
+
+int ot_autotune(ot_tree* t, const double* rho, double* phi, double* g, const ot_solve_opts* opts,
+                void* stream) {
+    if (!t) return OT_ERR_BAD_POINTER;
+    if (t->device < 0) return OT_ERR_INVALID_ARG;
+    ot_solve_opts o;
+    fill_opts(opts, o);
+    TRY(check_opts(o));
+    DeviceGuard guard(t->device);
+    TRY(check_dev_ptr(t, rho));
+    TRY(check_dev_ptr(t, phi));
+    TRY(check_dev_ptr(t, g));
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    TRYC(cudaEventCreate(&e0));
+    TRYC(cudaEventCreate(&e1));
+    const int chunks[] = {32, 64, 128, 263};
+    const int cps[] = {2, 4, 8};
+    float best = 1e30f;
+    int bc = t->chunk, bp = t->ctas_per_sm;
+    int err = OT_OK;
+    for (int c : chunks) {
+        t->chunk = c;
+        if ((err = ensure_plan(t, o.theta))) break;
+        enqueue_moments(t, rho, s);
+        for (int p : cps) {
+            t->ctas_per_sm = p;
+            float ms_sum = 0.0f;
+            for (int rep = 0; rep < 4 && err == OT_OK; rep++) {
+                cudaEventRecord(e0, s);
+                err = enqueue_interact(t, o, s);
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) ms_sum += ms;  // first run warms the plan
+            }
+            if (err) break;
+            if (ms_sum < best) {
+                best = ms_sum;
+                bc = c;
+                bp = p;
+            }
+        }
+        if (err) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    t->chunk = bc;
+    t->ctas_per_sm = bp;
+    TRY(err);
+    TRY(ensure_plan(t, o.theta));
+    t->tuned = true;
+    destroy_graphs(t);
+    TRY(solve_graph(t, rho, phi, g, o, s));
+    TRYC(cudaStreamSynchronize(s));
+    return OT_OK;
+}
+
+int ot_last_solve_times(ot_tree* t, float* interact_ms, float* solve_ms) {
+    if (!t) return OT_ERR_BAD_POINTER;
+    if (t->device < 0) return OT_ERR_INVALID_ARG;
+    DeviceGuard guard(t->device);
+    TRYC(cudaEventSynchronize(t->ev[3]));
+    if (interact_ms) TRYC(cudaEventElapsedTime(interact_ms, t->ev[1], t->ev[2]));
+    if (solve_ms) TRYC(cudaEventElapsedTime(solve_ms, t->ev[0], t->ev[3]));
+    return OT_OK;
+}
+
+int ot_tree_info(ot_tree* t, ot_tree_stats* st) {
+    if (!t || !st) return OT_ERR_BAD_POINTER;
+    std::memset(st, 0, sizeof(*st));
+    const HostTree& h = t->h;
+    st->n_levels = h.n_levels;
+    st->n_leaf = h.n_leaf;
+    for (int L = 0; L < h.n_levels && L < OT_MAX_LEVELS; L++) {
+        st->n_nodes[L] = h.level_first[L + 1] - h.level_first[L];
+        int64_t nl = 0;
+        for (int v = h.level_first[L]; v < h.level_first[L + 1]; v++) nl += h.node_leaf[v] >= 0;
+        st->n_leaf_nodes[L] = nl;
+    }
+    st->n_m2l = t->plan.n_m2l;
+    st->n_p2p = t->plan.n_p2p;
+    st->n_seam = t->plan.n_seam;
+    st->n_lattice = t->plan.n_lattice;
+    st->n_m2p = t->plan.n_class[kM2P];
+    st->n_p2m = t->plan.n_class[kP2M];
+    st->n_mm = t->plan.n_class[kMM];
+    st->flops_am = t->plan.flops_am;
+    st->flops_noam = t->plan.flops_noam;
+    st->flops_near = t->plan.flops_near;
+    st->n_work_items = (int64_t)t->plan.items.size();
+    st->tuned_chunk = t->chunk;
+    st->tuned_ctas_per_sm = t->ctas_per_sm;
+    st->tuned_warps_per_cta = t->warps_per_cta;
+    st->workspace_bytes = t->workspace_bytes;
+    if (t->device >= 0) {
+        DeviceGuard guard(t->device);
+        if (t->last_stream) cudaStreamSynchronize(t->last_stream);
+        int status = 0;
+        if (cudaMemcpy(&status, t->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            return OT_ERR_CUDA;
+        }
+        st->device_status = status;
+        if (status) return OT_ERR_DEVICE_STATUS;
+    }
+    return OT_OK;
+}
+
+}  // extern "C"

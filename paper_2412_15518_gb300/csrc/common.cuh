@@ -1,0 +1,81 @@
+// Shared device-side definitions of the GB300 FMM gravity library.
+//
+// Data layout in HBM (all levels concatenated, nodes in breadth-first order
+// with the 8 children of a node contiguous in octant order x + 2y + 4z):
+//   node arrays   [n_nodes]              level, leaf id (-1 interior), parent,
+//                                        first child, 27 same-level neighbours
+//   cell arrays   [component][n_cells]   structure of arrays, cell = node * 512
+//                                        + i + 8 j + 64 k
+//   moments       20 components: m, dX(3), M2(6), M3(10) in units of the cell's
+//                 own side h (dX = centre of mass - cell centre, M2 / h^2,
+//                 M3 / h^3), FP64 and an FP32 copy
+//   expansions    23 components: L0, L1(3), L2(6), L3(10), ac(3), physical
+//                 units, FP64
+// Packed symmetric index orders: M2/L2 = xx xy xz yy yz zz;
+// M3/L3 = xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace otfmm {
+
+constexpr int kCells = 512;      // 8^3 cells per node (Sec. 4.3.2)
+constexpr int kMom = 20;         // moment components per cell
+constexpr int kLoc = 23;         // expansion components per cell (+ correction)
+
+// Status word codes latched by kernels (never trapped).
+constexpr int kStatusBadIndex = 1;
+constexpr int kStatusBadItem = 2;
+
+// Device view of a tree and its current plan; passed by value to kernels.
+struct DevTree {
+    int n_levels;
+    int n_nodes;
+    int n_leaf;
+    long long n_cells;          // n_nodes * 512
+    double size;
+    const int* node_level;      // [n_nodes]
+    const int* node_leaf;       // [n_nodes] leaf id or -1
+    const int* node_parent;     // [n_nodes] or -1
+    const int* node_child;      // [n_nodes] first child or -1
+    const int* node_xyz;        // [n_nodes][3] node coordinates at its level
+    const int* nbr;             // [n_nodes][27] neighbour node or -1
+    const int* level_first;     // [n_levels + 1] first node of each level
+    double* mom64;              // [20][n_cells]
+    float* mom32;               // [20][n_cells]
+    double* loc;                // [23][n_cells]
+    int* status;                // device status word
+};
+
+// Stencil entries of a plan: int code = (dx+16) | (dy+16)<<5 | (dz+16)<<10 |
+// near<<15; lists are contiguous ranges of the entry array.
+struct DevPlan {
+    const int* entries;         // [n_entries]
+    const double2* tab64;       // [2 n_entries] (D0, D1x), (D1y, D1z) of the lattice offset
+    const float4* tab32;        // [n_entries]
+    const int* list_first;      // [9] first entry of list 0..8 (8 = level 0)
+    const int* list_len;        // [9]
+    const int4* items;          // [n_items]
+    int n_items;
+    int* counter;               // dynamic item counter of the persistent launch
+};
+
+__host__ __device__ inline int pack_entry(int dx, int dy, int dz, int near) {
+    return (dx + 16) | ((dy + 16) << 5) | ((dz + 16) << 10) | (near << 15);
+}
+__host__ __device__ inline int entry_dx(int e) { return (e & 31) - 16; }
+__host__ __device__ inline int entry_dy(int e) { return ((e >> 5) & 31) - 16; }
+__host__ __device__ inline int entry_dz(int e) { return ((e >> 10) & 31) - 16; }
+__host__ __device__ inline int entry_near(int e) { return (e >> 15) & 1; }
+
+// Work item: x = target node; y = level | parity << 8 | half << 11 | list << 12;
+// z, w = entry range [k0, k1) of that list.  32 target cells per item: the
+// cells of one parity class (px, py, pz) with z-index 2 (2 half + q) + pz,
+// q in {0, 1}.
+__host__ __device__ inline int item_level(int4 it) { return it.y & 0xff; }
+__host__ __device__ inline int item_parity(int4 it) { return (it.y >> 8) & 7; }
+__host__ __device__ inline int item_half(int4 it) { return (it.y >> 11) & 1; }
+__host__ __device__ inline int item_list(int4 it) { return (it.y >> 12) & 15; }
+
+}  // namespace otfmm

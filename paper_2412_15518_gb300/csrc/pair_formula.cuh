@@ -1,0 +1,158 @@
+// One cell-to-cell multipole interaction (M2L of total order 3 plus the
+// angular-momentum correction), written once as a template over the scalar
+// type: double for the FP64 form, float for the FP32-bulk form, and a
+// counting type on the host for the flop accounting of the roofline.
+//
+// Reading of the paper (Sec. 4.3.1: the FMM conserves linear momentum and,
+// through a special technique, angular momentum):
+//   R = X_A - X_B, D^(n) = grad^n (1/|R|);
+//   L^(n)_A += -G sum_{m <= 3-n} (-1)^m / m!  M^(m)_B ._m D^(n+m)(R)
+//   a_c,A   += -(G/6) D^(4)(R) ._3 [M3_B - (m_B / m_A) M3_A]
+// With f_k = (-1)^k (2k-1)!! / r^(2k+1), every contraction of a symmetric
+// tensor with D^(n) reduces to a few scalars: for S = M2 (Mx = M2 R,
+// xMx = R.M2.R, tr = trace) and T = M3 (q2 = T:RR, q3 = R.q2, t_i = T_ijj,
+// Rt = R.t):
+//   M2 : D2        = f2 xMx + f1 tr
+//   (D3 . M2)_i    = f3 R_i xMx + f2 (2 Mx_i + R_i tr)
+//   M3 : D3        = f3 q3 + 3 f2 Rt
+//   (D4 : M3)_i    = f4 R_i q3 + 3 f3 (q2_i + R_i Rt) + 3 f2 t_i
+// so no D tensor is ever formed.  Everything here is in units of the cell
+// side h (R' = R / h, M2' = M2 / h^2, M3' = M3 / h^3) and without the -G
+// factor; the caller scales L^(n) by -G h^-(n+1) and the correction sum S by
+// -(G/6) h^-2 once per target.
+#pragma once
+
+namespace otfmm {
+
+template <class T> struct Acc {
+    T L0, L1[3], L2[6], L3[10];
+    T d1;    // sum of m f1: the Kronecker part of L2 (added to xx, yy, zz)
+    T V[3];  // sum of m f2 R: the Kronecker part of L3
+    T S[3];  // correction sum
+};
+
+template <class T> __host__ __device__ __forceinline__ void acc_zero(Acc<T>& A) {
+    A.L0 = T(0.0);
+    A.d1 = T(0.0);
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        A.L1[i] = T(0.0);
+        A.V[i] = T(0.0);
+        A.S[i] = T(0.0);
+    }
+#pragma unroll
+    for (int i = 0; i < 6; i++) A.L2[i] = T(0.0);
+#pragma unroll
+    for (int i = 0; i < 10; i++) A.L3[i] = T(0.0);
+}
+
+__host__ __device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
+__host__ __device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
+#ifdef __CUDA_ARCH__
+__device__ __forceinline__ double rsqrt_(double a) { return rsqrt(a); }
+__device__ __forceinline__ float rsqrt_(float a) { return rsqrtf(a); }
+#else
+inline double rsqrt_(double a) { return 1.0 / sqrt(a); }
+inline float rsqrt_(float a) { return 1.0f / sqrtf(a); }
+#endif
+
+// q2 = T : R R for a packed symmetric rank-3 tensor (xxx xxy xxz xyy xyz xzz
+// yyy yyz yzz zzz), given the six products with the off-diagonal ones doubled.
+template <class T>
+__host__ __device__ __forceinline__ void contract_rr(const T* c, T xx, T yy, T zz, T xy2, T xz2,
+                                                     T yz2, T& qx, T& qy, T& qz) {
+    qx = fma_(c[0], xx, fma_(c[3], yy, fma_(c[5], zz, fma_(c[1], xy2, fma_(c[2], xz2, c[4] * yz2)))));
+    qy = fma_(c[1], xx, fma_(c[6], yy, fma_(c[8], zz, fma_(c[3], xy2, fma_(c[4], xz2, c[7] * yz2)))));
+    qz = fma_(c[2], xx, fma_(c[7], yy, fma_(c[9], zz, fma_(c[4], xy2, fma_(c[5], xz2, c[8] * yz2)))));
+}
+
+// TGT_FULL: the target is an interior cell (needs L2, L3 and the target part
+// of the correction).  SRC_MULTI: the source is an interior cell (has M2, M3).
+// AM: the correction is on.  (x, y, z) = R', m = source mass, b2/b3 = source
+// M2'/M3', ratio = m_B / m_A, a3/ta = target M3' and its trace vector.
+template <class T, bool TGT_FULL, bool SRC_MULTI, bool AM>
+__host__ __device__ __forceinline__ void m2l_pair(T x, T y, T z, T m, const T* b2, const T* b3,
+                                                  T ratio, const T* a3, const T* ta, Acc<T>& A) {
+    const T r2 = fma_(x, x, fma_(y, y, z * z));
+    const T f0 = rsqrt_(r2);
+    const T ri2 = f0 * f0;
+    const T f1 = -(f0 * ri2);
+    const T f2 = T(-3.0) * (f1 * ri2);
+    const T f3 = T(-5.0) * (f2 * ri2);
+    const T c1 = m * f1;
+    T f4 = T(0.0);
+    if (AM) f4 = T(-7.0) * (f3 * ri2);
+    const T xx = x * x, yy = y * y, zz = z * z;
+    const T xy = x * y, xz = x * z, yz = y * z;
+    if (SRC_MULTI) {
+        const T Mx = fma_(b2[0], x, fma_(b2[1], y, b2[2] * z));
+        const T My = fma_(b2[1], x, fma_(b2[3], y, b2[4] * z));
+        const T Mz = fma_(b2[2], x, fma_(b2[4], y, b2[5] * z));
+        const T xMx = fma_(x, Mx, fma_(y, My, z * Mz));
+        const T tr = b2[0] + b2[3] + b2[5];
+        T qx, qy, qz;
+        contract_rr(b3, xx, yy, zz, xy + xy, xz + xz, yz + yz, qx, qy, qz);
+        const T q3 = fma_(x, qx, fma_(y, qy, z * qz));
+        const T tx = b3[0] + b3[3] + b3[5];
+        const T ty = b3[1] + b3[6] + b3[8];
+        const T tz = b3[2] + b3[7] + b3[9];
+        const T Rt = fma_(x, tx, fma_(y, ty, z * tz));
+        // L0 += m f0 + (f2 xMx + f1 tr) / 2 - (f3 q3 + 3 f2 Rt) / 6
+        A.L0 += fma_(m, f0, fma_(T(0.5) * f1, tr, fma_(T(0.5) * f2, xMx - Rt, T(-1.0 / 6.0) * (f3 * q3))));
+        // L1 += R (m f1 + (f3 xMx + f2 tr) / 2) + f2 M2 R
+        const T g1 = fma_(T(0.5), fma_(f3, xMx, f2 * tr), c1);
+        A.L1[0] = fma_(g1, x, fma_(f2, Mx, A.L1[0]));
+        A.L1[1] = fma_(g1, y, fma_(f2, My, A.L1[1]));
+        A.L1[2] = fma_(g1, z, fma_(f2, Mz, A.L1[2]));
+        if (AM) {
+            const T u = T(3.0) * f3, w = T(3.0) * f2, v = f4 * q3;
+            A.S[0] += fma_(v, x, fma_(u, fma_(x, Rt, qx), w * tx));
+            A.S[1] += fma_(v, y, fma_(u, fma_(y, Rt, qy), w * ty));
+            A.S[2] += fma_(v, z, fma_(u, fma_(z, Rt, qz), w * tz));
+        }
+    } else {
+        A.L0 = fma_(m, f0, A.L0);
+        A.L1[0] = fma_(c1, x, A.L1[0]);
+        A.L1[1] = fma_(c1, y, A.L1[1]);
+        A.L1[2] = fma_(c1, z, A.L1[2]);
+    }
+    if (TGT_FULL) {
+        const T s2 = m * f2;
+        A.L2[0] = fma_(s2, xx, A.L2[0]);
+        A.L2[1] = fma_(s2, xy, A.L2[1]);
+        A.L2[2] = fma_(s2, xz, A.L2[2]);
+        A.L2[3] = fma_(s2, yy, A.L2[3]);
+        A.L2[4] = fma_(s2, yz, A.L2[4]);
+        A.L2[5] = fma_(s2, zz, A.L2[5]);
+        A.d1 += c1;
+        const T s3 = m * f3;
+        const T tx3 = s3 * x, ty3 = s3 * y, tz3 = s3 * z;
+        A.L3[0] = fma_(tx3, xx, A.L3[0]);
+        A.L3[1] = fma_(tx3, xy, A.L3[1]);
+        A.L3[2] = fma_(tx3, xz, A.L3[2]);
+        A.L3[3] = fma_(tx3, yy, A.L3[3]);
+        A.L3[4] = fma_(tx3, yz, A.L3[4]);
+        A.L3[5] = fma_(tx3, zz, A.L3[5]);
+        A.L3[6] = fma_(ty3, yy, A.L3[6]);
+        A.L3[7] = fma_(ty3, yz, A.L3[7]);
+        A.L3[8] = fma_(ty3, zz, A.L3[8]);
+        A.L3[9] = fma_(tz3, zz, A.L3[9]);
+        A.V[0] = fma_(s2, x, A.V[0]);
+        A.V[1] = fma_(s2, y, A.V[1]);
+        A.V[2] = fma_(s2, z, A.V[2]);
+        if (AM) {
+            // - (m_B / m_A) D4 : M3_A
+            T qx, qy, qz;
+            contract_rr(a3, xx, yy, zz, xy + xy, xz + xz, yz + yz, qx, qy, qz);
+            const T q3 = fma_(x, qx, fma_(y, qy, z * qz));
+            const T Rt = fma_(x, ta[0], fma_(y, ta[1], z * ta[2]));
+            const T u = T(3.0) * f3, w = T(3.0) * f2, v = f4 * q3;
+            const T nr = -ratio;
+            A.S[0] = fma_(nr, fma_(v, x, fma_(u, fma_(x, Rt, qx), w * ta[0])), A.S[0]);
+            A.S[1] = fma_(nr, fma_(v, y, fma_(u, fma_(y, Rt, qy), w * ta[1])), A.S[1]);
+            A.S[2] = fma_(nr, fma_(v, z, fma_(u, fma_(z, Rt, qz), w * ta[2])), A.S[2]);
+        }
+    }
+}
+
+}  // namespace otfmm

@@ -1,0 +1,278 @@
+// Host-side octree builder and interaction plan of the GB300 FMM library.
+//
+// The octree holds one 8x8x8 sub-grid of cells per node (Sec. 4.3.2); the
+// GPU kernels walk a fixed stencil of cell offsets instead of interaction
+// lists (Sec. 5.5).  This file validates the leaf list, lays the nodes out
+// for the device, and builds the stencil lists, the lattice tables of
+// leaf-leaf interactions and the work items of the persistent launch.
+#include "tree_host.hpp"
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <unordered_map>
+#include <unordered_set>
+
+#include "common.cuh"
+
+namespace otfmm {
+
+namespace {
+
+inline uint64_t nkey(int L, int x, int y, int z) {
+    return (uint64_t)L | ((uint64_t)(uint32_t)x << 4) | ((uint64_t)(uint32_t)y << 24) |
+           ((uint64_t)(uint32_t)z << 44);
+}
+
+}  // namespace
+
+int build_host_tree(const ot_tree_desc& desc, HostTree& t) {
+    t = HostTree();
+    if (desc.n_leaf <= 0 || !desc.leaves || !(desc.size > 0.0)) return OT_ERR_INVALID_ARG;
+    const int n = desc.n_leaf;
+    for (int a = 0; a < 3; a++) t.origin[a] = desc.origin[a];
+    t.size = desc.size;
+    t.n_leaf = n;
+    std::unordered_map<uint64_t, int> leafmap;
+    std::unordered_set<uint64_t> anc;
+    leafmap.reserve(2 * (size_t)n);
+    int Lmax = 0;
+    for (int i = 0; i < n; i++) {
+        const int* l = desc.leaves + 4 * i;
+        if (l[0] < 0 || l[0] >= OT_MAX_LEVELS) return OT_ERR_INVALID_TREE;
+        for (int a = 1; a < 4; a++)
+            if (l[a] < 0 || l[a] >= (1 << l[0])) return OT_ERR_INVALID_TREE;
+        if (!leafmap.emplace(nkey(l[0], l[1], l[2], l[3]), i).second) return OT_ERR_INVALID_TREE;
+        Lmax = std::max(Lmax, l[0]);
+    }
+    for (int i = 0; i < n; i++) {
+        const int* l = desc.leaves + 4 * i;
+        for (int q = l[0] - 1; q >= 0; q--) {
+            int s = l[0] - q;
+            if (!anc.insert(nkey(q, l[1] >> s, l[2] >> s, l[3] >> s)).second) break;
+        }
+    }
+    // breadth-first layout from the root
+    t.leaf_node.assign(n, -1);
+    std::vector<std::array<int, 4>> cur{{0, 0, 0, 0}}, next;
+    std::vector<std::unordered_map<uint64_t, int>> map;
+    int reached = 0;
+    for (int L = 0; !cur.empty(); L++) {
+        if (L >= OT_MAX_LEVELS) return OT_ERR_INVALID_TREE;
+        t.level_first.push_back(t.n_nodes());
+        map.emplace_back();
+        next.clear();
+        for (const auto& nd : cur) {
+            uint64_t k = nkey(L, nd[1], nd[2], nd[3]);
+            auto lf = leafmap.find(k);
+            bool is_leaf = lf != leafmap.end();
+            bool is_anc = anc.count(k) != 0;
+            if (is_leaf && is_anc) return OT_ERR_INVALID_TREE;   // a leaf inside a leaf
+            if (!is_leaf && !is_anc) return OT_ERR_INVALID_TREE; // a hole in the tiling
+            int id = t.n_nodes();
+            map[L][nkey(L, nd[1], nd[2], nd[3])] = id;
+            t.node_level.push_back(L);
+            t.node_xyz.insert(t.node_xyz.end(), {nd[1], nd[2], nd[3]});
+            t.node_parent.push_back(nd[0]);
+            t.node_child.push_back(-1);
+            if (is_leaf) {
+                t.node_leaf.push_back(lf->second);
+                t.leaf_node[lf->second] = id;
+                reached++;
+            } else {
+                t.node_leaf.push_back(-1);
+                for (int c = 0; c < 8; c++)
+                    next.push_back({id, 2 * nd[1] + (c & 1), 2 * nd[2] + ((c >> 1) & 1),
+                                    2 * nd[3] + (c >> 2)});
+            }
+        }
+        cur.swap(next);
+    }
+    t.node_parent[0] = -1;
+    if (reached != n) return OT_ERR_INVALID_TREE;
+    t.n_levels = (int)t.level_first.size();
+    t.level_first.push_back(t.n_nodes());
+    if (t.n_levels - 1 != Lmax) return OT_ERR_INVALID_TREE;
+    // first child of each interior node: children were appended in parent order
+    for (int v = 1; v < t.n_nodes(); v++) {
+        int p = t.node_parent[v];
+        if (t.node_child[p] < 0) t.node_child[p] = v;
+    }
+    // same-level neighbours
+    const int N = t.n_nodes();
+    t.nbr.assign((size_t)N * 27, -1);
+    for (int v = 0; v < N; v++) {
+        int L = t.node_level[v], side = 1 << L;
+        const int* p = &t.node_xyz[3 * v];
+        for (int s = 0; s < 27; s++) {
+            int q[3] = {p[0] + s % 3 - 1, p[1] + (s / 3) % 3 - 1, p[2] + s / 9 - 1};
+            if (q[0] < 0 || q[1] < 0 || q[2] < 0 || q[0] >= side || q[1] >= side || q[2] >= side)
+                continue;
+            auto it = map[L].find(nkey(L, q[0], q[1], q[2]));
+            if (it != map[L].end()) t.nbr[(size_t)v * 27 + s] = it->second;
+        }
+    }
+    // 2:1 balance: the region next to a leaf at level L is covered by nodes
+    // of level >= L - 1 (the finer side is checked from the finer leaves)
+    for (int v = 0; v < N; v++) {
+        if (t.node_leaf[v] < 0) continue;
+        int L = t.node_level[v], side = 1 << L;
+        const int* p = &t.node_xyz[3 * v];
+        for (int s = 0; s < 27; s++) {
+            if (s == 13 || t.nbr[(size_t)v * 27 + s] >= 0) continue;
+            int q[3] = {p[0] + s % 3 - 1, p[1] + (s / 3) % 3 - 1, p[2] + s / 9 - 1};
+            if (q[0] < 0 || q[1] < 0 || q[2] < 0 || q[0] >= side || q[1] >= side || q[2] >= side)
+                continue;
+            if (L < 1 || map[L - 1].find(nkey(L - 1, q[0] >> 1, q[1] >> 1, q[2] >> 1)) ==
+                             map[L - 1].end())
+                return OT_ERR_NOT_BALANCED;
+        }
+    }
+    return OT_OK;
+}
+
+int build_stencil(const HostTree& t, double theta, HostPlan& p) {
+    if (!(theta >= 0.3 && theta <= 1.0)) return OT_ERR_INVALID_ARG;
+    p = HostPlan();
+    p.theta = theta;
+    const double it2 = 1.0 / (theta * theta);
+    const int R = (int)std::floor(1.0 / theta + 1e-12);
+    const int W = 2 * R + 1;  // children of near parents are at most this far apart
+    std::vector<int> near;
+    for (int dz = -R; dz <= R; dz++)
+        for (int dy = -R; dy <= R; dy++)
+            for (int dx = -R; dx <= R; dx++) {
+                if (!(dx | dy | dz)) continue;
+                if ((double)(dx * dx + dy * dy + dz * dz) <= it2) near.push_back(pack_entry(dx, dy, dz, 1));
+            }
+    p.n_near = (int)near.size();
+    auto push = [&](int e) {
+        p.entries.push_back(e);
+        int d[3] = {entry_dx(e), entry_dy(e), entry_dz(e)};
+        double r = std::sqrt((double)(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
+        double r3 = r * r * r;
+        p.tab64.push_back({1.0 / r, -d[0] / r3, -d[1] / r3, -d[2] / r3});
+        p.tab32.push_back({(float)(1.0 / r), (float)(-d[0] / r3), (float)(-d[1] / r3),
+                           (float)(-d[2] / r3)});
+    };
+    for (int par = 0; par < 8; par++) {
+        int pp[3] = {par & 1, (par >> 1) & 1, par >> 2};
+        p.list_first[par] = (int)p.entries.size();
+        for (int e : near) push(e);
+        for (int dz = -W; dz <= W; dz++)
+            for (int dy = -W; dy <= W; dy++)
+                for (int dx = -W; dx <= W; dx++) {
+                    int d[3] = {dx, dy, dz};
+                    if ((double)(dx * dx + dy * dy + dz * dz) <= it2) continue;
+                    double P2 = 0.0;
+                    for (int a = 0; a < 3; a++) {
+                        int D = (pp[a] + d[a]) >> 1;  // floor division: parent offset
+                        P2 += (double)D * D;
+                    }
+                    if (P2 <= it2) push(pack_entry(dx, dy, dz, 0));
+                }
+        p.list_len[par] = (int)p.entries.size() - p.list_first[par];
+    }
+    // level 0: every non-near pair of the root's 8^3 cells is far
+    p.list_first[8] = (int)p.entries.size();
+    for (int e : near) push(e);
+    for (int dz = -7; dz <= 7; dz++)
+        for (int dy = -7; dy <= 7; dy++)
+            for (int dx = -7; dx <= 7; dx++) {
+                if ((double)(dx * dx + dy * dy + dz * dz) <= it2) continue;
+                push(pack_entry(dx, dy, dz, 0));
+            }
+    p.list_len[8] = (int)p.entries.size() - p.list_first[8];
+
+    // Interaction counts.  For a list and a neighbour slot, count the
+    // (target, entry) pairs of that list whose source falls in that slot,
+    // split into near and far entries; then every node adds the counts of
+    // its existing neighbours by class.
+    std::vector<int64_t> cn(kNumLists * 27, 0), cf(kNumLists * 27, 0);
+    for (int list = 0; list < kNumLists; list++) {
+        for (int c = 0; c < 512; c++) {
+            int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
+            if (list < 8 && (i & 1) + 2 * (j & 1) + 4 * (k & 1) != list) continue;
+            for (int q = 0; q < p.list_len[list]; q++) {
+                int e = p.entries[p.list_first[list] + q];
+                int s[3] = {i + entry_dx(e), j + entry_dy(e), k + entry_dz(e)};
+                int slot = ((s[0] >> 3) + 1) + 3 * ((s[1] >> 3) + 1) + 9 * ((s[2] >> 3) + 1);
+                (entry_near(e) ? cn : cf)[list * 27 + slot]++;
+            }
+        }
+    }
+    for (int v = 0; v < t.n_nodes(); v++) {
+        int L = t.node_level[v];
+        bool tl = t.node_leaf[v] >= 0;
+        int l0 = L == 0 ? 8 : 0, l1 = L == 0 ? 9 : 8;
+        for (int s = 0; s < 27; s++) {
+            int nb = t.nbr[(size_t)v * 27 + s];
+            if (nb < 0) continue;
+            bool sl = t.node_leaf[nb] >= 0;
+            for (int list = l0; list < l1; list++) {
+                int64_t nn = cn[list * 27 + s], nf = cf[list * 27 + s];
+                p.n_m2l += nf;
+                if (tl && sl) {
+                    p.n_p2p += nn;
+                    p.n_lattice += nf;
+                    p.n_class[kNearP2P] += nn;
+                    p.n_class[kLatticeFar] += nf;
+                } else if (tl) {
+                    p.n_seam += nn;
+                    p.n_class[kM2P] += nn + nf;
+                } else if (sl) {
+                    p.n_seam += nn;
+                    p.n_class[kP2M] += nn + nf;
+                } else {
+                    p.n_class[kMM] += nf;
+                }
+            }
+        }
+    }
+    double f[PairClasses][2];
+    pair_flops(f);
+    for (int c = 0; c < PairClasses; c++) {
+        p.flops_am += (double)p.n_class[c] * f[c][1];
+        p.flops_noam += (double)p.n_class[c] * f[c][0];
+    }
+    p.flops_near = (double)p.n_class[kNearP2P] * f[kNearP2P][1];
+    return OT_OK;
+}
+
+void build_items(const HostTree& t, int chunk, HostPlan& p) {
+    p.chunk = chunk;
+    p.items.clear();
+    std::vector<int64_t> cost;
+    for (int v = 0; v < t.n_nodes(); v++) {
+        int L = t.node_level[v];
+        bool tl = t.node_leaf[v] >= 0;
+        bool seam = false;
+        if (tl)
+            for (int s = 0; s < 27; s++) {
+                int nb = t.nbr[(size_t)v * 27 + s];
+                if (nb >= 0 && t.node_leaf[nb] < 0) seam = true;
+            }
+        for (int par = 0; par < 8; par++) {
+            int list = L == 0 ? 8 : par;
+            int len = p.list_len[list];
+            // leaf targets walk their whole list (cheap lattice pairs) unless
+            // they border interior cells; interior targets are chunked
+            int step = (tl && !seam && L > 0) ? len : std::max(1, chunk);
+            for (int half = 0; half < 2; half++)
+                for (int k0 = 0; k0 < len; k0 += step) {
+                    int k1 = std::min(len, k0 + step);
+                    p.items.push_back({v, L | (par << 8) | (half << 11) | (list << 12), k0, k1});
+                    cost.push_back((int64_t)(k1 - k0) * ((tl && !seam) ? 1 : 24));
+                }
+        }
+    }
+    // longest items first; ties keep the breadth-first node order
+    std::vector<int> order(p.items.size());
+    for (size_t i = 0; i < order.size(); i++) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<Item> sorted(p.items.size());
+    for (size_t i = 0; i < order.size(); i++) sorted[i] = p.items[order[i]];
+    p.items.swap(sorted);
+}
+
+}  // namespace otfmm

@@ -1,0 +1,69 @@
+// Host-side octree builder and interaction plan of the GB300 FMM library.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/octofmm.h"
+
+namespace otfmm {
+
+struct HostTree {
+    int n_levels = 0;  // Lmax + 1
+    int n_leaf = 0;
+    double origin[3] = {0, 0, 0};
+    double size = 1.0;
+    // nodes in breadth-first order, children of a node contiguous in octant
+    // order (bit 0 = x, bit 1 = y, bit 2 = z)
+    std::vector<int> level_first;  // [n_levels + 1]
+    std::vector<int> node_level, node_leaf, node_parent, node_child;
+    std::vector<int> node_xyz;     // [n_nodes][3]
+    std::vector<int> nbr;          // [n_nodes][27], slot = (ox+1) + 3 (oy+1) + 9 (oz+1)
+    std::vector<int> leaf_node;    // [n_leaf] node index of each caller leaf
+    int n_nodes() const { return (int)node_level.size(); }
+};
+
+// Builds the tree; returns OT_OK, OT_ERR_INVALID_ARG, OT_ERR_INVALID_TREE or
+// OT_ERR_NOT_BALANCED.
+int build_host_tree(const ot_tree_desc& desc, HostTree& t);
+
+struct Tab4d { double x, y, z, w; };
+struct Tab4f { float x, y, z, w; };
+struct Item { int x, y, z, w; };
+
+constexpr int kNumLists = 9;  // 8 parity classes at L >= 1, one list at L = 0
+
+// Pair classes: lattice far (two leaf cells), exact near (two leaf cells),
+// multipole source on a leaf target, leaf source on an interior target, two
+// interior cells.
+enum { kLatticeFar = 0, kNearP2P = 1, kM2P = 2, kP2M = 3, kMM = 4, PairClasses = 5 };
+
+// Flops of one pair of each class, [class][am] (counted from the executed
+// formula; fma = 2).
+void pair_flops(double out[PairClasses][2]);
+
+// Stencil and work list of a tree for one opening parameter.
+struct HostPlan {
+    double theta = 0.0;
+    int chunk = 0;                    // stencil entries per item of an interior target
+    std::vector<int> entries;         // packed offsets (see pack_entry)
+    std::vector<Tab4d> tab64;         // (1/|d|, -d/|d|^3) per entry, cell units
+    std::vector<Tab4f> tab32;
+    int list_first[kNumLists] = {0};
+    int list_len[kNumLists] = {0};
+    int n_near = 0;                   // near offsets (first entries of every list)
+    std::vector<Item> items;
+    int64_t n_m2l = 0, n_p2p = 0, n_seam = 0, n_lattice = 0;
+    int64_t n_class[PairClasses] = {0, 0, 0, 0, 0};
+    double flops_am = 0.0, flops_noam = 0.0;  // one interaction launch
+    double flops_near = 0.0;                  // the part kept in FP64 by the bulk form
+};
+
+// Stencil lists for theta (0.3 <= theta <= 1) and the interaction counts of
+// the tree; no work items.
+int build_stencil(const HostTree& t, double theta, HostPlan& p);
+
+// Work items of the persistent launch for a given chunk length.
+void build_items(const HostTree& t, int chunk, HostPlan& p);
+
+}  // namespace otfmm
