@@ -247,17 +247,20 @@ void enqueue_downward(ot_tree* t, const double* rho, double* phi, double* g,
                    phi, g, o.G, o.self_term ? 1 : 0, s);
 }
 
+// Enqueues the whole solve on the capture stream; the four timing events
+// become event-record nodes of the graph (external records), so every replay
+// re-records them.
 int enqueue_solve(ot_tree* t, const double* rho, double* phi, double* g, const ot_solve_opts& o,
                   cudaStream_t s) {
-    TRYC(cudaEventRecord(t->ev[0], s));
+    TRYC(cudaEventRecordWithFlags(t->ev[0], s, cudaEventRecordExternal));
     enqueue_moments(t, rho, s);
     TRYC(cudaGetLastError());
-    TRYC(cudaEventRecord(t->ev[1], s));
+    TRYC(cudaEventRecordWithFlags(t->ev[1], s, cudaEventRecordExternal));
     TRY(enqueue_interact(t, o, s));
-    TRYC(cudaEventRecord(t->ev[2], s));
+    TRYC(cudaEventRecordWithFlags(t->ev[2], s, cudaEventRecordExternal));
     enqueue_downward(t, rho, phi, g, o, s);
     TRYC(cudaGetLastError());
-    TRYC(cudaEventRecord(t->ev[3], s));
+    TRYC(cudaEventRecordWithFlags(t->ev[3], s, cudaEventRecordExternal));
     return OT_OK;
 }
 

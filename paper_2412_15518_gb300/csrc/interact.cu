@@ -11,9 +11,9 @@
 // level L need only the moments, which the upward pass has finished.
 //
 // Per (target A, source B) pair, decided per lane:
-//   both leaf cells           -> point-mass pair on the lattice: R = d h
-//                                exactly, so 1/|d| and -d/|d|^3 come from a
-//                                table and the pair costs 4 FMAs
+//   both leaf cells           -> point-mass pair on the lattice: R = -d h
+//                                exactly, so 1/|d| and D1(-d) = d/|d|^3 come
+//                                from a table and the pair costs 4 FMAs
 //   near, both interior       -> skipped (resolved one level down)
 //   otherwise                 -> M2L of order 3 + correction (pair_formula.cuh)
 // Each lane accumulates in registers (FP64, or FP32 for the bulk form with
@@ -101,9 +101,10 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
             continue;
         }
         if (FULL && !sleaf && entry_near(e)) continue;  // resolved at the next level
-        const T x = T(dx) + (dax - mom[N + sc]);
-        const T y = T(dy) + (day - mom[2 * N + sc]);
-        const T z = T(dz) + (daz - mom[3 * N + sc]);
+        // R' = X_A - X_B in cell units: the source sits at offset d from the target
+        const T x = (dax - mom[N + sc]) - T(dx);
+        const T y = (day - mom[2 * N + sc]) - T(dy);
+        const T z = (daz - mom[3 * N + sc]) - T(dz);
         const T m = mom[sc];
         if (sleaf) {
             m2l_pair<T, FULL, false, AM>(x, y, z, m, nullptr, nullptr, m * inv_ma, a3, ta, A);

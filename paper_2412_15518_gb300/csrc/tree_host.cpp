@@ -151,9 +151,10 @@ int build_stencil(const HostTree& t, double theta, HostPlan& p) {
         int d[3] = {entry_dx(e), entry_dy(e), entry_dz(e)};
         double r = std::sqrt((double)(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
         double r3 = r * r * r;
-        p.tab64.push_back({1.0 / r, -d[0] / r3, -d[1] / r3, -d[2] / r3});
-        p.tab32.push_back({(float)(1.0 / r), (float)(-d[0] / r3), (float)(-d[1] / r3),
-                           (float)(-d[2] / r3)});
+        // D0 and D1 = -R/|R|^3 at R = X_target - X_source = -d (cell units)
+        p.tab64.push_back({1.0 / r, d[0] / r3, d[1] / r3, d[2] / r3});
+        p.tab32.push_back({(float)(1.0 / r), (float)(d[0] / r3), (float)(d[1] / r3),
+                           (float)(d[2] / r3)});
     };
     for (int par = 0; par < 8; par++) {
         int pp[3] = {par & 1, (par >> 1) & 1, par >> 2};

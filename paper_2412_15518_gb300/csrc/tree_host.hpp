@@ -47,7 +47,7 @@ struct HostPlan {
     double theta = 0.0;
     int chunk = 0;                    // stencil entries per item of an interior target
     std::vector<int> entries;         // packed offsets (see pack_entry)
-    std::vector<Tab4d> tab64;         // (1/|d|, -d/|d|^3) per entry, cell units
+    std::vector<Tab4d> tab64;         // (1/|d|, d/|d|^3) per entry, cell units
     std::vector<Tab4f> tab32;
     int list_first[kNumLists] = {0};
     int list_len[kNumLists] = {0};
