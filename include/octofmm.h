@@ -58,6 +58,7 @@ extern "C" {
 #define OT_ERR_DEVICE_STATUS -8  /* a kernel latched an error in the status word  */
 #define OT_ERR_NO_MEMORY -9      /* host or device allocation failed              */
 #define OT_ERR_WRONG_DEVICE -10  /* buffer on another device than the tree        */
+#define OT_ERR_TOO_LARGE -11     /* problem exceeds a fixed-size scratch buffer   */
 
 #define OT_PRECISION_FP64 0      /* every step in FP64                           */
 #define OT_PRECISION_FP32_BULK 1 /* cell-to-cell multipole interactions in FP32,
@@ -171,6 +172,27 @@ int ot_last_solve_times(ot_tree* tree, float* interact_ms, float* solve_ms);
 /* Counts of the tree and of the current plan; synchronises the tree's last
  * stream to read the device status word. */
 int ot_tree_info(ot_tree* tree, ot_tree_stats* stats);
+
+/* Allocation-free solve for callers that cannot allocate device memory: code
+ * running inside a CUDA stream capture (an allocation there breaks the
+ * capture), plug-ins whose host application owns all device memory, and
+ * real-time loops that forbid allocation after start-up.  The paper has no
+ * counterpart; it is the same solve as ot_solve_gravity (same kernels, same
+ * results to rounding) for small trees, without a tree handle: every piece of
+ * scratch (node tables, moments, expansions, stencil tables, work items) lives
+ * in one fixed 3 MiB device array inside the library, held by every GPU that
+ * loads it until the process exits.  desc: host leaf list as for
+ * ot_build_tree, at most 9 nodes (the root leaf alone, or the root and its 8
+ * leaf children: 4,096 cells); rho, phi, g: device buffers on the CURRENT
+ * device, layouts as for ot_solve_gravity; opts as for ot_solve_gravity with
+ * 0.5 <= theta <= 1.  Larger trees return OT_ERR_TOO_LARGE.  No device
+ * memory is allocated (host-side planning uses the heap).  The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the array
+ * and each call clears what must start at zero; calls that overlap on the GPU
+ * race, so issue them on one stream or synchronise between them. */
+int ot_solve_gravity_static(const ot_tree_desc* desc, const double* rho, double* phi, double* g,
+                            const ot_solve_opts* opts, void* stream);
 
 /* Releases the workspace; NULL is ignored. */
 void ot_destroy_tree(ot_tree* tree);

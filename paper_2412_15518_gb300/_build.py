@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libotfmm.so")
-SOURCES = ["tree_host.cpp", "flops.cpp", "capi.cpp", "moments.cu", "interact.cu", "downward.cu"]
+SOURCES = ["tree_host.cpp", "flops.cpp", "capi.cpp", "moments.cu", "interact.cu", "downward.cu",
+           "static_solve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -313,6 +313,7 @@ const char* ot_error_string(int code) {
         case OT_ERR_DEVICE_STATUS: return "device status word latched an error";
         case OT_ERR_NO_MEMORY: return "out of memory";
         case OT_ERR_WRONG_DEVICE: return "buffer lives on another device";
+        case OT_ERR_TOO_LARGE: return "problem exceeds the fixed-size scratch of the allocation-free solve";
         default: return "unknown error";
     }
 }

@@ -66,6 +66,8 @@ _lib.ot_autotune.argtypes = [_P, _P, _P, _P, ctypes.POINTER(ot_solve_opts), _P]
 _lib.ot_tree_info.argtypes = [_P, ctypes.POINTER(ot_tree_stats)]
 _lib.ot_last_solve_times.argtypes = [_P, ctypes.POINTER(ctypes.c_float),
                                      ctypes.POINTER(ctypes.c_float)]
+_lib.ot_solve_gravity_static.argtypes = [ctypes.POINTER(ot_tree_desc), _P, _P, _P,
+                                         ctypes.POINTER(ot_solve_opts), _P]
 _lib.ot_destroy_tree.argtypes = [_P]
 _lib.ot_destroy_tree.restype = None
 _lib.ot_error_string.argtypes = [ctypes.c_int]
@@ -73,7 +75,7 @@ _lib.ot_error_string.restype = ctypes.c_char_p
 
 EXPORTS = ["ot_build_tree", "ot_compute_moments", "ot_solve_gravity", "ot_solve_gravity_host",
            "ot_gravity_backward", "ot_autotune", "ot_last_solve_times", "ot_tree_info",
-           "ot_destroy_tree", "ot_error_string"]
+           "ot_destroy_tree", "ot_error_string", "ot_solve_gravity_static"]
 
 
 class OTError(RuntimeError):
@@ -153,6 +155,21 @@ def ot_autotune(tree, rho, phi, g, opts: ot_solve_opts | None = None, stream=Non
     _check(_lib.ot_autotune(_P(tree), _ptr(rho), _ptr(phi), _ptr(g),
                             ctypes.byref(opts) if opts is not None else None, _stream(stream)),
            "ot_autotune")
+
+
+def ot_solve_gravity_static(leaves, rho, phi, g, opts: ot_solve_opts | None = None, stream=None,
+                            origin=(0.0, 0.0, 0.0), size: float = 1.0):
+    """Allocation-free solve of a small tree (at most 9 nodes) on the current
+    device, for callers that cannot allocate device memory (inside a stream
+    capture, inside a host application that owns all device memory, in a loop
+    that forbids allocation).  All scratch is a fixed array inside the
+    library; calls share it, so do not overlap them on the GPU."""
+    lv = np.ascontiguousarray(np.asarray(leaves, dtype=np.int32).reshape(-1, 4))
+    desc = ot_tree_desc((ctypes.c_double * 3)(*origin), float(size), lv.shape[0],
+                        lv.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    _check(_lib.ot_solve_gravity_static(ctypes.byref(desc), _ptr(rho), _ptr(phi), _ptr(g),
+                                        ctypes.byref(opts) if opts is not None else None,
+                                        _stream(stream)), "ot_solve_gravity_static")
 
 
 def ot_last_solve_times(tree):
