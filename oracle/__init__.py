@@ -75,6 +75,10 @@ def _load():
     lib.orc_l2l.argtypes = [_D, _D, _D]
     lib.orc_l2l.restype = None
     lib.orc_cube_self_constant.restype = ctypes.c_double
+    lib.orc_gradient.argtypes = [ctypes.c_int, _I32, _D, ctypes.c_double, _D, ctypes.c_double,
+                                 ctypes.c_double, ctypes.c_int, ctypes.c_int, _D, _D, _D]
+    lib.orc_dtensor5.argtypes = [_D, _D]
+    lib.orc_dtensor5.restype = None
     _lib = lib
     return lib
 
@@ -154,6 +158,28 @@ def solve_jvp(leaves, rho, v, theta=0.5, G=1.0, am_correction=True, self_term=Fa
                              int(bool(am_correction)), int(bool(self_term)), _p(phi), _p(g),
                              _p(dphi), _p(dg)))
     return phi, g, dphi, dg
+
+
+def gradient(leaves, rho, w1, w2, theta=0.5, G=1.0, am_correction=True, self_term=False,
+             origin=(0.0, 0.0, 0.0), size=1.0):
+    """Hand-written adjoint: dJ/drho for J = sum(w1 * phi + w2 * g)."""
+    lib = _load()
+    leaves, rho, org = _prep(leaves, rho, origin)
+    w1 = np.ascontiguousarray(w1, dtype=np.float64).reshape(rho.shape)
+    w2 = np.ascontiguousarray(w2, dtype=np.float64).reshape(rho.shape[0], 3, 512)
+    drho = np.empty_like(rho)
+    _check(lib.orc_gradient(leaves.shape[0], _p(leaves, _I32), _p(org), size, _p(rho), theta, G,
+                            int(bool(am_correction)), int(bool(self_term)), _p(w1), _p(w2),
+                            _p(drho)))
+    return drho
+
+
+def dtensor5(R):
+    """D^(5) of 1/|R| at R, [3, 3, 3, 3, 3]."""
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    out = np.empty(243)
+    _load().orc_dtensor5(_p(R), _p(out))
+    return out.reshape(3, 3, 3, 3, 3)
 
 
 def direct(leaves, rho, G=1.0, origin=(0.0, 0.0, 0.0), size=1.0):

@@ -628,6 +628,384 @@ int solve(const Tree& t, const T* rho, double theta, double G, int am, int self_
     return ORC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint (reverse sweep) of the solve, FP64, full unpacked tensors.
+// J = sum_c (w1_c phi_c + w2_c . g_c); every step above is reversed in the
+// opposite order with the chain rule written out entry by entry.
+
+// D^(5)_{ijklm}: next term of the same closed form: f5 RRRRR + f4 (10 terms
+// delta RRR) + f3 (15 terms delta delta R), f5 = -945 / r^11.
+void dtensor5(const double R[3], double D5[3][3][3][3][3]) {
+    double r2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
+    double r = std::sqrt(r2);
+    double inv = 1.0 / r, inv2 = inv * inv;
+    double f3 = -15.0 * inv * inv2 * inv2 * inv2;
+    double f4 = 105.0 * inv * inv2 * inv2 * inv2 * inv2;
+    double f5 = -945.0 * inv * inv2 * inv2 * inv2 * inv2 * inv2;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++)
+            for (int k = 0; k < 3; k++)
+                for (int l = 0; l < 3; l++)
+                    for (int m = 0; m < 3; m++) {
+                        double v = f5 * R[i] * R[j] * R[k] * R[l] * R[m];
+                        v += f4 * (kd(i, j) * R[k] * R[l] * R[m] + kd(i, k) * R[j] * R[l] * R[m] +
+                                   kd(i, l) * R[j] * R[k] * R[m] + kd(i, m) * R[j] * R[k] * R[l] +
+                                   kd(j, k) * R[i] * R[l] * R[m] + kd(j, l) * R[i] * R[k] * R[m] +
+                                   kd(j, m) * R[i] * R[k] * R[l] + kd(k, l) * R[i] * R[j] * R[m] +
+                                   kd(k, m) * R[i] * R[j] * R[l] + kd(l, m) * R[i] * R[j] * R[k]);
+                        v += f3 * (kd(i, j) * (kd(k, l) * R[m] + kd(k, m) * R[l] + kd(l, m) * R[k]) +
+                                   kd(i, k) * (kd(j, l) * R[m] + kd(j, m) * R[l] + kd(l, m) * R[j]) +
+                                   kd(i, l) * (kd(j, k) * R[m] + kd(j, m) * R[k] + kd(k, m) * R[j]) +
+                                   kd(i, m) * (kd(j, k) * R[l] + kd(j, l) * R[k] + kd(k, l) * R[j]) +
+                                   kd(j, k) * kd(l, m) * R[i] + kd(j, l) * kd(k, m) * R[i] +
+                                   kd(j, m) * kd(k, l) * R[i]);
+                        D5[i][j][k][l][m] = v;
+                    }
+}
+
+struct MomBar {
+    double m, X[3], M2[3][3], M3[3][3][3];
+};
+
+void zero_bar(MomBar& b) { std::memset(&b, 0, sizeof(b)); }
+void zero_locd(Loc<double>& a) { zero_loc(a); }
+
+// Reverse of m2l(A, B) given the adjoint E of the target expansion: adds the
+// adjoints of A's and/or B's moments (and positions).  as_target / as_source
+// select which side is accumulated (the pair is visited once from each side).
+void m2l_reverse(const Mom<double>& A, const Mom<double>& B, double G, int am,
+                 const Loc<double>& E, MomBar* bA, MomBar* bB, bool need_R) {
+    double R[3];
+    for (int i = 0; i < 3; i++) R[i] = A.X[i] - B.X[i];
+    DTens<double> D;
+    dtensors(R, D);
+    static thread_local double D5[3][3][3][3][3];
+    if (need_R && am) dtensor5(R, D5);
+    // adjoints of the D tensors
+    double b0, b1[3], b2[3][3], b3[3][3][3], b4[3][3][3][3];
+    b0 = -G * E.L0 * B.m;
+    for (int i = 0; i < 3; i++) b1[i] = -G * E.L1[i] * B.m;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            b2[i][j] = -G * (0.5 * E.L0 * B.M2[i][j] + E.L2[i][j] * B.m);
+            for (int k = 0; k < 3; k++)
+                b3[i][j][k] = -G * (-(1.0 / 6.0) * E.L0 * B.M3[i][j][k] +
+                                    0.5 * E.L1[i] * B.M2[j][k] + E.L3[i][j][k] * B.m);
+        }
+    double ratio = B.m / A.m;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++)
+            for (int k = 0; k < 3; k++)
+                for (int l = 0; l < 3; l++)
+                    b4[i][j][k][l] =
+                        am ? -(G / 6.0) * E.ac[i] * (B.M3[j][k][l] - ratio * A.M3[j][k][l]) : 0.0;
+    // R adjoint: sum_n bn . D^(n+1) (only needed when the side whose position
+    // adjoint is accumulated is an interior cell; leaf positions are constants)
+    double Rb[3] = {0.0, 0.0, 0.0};
+    for (int p = 0; p < 3 && need_R; p++) {
+        double v = b0 * D.D1[p];
+        for (int i = 0; i < 3; i++) {
+            v += b1[i] * D.D2[i][p];
+            for (int j = 0; j < 3; j++) {
+                v += b2[i][j] * D.D3[i][j][p];
+                for (int k = 0; k < 3; k++) {
+                    v += b3[i][j][k] * D.D4[i][j][k][p];
+                    if (am)
+                        for (int l = 0; l < 3; l++) v += b4[i][j][k][l] * D5[i][j][k][l][p];
+                }
+            }
+        }
+        Rb[p] = v;
+    }
+    if (bA) {
+        for (int p = 0; p < 3; p++) bA->X[p] += Rb[p];
+        if (am) {
+            // ac depends on A through -(m_B / m_A) M3_A
+            double s = 0.0;
+            for (int i = 0; i < 3; i++)
+                for (int j = 0; j < 3; j++)
+                    for (int k = 0; k < 3; k++)
+                        for (int l = 0; l < 3; l++) {
+                            double t = -(G / 6.0) * E.ac[i] * D.D4[i][j][k][l];
+                            bA->M3[j][k][l] += t * (-ratio);
+                            s += t * A.M3[j][k][l];
+                        }
+            bA->m += s * (B.m / (A.m * A.m));
+        }
+    }
+    if (bB) {
+        for (int p = 0; p < 3; p++) bB->X[p] -= Rb[p];
+        double mb = E.L0 * D.D0;
+        for (int i = 0; i < 3; i++) {
+            mb += E.L1[i] * D.D1[i];
+            for (int j = 0; j < 3; j++) {
+                mb += E.L2[i][j] * D.D2[i][j];
+                for (int k = 0; k < 3; k++) mb += E.L3[i][j][k] * D.D3[i][j][k];
+            }
+        }
+        bB->m += -G * mb;
+        for (int j = 0; j < 3; j++)
+            for (int k = 0; k < 3; k++) {
+                double t = 0.5 * E.L0 * D.D2[j][k];
+                for (int i = 0; i < 3; i++) t += 0.5 * E.L1[i] * D.D3[i][j][k];
+                bB->M2[j][k] += -G * t;
+                for (int l = 0; l < 3; l++) bB->M3[j][k][l] += -G * (-(1.0 / 6.0)) * E.L0 * D.D3[j][k][l];
+            }
+        if (am) {
+            double s = 0.0;
+            for (int i = 0; i < 3; i++)
+                for (int j = 0; j < 3; j++)
+                    for (int k = 0; k < 3; k++)
+                        for (int l = 0; l < 3; l++) {
+                            double t = -(G / 6.0) * E.ac[i] * D.D4[i][j][k][l];
+                            bB->M3[j][k][l] += t;
+                            s += t * A.M3[j][k][l];
+                        }
+            bB->m += s * (-1.0 / A.m);
+        }
+    }
+}
+
+// Reverse of l2l(P, d, C) given the child adjoint Cb: adds into the parent
+// adjoint Pb and returns the adjoint of d.
+void l2l_reverse(const Loc<double>& P, const double d[3], const Loc<double>& Cb, Loc<double>& Pb,
+                 double db[3]) {
+    Pb.L0 += Cb.L0;
+    for (int i = 0; i < 3; i++) {
+        Pb.L1[i] += Cb.L0 * d[i] + Cb.L1[i];
+        Pb.ac[i] += Cb.ac[i];
+        for (int j = 0; j < 3; j++) {
+            Pb.L2[i][j] += 0.5 * Cb.L0 * d[i] * d[j] + Cb.L1[i] * d[j] + Cb.L2[i][j];
+            for (int k = 0; k < 3; k++)
+                Pb.L3[i][j][k] += (1.0 / 6.0) * Cb.L0 * d[i] * d[j] * d[k] +
+                                  0.5 * Cb.L1[i] * d[j] * d[k] + Cb.L2[i][j] * d[k] + Cb.L3[i][j][k];
+        }
+    }
+    for (int p = 0; p < 3; p++) {
+        double a0 = P.L1[p];
+        for (int j = 0; j < 3; j++) {
+            a0 += 0.5 * (P.L2[p][j] + P.L2[j][p]) * d[j];
+            for (int k = 0; k < 3; k++)
+                a0 += (1.0 / 6.0) * (P.L3[p][j][k] + P.L3[j][p][k] + P.L3[j][k][p]) * d[j] * d[k];
+        }
+        double v = Cb.L0 * a0;
+        for (int i = 0; i < 3; i++) {
+            double a1 = P.L2[i][p];
+            for (int k = 0; k < 3; k++) a1 += 0.5 * (P.L3[i][p][k] + P.L3[i][k][p]) * d[k];
+            v += Cb.L1[i] * a1;
+            for (int j = 0; j < 3; j++) v += Cb.L2[i][j] * P.L3[i][j][p];
+        }
+        db[p] = v;
+    }
+}
+
+// Reverse of m2m(ch, 8, P) given the parent adjoint Pb (its X entry is the
+// total adjoint of the parent's centre of mass from all other uses): adds
+// into the children's adjoints.
+void m2m_reverse(const Mom<double>* ch, int n, const Mom<double>& P, const MomBar& Pb,
+                 MomBar* cb) {
+    double Xb[3] = {Pb.X[0], Pb.X[1], Pb.X[2]};
+    for (int c = 0; c < n; c++) {
+        double d[3];
+        for (int i = 0; i < 3; i++) d[i] = ch[c].X[i] - P.X[i];
+        double dbar[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                double t2 = Pb.M2[i][j];
+                cb[c].M2[i][j] += t2;
+                cb[c].m += t2 * d[i] * d[j];
+                dbar[i] += t2 * ch[c].m * d[j];
+                dbar[j] += t2 * ch[c].m * d[i];
+                for (int k = 0; k < 3; k++) {
+                    double t3 = Pb.M3[i][j][k];
+                    cb[c].M3[i][j][k] += t3;
+                    cb[c].M2[i][j] += t3 * d[k];
+                    cb[c].M2[i][k] += t3 * d[j];
+                    cb[c].M2[j][k] += t3 * d[i];
+                    dbar[k] += t3 * ch[c].M2[i][j];
+                    dbar[j] += t3 * ch[c].M2[i][k];
+                    dbar[i] += t3 * ch[c].M2[j][k];
+                    cb[c].m += t3 * d[i] * d[j] * d[k];
+                    dbar[i] += t3 * ch[c].m * d[j] * d[k];
+                    dbar[j] += t3 * ch[c].m * d[i] * d[k];
+                    dbar[k] += t3 * ch[c].m * d[i] * d[j];
+                }
+            }
+        for (int i = 0; i < 3; i++) {
+            cb[c].X[i] += dbar[i];
+            Xb[i] -= dbar[i];
+        }
+    }
+    // X_P = sum m_k X_k / M,  M = sum m_k
+    for (int c = 0; c < n; c++) {
+        double s = 0.0;
+        for (int i = 0; i < 3; i++) {
+            cb[c].X[i] += Xb[i] * ch[c].m / P.m;
+            s += Xb[i] * (ch[c].X[i] - P.X[i]) / P.m;
+        }
+        cb[c].m += s + Pb.m;
+    }
+}
+
+int gradient(const Tree& t, const double* rho, double theta, double G, int am, int self_term,
+             const double* w1, const double* w2, double* drho) {
+    long n_leaf = 0;
+    for (int L = 0; L <= t.Lmax; L++)
+        for (const Node& nd : t.lev[L]) n_leaf += nd.leaf_id >= 0;
+    std::vector<std::pair<int, long>> leaf_cell_of(n_leaf);
+    for (int L = 0; L <= t.Lmax; L++)
+        for (long n = 0; n < (long)t.lev[L].size(); n++)
+            if (t.lev[L][n].leaf_id >= 0) leaf_cell_of[t.lev[L][n].leaf_id] = {L, n};
+    Work<double> w;
+    mark_need(t, w, nullptr, 0, leaf_cell_of);
+    upward(t, rho, w);
+    interactions(t, theta, G, am, w, false);
+    downward(t, w);
+    // adjoints of the expansions: seeds at leaf cells
+    std::vector<std::vector<Loc<double>>> Eb(t.Lmax + 1);
+    std::vector<std::vector<MomBar>> Mb(t.Lmax + 1);
+    for (int L = 0; L <= t.Lmax; L++) {
+        long nc = (long)t.lev[L].size() * 512;
+        Eb[L].resize(nc);
+        Mb[L].resize(nc);
+        for (long ci = 0; ci < nc; ci++) {
+            zero_loc(Eb[L][ci]);
+            zero_bar(Mb[L][ci]);
+        }
+        for (long n = 0; n < (long)t.lev[L].size(); n++) {
+            int leaf = t.lev[L][n].leaf_id;
+            if (leaf < 0) continue;
+            for (int l = 0; l < 512; l++) {
+                Loc<double>& e = Eb[L][n * 512 + l];
+                e.L0 = w1[(long)leaf * 512 + l];
+                for (int i = 0; i < 3; i++) {
+                    double wg = w2[((long)leaf * 3 + i) * 512 + l];
+                    e.L1[i] = -wg;
+                    e.ac[i] = wg;
+                }
+            }
+        }
+    }
+    // L2L reverse, bottom-up, gathered at each parent
+    for (int L = t.Lmax; L >= 1; L--) {
+        const auto& pn = t.lev[L - 1];
+        long np = (long)pn.size() * 512;
+#pragma omp parallel for schedule(static)
+        for (long pi = 0; pi < np; pi++) {
+            const Node& nd = pn[pi / 512];
+            if (nd.leaf_id >= 0) continue;
+            int l = (int)(pi % 512);
+            int a[3] = {8 * nd.x + (l & 7), 8 * nd.y + ((l >> 3) & 7), 8 * nd.z + (l >> 6)};
+            for (int c = 0; c < 8; c++) {
+                long ci = t.cell(L, 2 * a[0] + (c & 1), 2 * a[1] + ((c >> 1) & 1), 2 * a[2] + (c >> 2));
+                double d[3], db[3];
+                for (int i = 0; i < 3; i++) d[i] = w.mom[L][ci].X[i] - w.mom[L - 1][pi].X[i];
+                l2l_reverse(w.loc[L - 1][pi], d, Eb[L][ci], Eb[L - 1][pi], db);
+                for (int i = 0; i < 3; i++) {
+                    Mb[L][ci].X[i] += db[i];
+                    Mb[L - 1][pi].X[i] -= db[i];
+                }
+            }
+        }
+    }
+    // M2L and near-pair reverse, gathered per cell over both of its roles
+    double it2 = 1.0 / (theta * theta);
+    int W = window(theta);
+    for (int L = 0; L <= t.Lmax; L++) {
+        const auto& nodes = t.lev[L];
+        long nc = (long)nodes.size() * 512;
+        int ncell = 8 << L;
+        int lo_w = (L == 0) ? ncell : W;
+#pragma omp parallel for schedule(dynamic, 1)
+        for (long ci = 0; ci < nc; ci++) {
+            const Node& nd = nodes[ci / 512];
+            int l = (int)(ci % 512);
+            int a[3] = {8 * nd.x + (l & 7), 8 * nd.y + ((l >> 3) & 7), 8 * nd.z + (l >> 6)};
+            bool leaf_a = nd.leaf_id >= 0;
+            const Mom<double>& C = w.mom[L][ci];
+            int lo[3], hi[3];
+            for (int i = 0; i < 3; i++) {
+                lo[i] = a[i] - lo_w < 0 ? 0 : a[i] - lo_w;
+                hi[i] = a[i] + lo_w > ncell - 1 ? ncell - 1 : a[i] + lo_w;
+            }
+            for (int bz = lo[2]; bz <= hi[2]; bz++)
+                for (int by = lo[1]; by <= hi[1]; by++)
+                    for (int bx = lo[0]; bx <= hi[0]; bx++) {
+                        int b[3] = {bx, by, bz};
+                        if (bx == a[0] && by == a[1] && bz == a[2]) continue;
+                        int bn = t.find(L, bx >> 3, by >> 3, bz >> 3);
+                        if (bn < 0) continue;
+                        bool leaf_b = nodes[bn].leaf_id >= 0;
+                        int cls = classify(L, a, b, it2, leaf_a, leaf_b);  // symmetric in a, b
+                        if (cls == 0 || cls == 4) continue;
+                        long bi = (long)bn * 512 + local_of(bx & 7, by & 7, bz & 7);
+                        const Mom<double>& P = w.mom[L][bi];
+                        if (cls == 2) {
+                            // C as the source of P's exact near pair
+                            double r[3];
+                            for (int i = 0; i < 3; i++) r[i] = P.X[i] - C.X[i];
+                            double rr = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+                            long pl = (long)nodes[bn].leaf_id * 512 + local_of(bx & 7, by & 7, bz & 7);
+                            double v = w1[pl] / rr;
+                            for (int i = 0; i < 3; i++) v += w2[(pl / 512 * 3 + i) * 512 + pl % 512] * r[i] / (rr * rr * rr);
+                            Mb[L][ci].m += -G * v;
+                            continue;
+                        }
+                        // C as target of P, then C as source for P
+                        m2l_reverse(C, P, G, am, Eb[L][ci], &Mb[L][ci], nullptr, !leaf_a);
+                        m2l_reverse(P, C, G, am, Eb[L][bi], nullptr, &Mb[L][ci], !leaf_a);
+                    }
+        }
+    }
+    // M2M reverse, top-down
+    for (int L = 0; L < t.Lmax; L++) {
+        const auto& nodes = t.lev[L];
+        long nc = (long)nodes.size() * 512;
+#pragma omp parallel for schedule(static)
+        for (long pi = 0; pi < nc; pi++) {
+            const Node& nd = nodes[pi / 512];
+            if (nd.leaf_id >= 0) continue;
+            int l = (int)(pi % 512);
+            int a[3] = {8 * nd.x + (l & 7), 8 * nd.y + ((l >> 3) & 7), 8 * nd.z + (l >> 6)};
+            Mom<double> ch[8];
+            long cix[8];
+            MomBar cb[8];
+            for (int c = 0; c < 8; c++) {
+                cix[c] = t.cell(L + 1, 2 * a[0] + (c & 1), 2 * a[1] + ((c >> 1) & 1), 2 * a[2] + (c >> 2));
+                ch[c] = w.mom[L + 1][cix[c]];
+                zero_bar(cb[c]);
+            }
+            m2m_reverse(ch, 8, w.mom[L][pi], Mb[L][pi], cb);
+            for (int c = 0; c < 8; c++) {
+                MomBar& o = Mb[L + 1][cix[c]];
+                o.m += cb[c].m;
+                for (int i = 0; i < 3; i++) {
+                    o.X[i] += cb[c].X[i];
+                    for (int j = 0; j < 3; j++) {
+                        o.M2[i][j] += cb[c].M2[i][j];
+                        for (int k = 0; k < 3; k++) o.M3[i][j][k] += cb[c].M3[i][j][k];
+                    }
+                }
+            }
+        }
+    }
+    // leaf masses m = rho h^3 (leaf positions are constants)
+    double Cc = self_term ? cube_self_constant() : 0.0;
+    for (int L = 0; L <= t.Lmax; L++) {
+        double h = t.h(L);
+        for (long n = 0; n < (long)t.lev[L].size(); n++) {
+            int leaf = t.lev[L][n].leaf_id;
+            if (leaf < 0) continue;
+            for (int l = 0; l < 512; l++) {
+                long o = (long)leaf * 512 + l;
+                drho[o] = Mb[L][n * 512 + l].m * h * h * h;
+                if (self_term) drho[o] += -G * h * h * Cc * w1[o];
+            }
+        }
+    }
+    return ORC_OK;
+}
+
 void pack_mom(const Mom<double>& M, double* o) {
     o[0] = M.m;
     for (int i = 0; i < 3; i++) o[1 + i] = M.X[i];
@@ -854,5 +1232,24 @@ void orc_l2l(const double* loc, const double* delta, double* out) {
 }
 
 double orc_cube_self_constant() { return cube_self_constant(); }
+
+// Hand-written adjoint: drho = dJ/drho for J = sum (w1 phi + w2 . g);
+// w1 [n_leaf][512], w2 [n_leaf][3][512], drho [n_leaf][512].
+int orc_gradient(int n_leaf, const int32_t* leaves, const double* origin, double size,
+                 const double* rho, double theta, double G, int am, int self_term,
+                 const double* w1, const double* w2, double* drho) {
+    Tree t;
+    int e = build_tree(n_leaf, leaves, origin, size, t);
+    if (e) return e;
+    return gradient(t, rho, theta, G, am, self_term, w1, w2, drho);
+}
+
+// D^(5) at R: out [243].
+void orc_dtensor5(const double* R, double* out) {
+    double D5[3][3][3][3][3];
+    double r[3] = {R[0], R[1], R[2]};
+    dtensor5(r, D5);
+    std::memcpy(out, D5, sizeof(D5));
+}
 
 }  // extern "C"

@@ -419,3 +419,79 @@ def test_invalid_trees_are_rejected():
     assert O.check_tree(np.concatenate([good, good[:1]])) == -2          # duplicate
     assert O.check_tree(np.concatenate([good, [[2, 0, 0, 0]]])) == -2    # leaf inside a leaf
     assert O.check_tree(np.array([[1, 2, 0, 0]], np.int32)) == -1        # out of range
+
+
+# --------------------------------------------------------------------------
+# Adjoint of the solve (hand-written reverse sweep in the oracle).
+def test_dtensor5_is_derivative_of_d4():
+    rng = np.random.default_rng(8)
+    for _ in range(3):
+        R = rng.normal(size=3)
+        D5 = O.dtensor5(R)
+        eps = 1e-5
+        fd = np.zeros((3,) * 5)
+        for i in range(3):
+            e = np.zeros(3)
+            e[i] = eps
+            fd[..., i] = (O.dtensor(R + e)[4] - O.dtensor(R - e)[4]) / (2 * eps)
+        assert np.abs(fd - D5).max() < 1e-8 * np.abs(D5).max()
+        assert np.abs(np.trace(D5, axis1=1, axis2=3)).max() < 1e-12 * np.abs(D5).max()
+        for p in itertools.permutations(range(5)):
+            assert np.abs(D5 - np.transpose(D5, p)).max() < 1e-13 * np.abs(D5).max()
+
+
+def J_of(lv, rho, w1, w2, **kw):
+    phi, g = O.solve(lv, rho, **kw)
+    return float((w1 * phi).sum() + (w2 * g).sum())
+
+
+@pytest.mark.parametrize("which", ["sphere", "small_amr"])
+@pytest.mark.parametrize("am", [True, False])
+def test_gradient_matches_dual_number_directional_derivative(which, am, request):
+    """<dJ/drho, v> from the reverse sweep equals the forward-mode (dual
+    number) derivative of J along v: two independent differentiations of the
+    same discrete solve (through centres of mass and the mass ratio)."""
+    lv, rho = request.getfixturevalue(which)
+    w1, w2 = I.weights(lv.shape[0])
+    gr = O.gradient(lv, rho, w1, w2, am_correction=am)
+    for seed in (3, 4):
+        v = np.random.default_rng(seed).normal(size=rho.shape) * rho
+        _, _, dphi, dg = O.solve_jvp(lv, rho, v, am_correction=am)
+        jvp = (w1 * dphi).sum() + (w2 * dg).sum()
+        assert abs((gr * v).sum() - jvp) < 1e-12 * abs(jvp)
+
+
+def test_gradient_euler_identity(small_amr):
+    """J is homogeneous of degree 1 in rho, so sum rho dJ/drho = J."""
+    lv, rho = small_amr
+    w1, w2 = I.weights(lv.shape[0])
+    gr = O.gradient(lv, rho, w1, w2)
+    J = J_of(lv, rho, w1, w2)
+    assert abs((gr * rho).sum() - J) < 1e-13 * abs(J)
+
+
+def test_gradient_central_differences(sphere):
+    """Central differences with h = 1e-6 (densities in units of the central
+    density) at 16 seeded cells inside the star."""
+    lv, rho = sphere
+    w1, w2 = I.weights(lv.shape[0])
+    gr = O.gradient(lv, rho, w1, w2).reshape(-1)
+    inside = np.nonzero(rho.reshape(-1) > 1e-2)[0]
+    cells = np.random.default_rng(3).choice(inside, size=16, replace=False)
+    h = 1e-6
+    for c in cells:
+        rp = rho.copy().reshape(-1)
+        rm = rho.copy().reshape(-1)
+        rp[c] += h
+        rm[c] -= h
+        fd = (J_of(lv, rp.reshape(rho.shape), w1, w2) - J_of(lv, rm.reshape(rho.shape), w1, w2)) / (2 * h)
+        assert abs(fd - gr[c]) < 1e-6 * abs(gr).max(), (c, fd, gr[c])
+
+
+def test_gradient_self_term(sphere):
+    lv, rho = sphere
+    w1, w2 = I.weights(lv.shape[0])
+    g0 = O.gradient(lv, rho, w1, w2)
+    g1 = O.gradient(lv, rho, w1, w2, self_term=True)
+    C = 3 * (np.log(2 + np.sqrt(3)) - np.pi / 6)
+    assert np.abs(g1 - g0 + w1 * (1.0 / 16) ** 2 * C).max() < 1e-12 * np.abs(g0).max()
