@@ -151,9 +151,11 @@ int ot_solve_gravity_host(ot_tree* tree, const double* rho_host, double* phi_hos
 
 /* Adjoint of the solve: drho = dJ/drho for J = sum_c (w1_c phi_c + w2_c . g_c),
  * the exact derivative of the discrete solve (through the centres of mass
- * and the correction's mass ratio).  w1: device float64 [n_leaf][512];
- * w2: device float64 [n_leaf][3][512]; drho: device float64 [n_leaf][512]
- * (overwritten).  Runs the upward pass itself. */
+ * and the correction's mass ratio), FP64 only (OT_PRECISION_FP64).  w1:
+ * device float64 [n_leaf][512]; w2: device float64 [n_leaf][3][512]; drho:
+ * device float64 [n_leaf][512] (overwritten).  Runs the forward solve itself
+ * (its outputs go to internal buffers) and then the reverse sweep.  The
+ * first call allocates the adjoint workspace (43 doubles per cell). */
 int ot_gravity_backward(ot_tree* tree, const double* rho, const double* w1, const double* w2,
                         double* drho, const ot_solve_opts* opts, void* stream);
 

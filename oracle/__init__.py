@@ -77,6 +77,8 @@ def _load():
     lib.orc_cube_self_constant.restype = ctypes.c_double
     lib.orc_gradient.argtypes = [ctypes.c_int, _I32, _D, ctypes.c_double, _D, ctypes.c_double,
                                  ctypes.c_double, ctypes.c_int, ctypes.c_int, _D, _D, _D]
+    lib.orc_m2l_reverse.argtypes = [_D, _D, ctypes.c_double, ctypes.c_int, _D, _D, _D]
+    lib.orc_m2l_reverse.restype = None
     lib.orc_dtensor5.argtypes = [_D, _D]
     lib.orc_dtensor5.restype = None
     _lib = lib
@@ -172,6 +174,17 @@ def gradient(leaves, rho, w1, w2, theta=0.5, G=1.0, am_correction=True, self_ter
                             int(bool(am_correction)), int(bool(self_term)), _p(w1), _p(w2),
                             _p(drho)))
     return drho
+
+
+def m2l_reverse(momA, momB, Ebar, G=1.0, am_correction=True):
+    """Reverse of one pair: adjoints (packed 40 each) of A and of B given the
+    adjoint Ebar (43) of A's expansion."""
+    a = np.ascontiguousarray(momA, dtype=np.float64)
+    b = np.ascontiguousarray(momB, dtype=np.float64)
+    e = np.ascontiguousarray(Ebar, dtype=np.float64)
+    oa, ob = np.empty(40), np.empty(40)
+    _load().orc_m2l_reverse(_p(a), _p(b), G, int(bool(am_correction)), _p(e), _p(oa), _p(ob))
+    return oa, ob
 
 
 def dtensor5(R):

@@ -1244,6 +1244,34 @@ int orc_gradient(int n_leaf, const int32_t* leaves, const double* origin, double
     return gradient(t, rho, theta, G, am, self_term, w1, w2, drho);
 }
 
+// Reverse of one pair (test primitive): momA/momB packed as in orc_m2l,
+// Ebar [43] = adjoint of the target expansion (L0, L1[3], L2[9], L3[27],
+// ac[3]); outA/outB [40] = adjoints (m, X[3], M2[9], M3[27]).
+void orc_m2l_reverse(const double* momA, const double* momB, double G, int am, const double* Ebar,
+                     double* outA, double* outB) {
+    Mom<double> A, B;
+    unpack_mom(momA, A);
+    unpack_mom(momB, B);
+    Loc<double> E;
+    unpack_loc(Ebar, E);
+    MomBar bA, bB;
+    zero_bar(bA);
+    zero_bar(bB);
+    m2l_reverse(A, B, G, am, E, &bA, &bB, true);
+    double* outs[2] = {outA, outB};
+    MomBar* bs[2] = {&bA, &bB};
+    for (int q = 0; q < 2; q++) {
+        double* o = outs[q];
+        o[0] = bs[q]->m;
+        for (int i = 0; i < 3; i++) o[1 + i] = bs[q]->X[i];
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                o[4 + 3 * i + j] = bs[q]->M2[i][j];
+                for (int k = 0; k < 3; k++) o[13 + 9 * i + 3 * j + k] = bs[q]->M3[i][j][k];
+            }
+    }
+}
+
 // D^(5) at R: out [243].
 void orc_dtensor5(const double* R, double* out) {
     double D5[3][3][3][3][3];

@@ -1,0 +1,451 @@
+// Hand-written adjoint of the FMM gravity solve on GB300 (FP64).
+//
+// For J = sum_c (w1_c phi_c + w2_c . g_c) the reverse sweep runs the forward
+// steps backwards:
+//   seeds      leaf cells: E0 = w1, E1 = -w2, a = w2 (phi = L0, g = -L1 + a_c)
+//   L2L^T      per interior cell, gathered over its 8 children, bottom-up:
+//              E_parent = sum shift^T(E_child, delta), a_parent = sum a_child,
+//              delta-bar to the children's and the parent's centre of mass
+//   M2L^T      every cell gathers over its stencil both of its roles: as the
+//              source of each partner's expansion (adjoints of its moments and
+//              of its centre of mass) and as the target (its centre of mass and
+//              the correction's mass ratio); leaf-leaf pairs use the lattice
+//              table transposed; one persistent launch over all levels
+//   M2M^T      per interior cell, top-down: adjoints of the 8 children's
+//              moments and centres of mass
+//   density    drho = h^3 dJ/dm (+ the self term)
+// Adjoint arrays (physical units, FP64, structure of arrays):
+//   locbar [23][cells]  E0, E1(3), E2(6), E3(10) symmetric adjoints of the
+//                       expansion, and the adjoint of a_c (3)
+//   mombar [20][cells]  dJ/dm, dJ/dX(3), dJ/dM2(6), dJ/dM3(10) (symmetric)
+#include "adjoint.hpp"
+#include "adjoint_pair.cuh"
+
+namespace otfmm {
+
+namespace {
+
+__host__ __device__ inline double cube_self_c() {
+    return 3.0 * (log(2.0 + sqrt(3.0)) - 3.14159265358979323846 / 6.0);
+}
+
+__global__ void __launch_bounds__(256) k_adj_seed(DevTree t, const int* __restrict__ leaf_node,
+                                                  const double* __restrict__ w1,
+                                                  const double* __restrict__ w2, double* locbar) {
+    const int leaf = blockIdx.x;
+    const int node = leaf_node[leaf];
+    const long long N = t.n_cells;
+    for (int c = threadIdx.x; c < kCells; c += blockDim.x) {
+        const long long cell = (long long)node * kCells + c;
+        locbar[cell] = w1[(long long)leaf * kCells + c];
+        for (int a = 0; a < 3; a++) {
+            const double wg = w2[((long long)leaf * 3 + a) * kCells + c];
+            locbar[(1 + a) * N + cell] = -wg;
+            locbar[(20 + a) * N + cell] = wg;
+        }
+        for (int r = 4; r < 20; r++) locbar[r * N + cell] = 0.0;
+    }
+}
+
+// packed index tables
+__constant__ int c_i2[6] = {0, 0, 0, 1, 1, 2};
+__constant__ int c_j2[6] = {0, 1, 2, 1, 2, 2};
+__constant__ int c_i3[10] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 2};
+__constant__ int c_j3[10] = {0, 0, 0, 1, 1, 2, 1, 1, 2, 2};
+__constant__ int c_k3[10] = {0, 1, 2, 1, 2, 2, 1, 2, 2, 2};
+
+__device__ __forceinline__ int pk2(int i, int j) {
+    if (i > j) { int s = i; i = j; j = s; }
+    return i == 0 ? j : (i == 1 ? 2 + j : 5);
+}
+__device__ __forceinline__ int pk3(int i, int j, int k) {
+    // sort i <= j <= k
+    if (i > j) { int s = i; i = j; j = s; }
+    if (j > k) { int s = j; j = k; k = s; }
+    if (i > j) { int s = i; i = j; j = s; }
+    const int tab[3][3][3] = {{{0, 1, 2}, {1, 3, 4}, {2, 4, 5}},
+                              {{1, 3, 4}, {3, 6, 7}, {4, 7, 8}},
+                              {{2, 4, 5}, {4, 7, 8}, {5, 8, 9}}};
+    return tab[i][j][k];
+}
+
+// L2L reverse at parent level: one thread per parent cell.
+__global__ void __launch_bounds__(128) k_l2l_reverse(DevTree t, int first, double* locbar,
+                                                     double* mombar) {
+    const int node = first + blockIdx.x;
+    const int child0 = t.node_child[node];
+    if (child0 < 0) return;
+    const long long N = t.n_cells;
+    const int L = t.node_level[node];
+    const double hc = t.size / (double)(16 << L);  // child cell side
+    for (int c = threadIdx.x; c < kCells; c += blockDim.x) {
+        const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
+        const long long pcell = (long long)node * kCells + c;
+        double P[20];
+#pragma unroll
+        for (int r = 0; r < 20; r++) P[r] = t.loc[r * N + pcell];
+        const double* L2 = P + 4;
+        const double* L3 = P + 10;
+        const double pd[3] = {t.mom64[N + pcell], t.mom64[2 * N + pcell], t.mom64[3 * N + pcell]};
+        double E[20], A[3];
+#pragma unroll
+        for (int r = 0; r < 20; r++) E[r] = 0.0;
+        A[0] = A[1] = A[2] = 0.0;
+        double Xp[3] = {0.0, 0.0, 0.0};
+        const int cn = child0 + (i >> 2) + 2 * (j >> 2) + 4 * (k >> 2);
+#pragma unroll 1
+        for (int q = 0; q < 8; q++) {
+            const int a = q & 1, b = (q >> 1) & 1, e = q >> 2;
+            const long long cc = (long long)cn * kCells + (2 * (i & 3) + a) + 8 * (2 * (j & 3) + b) +
+                                 64 * (2 * (k & 3) + e);
+            const double off[3] = {(double)a, (double)b, (double)e};
+            double d[3];
+#pragma unroll
+            for (int s = 0; s < 3; s++)
+                d[s] = hc * ((off[s] - 0.5) + t.mom64[(1 + s) * N + cc] - 2.0 * pd[s]);
+            double C[20];
+#pragma unroll
+            for (int r = 0; r < 20; r++) C[r] = locbar[r * N + cc];
+            const double C0 = C[0];
+            const double* C1 = C + 1;
+            const double* C2 = C + 4;
+            const double* C3 = C + 10;
+            // E0 += C0; E1 += C0 d + C1
+            E[0] += C0;
+#pragma unroll
+            for (int s = 0; s < 3; s++) E[1 + s] += C0 * d[s] + C1[s];
+            // E2 += C0 dd / 2 + sym(C1 d) + C2
+#pragma unroll
+            for (int n = 0; n < 6; n++) {
+                const int u = c_i2[n], v = c_j2[n];
+                E[4 + n] += 0.5 * C0 * d[u] * d[v] + 0.5 * (C1[u] * d[v] + C1[v] * d[u]) + C2[n];
+            }
+            // E3 += C0 ddd / 6 + sym(C1 dd) / 2 + sym(C2 d) + C3
+#pragma unroll
+            for (int n = 0; n < 10; n++) {
+                const int u = c_i3[n], v = c_j3[n], w = c_k3[n];
+                E[10 + n] += (1.0 / 6.0) * C0 * d[u] * d[v] * d[w] +
+                             (1.0 / 6.0) * (C1[u] * d[v] * d[w] + C1[v] * d[u] * d[w] + C1[w] * d[u] * d[v]) +
+                             (1.0 / 3.0) * (C2[pk2(u, v)] * d[w] + C2[pk2(u, w)] * d[v] + C2[pk2(v, w)] * d[u]) +
+                             C3[n];
+            }
+#pragma unroll
+            for (int s = 0; s < 3; s++) A[s] += locbar[(20 + s) * N + cc];
+            // delta-bar = C0 (L1 + L2 d + L3:dd / 2) + C1 . (L2 + L3 d) + C2 : L3
+            double db[3];
+#pragma unroll
+            for (int p = 0; p < 3; p++) {
+                double l2d = 0.0, l3dd = 0.0;
+#pragma unroll
+                for (int s = 0; s < 3; s++) {
+                    l2d += L2[pk2(p, s)] * d[s];
+#pragma unroll
+                    for (int u = 0; u < 3; u++) l3dd += L3[pk3(p, s, u)] * d[s] * d[u];
+                }
+                double v = C0 * (P[1 + p] + l2d + 0.5 * l3dd);
+#pragma unroll
+                for (int s = 0; s < 3; s++) {
+                    double l3d = 0.0;
+#pragma unroll
+                    for (int u = 0; u < 3; u++) l3d += L3[pk3(s, p, u)] * d[u];
+                    v += C1[s] * (L2[pk2(s, p)] + l3d);
+#pragma unroll
+                    for (int u = 0; u < 3; u++) v += C2[pk2(s, u)] * L3[pk3(s, u, p)];
+                }
+                db[p] = v;
+            }
+#pragma unroll
+            for (int s = 0; s < 3; s++) {
+                mombar[(1 + s) * N + cc] += db[s];
+                Xp[s] -= db[s];
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 20; r++) locbar[r * N + pcell] = E[r];
+#pragma unroll
+        for (int s = 0; s < 3; s++) {
+            locbar[(20 + s) * N + pcell] = A[s];
+            mombar[(1 + s) * N + pcell] += Xp[s];
+        }
+    }
+}
+
+// M2L / near-pair reverse: persistent over the forward's work items.
+__global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const double* locbar,
+                                                     double* mombar, double G, int am) {
+    __shared__ int s_nb[4][28];
+    __shared__ int s_lf[4][28];
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    const long long N = t.n_cells;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(p.counter, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= p.n_items) break;
+        const int4 it = __ldg(p.items + item);
+        if (lane < 27) {
+            const int nb = t.nbr[(long long)it.x * 27 + lane];
+            s_nb[w][lane] = nb;
+            s_lf[w][lane] = nb >= 0 ? (t.node_leaf[nb] >= 0) : 0;
+        }
+        __syncwarp();
+        const int node = it.x;
+        const bool cleaf = t.node_leaf[node] >= 0;
+        const int L = item_level(it), par = item_parity(it), half = item_half(it);
+        const int i = 2 * (lane & 3) + (par & 1);
+        const int j = 2 * ((lane >> 2) & 3) + ((par >> 1) & 1);
+        const int k = 2 * (2 * half + (lane >> 4)) + (par >> 2);
+        const long long cell = (long long)node * kCells + i + 8 * j + 64 * k;
+        const double h = t.size / (double)(8 << L);
+        const double h2 = h * h, h3 = h2 * h;
+        // own moments (physical) and own expansion adjoints
+        const double mC = t.mom64[cell];
+        const double dC[3] = {t.mom64[N + cell], t.mom64[2 * N + cell], t.mom64[3 * N + cell]};
+        double M2C[6], M3C[10], EC[20], aC[3];
+        if (!cleaf) {
+#pragma unroll
+            for (int r = 0; r < 6; r++) M2C[r] = h2 * t.mom64[(4 + r) * N + cell];
+#pragma unroll
+            for (int r = 0; r < 10; r++) M3C[r] = h3 * t.mom64[(10 + r) * N + cell];
+#pragma unroll
+            for (int r = 0; r < 20; r++) EC[r] = locbar[r * N + cell];
+#pragma unroll
+            for (int r = 0; r < 3; r++) aC[r] = locbar[(20 + r) * N + cell];
+        } else {
+#pragma unroll
+            for (int r = 0; r < 6; r++) M2C[r] = 0.0;
+#pragma unroll
+            for (int r = 0; r < 10; r++) M3C[r] = 0.0;
+        }
+        PairAdjOut acc;
+        adj_zero(acc);
+        double Xs[3] = {0.0, 0.0, 0.0};  // signed position adjoint of this cell
+        double lat = 0.0;                // lattice pairs: dJ/dm of this leaf cell
+        const int base = p.list_first[item_list(it)];
+#pragma unroll 1
+        for (int q = it.z; q < it.w; q++) {
+            const int e = __ldg(p.entries + base + q);
+            const int dx = entry_dx(e), dy = entry_dy(e), dz = entry_dz(e);
+            const int sx = i + dx, sy = j + dy, sz = k + dz;
+            const int slot = ((sx >> 3) + 1) + 3 * ((sy >> 3) + 1) + 9 * ((sz >> 3) + 1);
+            const int nb = s_nb[w][slot];
+            if (nb < 0) continue;
+            const bool pleaf = s_lf[w][slot] != 0;
+            const long long pc = (long long)nb * kCells + (sx & 7) + 8 * (sy & 7) + 64 * (sz & 7);
+            if (cleaf && pleaf) {
+                // transposed lattice pair: this cell is the source of P's point-mass pair
+                const double2 t0 = __ldg(p.tab64 + 2 * (base + q)), t1 = __ldg(p.tab64 + 2 * (base + q) + 1);
+                lat += locbar[pc] * t0.x / h -
+                       (locbar[N + pc] * t0.y + locbar[2 * N + pc] * t1.x + locbar[3 * N + pc] * t1.y) / h2;
+                continue;
+            }
+            if (!cleaf && !pleaf && entry_near(e)) continue;
+            // partner moments (physical) and R = X_P - X_C
+            const double mP = t.mom64[pc];
+            double R[3] = {h * ((double)dx + t.mom64[N + pc] - dC[0]),
+                           h * ((double)dy + t.mom64[2 * N + pc] - dC[1]),
+                           h * ((double)dz + t.mom64[3 * N + pc] - dC[2])};
+            double M2P[6], M3P[10];
+            if (!pleaf) {
+#pragma unroll
+                for (int r = 0; r < 6; r++) M2P[r] = h2 * t.mom64[(4 + r) * N + pc];
+#pragma unroll
+                for (int r = 0; r < 10; r++) M3P[r] = h3 * t.mom64[(10 + r) * N + pc];
+            } else {
+#pragma unroll
+                for (int r = 0; r < 6; r++) M2P[r] = 0.0;
+#pragma unroll
+                for (int r = 0; r < 10; r++) M3P[r] = 0.0;
+            }
+            // (ii) this cell as the source of P's expansion (R = X_P - X_C)
+            {
+                double EP[20], aP[3];
+#pragma unroll
+                for (int r = 0; r < 20; r++) EP[r] = locbar[r * N + pc];
+#pragma unroll
+                for (int r = 0; r < 3; r++) aP[r] = locbar[(20 + r) * N + pc];
+                if (pleaf) {
+#pragma unroll
+                    for (int r = 4; r < 20; r++) EP[r] = 0.0;
+                }
+                PairAdjOut o;
+                adj_zero(o);
+                m2l_pair_reverse(R, G, am, mC, M2C, M3C, !cleaf, mP, M3P, !pleaf, EP[0], EP + 1,
+                                 EP + 4, EP + 10, aP, true, false, !cleaf, o);
+                acc.mB += o.mB;
+#pragma unroll
+                for (int r = 0; r < 6; r++) acc.M2B[r] += o.M2B[r];
+#pragma unroll
+                for (int r = 0; r < 10; r++) acc.M3B[r] += o.M3B[r];
+#pragma unroll
+                for (int s = 0; s < 3; s++) Xs[s] -= o.R[s];
+            }
+            // (i) this cell as the target of P (R = X_C - X_P): position and ratio
+            if (!cleaf) {
+                const double Rn[3] = {-R[0], -R[1], -R[2]};
+                PairAdjOut o;
+                adj_zero(o);
+                m2l_pair_reverse(Rn, G, am, mP, M2P, M3P, !pleaf, mC, M3C, true, EC[0], EC + 1,
+                                 EC + 4, EC + 10, aC, false, true, true, o);
+                acc.mA += o.mA;
+#pragma unroll
+                for (int r = 0; r < 10; r++) acc.M3A[r] += o.M3A[r];
+#pragma unroll
+                for (int s = 0; s < 3; s++) Xs[s] += o.R[s];
+            }
+        }
+        atomicAdd(mombar + cell, acc.mB + acc.mA - G * lat);
+        if (!cleaf) {
+#pragma unroll
+            for (int s = 0; s < 3; s++) atomicAdd(mombar + (1 + s) * N + cell, Xs[s]);
+#pragma unroll
+            for (int r = 0; r < 6; r++) atomicAdd(mombar + (4 + r) * N + cell, acc.M2B[r]);
+#pragma unroll
+            for (int r = 0; r < 10; r++) atomicAdd(mombar + (10 + r) * N + cell, acc.M3B[r] + acc.M3A[r]);
+        }
+        __syncwarp();
+    }
+}
+
+// M2M reverse at parent level: one thread per parent cell, writes its children.
+__global__ void __launch_bounds__(128) k_m2m_reverse(DevTree t, int first, double* mombar) {
+    const int node = first + blockIdx.x;
+    const int child0 = t.node_child[node];
+    if (child0 < 0) return;
+    const long long N = t.n_cells;
+    const int L = t.node_level[node];
+    const double hp = t.size / (double)(8 << L), hc = 0.5 * hp;
+    for (int c = threadIdx.x; c < kCells; c += blockDim.x) {
+        const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
+        const long long pcell = (long long)node * kCells + c;
+        const double M = t.mom64[pcell];
+        const double XP[3] = {t.mom64[N + pcell], t.mom64[2 * N + pcell], t.mom64[3 * N + pcell]};
+        double Bm = mombar[pcell];
+        double BX[3], B2[6], B3[10];
+#pragma unroll
+        for (int s = 0; s < 3; s++) BX[s] = mombar[(1 + s) * N + pcell];
+#pragma unroll
+        for (int r = 0; r < 6; r++) B2[r] = mombar[(4 + r) * N + pcell];
+#pragma unroll
+        for (int r = 0; r < 10; r++) B3[r] = mombar[(10 + r) * N + pcell];
+        const int cn = child0 + (i >> 2) + 2 * (j >> 2) + 4 * (k >> 2);
+        double Xtot[3] = {BX[0], BX[1], BX[2]};
+        double dk[8][3];
+        long long cix[8];
+        // first pass: moment adjoints and delta-bar
+#pragma unroll 1
+        for (int q = 0; q < 8; q++) {
+            const int a = q & 1, b = (q >> 1) & 1, e = q >> 2;
+            const long long cc = (long long)cn * kCells + (2 * (i & 3) + a) + 8 * (2 * (j & 3) + b) +
+                                 64 * (2 * (k & 3) + e);
+            cix[q] = cc;
+            const double off[3] = {(double)a, (double)b, (double)e};
+            const double m = t.mom64[cc];
+            double d[3];
+#pragma unroll
+            for (int s = 0; s < 3; s++) {
+                d[s] = hp * (0.5 * ((off[s] - 0.5) + t.mom64[(1 + s) * N + cc]) - XP[s]);
+                dk[q][s] = d[s];
+            }
+            double M2k[6];
+#pragma unroll
+            for (int r = 0; r < 6; r++) M2k[r] = hc * hc * t.mom64[(4 + r) * N + cc];
+            // M3bar_k += B3 ; M2bar_k += B2 + 3 B3 . d
+            double add2[6];
+#pragma unroll
+            for (int n = 0; n < 6; n++) {
+                const int u = c_i2[n], v = c_j2[n];
+                double s3 = 0.0;
+#pragma unroll
+                for (int l = 0; l < 3; l++) s3 += B3[pk3(u, v, l)] * d[l];
+                add2[n] = B2[n] + 3.0 * s3;
+            }
+            // mbar_k += B2 : dd + B3 : ddd
+            double B2d[3];
+            sym2_vec(B2, d, B2d);
+            double B3dd[3];
+            sym3_rr(B3, d, B3dd);
+            const double dd = B2d[0] * d[0] + B2d[1] * d[1] + B2d[2] * d[2];
+            const double ddd = B3dd[0] * d[0] + B3dd[1] * d[1] + B3dd[2] * d[2];
+            // dbar = 2 m B2 d + 3 B3 : M2_k + 3 m B3 : dd
+            double db[3];
+#pragma unroll
+            for (int p = 0; p < 3; p++) {
+                double s = 0.0;
+#pragma unroll
+                for (int n = 0; n < 6; n++) {
+                    const int u = c_i2[n], v = c_j2[n];
+                    const double mult = (u == v) ? 1.0 : 2.0;
+                    s += mult * B3[pk3(p, u, v)] * M2k[n];
+                }
+                db[p] = 2.0 * m * B2d[p] + 3.0 * s + 3.0 * m * B3dd[p];
+                Xtot[p] -= db[p];
+            }
+            mombar[cc] += dd + ddd;
+#pragma unroll
+            for (int s = 0; s < 3; s++) mombar[(1 + s) * N + cc] += db[s];
+#pragma unroll
+            for (int n = 0; n < 6; n++) mombar[(4 + n) * N + cc] += add2[n];
+#pragma unroll
+            for (int n = 0; n < 10; n++) mombar[(10 + n) * N + cc] += B3[n];
+        }
+        // second pass: the centre of mass X_P = sum m_k X_k / M and M = sum m_k
+#pragma unroll 1
+        for (int q = 0; q < 8; q++) {
+            const long long cc = cix[q];
+            const double m = t.mom64[cc];
+            double s = 0.0;
+#pragma unroll
+            for (int p = 0; p < 3; p++) {
+                mombar[(1 + p) * N + cc] += Xtot[p] * m / M;
+                s += Xtot[p] * dk[q][p] / M;
+            }
+            mombar[cc] += s + Bm;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_rho_bar(DevTree t, const int* __restrict__ leaf_node,
+                                                 const double* __restrict__ mombar,
+                                                 const double* __restrict__ w1, double* drho,
+                                                 double G, int self_term) {
+    const int leaf = blockIdx.x;
+    const int node = leaf_node[leaf];
+    const int L = t.node_level[node];
+    const double h = t.size / (double)(8 << L);
+    for (int c = threadIdx.x; c < kCells; c += blockDim.x) {
+        const long long o = (long long)leaf * kCells + c;
+        double v = mombar[(long long)node * kCells + c] * h * h * h;
+        if (self_term) v += -G * h * h * cube_self_c() * w1[o];
+        drho[o] = v;
+    }
+}
+
+}  // namespace
+
+void launch_adj_seed(const DevTree& t, const int* leaf_node, const double* w1, const double* w2,
+                     double* locbar, cudaStream_t s) {
+    k_adj_seed<<<t.n_leaf, 256, 0, s>>>(t, leaf_node, w1, w2, locbar);
+}
+
+void launch_l2l_reverse(const DevTree& t, int first, int count, double* locbar, double* mombar,
+                        cudaStream_t s) {
+    if (count > 0) k_l2l_reverse<<<count, 128, 0, s>>>(t, first, locbar, mombar);
+}
+
+void launch_m2l_reverse(const DevTree& t, const DevPlan& p, const double* locbar, double* mombar,
+                        double G, int am, int ctas, cudaStream_t s) {
+    k_m2l_reverse<<<ctas, 128, 0, s>>>(t, p, locbar, mombar, G, am);
+}
+
+void launch_m2m_reverse(const DevTree& t, int first, int count, double* mombar, cudaStream_t s) {
+    if (count > 0) k_m2m_reverse<<<count, 128, 0, s>>>(t, first, mombar);
+}
+
+void launch_rho_bar(const DevTree& t, const int* leaf_node, const double* mombar, const double* w1,
+                    double* drho, double G, int self_term, cudaStream_t s) {
+    k_rho_bar<<<t.n_leaf, 256, 0, s>>>(t, leaf_node, mombar, w1, drho, G, self_term);
+}
+
+}  // namespace otfmm

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/octofmm.h"
+#include "adjoint.hpp"
 #include "kernels.hpp"
 #include "tree_host.hpp"
 
@@ -66,6 +67,9 @@ struct ot_tree {
     size_t items_cap = 0;
     size_t entries_cap = 0;
     int* d_counter = nullptr;
+    // adjoint workspace (allocated by the first backward call)
+    double* d_locbar = nullptr;
+    double* d_mombar = nullptr;
     // staging of the host-buffer solve
     double *d_rho_in = nullptr, *d_phi_out = nullptr, *d_g_out = nullptr;
     // tuning of the persistent launch
@@ -391,7 +395,7 @@ void ot_destroy_tree(ot_tree* t) {
                         t->d_level_first, t->d_leaf_node, t->d_mom64, t->d_mom32, t->d_loc,
                         t->d_status, t->d_entries, t->d_tab64, t->d_tab32, t->d_list_first,
                         t->d_list_len, t->d_items, t->d_counter, t->d_rho_in, t->d_phi_out,
-                        t->d_g_out};
+                        t->d_g_out, t->d_locbar, t->d_mombar};
         for (void* p : ptrs)
             if (p) cudaFree(p);
     }
@@ -449,9 +453,45 @@ int ot_solve_gravity_host(ot_tree* t, const double* rho_host, double* phi_host, 
 
 int ot_gravity_backward(ot_tree* t, const double* rho, const double* w1, const double* w2,
                         double* drho, const ot_solve_opts* opts, void* stream) {
-    (void)rho; (void)w1; (void)w2; (void)drho; (void)opts; (void)stream;
     if (!t) return OT_ERR_BAD_POINTER;
-    return OT_ERR_INVALID_ARG;
+    if (t->device < 0) return OT_ERR_INVALID_ARG;
+    ot_solve_opts o;
+    fill_opts(opts, o);
+    TRY(check_opts(o));
+    if (o.precision != OT_PRECISION_FP64) return OT_ERR_INVALID_ARG;
+    DeviceGuard guard(t->device);
+    TRY(check_dev_ptr(t, rho));
+    TRY(check_dev_ptr(t, w1));
+    TRY(check_dev_ptr(t, w2));
+    TRY(check_dev_ptr(t, drho));
+    TRY(ensure_plan(t, o.theta));
+    const size_t cells = (size_t)t->h.n_nodes() * kCells;
+    if (!t->d_locbar) TRY(dalloc(t, &t->d_locbar, kLoc * cells));
+    if (!t->d_mombar) TRY(dalloc(t, &t->d_mombar, kMom * cells));
+    cudaStream_t s = (cudaStream_t)stream;
+    t->last_stream = s;
+    // forward pass: moments and complete expansions stay in the workspace
+    enqueue_moments(t, rho, s);
+    TRY(enqueue_interact(t, o, s));
+    enqueue_downward(t, rho, t->d_phi_out, t->d_g_out, o, s);
+    TRYC(cudaGetLastError());
+    // reverse sweep
+    DevTree d = dev_tree(t);
+    const HostTree& h = t->h;
+    TRYC(cudaMemsetAsync(t->d_mombar, 0, sizeof(double) * kMom * cells, s));
+    launch_adj_seed(d, t->d_leaf_node, w1, w2, t->d_locbar, s);
+    for (int L = h.n_levels - 2; L >= 0; L--)
+        launch_l2l_reverse(d, h.level_first[L], h.level_first[L + 1] - h.level_first[L],
+                           t->d_locbar, t->d_mombar, s);
+    TRYC(cudaMemsetAsync(t->d_counter, 0, sizeof(int), s));
+    launch_m2l_reverse(d, dev_plan(t), t->d_locbar, t->d_mombar, o.G, o.am_correction ? 1 : 0,
+                       std::max(1, t->num_sms * 4), s);
+    for (int L = 0; L + 1 < h.n_levels; L++)
+        launch_m2m_reverse(d, h.level_first[L], h.level_first[L + 1] - h.level_first[L],
+                           t->d_mombar, s);
+    launch_rho_bar(d, t->d_leaf_node, t->d_mombar, w1, drho, o.G, o.self_term ? 1 : 0, s);
+    TRYC(cudaGetLastError());
+    return OT_OK;
 }
 
 int ot_autotune(ot_tree* t, const double* rho, double* phi, double* g, const ot_solve_opts* opts,
