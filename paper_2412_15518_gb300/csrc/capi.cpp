@@ -14,6 +14,7 @@
 #include "../../include/octofmm.h"
 #include "adjoint.hpp"
 #include "kernels.hpp"
+#include "lattice.hpp"
 #include "tree_host.hpp"
 
 using namespace otfmm;
@@ -64,6 +65,11 @@ struct ot_tree {
     int* d_list_first = nullptr;
     int* d_list_len = nullptr;
     int4* d_items = nullptr;
+    int4* d_items_adj = nullptr;
+    size_t items_adj_cap = 0;
+    int* d_hoff_far = nullptr;
+    int* d_hoff_near = nullptr;
+    int* d_lattice_nodes = nullptr;
     size_t items_cap = 0;
     size_t entries_cap = 0;
     int* d_counter = nullptr;
@@ -152,6 +158,18 @@ DevPlan dev_plan(const ot_tree* t) {
     return p;
 }
 
+DevLattice dev_lattice(const ot_tree* t) {
+    DevLattice l;
+    l.hoff_far = t->d_hoff_far;
+    l.hoff_near = t->d_hoff_near;
+    l.nodes = t->d_lattice_nodes;
+    l.n_nodes = (int)t->plan.lattice_nodes.size();
+    l.w_far = t->plan.w_far;
+    l.w_near = t->plan.w_near;
+    l.n_near = t->plan.n_near;
+    return l;
+}
+
 void destroy_graphs(ot_tree* t) {
     for (auto& g : t->graphs) cudaGraphExecDestroy(g.exec);
     t->graphs.clear();
@@ -167,24 +185,40 @@ int ensure_plan(ot_tree* t, double theta) {
         cudaFree(t->d_entries);
         cudaFree(t->d_tab64);
         cudaFree(t->d_tab32);
+        cudaFree(t->d_hoff_far);
+        cudaFree(t->d_hoff_near);
         t->entries_cap = p.entries.size();
         TRY(dalloc(t, &t->d_entries, t->entries_cap));
         TRY(dalloc(t, &t->d_tab64, 2 * t->entries_cap));
         TRY(dalloc(t, &t->d_tab32, t->entries_cap));
+        TRY(dalloc(t, &t->d_hoff_far, t->entries_cap));
+        TRY(dalloc(t, &t->d_hoff_near, t->entries_cap));
     }
+    if (!t->d_lattice_nodes) TRY(dalloc(t, &t->d_lattice_nodes, (size_t)t->h.n_leaf));
     if (p.items.size() > t->items_cap) {
         cudaFree(t->d_items);
         t->items_cap = p.items.size();
         TRY(dalloc(t, &t->d_items, t->items_cap));
     }
+    if (p.items_adj.size() > t->items_adj_cap) {
+        cudaFree(t->d_items_adj);
+        t->items_adj_cap = p.items_adj.size();
+        TRY(dalloc(t, &t->d_items_adj, t->items_adj_cap));
+    }
     TRY(upload(t->d_entries, p.entries));
+    TRY(upload(t->d_hoff_far, p.hoff_far));
+    TRY(upload(t->d_hoff_near, p.hoff_near));
+    TRY(upload(t->d_lattice_nodes, p.lattice_nodes));
     TRYC(cudaMemcpy(t->d_tab64, p.tab64.data(), p.tab64.size() * 2 * sizeof(double2),
                     cudaMemcpyHostToDevice));
     TRYC(cudaMemcpy(t->d_tab32, p.tab32.data(), p.tab32.size() * sizeof(float4),
                     cudaMemcpyHostToDevice));
     TRYC(cudaMemcpy(t->d_list_first, p.list_first, sizeof(p.list_first), cudaMemcpyHostToDevice));
     TRYC(cudaMemcpy(t->d_list_len, p.list_len, sizeof(p.list_len), cudaMemcpyHostToDevice));
-    TRYC(cudaMemcpy(t->d_items, p.items.data(), p.items.size() * sizeof(Item),
+    if (!p.items.empty())
+        TRYC(cudaMemcpy(t->d_items, p.items.data(), p.items.size() * sizeof(Item),
+                        cudaMemcpyHostToDevice));
+    TRYC(cudaMemcpy(t->d_items_adj, p.items_adj.data(), p.items_adj.size() * sizeof(Item),
                     cudaMemcpyHostToDevice));
     t->plan = std::move(p);
     t->have_plan = true;
@@ -234,8 +268,9 @@ void enqueue_moments(ot_tree* t, const double* rho, cudaStream_t s) {
 // Enqueues the interaction launch (expansions zeroed first).
 int enqueue_interact(ot_tree* t, const ot_solve_opts& o, cudaStream_t s) {
     DevTree d = dev_tree(t);
-    TRYC(cudaMemsetAsync(t->d_loc, 0, sizeof(double) * kLoc * (size_t)d.n_cells, s));
+    // the expansions were zeroed by the upward pass (leaf and M2M kernels)
     TRYC(cudaMemsetAsync(t->d_counter, 0, sizeof(int), s));
+    launch_lattice(d, dev_plan(t), dev_lattice(t), o.precision, o.G, s);
     int ctas = std::max(1, t->num_sms * t->ctas_per_sm);
     launch_interact(d, dev_plan(t), o.precision, o.G, o.am_correction ? 1 : 0, ctas,
                     t->warps_per_cta, s);
@@ -378,6 +413,7 @@ int ot_build_tree(const ot_tree_desc* desc, int device, ot_tree** out) {
         return fail(OT_ERR_CUDA);
     }
     t->have_plan = false;
+    if (configure_lattice() != 0) return fail(OT_ERR_CUDA);
     if ((e = ensure_plan(t, 0.5))) return fail(e);
     *out = t;
     return OT_OK;
@@ -395,6 +431,7 @@ void ot_destroy_tree(ot_tree* t) {
                         t->d_level_first, t->d_leaf_node, t->d_mom64, t->d_mom32, t->d_loc,
                         t->d_status, t->d_entries, t->d_tab64, t->d_tab32, t->d_list_first,
                         t->d_list_len, t->d_items, t->d_counter, t->d_rho_in, t->d_phi_out,
+                        t->d_hoff_far, t->d_hoff_near, t->d_lattice_nodes, t->d_items_adj,
                         t->d_g_out, t->d_locbar, t->d_mombar};
         for (void* p : ptrs)
             if (p) cudaFree(p);
@@ -484,7 +521,10 @@ int ot_gravity_backward(ot_tree* t, const double* rho, const double* w1, const d
         launch_l2l_reverse(d, h.level_first[L], h.level_first[L + 1] - h.level_first[L],
                            t->d_locbar, t->d_mombar, s);
     TRYC(cudaMemsetAsync(t->d_counter, 0, sizeof(int), s));
-    launch_m2l_reverse(d, dev_plan(t), t->d_locbar, t->d_mombar, o.G, o.am_correction ? 1 : 0,
+    DevPlan pa = dev_plan(t);
+    pa.items = t->d_items_adj;
+    pa.n_items = (int)t->plan.items_adj.size();
+    launch_m2l_reverse(d, pa, t->d_locbar, t->d_mombar, o.G, o.am_correction ? 1 : 0,
                        std::max(1, t->num_sms * 4), s);
     for (int L = 0; L + 1 < h.n_levels; L++)
         launch_m2m_reverse(d, h.level_first[L], h.level_first[L + 1] - h.level_first[L],

@@ -69,6 +69,38 @@ __host__ __device__ inline int entry_dy(int e) { return ((e >> 5) & 31) - 16; }
 __host__ __device__ inline int entry_dz(int e) { return ((e >> 10) & 31) - 16; }
 __host__ __device__ inline int entry_near(int e) { return (e >> 15) & 1; }
 
+// Shared-memory halo of leaf masses used by the lattice kernel: the cells of
+// a node and of a margin w around it, split into 8 parity sub-halos so that a
+// warp of same-parity targets reads consecutive words.  In a sub-halo the
+// cell at node-local (x, y, z) (x in [-w, 8+w)) sits at
+//   ((x+w)>>1) + kHaloPy ((y+w)>>1) + halo_pz(w) ((z+w)>>1),
+// and sub-halo (x&1) + 2 (y&1) + 4 (z&1) starts at that index times
+// halo_sub(w).  kHaloPy = 12 and halo_pz = 16 (mod 32) make the 32 lanes of a
+// warp (4 x 4 x 2 targets) hit 32 distinct banks.
+constexpr int kHaloPy = 12;
+__host__ __device__ inline int halo_hh(int w) { return w + 4; }
+__host__ __device__ inline int halo_pz(int w) {
+    const int need = kHaloPy * (w + 4);
+    return need + (((16 - need) % 32) + 32) % 32;
+}
+__host__ __device__ inline int halo_sub(int w) { return halo_pz(w) * halo_hh(w); }
+__host__ __device__ inline int halo_index(int x, int y, int z, int w) {
+    return ((x & 1) + 2 * (y & 1) + 4 * (z & 1)) * halo_sub(w) + ((x + w) >> 1) +
+           kHaloPy * ((y + w) >> 1) + halo_pz(w) * ((z + w) >> 1);
+}
+
+// Lattice part of a plan: halo offsets of every entry of the 8 parity lists
+// (far halo of width w_far, near halo of width w_near), and the leaf nodes of
+// level >= 1 whose leaf-leaf pairs the lattice kernel computes.
+struct DevLattice {
+    const int* hoff_far;        // [n_entries]
+    const int* hoff_near;       // [n_entries] (near entries only)
+    const int* nodes;           // [n_nodes_lattice]
+    int n_nodes;
+    int w_far, w_near;
+    int n_near;
+};
+
 // Work item: x = target node; y = level | parity << 8 | half << 11 | list << 12;
 // z, w = entry range [k0, k1) of that list.  32 target cells per item: the
 // cells of one parity class (px, py, pz) with z-index 2 (2 half + q) + pz,

@@ -5,8 +5,8 @@
 // delta = X_cell - X_parent, and inherits the parent's angular-momentum
 // correction acceleration (Sec. 4.3.1).  At a leaf cell (X = cell centre) the
 // result is evaluated: phi = L0 (+ the optional uniform-cube self term) and
-// g = -L1 + a_c.  One thread per cell, one block per node, levels top-down,
-// FP64 throughout.
+// g = -L1 + a_c.  One thread per cell, 8 blocks of 64 threads per node (so the
+// coarse levels spread over many SMs), levels top-down, FP64 throughout.
 #include "kernels.hpp"
 
 namespace otfmm {
@@ -19,22 +19,26 @@ __host__ __device__ inline double cube_self_constant() {
     return 3.0 * (log(2.0 + sqrt(3.0)) - 3.14159265358979323846 / 6.0);
 }
 
-__global__ void __launch_bounds__(256) k_l2l(DevTree t, int first, const double* __restrict__ rho,
-                                             double* __restrict__ phi, double* __restrict__ g,
-                                             double G, int self_term) {
-    const int node = first + blockIdx.x;
+// 64 threads per block, 8 blocks per node (one z-layer of 64 cells each).
+__global__ void __launch_bounds__(64) k_l2l(DevTree t, int first, const double* __restrict__ rho,
+                                            double* __restrict__ phi, double* __restrict__ g,
+                                            double G, int self_term) {
+    const int node = first + (blockIdx.x >> 3);
     const int L = t.node_level[node];
     const int parent = t.node_parent[node];
     const int leaf = t.node_leaf[node];
     const long long N = t.n_cells;
     const double h = t.size / (double)(8 << L);
     const int* xyz = t.node_xyz + 3 * node;
-    for (int c = threadIdx.x; c < kCells; c += blockDim.x) {
+    {
+        const int c = ((blockIdx.x & 7) << 6) + threadIdx.x;
         const int ci[3] = {c & 7, (c >> 3) & 7, c >> 6};
         const long long cell = (long long)node * kCells + c;
         double E[kLoc];
+        // a leaf cell's expansion holds only L0, L1 and the correction
 #pragma unroll
-        for (int r = 0; r < kLoc; r++) E[r] = t.loc[r * N + cell];
+        for (int r = 0; r < kLoc; r++)
+            E[r] = (leaf < 0 || r < 4 || r >= 20) ? t.loc[r * N + cell] : 0.0;
         if (parent >= 0) {
             // parent cell and the cell's offset (0 or 1 per axis) inside it
             int pl = 0, off[3];
@@ -108,7 +112,7 @@ __global__ void __launch_bounds__(256) k_l2l(DevTree t, int first, const double*
 void launch_l2l(const DevTree& t, int level, int first, int count, const double* rho,
                 double* phi, double* g, double G, int self_term, cudaStream_t s) {
     (void)level;
-    if (count > 0) k_l2l<<<count, 256, 0, s>>>(t, first, rho, phi, g, G, self_term);
+    if (count > 0) k_l2l<<<count * 8, 64, 0, s>>>(t, first, rho, phi, g, G, self_term);
 }
 
 }  // namespace otfmm

@@ -11,9 +11,10 @@
 // level L need only the moments, which the upward pass has finished.
 //
 // Per (target A, source B) pair, decided per lane:
-//   both leaf cells           -> point-mass pair on the lattice: R = -d h
-//                                exactly, so 1/|d| and D1(-d) = d/|d|^3 come
-//                                from a table and the pair costs 4 FMAs
+//   both leaf cells           -> done by the lattice kernel (lattice.cu) for
+//                                leaf nodes of level >= 1; for a leaf root
+//                                here, from the same table (R = -d h exactly,
+//                                1/|d| and D1(-d) = d/|d|^3, 4 FMAs)
 //   near, both interior       -> skipped (resolved one level down)
 //   otherwise                 -> M2L of order 3 + correction (pair_formula.cuh)
 // Each lane accumulates in registers (FP64, or FP32 for the bulk form with
@@ -80,7 +81,8 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
         const bool sleaf = s_lf[slot] != 0;
         const long long sc = (long long)nb * kCells + (sx & 7) + 8 * (sy & 7) + 64 * (sz & 7);
         if (!FULL && sleaf) {
-            // two point masses on the lattice
+            if (L > 0) continue;  // leaf-leaf pairs of level >= 1: lattice kernel
+            // two point masses on the lattice (a leaf root)
             if (sizeof(T) == 4 && entry_near(e)) {
                 double a, b, c, d;
                 tab_of(p, base + q, a, b, c, d);

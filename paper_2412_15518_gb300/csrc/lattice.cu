@@ -1,0 +1,155 @@
+// Leaf-leaf pairs of every leaf node of level >= 1: the lattice part of the
+// cell-to-cell interactions (stencil approach, Sec. 5.5).
+//
+// Two leaf cells are point masses at their cell centres, so their pair vector
+// is R = -d h exactly and the pair adds m_B (1/|d|, D1(-d)) / (h, h^2) to the
+// target's (L0, L1) -- near pairs exactly (the monopole-monopole field) and
+// far pairs as the order-3 M2L of two monopoles, which reduces to the same
+// two terms at a leaf target.  Over one leaf node this is a small 3-D
+// convolution of the masses with a parity-dependent stencil.
+//
+// One CTA per leaf node, 8 warps (one per parity class of targets), each lane
+// 2 targets 4 cells apart in z.  The masses of the node and of a margin w
+// around it are staged once in shared memory (parity-split, padded so a warp
+// reads 32 banks); cells of absent or interior neighbours are stored as zero
+// mass, so the inner loop has no branches: per stencil entry one broadcast
+// load of the table and the halo offset, two shared loads, eight FMAs.
+// FP64 form: one FP64 halo for every pair.  FP32-bulk form: far pairs from an
+// FP32 halo with FP32 arithmetic, near pairs from an FP64 halo of width
+// floor(1/theta) in FP64; both accumulated and flushed in FP64.
+#include "lattice.hpp"
+
+namespace otfmm {
+
+namespace {
+
+template <class T> __device__ __forceinline__ const T* lat_mom(const DevTree& t);
+template <> __device__ __forceinline__ const double* lat_mom<double>(const DevTree& t) { return t.mom64; }
+template <> __device__ __forceinline__ const float* lat_mom<float>(const DevTree& t) { return t.mom32; }
+
+// Fills a parity-split halo of width w with the masses of the leaf cells
+// around `node` (zero where there is no leaf cell at this level).
+template <class T>
+__device__ __forceinline__ void fill_halo(const DevTree& t, int node, int w, T* halo,
+                                          const T* __restrict__ mass) {
+    const int hw = 8 + 2 * w;
+    const int total = hw * hw * hw;
+    const int* nbr = t.nbr + (long long)node * 27;
+    for (int u = threadIdx.x; u < total; u += blockDim.x) {
+        const int x = u % hw - w, y = (u / hw) % hw - w, z = u / (hw * hw) - w;
+        const int slot = ((x >> 3) + 1) + 3 * ((y >> 3) + 1) + 9 * ((z >> 3) + 1);
+        const int nb = __ldg(nbr + slot);
+        T v = T(0.0);
+        if (nb >= 0 && __ldg(t.node_leaf + nb) >= 0)
+            v = mass[(long long)nb * kCells + (x & 7) + 8 * (y & 7) + 64 * (z & 7)];
+        halo[halo_index(x, y, z, w)] = v;
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_lattice(DevTree t, DevPlan p, DevLattice lp, double G) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int node = lp.nodes[blockIdx.x];
+    const int wf = lp.w_far, wn = lp.w_near;
+    T* hfar = reinterpret_cast<T*>(smem);
+    double* hnear = reinterpret_cast<double*>(smem + sizeof(T) * 8 * halo_sub(wf));
+    fill_halo<T>(t, node, wf, hfar, lat_mom<T>(t));
+    if (sizeof(T) == 4) fill_halo<double>(t, node, wn, hnear, t.mom64);
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int par = threadIdx.x >> 5;  // one parity class per warp
+    const int a = lane & 3, b = (lane >> 2) & 3, c = lane >> 4;
+    const int px = par & 1, py = (par >> 1) & 1, pz = par >> 2;
+    const int base = p.list_first[par];
+    const int len = p.list_len[par];
+    const int tf = a + kHaloPy * b + halo_pz(wf) * c;  // lane offset in the far halo
+    const int tf2 = 2 * halo_pz(wf);                    // second target: 4 cells up in z
+    double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;     // FP64 sums, target 1
+    double e0 = 0.0, e1 = 0.0, e2 = 0.0, e3 = 0.0;     // FP64 sums, target 2
+    int q0 = 0;
+    if (sizeof(T) == 4) {
+        // near pairs in FP64 from the FP64 halo
+        const int tn = a + kHaloPy * b + halo_pz(wn) * c;
+        const int tn2 = 2 * halo_pz(wn);
+#pragma unroll 4
+        for (int q = 0; q < lp.n_near; q++) {
+            const int o = __ldg(lp.hoff_near + base + q) + tn;
+            const double2 k0 = __ldg(p.tab64 + 2 * (base + q)), k1 = __ldg(p.tab64 + 2 * (base + q) + 1);
+            const double m1 = hnear[o], m2 = hnear[o + tn2];
+            d0 = fma(m1, k0.x, d0); d1 = fma(m1, k0.y, d1); d2 = fma(m1, k1.x, d2); d3 = fma(m1, k1.y, d3);
+            e0 = fma(m2, k0.x, e0); e1 = fma(m2, k0.y, e1); e2 = fma(m2, k1.x, e2); e3 = fma(m2, k1.y, e3);
+        }
+        q0 = lp.n_near;
+        float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
+        const float* hf = reinterpret_cast<const float*>(hfar);
+#pragma unroll 4
+        for (int q = q0; q < len; q++) {
+            const int o = __ldg(lp.hoff_far + base + q) + tf;
+            const float4 k = __ldg(p.tab32 + base + q);
+            const float m1 = hf[o], m2 = hf[o + tf2];
+            f0 = fmaf(m1, k.x, f0); f1 = fmaf(m1, k.y, f1); f2 = fmaf(m1, k.z, f2); f3 = fmaf(m1, k.w, f3);
+            g0 = fmaf(m2, k.x, g0); g1 = fmaf(m2, k.y, g1); g2 = fmaf(m2, k.z, g2); g3 = fmaf(m2, k.w, g3);
+        }
+        d0 += f0; d1 += f1; d2 += f2; d3 += f3;
+        e0 += g0; e1 += g1; e2 += g2; e3 += g3;
+    } else {
+        const double* hd = reinterpret_cast<const double*>(hfar);
+#pragma unroll 4
+        for (int q = 0; q < len; q++) {
+            const int o = __ldg(lp.hoff_far + base + q) + tf;
+            const double2 k0 = __ldg(p.tab64 + 2 * (base + q)), k1 = __ldg(p.tab64 + 2 * (base + q) + 1);
+            const double m1 = hd[o], m2 = hd[o + tf2];
+            d0 = fma(m1, k0.x, d0); d1 = fma(m1, k0.y, d1); d2 = fma(m1, k1.x, d2); d3 = fma(m1, k1.y, d3);
+            e0 = fma(m2, k0.x, e0); e1 = fma(m2, k0.y, e1); e2 = fma(m2, k1.x, e2); e3 = fma(m2, k1.y, e3);
+        }
+    }
+    // to physical units: L0 * (-G / h), L1 * (-G / h^2)
+    const int L = t.node_level[node];
+    const double hi = (double)(8 << L) / t.size;
+    const double s1 = -G * hi, s2 = s1 * hi;
+    const long long N = t.n_cells;
+    const long long c1 = (long long)node * kCells + (2 * a + px) + 8 * (2 * b + py) + 64 * (2 * c + pz);
+    const long long c2 = c1 + 256;
+    double* loc = t.loc;
+    atomicAdd(loc + c1, s1 * d0);
+    atomicAdd(loc + N + c1, s2 * d1);
+    atomicAdd(loc + 2 * N + c1, s2 * d2);
+    atomicAdd(loc + 3 * N + c1, s2 * d3);
+    atomicAdd(loc + c2, s1 * e0);
+    atomicAdd(loc + N + c2, s2 * e1);
+    atomicAdd(loc + 2 * N + c2, s2 * e2);
+    atomicAdd(loc + 3 * N + c2, s2 * e3);
+}
+
+}  // namespace
+
+size_t lattice_smem_bytes(int precision, int w_far, int w_near) {
+    if (precision == 1)
+        return sizeof(float) * 8 * (size_t)halo_sub(w_far) + sizeof(double) * 8 * (size_t)halo_sub(w_near);
+    return sizeof(double) * 8 * (size_t)halo_sub(w_far);
+}
+
+int configure_lattice() {
+    const int bytes = 160 * 1024;
+    if (cudaFuncSetAttribute(k_lattice<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_lattice<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return 0;
+}
+
+void launch_lattice(const DevTree& t, const DevPlan& p, const DevLattice& lp, int precision,
+                    double G, cudaStream_t s) {
+    if (lp.n_nodes <= 0) return;
+    const size_t smem = lattice_smem_bytes(precision, lp.w_far, lp.w_near);
+    if (precision == 1)
+        k_lattice<float><<<lp.n_nodes, 256, smem, s>>>(t, p, lp, G);
+    else
+        k_lattice<double><<<lp.n_nodes, 256, smem, s>>>(t, p, lp, G);
+}
+
+}  // namespace otfmm

@@ -5,8 +5,14 @@
 // interior cell's moments are the exact moments of its 8 children about the
 // parent's centre of mass (multipole moments up to order 3, implied by the
 // FMM of Sec. 4.3.2).  Everything is FP64; an FP32 copy is written for the
-// FP32-bulk interaction form.  One thread per cell, one block per node, all
-// loads and stores structure-of-arrays and coalesced across the block.
+// FP32-bulk interaction form.  Both kernels also zero the expansions of their
+// cells, which the interaction kernels then accumulate into.
+//
+// M2M uses 8 threads per parent cell, one per child: the children's masses
+// and mass-weighted positions are summed by warp shuffles, every lane forms
+// its child's contribution about the common centre of mass, and a second
+// shuffle reduction sums them.  So the coarse levels (1 node at level 0,
+// 8 at level 1) still spread over many SMs of the FP64 pipe.
 #include "kernels.hpp"
 
 namespace otfmm {
@@ -20,15 +26,26 @@ __global__ void __launch_bounds__(256) k_leaf_moments(DevTree t, const int* __re
     const int L = t.node_level[node];
     const double h = t.size / (double)(8 << L);
     const double h3 = h * h * h;
+    const long long N = t.n_cells;
     for (int c = threadIdx.x; c < kCells; c += blockDim.x) {
         const double m = rho[(long long)leaf * kCells + c] * h3;
         const long long cell = (long long)node * kCells + c;
         t.mom64[cell] = m;
         t.mom32[cell] = (float)m;
+        // a leaf cell's expansion: L0, L1 and the correction acceleration
+        t.loc[cell] = 0.0;
+        t.loc[N + cell] = 0.0;
+        t.loc[2 * N + cell] = 0.0;
+        t.loc[3 * N + cell] = 0.0;
+        t.loc[20 * N + cell] = 0.0;
+        t.loc[21 * N + cell] = 0.0;
+        t.loc[22 * N + cell] = 0.0;
     }
 }
 
-// (i, j, k) of the 10 packed components of a symmetric rank-3 tensor
+// (i, j, k) of the packed components of symmetric rank-2 and rank-3 tensors
+__constant__ int c_i2[6] = {0, 0, 0, 1, 1, 2};
+__constant__ int c_j2[6] = {0, 1, 2, 1, 2, 2};
 __constant__ int c_t3[10][3] = {{0, 0, 0}, {0, 0, 1}, {0, 0, 2}, {0, 1, 1}, {0, 1, 2},
                                 {0, 2, 2}, {1, 1, 1}, {1, 1, 2}, {1, 2, 2}, {2, 2, 2}};
 
@@ -37,79 +54,80 @@ __device__ __forceinline__ int p2(int i, int j) {
     return i <= j ? (i == 0 ? j : (i == 1 ? 2 + j : 5)) : (j == 0 ? i : (j == 1 ? 2 + i : 5));
 }
 
+// sum over the 8 lanes of a parent cell (lanes 8g .. 8g+7 of a warp)
+__device__ __forceinline__ double sum8(double v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    return v;
+}
+
+// 256 threads = 32 parent cells x 8 children; 16 blocks per node.
 __global__ void __launch_bounds__(256) k_m2m(DevTree t, int first) {
-    const int node = first + blockIdx.x;
+    const int node = first + (blockIdx.x >> 4);
     const int child0 = t.node_child[node];
     if (child0 < 0) return;  // leaf node: moments come from rho
     const long long N = t.n_cells;
-    for (int c = threadIdx.x; c < kCells; c += blockDim.x) {
-        const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
-        // the 8 children of cell (i, j, k) lie in child node (i>>2, j>>2, k>>2)
-        const int cn = child0 + (i >> 2) + 2 * (j >> 2) + 4 * (k >> 2);
-        const long long cbase = (long long)cn * kCells;
-        double m[8], pos[8][3];
-        double M = 0.0;
+    const int c = ((blockIdx.x & 15) << 5) + (threadIdx.x >> 3);  // parent cell in the node
+    const int q = threadIdx.x & 7;                                  // child octant
+    const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
+    const int a = q & 1, b = (q >> 1) & 1, e = q >> 2;
+    // the 8 children of cell (i, j, k) lie in child node (i>>2, j>>2, k>>2)
+    const int cn = child0 + (i >> 2) + 2 * (j >> 2) + 4 * (k >> 2);
+    const bool cleaf = t.node_child[cn] < 0;
+    const long long cc = (long long)cn * kCells + (2 * (i & 3) + a) + 8 * (2 * (j & 3) + b) +
+                         64 * (2 * (k & 3) + e);
+    const double m = t.mom64[cc];
+    // child centre of mass relative to the parent cell centre, parent units
+    double pos[3];
+    pos[0] = 0.5 * ((a - 0.5) + t.mom64[N + cc]);
+    pos[1] = 0.5 * ((b - 0.5) + t.mom64[2 * N + cc]);
+    pos[2] = 0.5 * ((e - 0.5) + t.mom64[3 * N + cc]);
+    const double M = sum8(m);
+    double X[3];
 #pragma unroll
-        for (int q = 0; q < 8; q++) {
-            const int a = q & 1, b = (q >> 1) & 1, e = q >> 2;
-            const long long cc = cbase + (2 * (i & 3) + a) + 8 * (2 * (j & 3) + b) + 64 * (2 * (k & 3) + e);
-            m[q] = t.mom64[cc];
-            // child centre of mass relative to the parent cell centre, parent units
-            pos[q][0] = 0.5 * ((a - 0.5) + t.mom64[N + cc]);
-            pos[q][1] = 0.5 * ((b - 0.5) + t.mom64[2 * N + cc]);
-            pos[q][2] = 0.5 * ((e - 0.5) + t.mom64[3 * N + cc]);
-            M += m[q];
-        }
-        double X[3] = {0.0, 0.0, 0.0};
+    for (int s = 0; s < 3; s++) X[s] = sum8(m * pos[s]) / M;
+    const double d[3] = {pos[0] - X[0], pos[1] - X[1], pos[2] - X[2]};
+    double c2[6], S[16];
+    if (cleaf) {
 #pragma unroll
-        for (int q = 0; q < 8; q++)
+        for (int r = 0; r < 6; r++) c2[r] = 0.0;
+    } else {
 #pragma unroll
-            for (int a = 0; a < 3; a++) X[a] = fma(m[q], pos[q][a], X[a]);
-        const double iM = 1.0 / M;
+        for (int r = 0; r < 6; r++) c2[r] = 0.25 * t.mom64[(4 + r) * N + cc];  // child units -> parent
+    }
+    const double md[3] = {m * d[0], m * d[1], m * d[2]};
 #pragma unroll
-        for (int a = 0; a < 3; a++) X[a] *= iM;
-        double S2[6] = {0, 0, 0, 0, 0, 0}, S3[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int r = 0; r < 6; r++) S[r] = c2[r] + md[c_i2[r]] * d[c_j2[r]];
 #pragma unroll
-        for (int q = 0; q < 8; q++) {
-            const int a = q & 1, b = (q >> 1) & 1, e = q >> 2;
-            const long long cc = cbase + (2 * (i & 3) + a) + 8 * (2 * (j & 3) + b) + 64 * (2 * (k & 3) + e);
-            const double d[3] = {pos[q][0] - X[0], pos[q][1] - X[1], pos[q][2] - X[2]};
-            double c2[6];
+    for (int r = 0; r < 10; r++) {
+        const int ii = c_t3[r][0], jj = c_t3[r][1], kk = c_t3[r][2];
+        double v = md[ii] * d[jj] * d[kk];
+        if (!cleaf)
+            v += 0.125 * t.mom64[(10 + r) * N + cc] + c2[p2(ii, jj)] * d[kk] + c2[p2(ii, kk)] * d[jj] +
+                 c2[p2(jj, kk)] * d[ii];
+        S[6 + r] = v;
+    }
 #pragma unroll
-            for (int r = 0; r < 6; r++) c2[r] = 0.25 * t.mom64[(4 + r) * N + cc];  // child units -> parent
+    for (int r = 0; r < 16; r++) S[r] = sum8(S[r]);
+    const long long cell = (long long)node * kCells + c;
+    // lane q writes the components it owns: 20 moments, 23 zeroed expansions
+    double vals[20];
+    vals[0] = M;
+    vals[1] = X[0];
+    vals[2] = X[1];
+    vals[3] = X[2];
 #pragma unroll
-            for (int r = 0; r < 6; r++) {
-                const int ii = r < 3 ? 0 : (r < 5 ? 1 : 2);
-                const int jj = r < 3 ? r : (r < 5 ? r - 2 : 2);
-                S2[r] += c2[r] + m[q] * d[ii] * d[jj];
-            }
+    for (int r = 0; r < 16; r++) vals[4 + r] = S[r];
 #pragma unroll
-            for (int r = 0; r < 10; r++) {
-                const int ii = c_t3[r][0], jj = c_t3[r][1], kk = c_t3[r][2];
-                S3[r] += 0.125 * t.mom64[(10 + r) * N + cc] + c2[p2(ii, jj)] * d[kk] +
-                         c2[p2(ii, kk)] * d[jj] + c2[p2(jj, kk)] * d[ii] +
-                         m[q] * d[ii] * d[jj] * d[kk];
-            }
-        }
-        const long long cell = (long long)node * kCells + c;
-        t.mom64[cell] = M;
-        t.mom32[cell] = (float)M;
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            t.mom64[(1 + a) * N + cell] = X[a];
-            t.mom32[(1 + a) * N + cell] = (float)X[a];
-        }
-#pragma unroll
-        for (int r = 0; r < 6; r++) {
-            t.mom64[(4 + r) * N + cell] = S2[r];
-            t.mom32[(4 + r) * N + cell] = (float)S2[r];
-        }
-#pragma unroll
-        for (int r = 0; r < 10; r++) {
-            t.mom64[(10 + r) * N + cell] = S3[r];
-            t.mom32[(10 + r) * N + cell] = (float)S3[r];
+    for (int r = 0; r < 20; r++) {
+        if ((r & 7) == q) {
+            t.mom64[r * N + cell] = vals[r];
+            t.mom32[r * N + cell] = (float)vals[r];
         }
     }
+#pragma unroll
+    for (int r = q; r < kLoc; r += 8) t.loc[r * N + cell] = 0.0;
 }
 
 }  // namespace
@@ -121,7 +139,7 @@ void launch_leaf_moments(const DevTree& t, const int* leaf_node, const double* r
 
 void launch_m2m(const DevTree& t, int level, int first, int count, cudaStream_t s) {
     (void)level;
-    if (count > 0) k_m2m<<<count, 256, 0, s>>>(t, first);
+    if (count > 0) k_m2m<<<count * 16, 256, 0, s>>>(t, first);
 }
 
 }  // namespace otfmm

@@ -35,6 +35,7 @@
 
 #include "../../include/octofmm.h"
 #include "kernels.hpp"
+#include "lattice.hpp"
 #include "tree_host.hpp"
 
 namespace otfmm {
@@ -58,6 +59,7 @@ struct Layout {
     size_t level, leaf, parent, child, xyz, nbr, level_first, leaf_node;
     size_t mom64, mom32, loc, status, counter;
     size_t entries, tab64, tab32, list_first, list_len, items;
+    size_t hoff_far, hoff_near, lattice_nodes;
     size_t end;
 };
 
@@ -89,6 +91,9 @@ Layout make_layout() {
     l.list_first = take(sizeof(int) * kNumLists);
     l.list_len = take(sizeof(int) * kNumLists);
     l.items = take(sizeof(int) * 4 * kMaxItems);
+    l.hoff_far = take(sizeof(int) * kMaxEntries);
+    l.hoff_near = take(sizeof(int) * kMaxEntries);
+    l.lattice_nodes = take(sizeof(int) * kMaxNodes);
     l.end = o;
     return l;
 }
@@ -102,6 +107,7 @@ int scratch_address(int device, unsigned char** out) {
             cudaGetLastError();
             return OT_ERR_CUDA;
         }
+        if (configure_lattice() != 0) return OT_ERR_CUDA;
         g_scratch_addr[device] = (unsigned char*)p;
     }
     *out = g_scratch_addr[device];
@@ -181,7 +187,10 @@ extern "C" int ot_solve_gravity_static(const ot_tree_desc* desc, const double* r
         (e = put(base, l.tab32, &p.tab32[0].x, 4 * p.tab32.size(), s)) ||
         (e = put(base, l.list_first, p.list_first, kNumLists, s)) ||
         (e = put(base, l.list_len, p.list_len, kNumLists, s)) ||
-        (e = put(base, l.items, &p.items[0].x, 4 * p.items.size(), s)))
+        (e = put(base, l.hoff_far, p.hoff_far.data(), p.hoff_far.size(), s)) ||
+        (e = put(base, l.hoff_near, p.hoff_near.data(), p.hoff_near.size(), s)) ||
+        (e = put(base, l.lattice_nodes, p.lattice_nodes.data(), p.lattice_nodes.size(), s)) ||
+        (p.items.size() && (e = put(base, l.items, &p.items[0].x, 4 * p.items.size(), s))))
         return e;
     // what must start at zero: leaf offsets and higher moments, expansions,
     // the item counter and the status word
@@ -227,6 +236,15 @@ extern "C" int ot_solve_gravity_static(const ot_tree_desc* desc, const double* r
     launch_leaf_moments(d, (const int*)(base + l.leaf_node), rho, s);
     for (int L = h.n_levels - 2; L >= 0; L--)
         launch_m2m(d, L, h.level_first[L], h.level_first[L + 1] - h.level_first[L], s);
+    DevLattice dl;
+    dl.hoff_far = (const int*)(base + l.hoff_far);
+    dl.hoff_near = (const int*)(base + l.hoff_near);
+    dl.nodes = (const int*)(base + l.lattice_nodes);
+    dl.n_nodes = (int)p.lattice_nodes.size();
+    dl.w_far = p.w_far;
+    dl.w_near = p.w_near;
+    dl.n_near = p.n_near;
+    launch_lattice(d, dp, dl, o.precision, o.G, s);
     launch_interact(d, dp, o.precision, o.G, o.am_correction ? 1 : 0, 4 * sms, 4, s);
     for (int L = 0; L < h.n_levels; L++)
         launch_l2l(d, L, h.level_first[L], h.level_first[L + 1] - h.level_first[L], rho, phi, g,

@@ -174,6 +174,22 @@ int build_stencil(const HostTree& t, double theta, HostPlan& p) {
                 }
         p.list_len[par] = (int)p.entries.size() - p.list_first[par];
     }
+    // halo offsets of the parity lists for the lattice kernel
+    p.w_far = W;
+    p.w_near = R;
+    p.hoff_far.assign(p.entries.size(), 0);
+    p.hoff_near.assign(p.entries.size(), 0);
+    for (int par = 0; par < 8; par++) {
+        int pp[3] = {par & 1, (par >> 1) & 1, par >> 2};
+        for (int q = 0; q < p.list_len[par]; q++) {
+            int e = p.entries[p.list_first[par] + q];
+            int d[3] = {entry_dx(e), entry_dy(e), entry_dz(e)};
+            p.hoff_far[p.list_first[par] + q] = halo_index(pp[0] + d[0], pp[1] + d[1], pp[2] + d[2], W);
+            if (entry_near(e))
+                p.hoff_near[p.list_first[par] + q] =
+                    halo_index(pp[0] + d[0], pp[1] + d[1], pp[2] + d[2], R);
+        }
+    }
     // level 0: every non-near pair of the root's 8^3 cells is far
     p.list_first[8] = (int)p.entries.size();
     for (int e : near) push(e);
@@ -184,6 +200,8 @@ int build_stencil(const HostTree& t, double theta, HostPlan& p) {
                 push(pack_entry(dx, dy, dz, 0));
             }
     p.list_len[8] = (int)p.entries.size() - p.list_first[8];
+    p.hoff_far.resize(p.entries.size(), 0);
+    p.hoff_near.resize(p.entries.size(), 0);
 
     // Interaction counts.  For a list and a neighbour slot, count the
     // (target, entry) pairs of that list whose source falls in that slot,
@@ -240,9 +258,14 @@ int build_stencil(const HostTree& t, double theta, HostPlan& p) {
     return OT_OK;
 }
 
-void build_items(const HostTree& t, int chunk, HostPlan& p) {
-    p.chunk = chunk;
-    p.items.clear();
+namespace {
+
+// Items of every node that needs the general kernel; with `all`, leaf nodes
+// of level >= 1 without interior neighbours get one item per parity half
+// covering their whole list (their pairs are all lattice pairs).
+std::vector<Item> make_items(const HostTree& t, int chunk, const HostPlan& p, bool all,
+                             std::vector<int>* lattice_nodes) {
+    std::vector<Item> items;
     std::vector<int64_t> cost;
     for (int v = 0; v < t.n_nodes(); v++) {
         int L = t.node_level[v];
@@ -253,27 +276,37 @@ void build_items(const HostTree& t, int chunk, HostPlan& p) {
                 int nb = t.nbr[(size_t)v * 27 + s];
                 if (nb >= 0 && t.node_leaf[nb] < 0) seam = true;
             }
+        bool lattice_only = tl && L > 0 && !seam;
+        if (tl && L > 0 && lattice_nodes) lattice_nodes->push_back(v);
+        if (lattice_only && !all) continue;
         for (int par = 0; par < 8; par++) {
             int list = L == 0 ? 8 : par;
             int len = p.list_len[list];
-            // leaf targets walk their whole list (cheap lattice pairs) unless
-            // they border interior cells; interior targets are chunked
-            int step = (tl && !seam && L > 0) ? len : std::max(1, chunk);
+            int step = lattice_only ? len : std::max(1, chunk);
             for (int half = 0; half < 2; half++)
                 for (int k0 = 0; k0 < len; k0 += step) {
                     int k1 = std::min(len, k0 + step);
-                    p.items.push_back({v, L | (par << 8) | (half << 11) | (list << 12), k0, k1});
-                    cost.push_back((int64_t)(k1 - k0) * ((tl && !seam) ? 1 : 24));
+                    items.push_back({v, L | (par << 8) | (half << 11) | (list << 12), k0, k1});
+                    cost.push_back((int64_t)(k1 - k0) * (lattice_only ? 1 : (tl ? 4 : 24)));
                 }
         }
     }
     // longest items first; ties keep the breadth-first node order
-    std::vector<int> order(p.items.size());
+    std::vector<int> order(items.size());
     for (size_t i = 0; i < order.size(); i++) order[i] = (int)i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-    std::vector<Item> sorted(p.items.size());
-    for (size_t i = 0; i < order.size(); i++) sorted[i] = p.items[order[i]];
-    p.items.swap(sorted);
+    std::vector<Item> sorted(items.size());
+    for (size_t i = 0; i < order.size(); i++) sorted[i] = items[order[i]];
+    return sorted;
+}
+
+}  // namespace
+
+void build_items(const HostTree& t, int chunk, HostPlan& p) {
+    p.chunk = chunk;
+    p.lattice_nodes.clear();
+    p.items = make_items(t, chunk, p, false, &p.lattice_nodes);
+    p.items_adj = make_items(t, chunk, p, true, nullptr);
 }
 
 }  // namespace otfmm

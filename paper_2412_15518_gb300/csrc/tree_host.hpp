@@ -52,7 +52,11 @@ struct HostPlan {
     int list_first[kNumLists] = {0};
     int list_len[kNumLists] = {0};
     int n_near = 0;                   // near offsets (first entries of every list)
+    int w_far = 0, w_near = 0;        // halo widths of the lattice kernel
+    std::vector<int> hoff_far, hoff_near;  // halo offsets per entry (parity lists)
+    std::vector<int> lattice_nodes;   // leaf nodes of level >= 1
     std::vector<Item> items;
+    std::vector<Item> items_adj;      // every node (the adjoint has no lattice kernel)
     int64_t n_m2l = 0, n_p2p = 0, n_seam = 0, n_lattice = 0;
     int64_t n_class[PairClasses] = {0, 0, 0, 0, 0};
     double flops_am = 0.0, flops_noam = 0.0;  // one interaction launch
@@ -63,7 +67,10 @@ struct HostPlan {
 // the tree; no work items.
 int build_stencil(const HostTree& t, double theta, HostPlan& p);
 
-// Work items of the persistent launch for a given chunk length.
+// Work items of the persistent launch for a given chunk length: interior
+// targets (chunked), leaf targets that border interior cells (their pairs
+// with interior cells), and a leaf root; the leaf-leaf pairs of leaf nodes
+// of level >= 1 go to the lattice kernel (lattice_nodes).
 void build_items(const HostTree& t, int chunk, HostPlan& p);
 
 }  // namespace otfmm
