@@ -140,6 +140,7 @@ DevTree dev_tree(const ot_tree* t) {
     d.level_first = t->d_level_first;
     d.mom64 = t->d_mom64;
     d.mom32 = t->d_mom32;
+    d.inv_side8 = 8.0 / t->h.size;
     d.loc = t->d_loc;
     d.status = t->d_status;
     return d;

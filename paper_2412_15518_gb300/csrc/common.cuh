@@ -8,7 +8,9 @@
 //                                        + i + 8 j + 64 k
 //   moments       20 components: m, dX(3), M2(6), M3(10) in units of the cell's
 //                 own side h (dX = centre of mass - cell centre, M2 / h^2,
-//                 M3 / h^3), FP64 and an FP32 copy
+//                 M3 / h^3); FP64 structure of arrays [20][n_cells], and an
+//                 FP32 copy as an array of 80-byte records [n_cells][20] (one
+//                 source cell = five 16-byte loads)
 //   expansions    23 components: L0, L1(3), L2(6), L3(10), ac(3), physical
 //                 units, FP64
 // Packed symmetric index orders: M2/L2 = xx xy xz yy yz zz;
@@ -43,7 +45,8 @@ struct DevTree {
     const int* nbr;             // [n_nodes][27] neighbour node or -1
     const int* level_first;     // [n_levels + 1] first node of each level
     double* mom64;              // [20][n_cells]
-    float* mom32;               // [20][n_cells]
+    float* mom32;               // [n_cells][20]
+    double inv_side8;           // 8 / size: 1/h at level 0
     double* loc;                // [23][n_cells]
     int* status;                // device status word
 };

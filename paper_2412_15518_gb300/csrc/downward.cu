@@ -30,6 +30,7 @@ __global__ void __launch_bounds__(64) k_l2l(DevTree t, int first, const double* 
     const long long N = t.n_cells;
     const double h = t.size / (double)(8 << L);
     const int* xyz = t.node_xyz + 3 * node;
+    if (leaf >= 0 && parent >= 0) return;  // leaf cells of level >= 1: k_l2l_leafkids
     {
         const int c = ((blockIdx.x & 7) << 6) + threadIdx.x;
         const int ci[3] = {c & 7, (c >> 3) & 7, c >> 6};
@@ -107,12 +108,140 @@ __global__ void __launch_bounds__(64) k_l2l(DevTree t, int first, const double* 
     }
 }
 
+// Packed index of (i, j, k) in a symmetric rank-3 tensor.
+__device__ __forceinline__ int pk3(int i, int j, int k) {
+    if (i > j) { const int s = i; i = j; j = s; }
+    if (j > k) { const int s = j; j = k; k = s; }
+    if (i > j) { const int s = i; i = j; j = s; }
+    return i == 0 ? (j == 0 ? k : (j == 1 ? 2 + k : 5)) : (i == 1 ? (j == 1 ? 5 + k : 8) : 9);
+}
+
+// Values at the 8 corners s in {-1, 1}^3 (index bits x = 1, y = 2, z = 4, bit
+// set means s = +1) of v(s) = sum_q c_q prod_{axes in q} s_axis, in place.
+__device__ __forceinline__ void corners8(double* c) {
+#pragma unroll
+    for (int bit = 1; bit < 8; bit <<= 1)
+#pragma unroll
+        for (int q = 0; q < 8; q++)
+            if (!(q & bit)) {
+                const double u = c[q], v = c[q | bit];
+                c[q] = u - v;
+                c[q | bit] = u + v;
+            }
+}
+
+// Downward pass into leaf children: one thread per parent cell whose 8
+// children are leaf cells.  The parent's expansion is shifted once to the
+// parent cell centre (coefficients A); the children sit at e = eps s with
+// eps = h/4 and s in {-1, 1}^3, so the degree-3 polynomial and its gradient
+// at the 8 children are sums of a few coefficients with sign patterns:
+//   phi(s) = A0 + eps A1.s + eps^2 s.A2.s / 2 + eps^3 A3:sss / 6
+//   grad(s) = A1 + eps A2 s + eps^2 A3:ss / 2
+// evaluated as 8-point sign transforms.  Each child adds its own-level
+// terms (L0, L1, a_c) and the parent's correction acceleration.
+__global__ void __launch_bounds__(256) k_l2l_leafkids(DevTree t, int first,
+                                                      const double* __restrict__ rho,
+                                                      double* __restrict__ phi,
+                                                      double* __restrict__ g, double G,
+                                                      int self_term) {
+    const int node = first + (blockIdx.x >> 1);
+    const int child0 = t.node_child[node];
+    if (child0 < 0) return;
+    const long long N = t.n_cells;
+    const int c = ((blockIdx.x & 1) << 8) + threadIdx.x;
+    const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
+    const int cn = child0 + (i >> 2) + 2 * (j >> 2) + 4 * (k >> 2);
+    const int leaf = t.node_leaf[cn];
+    if (leaf < 0) return;  // interior children: k_l2l at the next level
+    const int L = t.node_level[node];
+    const double h = t.size / (double)(8 << L);
+    const long long pcell = (long long)node * kCells + c;
+    double P[kLoc];
+#pragma unroll
+    for (int r = 0; r < kLoc; r++) P[r] = t.loc[r * N + pcell];
+    // shift from the parent's centre of mass to its cell centre
+    const double x = -h * t.mom64[N + pcell], y = -h * t.mom64[2 * N + pcell],
+                 z = -h * t.mom64[3 * N + pcell];
+    const double* L2 = P + 4;
+    const double* L3 = P + 10;
+    const double A2x = fma(L2[0], x, fma(L2[1], y, L2[2] * z));
+    const double A2y = fma(L2[1], x, fma(L2[3], y, L2[4] * z));
+    const double A2z = fma(L2[2], x, fma(L2[4], y, L2[5] * z));
+    const double xx = x * x, yy = y * y, zz = z * z, xy2 = 2 * x * y, xz2 = 2 * x * z, yz2 = 2 * y * z;
+    const double B3x = fma(L3[0], xx, fma(L3[3], yy, fma(L3[5], zz, fma(L3[1], xy2, fma(L3[2], xz2, L3[4] * yz2)))));
+    const double B3y = fma(L3[1], xx, fma(L3[6], yy, fma(L3[8], zz, fma(L3[3], xy2, fma(L3[4], xz2, L3[7] * yz2)))));
+    const double B3z = fma(L3[2], xx, fma(L3[7], yy, fma(L3[9], zz, fma(L3[4], xy2, fma(L3[5], xz2, L3[8] * yz2)))));
+    double A[20];
+    A[0] = P[0] + fma(P[1], x, fma(P[2], y, P[3] * z)) + 0.5 * fma(A2x, x, fma(A2y, y, A2z * z)) +
+           (1.0 / 6.0) * fma(B3x, x, fma(B3y, y, B3z * z));
+    A[1] = P[1] + A2x + 0.5 * B3x;
+    A[2] = P[2] + A2y + 0.5 * B3y;
+    A[3] = P[3] + A2z + 0.5 * B3z;
+    A[4] = L2[0] + fma(L3[0], x, fma(L3[1], y, L3[2] * z));
+    A[5] = L2[1] + fma(L3[1], x, fma(L3[3], y, L3[4] * z));
+    A[6] = L2[2] + fma(L3[2], x, fma(L3[4], y, L3[5] * z));
+    A[7] = L2[3] + fma(L3[3], x, fma(L3[6], y, L3[7] * z));
+    A[8] = L2[4] + fma(L3[4], x, fma(L3[7], y, L3[8] * z));
+    A[9] = L2[5] + fma(L3[5], x, fma(L3[8], y, L3[9] * z));
+#pragma unroll
+    for (int r = 0; r < 10; r++) A[10 + r] = L3[r];
+    const double* A2 = A + 4;
+    const double* A3 = A + 10;
+    const double e1 = 0.25 * h, e2 = e1 * e1, e3 = e2 * e1;
+    // potential: sign-pattern coefficients, then the 8 corner values
+    double cp[8];
+    cp[0] = A[0] + 0.5 * e2 * (A2[0] + A2[3] + A2[5]);
+    cp[1] = e1 * A[1] + (e3 / 6.0) * (A3[0] + 3.0 * (A3[3] + A3[5]));
+    cp[2] = e1 * A[2] + (e3 / 6.0) * (A3[6] + 3.0 * (A3[1] + A3[8]));
+    cp[4] = e1 * A[3] + (e3 / 6.0) * (A3[9] + 3.0 * (A3[2] + A3[7]));
+    cp[3] = e2 * A2[1];
+    cp[5] = e2 * A2[2];
+    cp[6] = e2 * A2[4];
+    cp[7] = e3 * A3[4];
+    corners8(cp);
+    // gradient, one component at a time
+    double cg[3][8];
+#pragma unroll
+    for (int p = 0; p < 3; p++) {
+        const int pa = p == 0 ? 0 : (p == 1 ? 1 : 2);  // packed (p, x)
+        const int pb = p == 0 ? 1 : (p == 1 ? 3 : 4);  // packed (p, y)
+        const int pc = p == 0 ? 2 : (p == 1 ? 4 : 5);  // packed (p, z)
+        double* v = cg[p];
+        v[0] = A[1 + p] + 0.5 * e2 * (A3[pk3(p, 0, 0)] + A3[pk3(p, 1, 1)] + A3[pk3(p, 2, 2)]);
+        v[1] = e1 * A2[pa];
+        v[2] = e1 * A2[pb];
+        v[4] = e1 * A2[pc];
+        v[3] = e2 * A3[pk3(p, 0, 1)];
+        v[5] = e2 * A3[pk3(p, 0, 2)];
+        v[6] = e2 * A3[pk3(p, 1, 2)];
+        v[7] = 0.0;
+        corners8(v);
+    }
+    const double hc = 0.5 * h;
+    const double selfc = self_term ? -G * hc * hc * cube_self_constant() : 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+        const int cl = 2 * (i & 3) + (q & 1) + 8 * (2 * (j & 3) + ((q >> 1) & 1)) + 64 * (2 * (k & 3) + (q >> 2));
+        const long long cc = (long long)cn * kCells + cl;
+        const long long o = (long long)leaf * kCells + cl;
+        double pv = t.loc[cc] + cp[q];
+        if (self_term) pv += selfc * rho[o];
+        phi[o] = pv;
+#pragma unroll
+        for (int p = 0; p < 3; p++)
+            g[((long long)leaf * 3 + p) * kCells + cl] =
+                -(t.loc[(1 + p) * N + cc] + cg[p][q]) + t.loc[(20 + p) * N + cc] + P[20 + p];
+    }
+}
+
 }  // namespace
 
 void launch_l2l(const DevTree& t, int level, int first, int count, const double* rho,
                 double* phi, double* g, double G, int self_term, cudaStream_t s) {
     (void)level;
-    if (count > 0) k_l2l<<<count * 8, 64, 0, s>>>(t, first, rho, phi, g, G, self_term);
+    if (count <= 0) return;
+    k_l2l<<<count * 8, 64, 0, s>>>(t, first, rho, phi, g, G, self_term);
+    k_l2l_leafkids<<<count * 2, 256, 0, s>>>(t, first, rho, phi, g, G, self_term);
 }
 
 }  // namespace otfmm

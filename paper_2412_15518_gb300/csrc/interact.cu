@@ -27,9 +27,6 @@ namespace otfmm {
 
 namespace {
 
-template <class T> __device__ __forceinline__ const T* mom_of(const DevTree& t);
-template <> __device__ __forceinline__ const double* mom_of<double>(const DevTree& t) { return t.mom64; }
-template <> __device__ __forceinline__ const float* mom_of<float>(const DevTree& t) { return t.mom32; }
 
 __device__ __forceinline__ void tab_of(const DevPlan& p, int k, double& a, double& b, double& c,
                                        double& d) {
@@ -44,6 +41,45 @@ __device__ __forceinline__ void tab_of(const DevPlan& p, int k, float& a, float&
 
 constexpr int kMaxWarps = 16;
 
+// Source/target moment loads: FP64 from the structure of arrays, FP32 from
+// the 80-byte records (head = m, dX; tail = M2, M3).
+__device__ __forceinline__ void load_head(const DevTree& t, long long c, double& m, double& x,
+                                          double& y, double& z) {
+    const long long N = t.n_cells;
+    m = t.mom64[c];
+    x = t.mom64[N + c];
+    y = t.mom64[2 * N + c];
+    z = t.mom64[3 * N + c];
+}
+__device__ __forceinline__ void load_head(const DevTree& t, long long c, float& m, float& x,
+                                          float& y, float& z) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(t.mom32 + c * kMom));
+    m = v.x;
+    x = v.y;
+    y = v.z;
+    z = v.w;
+}
+__device__ __forceinline__ void load_tail(const DevTree& t, long long c, double* b2, double* b3) {
+    const long long N = t.n_cells;
+#pragma unroll
+    for (int r = 0; r < 6; r++) b2[r] = t.mom64[(4 + r) * N + c];
+#pragma unroll
+    for (int r = 0; r < 10; r++) b3[r] = t.mom64[(10 + r) * N + c];
+}
+__device__ __forceinline__ void load_tail(const DevTree& t, long long c, float* b2, float* b3) {
+    const float4* p = reinterpret_cast<const float4*>(t.mom32 + c * kMom);
+    const float4 v1 = __ldg(p + 1), v2 = __ldg(p + 2), v3 = __ldg(p + 3), v4 = __ldg(p + 4);
+    b2[0] = v1.x; b2[1] = v1.y; b2[2] = v1.z; b2[3] = v1.w; b2[4] = v2.x; b2[5] = v2.y;
+    b3[0] = v2.z; b3[1] = v2.w; b3[2] = v3.x; b3[3] = v3.y; b3[4] = v3.z; b3[5] = v3.w;
+    b3[6] = v4.x; b3[7] = v4.y; b3[8] = v4.z; b3[9] = v4.w;
+}
+
+// Scales a partial sum to physical units and widens it: the FP64 form
+// multiplies in FP64; the FP32 form multiplies in FP32 (one more rounding of
+// the same size as the sum's own) and converts once.
+__device__ __forceinline__ double scaled(double v, double s) { return s * v; }
+__device__ __forceinline__ double scaled(float v, double s) { return (double)(v * (float)s); }
+
 template <class T, bool FULL, bool AM>
 __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, const int4 it,
                                          const int lane, const int* s_nb, const int* s_lf,
@@ -55,13 +91,13 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
     const int k = 2 * (2 * half + (lane >> 4)) + (par >> 2);
     const long long N = t.n_cells;
     const long long cell = (long long)node * kCells + i + 8 * j + 64 * k;
-    const T* __restrict__ mom = mom_of<T>(t);
-    const T dax = mom[N + cell], day = mom[2 * N + cell], daz = mom[3 * N + cell];
+    T ma, dax, day, daz;
+    load_head(t, cell, ma, dax, day, daz);
     T inv_ma = T(0.0), a3[10], ta[3];
     if (FULL && AM) {
-        inv_ma = T(1.0 / t.mom64[cell]);
-#pragma unroll
-        for (int r = 0; r < 10; r++) a3[r] = mom[(10 + r) * N + cell];
+        T a2[6];
+        inv_ma = T(1.0) / ma;
+        load_tail(t, cell, a2, a3);
         ta[0] = a3[0] + a3[3] + a3[5];
         ta[1] = a3[1] + a3[6] + a3[8];
         ta[2] = a3[2] + a3[7] + a3[9];
@@ -94,7 +130,8 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
             } else {
                 T a, b, c, d;
                 tab_of(p, base + q, a, b, c, d);
-                const T m = mom[sc];
+                T m, u0, u1, u2;
+                load_head(t, sc, m, u0, u1, u2);
                 A.L0 = fma_(m, a, A.L0);
                 A.L1[0] = fma_(m, b, A.L1[0]);
                 A.L1[1] = fma_(m, c, A.L1[1]);
@@ -103,48 +140,46 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
             continue;
         }
         if (FULL && !sleaf && entry_near(e)) continue;  // resolved at the next level
+        T m, bx, by, bz;
+        load_head(t, sc, m, bx, by, bz);
         // R' = X_A - X_B in cell units: the source sits at offset d from the target
-        const T x = (dax - mom[N + sc]) - T(dx);
-        const T y = (day - mom[2 * N + sc]) - T(dy);
-        const T z = (daz - mom[3 * N + sc]) - T(dz);
-        const T m = mom[sc];
+        const T x = (dax - bx) - T(dx);
+        const T y = (day - by) - T(dy);
+        const T z = (daz - bz) - T(dz);
         if (sleaf) {
             m2l_pair<T, FULL, false, AM>(x, y, z, m, nullptr, nullptr, m * inv_ma, a3, ta, A);
         } else {
             T b2[6], b3[10];
-#pragma unroll
-            for (int r = 0; r < 6; r++) b2[r] = mom[(4 + r) * N + sc];
-#pragma unroll
-            for (int r = 0; r < 10; r++) b3[r] = mom[(10 + r) * N + sc];
+            load_tail(t, sc, b2, b3);
             m2l_pair<T, FULL, true, AM>(x, y, z, m, b2, b3, m * inv_ma, a3, ta, A);
         }
     }
     // scale to physical units: L^(n) * (-G h^-(n+1)), correction * -(G/6) h^-2
-    const double hi = (double)(8 << L) / t.size;
+    const double hi = t.inv_side8 * (double)(1 << L);
     const double s1 = -G * hi, s2 = s1 * hi, s3 = s2 * hi, s4 = s3 * hi;
     double* loc = t.loc;
-    atomicAdd(loc + cell, s1 * ((double)A.L0 + n0));
-    atomicAdd(loc + N + cell, s2 * ((double)A.L1[0] + n1));
-    atomicAdd(loc + 2 * N + cell, s2 * ((double)A.L1[1] + n2));
-    atomicAdd(loc + 3 * N + cell, s2 * ((double)A.L1[2] + n3));
+    atomicAdd(loc + cell, scaled(A.L0, s1) + s1 * n0);
+    atomicAdd(loc + N + cell, scaled(A.L1[0], s2) + s2 * n1);
+    atomicAdd(loc + 2 * N + cell, scaled(A.L1[1], s2) + s2 * n2);
+    atomicAdd(loc + 3 * N + cell, scaled(A.L1[2], s2) + s2 * n3);
     if (FULL) {
-        const double d1 = (double)A.d1;
-        atomicAdd(loc + 4 * N + cell, s3 * ((double)A.L2[0] + d1));
-        atomicAdd(loc + 5 * N + cell, s3 * (double)A.L2[1]);
-        atomicAdd(loc + 6 * N + cell, s3 * (double)A.L2[2]);
-        atomicAdd(loc + 7 * N + cell, s3 * ((double)A.L2[3] + d1));
-        atomicAdd(loc + 8 * N + cell, s3 * (double)A.L2[4]);
-        atomicAdd(loc + 9 * N + cell, s3 * ((double)A.L2[5] + d1));
-        const double Vx = (double)A.V[0], Vy = (double)A.V[1], Vz = (double)A.V[2];
+        const T d1 = A.d1;
+        atomicAdd(loc + 4 * N + cell, scaled(A.L2[0] + d1, s3));
+        atomicAdd(loc + 5 * N + cell, scaled(A.L2[1], s3));
+        atomicAdd(loc + 6 * N + cell, scaled(A.L2[2], s3));
+        atomicAdd(loc + 7 * N + cell, scaled(A.L2[3] + d1, s3));
+        atomicAdd(loc + 8 * N + cell, scaled(A.L2[4], s3));
+        atomicAdd(loc + 9 * N + cell, scaled(A.L2[5] + d1, s3));
+        const T Vx = A.V[0], Vy = A.V[1], Vz = A.V[2];
         // Kronecker part of L3: delta_ij V_k + delta_ik V_j + delta_jk V_i
-        const double k3[10] = {3 * Vx, Vy, Vz, Vx, 0.0, Vx, 3 * Vy, Vz, Vy, 3 * Vz};
+        const T k3[10] = {T(3.0) * Vx, Vy, Vz, Vx, T(0.0), Vx, T(3.0) * Vy, Vz, Vy, T(3.0) * Vz};
 #pragma unroll
-        for (int r = 0; r < 10; r++) atomicAdd(loc + (10 + r) * N + cell, s4 * ((double)A.L3[r] + k3[r]));
+        for (int r = 0; r < 10; r++) atomicAdd(loc + (10 + r) * N + cell, scaled(A.L3[r] + k3[r], s4));
     }
     if (AM) {
         const double sa = -(G / 6.0) * hi * hi;
 #pragma unroll
-        for (int a = 0; a < 3; a++) atomicAdd(loc + (20 + a) * N + cell, sa * (double)A.S[a]);
+        for (int a = 0; a < 3; a++) atomicAdd(loc + (20 + a) * N + cell, scaled(A.S[a], sa));
     }
 }
 

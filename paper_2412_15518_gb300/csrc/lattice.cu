@@ -28,20 +28,25 @@ template <> __device__ __forceinline__ const double* lat_mom<double>(const DevTr
 template <> __device__ __forceinline__ const float* lat_mom<float>(const DevTree& t) { return t.mom32; }
 
 // Fills a parity-split halo of width w with the masses of the leaf cells
-// around `node` (zero where there is no leaf cell at this level).
+// around `node` (zero where there is no leaf cell at this level): one warp
+// per row of the halo, lanes along x.  `stride` is the distance between two
+// cells' masses in `mass` (1 for the FP64 arrays, 20 for the FP32 records).
 template <class T>
 __device__ __forceinline__ void fill_halo(const DevTree& t, int node, int w, T* halo,
-                                          const T* __restrict__ mass) {
+                                          const T* __restrict__ mass, int stride) {
     const int hw = 8 + 2 * w;
-    const int total = hw * hw * hw;
     const int* nbr = t.nbr + (long long)node * 27;
-    for (int u = threadIdx.x; u < total; u += blockDim.x) {
-        const int x = u % hw - w, y = (u / hw) % hw - w, z = u / (hw * hw) - w;
+    const int lane = threadIdx.x & 31;
+    const int nwarp = blockDim.x >> 5;
+    for (int row = threadIdx.x >> 5; row < hw * hw; row += nwarp) {
+        const int y = row % hw - w, z = row / hw - w;
+        const int x = lane - w;
+        if (lane >= hw) continue;
         const int slot = ((x >> 3) + 1) + 3 * ((y >> 3) + 1) + 9 * ((z >> 3) + 1);
         const int nb = __ldg(nbr + slot);
         T v = T(0.0);
         if (nb >= 0 && __ldg(t.node_leaf + nb) >= 0)
-            v = mass[(long long)nb * kCells + (x & 7) + 8 * (y & 7) + 64 * (z & 7)];
+            v = mass[((long long)nb * kCells + (x & 7) + 8 * (y & 7) + 64 * (z & 7)) * stride];
         halo[halo_index(x, y, z, w)] = v;
     }
 }
@@ -53,8 +58,8 @@ __global__ void __launch_bounds__(256) k_lattice(DevTree t, DevPlan p, DevLattic
     const int wf = lp.w_far, wn = lp.w_near;
     T* hfar = reinterpret_cast<T*>(smem);
     double* hnear = reinterpret_cast<double*>(smem + sizeof(T) * 8 * halo_sub(wf));
-    fill_halo<T>(t, node, wf, hfar, lat_mom<T>(t));
-    if (sizeof(T) == 4) fill_halo<double>(t, node, wn, hnear, t.mom64);
+    fill_halo<T>(t, node, wf, hfar, lat_mom<T>(t), sizeof(T) == 4 ? kMom : 1);
+    if (sizeof(T) == 4) fill_halo<double>(t, node, wn, hnear, t.mom64, 1);
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
@@ -106,7 +111,7 @@ __global__ void __launch_bounds__(256) k_lattice(DevTree t, DevPlan p, DevLattic
     }
     // to physical units: L0 * (-G / h), L1 * (-G / h^2)
     const int L = t.node_level[node];
-    const double hi = (double)(8 << L) / t.size;
+    const double hi = t.inv_side8 * (double)(1 << L);
     const double s1 = -G * hi, s2 = s1 * hi;
     const long long N = t.n_cells;
     const long long c1 = (long long)node * kCells + (2 * a + px) + 8 * (2 * b + py) + 64 * (2 * c + pz);

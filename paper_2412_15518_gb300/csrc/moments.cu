@@ -8,11 +8,14 @@
 // FP32-bulk interaction form.  Both kernels also zero the expansions of their
 // cells, which the interaction kernels then accumulate into.
 //
-// M2M uses 8 threads per parent cell, one per child: the children's masses
+// M2M of cells with interior children uses 8 threads per parent cell, one
+// per child: the children's masses
 // and mass-weighted positions are summed by warp shuffles, every lane forms
 // its child's contribution about the common centre of mass, and a second
 // shuffle reduction sums them.  So the coarse levels (1 node at level 0,
-// 8 at level 1) still spread over many SMs of the FP64 pipe.
+// 8 at level 1) still spread over many SMs of the FP64 pipe.  Cells whose
+// children are leaves (the most numerous) take a cheaper path: their children
+// sit at fixed offsets, so the moments are signed sums of 8 masses.
 #include "kernels.hpp"
 
 namespace otfmm {
@@ -31,7 +34,7 @@ __global__ void __launch_bounds__(256) k_leaf_moments(DevTree t, const int* __re
         const double m = rho[(long long)leaf * kCells + c] * h3;
         const long long cell = (long long)node * kCells + c;
         t.mom64[cell] = m;
-        t.mom32[cell] = (float)m;
+        t.mom32[cell * kMom] = (float)m;
         // a leaf cell's expansion: L0, L1 and the correction acceleration
         t.loc[cell] = 0.0;
         t.loc[N + cell] = 0.0;
@@ -62,7 +65,9 @@ __device__ __forceinline__ double sum8(double v) {
     return v;
 }
 
-// 256 threads = 32 parent cells x 8 children; 16 blocks per node.
+// 256 threads = 32 parent cells x 8 children; 16 blocks per node.  Cells
+// whose children are leaf cells are left to k_m2m_leafkids.  The 4 cells of a
+// warp share one child node, so that test is uniform per warp.
 __global__ void __launch_bounds__(256) k_m2m(DevTree t, int first) {
     const int node = first + (blockIdx.x >> 4);
     const int child0 = t.node_child[node];
@@ -74,7 +79,7 @@ __global__ void __launch_bounds__(256) k_m2m(DevTree t, int first) {
     const int a = q & 1, b = (q >> 1) & 1, e = q >> 2;
     // the 8 children of cell (i, j, k) lie in child node (i>>2, j>>2, k>>2)
     const int cn = child0 + (i >> 2) + 2 * (j >> 2) + 4 * (k >> 2);
-    const bool cleaf = t.node_child[cn] < 0;
+    if (t.node_child[cn] < 0) return;  // leaf children: k_m2m_leafkids
     const long long cc = (long long)cn * kCells + (2 * (i & 3) + a) + 8 * (2 * (j & 3) + b) +
                          64 * (2 * (k & 3) + e);
     const double m = t.mom64[cc];
@@ -89,24 +94,16 @@ __global__ void __launch_bounds__(256) k_m2m(DevTree t, int first) {
     for (int s = 0; s < 3; s++) X[s] = sum8(m * pos[s]) / M;
     const double d[3] = {pos[0] - X[0], pos[1] - X[1], pos[2] - X[2]};
     double c2[6], S[16];
-    if (cleaf) {
 #pragma unroll
-        for (int r = 0; r < 6; r++) c2[r] = 0.0;
-    } else {
-#pragma unroll
-        for (int r = 0; r < 6; r++) c2[r] = 0.25 * t.mom64[(4 + r) * N + cc];  // child units -> parent
-    }
+    for (int r = 0; r < 6; r++) c2[r] = 0.25 * t.mom64[(4 + r) * N + cc];  // child units -> parent
     const double md[3] = {m * d[0], m * d[1], m * d[2]};
 #pragma unroll
     for (int r = 0; r < 6; r++) S[r] = c2[r] + md[c_i2[r]] * d[c_j2[r]];
 #pragma unroll
     for (int r = 0; r < 10; r++) {
         const int ii = c_t3[r][0], jj = c_t3[r][1], kk = c_t3[r][2];
-        double v = md[ii] * d[jj] * d[kk];
-        if (!cleaf)
-            v += 0.125 * t.mom64[(10 + r) * N + cc] + c2[p2(ii, jj)] * d[kk] + c2[p2(ii, kk)] * d[jj] +
-                 c2[p2(jj, kk)] * d[ii];
-        S[6 + r] = v;
+        S[6 + r] = md[ii] * d[jj] * d[kk] + 0.125 * t.mom64[(10 + r) * N + cc] +
+                   c2[p2(ii, jj)] * d[kk] + c2[p2(ii, kk)] * d[jj] + c2[p2(jj, kk)] * d[ii];
     }
 #pragma unroll
     for (int r = 0; r < 16; r++) S[r] = sum8(S[r]);
@@ -123,11 +120,85 @@ __global__ void __launch_bounds__(256) k_m2m(DevTree t, int first) {
     for (int r = 0; r < 20; r++) {
         if ((r & 7) == q) {
             t.mom64[r * N + cell] = vals[r];
-            t.mom32[r * N + cell] = (float)vals[r];
+            t.mom32[cell * kMom + r] = (float)vals[r];
         }
     }
 #pragma unroll
     for (int r = q; r < kLoc; r += 8) t.loc[r * N + cell] = 0.0;
+}
+
+// In-place Walsh transform of 8 values indexed by octant bits (x = bit 0):
+// on return w[q] = sum_k v[k] (-1)^popcount(q & k).
+__device__ __forceinline__ void walsh8(double* w) {
+#pragma unroll
+    for (int bit = 1; bit < 8; bit <<= 1)
+#pragma unroll
+        for (int q = 0; q < 8; q++)
+            if (!(q & bit)) {
+                const double u = w[q], v = w[q | bit];
+                w[q] = u + v;
+                w[q | bit] = u - v;
+            }
+}
+
+// M2M of a cell whose 8 children are leaf cells: point masses at offsets
+// s/4 (s in {-1, 1}^3, parent units) from the parent centre, with no offset
+// or higher moment of their own.  Their moments about the parent centre are
+// signed sums of the masses (a Walsh transform); the parallel-axis shift to
+// the centre of mass X gives
+//   M2 = P2 - M X X,   M3 = P3 - 3 sym(X P2) + 2 M X X X.
+// One thread per parent cell, 2 blocks of 256 per node.
+__global__ void __launch_bounds__(256) k_m2m_leafkids(DevTree t, int first) {
+    const int node = first + (blockIdx.x >> 1);
+    const int child0 = t.node_child[node];
+    if (child0 < 0) return;
+    const long long N = t.n_cells;
+    const int c = ((blockIdx.x & 1) << 8) + threadIdx.x;
+    const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
+    const int cn = child0 + (i >> 2) + 2 * (j >> 2) + 4 * (k >> 2);
+    if (t.node_child[cn] >= 0) return;  // interior children: k_m2m
+    const long long cbase = (long long)cn * kCells + 2 * (i & 3) + 16 * (j & 3) + 128 * (k & 3);
+    double w[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) w[q] = t.mom64[cbase + (q & 1) + 8 * ((q >> 1) & 1) + 64 * (q >> 2)];
+    walsh8(w);
+    // sums of m s_x, m s_y, ... (s = 2 bit - 1, so a bit set counts +)
+    const double M = w[0];
+    const double Sx = -w[1], Sy = -w[2], Sz = -w[4];
+    const double Sxy = w[3], Sxz = w[5], Syz = w[6], Sxyz = -w[7];
+    const double iM = 1.0 / M;
+    const double X[3] = {0.25 * Sx * iM, 0.25 * Sy * iM, 0.25 * Sz * iM};
+    // raw moments about the parent centre (packed xx xy xz yy yz zz, ...)
+    const double P2[6] = {0.0625 * M, 0.0625 * Sxy, 0.0625 * Sxz, 0.0625 * M, 0.0625 * Syz, 0.0625 * M};
+    const double s64 = 1.0 / 64.0;
+    const double P3[10] = {s64 * Sx, s64 * Sy, s64 * Sz, s64 * Sx, s64 * Sxyz,
+                           s64 * Sx, s64 * Sy, s64 * Sz, s64 * Sy, s64 * Sz};
+    double S2[6], S3[10];
+    const double MX[3] = {M * X[0], M * X[1], M * X[2]};
+#pragma unroll
+    for (int r = 0; r < 6; r++) S2[r] = P2[r] - MX[c_i2[r]] * X[c_j2[r]];
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        const int ii = c_t3[r][0], jj = c_t3[r][1], kk = c_t3[r][2];
+        S3[r] = P3[r] - (X[ii] * P2[p2(jj, kk)] + X[jj] * P2[p2(ii, kk)] + X[kk] * P2[p2(ii, jj)]) +
+                2.0 * MX[ii] * X[jj] * X[kk];
+    }
+    const long long cell = (long long)node * kCells + c;
+    float4* m32 = reinterpret_cast<float4*>(t.mom32 + cell * kMom);
+    t.mom64[cell] = M;
+#pragma unroll
+    for (int s = 0; s < 3; s++) t.mom64[(1 + s) * N + cell] = X[s];
+#pragma unroll
+    for (int r = 0; r < 6; r++) t.mom64[(4 + r) * N + cell] = S2[r];
+#pragma unroll
+    for (int r = 0; r < 10; r++) t.mom64[(10 + r) * N + cell] = S3[r];
+    m32[0] = make_float4((float)M, (float)X[0], (float)X[1], (float)X[2]);
+    m32[1] = make_float4((float)S2[0], (float)S2[1], (float)S2[2], (float)S2[3]);
+    m32[2] = make_float4((float)S2[4], (float)S2[5], (float)S3[0], (float)S3[1]);
+    m32[3] = make_float4((float)S3[2], (float)S3[3], (float)S3[4], (float)S3[5]);
+    m32[4] = make_float4((float)S3[6], (float)S3[7], (float)S3[8], (float)S3[9]);
+#pragma unroll
+    for (int r = 0; r < kLoc; r++) t.loc[r * N + cell] = 0.0;
 }
 
 }  // namespace
@@ -139,7 +210,9 @@ void launch_leaf_moments(const DevTree& t, const int* leaf_node, const double* r
 
 void launch_m2m(const DevTree& t, int level, int first, int count, cudaStream_t s) {
     (void)level;
-    if (count > 0) k_m2m<<<count * 16, 256, 0, s>>>(t, first);
+    if (count <= 0) return;
+    k_m2m<<<count * 16, 256, 0, s>>>(t, first);
+    k_m2m_leafkids<<<count * 2, 256, 0, s>>>(t, first);
 }
 
 }  // namespace otfmm

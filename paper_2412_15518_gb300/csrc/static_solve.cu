@@ -217,6 +217,7 @@ extern "C" int ot_solve_gravity_static(const ot_tree_desc* desc, const double* r
     d.level_first = (const int*)(base + l.level_first);
     d.mom64 = (double*)(base + l.mom64);
     d.mom32 = (float*)(base + l.mom32);
+    d.inv_side8 = 8.0 / h.size;
     d.loc = (double*)(base + l.loc);
     d.status = (int*)(base + l.status);
     DevPlan dp;
