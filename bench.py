@@ -63,7 +63,8 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_bulk"])
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the companion FP32-bulk run and the CPU baseline")
-    ap.add_argument("--autotune", action="store_true", help="autotune the persistent launch first")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the autotuner (default: tune the persistent launch before timing)")
     return ap.parse_args()
 
 
@@ -268,7 +269,7 @@ def run_ours(args):
     tree = fmm.Tree(leaves, device=local)
     rho = torch.from_numpy(rho_np).cuda()
     phi, g = tree.empty_outputs()
-    if args.autotune:
+    if not args.no_autotune:
         tree.autotune(rho, precision=prec)
     info = tree.info()
     n_int = info["n_m2l"] + info["n_p2p"] + info["n_seam"]
@@ -334,6 +335,8 @@ def run_ours(args):
             # the FP32-bulk form on the same workload, and its error against FP64
             ref_phi, ref_g = phi.clone(), g.clone()
             o32 = dict(precision=fmm.OT_PRECISION_FP32_BULK)
+            if not args.no_autotune:
+                tree.autotune(rho, precision=fmm.OT_PRECISION_FP32_BULK)
             time_steps(tree, rho, phi, g, o32, 3, flush)
             ms32, int32 = time_steps(tree, rho, phi, g, o32, args.steps, flush)
             torch.cuda.synchronize()
@@ -348,9 +351,30 @@ def run_ours(args):
                 "max_rel_err_vs_fp64": {"phi": ep, "g": eg},
                 "interact_ms": statistics.mean(int32),
                 "interact_fp32_tflops": a32, "frac_of_fp32_peak": a32 / PEAK_FP32_TFLOPS}
+            # the adjoint (FP64): dJ/drho for J = sum(w1 phi + w2 . g)
+            w1n, w2n = inputs.weights(leaves.shape[0])
+            w1, w2 = torch.from_numpy(w1n).cuda(), torch.from_numpy(w2n).cuda()
+            drho = torch.empty_like(rho)
+            for _ in range(2):
+                tree.backward(rho, w1, w2, drho)
+            torch.cuda.synchronize()
+            bms = []
+            for _ in range(args.steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                tree.backward(rho, w1, w2, drho)
+                e1.record(stream)
+                e1.synchronize()
+                bms.append(e0.elapsed_time(e1))
+            extra["adjoint_fp64"] = {"ms_per_step": sum(bms) / args.steps,
+                                     "includes": "forward solve + reverse sweep",
+                                     "ratio_to_forward": sum(bms) / sum(solve_ms)}
         extra["cpu_baseline"] = cpu_baseline(leaves, rho_np)
-    # leaf moments, M2M per interior level, lattice, interactions, L2L per level
-    launches = (1 + (info["n_levels"] - 1) + 2 + info["n_levels"]) * args.steps
+    # leaf moments, 2 M2M kernels per interior level, lattice, interactions,
+    # 2 L2L kernels per level
+    launches = (1 + 2 * (info["n_levels"] - 1) + 2 + 2 * info["n_levels"]) * args.steps
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,

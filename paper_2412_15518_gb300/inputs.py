@@ -82,34 +82,55 @@ def _covering_level(leafset: set, L: int, x: int, y: int, z: int) -> int:
     return L + 1
 
 
+def _code(x, y, z):
+    return x.astype(np.int64) | (y.astype(np.int64) << 20) | (z.astype(np.int64) << 40)
+
+
+def _decode(c):
+    m = (1 << 20) - 1
+    return c & m, (c >> 20) & m, (c >> 40) & m
+
+
 def balance(leaves) -> np.ndarray:
     """Refine leaves until every pair of face/edge/corner-adjacent leaves
-    differs by at most one level (2:1 balance)."""
-    leafset = set(map(tuple, np.asarray(leaves).tolist()))
+    differs by at most one level (2:1 balance): a leaf of level l that covers
+    a same-level neighbour position of a leaf of level L >= l + 2 is split,
+    until nothing changes (the minimal balanced refinement)."""
+    leaves = np.asarray(leaves, dtype=np.int64)
+    lmax = int(leaves[:, 0].max())
+    levels = {L: np.unique(_code(*leaves[leaves[:, 0] == L, 1:4].T)) for L in range(lmax + 1)}
+    offs = np.array([(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+                     if (dx, dy, dz) != (0, 0, 0)], dtype=np.int64)
     changed = True
     while changed:
         changed = False
-        for (L, x, y, z) in sorted(leafset, key=lambda t: -t[0]):
-            if (L, x, y, z) not in leafset:
+        for L in range(lmax, 1, -1):
+            if levels[L].size == 0:
                 continue
+            x, y, z = _decode(levels[L])
             n = 1 << L
-            for dz in (-1, 0, 1):
-                for dy in (-1, 0, 1):
-                    for dx in (-1, 0, 1):
-                        qx, qy, qz = x + dx, y + dy, z + dz
-                        if (dx | dy | dz) == 0 or min(qx, qy, qz) < 0 or max(qx, qy, qz) >= n:
-                            continue
-                        cl = _covering_level(leafset, L, qx, qy, qz)
-                        if cl < L - 1:
-                            s = L - cl
-                            cx, cy, cz = qx >> s, qy >> s, qz >> s
-                            leafset.discard((cl, cx, cy, cz))
-                            for c in range(8):
-                                leafset.add((cl + 1, 2 * cx + (c & 1), 2 * cy + ((c >> 1) & 1),
-                                             2 * cz + (c >> 2)))
-                            changed = True
-    out = np.array(sorted(leafset), dtype=np.int32)
-    return np.ascontiguousarray(out)
+            q = np.stack([x, y, z], 1)[:, None, :] + offs[None]
+            q = q.reshape(-1, 3)
+            q = q[np.all((q >= 0) & (q < n), 1)]
+            for l in range(L - 2, -1, -1):
+                s = L - l
+                cand = np.unique(_code(q[:, 0] >> s, q[:, 1] >> s, q[:, 2] >> s))
+                hit = cand[np.isin(cand, levels[l], assume_unique=True)]
+                if hit.size == 0:
+                    continue
+                changed = True
+                levels[l] = np.setdiff1d(levels[l], hit, assume_unique=True)
+                hx, hy, hz = _decode(hit)
+                kids = [_code(2 * hx + (c & 1), 2 * hy + ((c >> 1) & 1), 2 * hz + (c >> 2))
+                        for c in range(8)]
+                levels[l + 1] = np.union1d(levels[l + 1], np.concatenate(kids))
+    out = []
+    for L in range(lmax + 1):
+        x, y, z = _decode(levels[L])
+        out.append(np.stack([np.full(x.size, L), x, y, z], 1))
+    out = np.concatenate(out).astype(np.int32)
+    order = np.lexsort((out[:, 3], out[:, 2], out[:, 1], out[:, 0]))
+    return np.ascontiguousarray(out[order])
 
 
 def is_balanced(leaves) -> bool:

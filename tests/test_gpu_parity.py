@@ -203,3 +203,35 @@ def test_error_codes(fmm):
     torch.cuda.synchronize()
     assert tree.info()["device_status"] == 0
     tree.close()
+
+
+def test_amr8_full_size_sampled(fmm):
+    """The level-8 AMR binary (43,240 leaves, 22.1M cells) at full size, in the
+    launch configuration the benchmark times: both forms on the GPU, the
+    oracle on 2,000 seeded leaf cells (and the expansions of their
+    ancestors); momentum and torque residuals over every cell."""
+    lv, rho = I.workload("binary_amr8")
+    rng = np.random.default_rng(12)
+    sample = rng.choice(lv.shape[0] * 512, size=2000, replace=False)
+    phi_s, g_s = O.solve_sample(lv, rho, sample)
+    tree = fmm.Tree(lv)
+    r = torch.from_numpy(rho).cuda()
+    for prec, tol in ((fmm.OT_PRECISION_FP64, TOL64), (fmm.OT_PRECISION_FP32_BULK, TOL32)):
+        tree.autotune(r, precision=prec)
+        phi, g = tree.solve(r, precision=prec)
+        torch.cuda.synchronize()
+        assert rel(phi.view(-1)[torch.from_numpy(sample).cuda()].cpu().numpy(), phi_s) < tol, prec
+        gs = g.permute(0, 2, 1).reshape(-1, 3)[torch.from_numpy(sample).cuda()].cpu().numpy()
+        assert rel(gs, g_s) < tol, prec
+        if prec == fmm.OT_PRECISION_FP64:
+            h = torch.from_numpy(1.0 / (8.0 * 2.0 ** lv[:, 0])).cuda()
+            m = r * (h ** 3)[:, None]
+            f = m[:, None, :] * g                                   # [n, 3, 512]
+            x = torch.from_numpy(I.cell_centres(lv) - 0.5).cuda()   # [n, 512, 3]
+            mom = (f.sum((0, 2)).abs().max() / f.abs().sum()).item()
+            fx = f.permute(0, 2, 1)
+            tq = torch.cross(x, fx, dim=2)
+            ang = (tq.sum((0, 1)).abs().max() / tq.abs().sum()).item()
+            print(f"amr8 residuals: momentum {mom:.2e}, torque {ang:.2e}")
+            assert mom < 1e-13 and ang < 1e-11
+    tree.close()
