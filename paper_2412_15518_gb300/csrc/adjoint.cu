@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
         PairAdjOut acc;
         adj_zero(acc);
         double Xs[3] = {0.0, 0.0, 0.0};  // signed position adjoint of this cell
-        double lat = 0.0;                // lattice pairs: dJ/dm of this leaf cell
+        double lat0 = 0.0, lat1 = 0.0;   // lattice pairs: dJ/dm of this leaf cell (h, h^2 parts)
         const int base = p.list_first[item_list(it)];
 #pragma unroll 1
         for (int q = it.z; q < it.w; q++) {
@@ -236,8 +236,8 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
             if (cleaf && pleaf) {
                 // transposed lattice pair: this cell is the source of P's point-mass pair
                 const double2 t0 = __ldg(p.tab64 + 2 * (base + q)), t1 = __ldg(p.tab64 + 2 * (base + q) + 1);
-                lat += locbar[pc] * t0.x / h -
-                       (locbar[N + pc] * t0.y + locbar[2 * N + pc] * t1.x + locbar[3 * N + pc] * t1.y) / h2;
+                lat0 = fma(locbar[pc], t0.x, lat0);
+                lat1 = fma(locbar[N + pc], t0.y, fma(locbar[2 * N + pc], t1.x, fma(locbar[3 * N + pc], t1.y, lat1)));
                 continue;
             }
             if (!cleaf && !pleaf && entry_near(e)) continue;
@@ -295,7 +295,8 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
                 for (int s = 0; s < 3; s++) Xs[s] += o.R[s];
             }
         }
-        atomicAdd(mombar + cell, acc.mB + acc.mA - G * lat);
+        const double hi = 1.0 / h;
+        atomicAdd(mombar + cell, acc.mB + acc.mA - G * (lat0 * hi - lat1 * hi * hi));
         if (!cleaf) {
 #pragma unroll
             for (int s = 0; s < 3; s++) atomicAdd(mombar + (1 + s) * N + cell, Xs[s]);

@@ -85,6 +85,8 @@ struct ot_tree {
     bool tuned = false;
     // graphs
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t side_stream = nullptr;      // second branch: the lattice kernel
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::vector<GraphEntry> graphs;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // solve start, interact start/end, solve end
     int64_t workspace_bytes = 0;
@@ -269,12 +271,20 @@ void enqueue_moments(ot_tree* t, const double* rho, cudaStream_t s) {
 // Enqueues the interaction launch (expansions zeroed first).
 int enqueue_interact(ot_tree* t, const ot_solve_opts& o, cudaStream_t s) {
     DevTree d = dev_tree(t);
-    // the expansions were zeroed by the upward pass (leaf and M2M kernels)
+    // the expansions were zeroed by the upward pass (leaf and M2M kernels).
+    // The lattice kernel (leaf-leaf pairs) and the general kernel (pairs with
+    // an interior cell) only add into the expansions with atomics, so they
+    // run as two concurrent branches: in the bulk form one is mostly FP64 and
+    // the other mostly FP32 work, and the two pipes overlap.
+    TRYC(cudaEventRecord(t->ev_fork, s));
+    TRYC(cudaStreamWaitEvent(t->side_stream, t->ev_fork, 0));
+    launch_lattice(d, dev_plan(t), dev_lattice(t), o.precision, o.G, t->side_stream);
+    TRYC(cudaEventRecord(t->ev_join, t->side_stream));
     TRYC(cudaMemsetAsync(t->d_counter, 0, sizeof(int), s));
-    launch_lattice(d, dev_plan(t), dev_lattice(t), o.precision, o.G, s);
     int ctas = std::max(1, t->num_sms * t->ctas_per_sm);
     launch_interact(d, dev_plan(t), o.precision, o.G, o.am_correction ? 1 : 0, ctas,
                     t->warps_per_cta, s);
+    TRYC(cudaStreamWaitEvent(s, t->ev_join, 0));
     TRYC(cudaGetLastError());
     return OT_OK;
 }
@@ -408,6 +418,9 @@ int ot_build_tree(const ot_tree_desc* desc, int device, ot_tree** out) {
         cudaMemset(t->d_mom32, 0, sizeof(float) * kMom * C) != cudaSuccess ||
         cudaMemset(t->d_status, 0, sizeof(int)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&t->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&t->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&t->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&t->ev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreate(&t->ev[0]) != cudaSuccess || cudaEventCreate(&t->ev[1]) != cudaSuccess ||
         cudaEventCreate(&t->ev[2]) != cudaSuccess || cudaEventCreate(&t->ev[3]) != cudaSuccess) {
         cudaGetLastError();
@@ -426,6 +439,9 @@ void ot_destroy_tree(ot_tree* t) {
         DeviceGuard guard(t->device);
         destroy_graphs(t);
         if (t->cap_stream) cudaStreamDestroy(t->cap_stream);
+        if (t->side_stream) cudaStreamDestroy(t->side_stream);
+        if (t->ev_fork) cudaEventDestroy(t->ev_fork);
+        if (t->ev_join) cudaEventDestroy(t->ev_join);
         for (cudaEvent_t e : t->ev)
             if (e) cudaEventDestroy(e);
         void* ptrs[] = {t->d_level, t->d_leaf, t->d_parent, t->d_child, t->d_xyz, t->d_nbr,

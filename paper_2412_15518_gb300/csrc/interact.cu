@@ -75,10 +75,10 @@ __device__ __forceinline__ void load_tail(const DevTree& t, long long c, float* 
 }
 
 // Scales a partial sum to physical units and widens it: the FP64 form
-// multiplies in FP64; the FP32 form multiplies in FP32 (one more rounding of
-// the same size as the sum's own) and converts once.
+// multiplies in FP64; the FP32 form multiplies by the scale rounded to FP32
+// (one more rounding of the size of the sum's own) and converts once.
 __device__ __forceinline__ double scaled(double v, double s) { return s * v; }
-__device__ __forceinline__ double scaled(float v, double s) { return (double)(v * (float)s); }
+__device__ __forceinline__ double scaled(float v, float s) { return (double)(v * s); }
 
 template <class T, bool FULL, bool AM>
 __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, const int4 it,
@@ -156,12 +156,14 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
     }
     // scale to physical units: L^(n) * (-G h^-(n+1)), correction * -(G/6) h^-2
     const double hi = t.inv_side8 * (double)(1 << L);
-    const double s1 = -G * hi, s2 = s1 * hi, s3 = s2 * hi, s4 = s3 * hi;
+    const double s1d = -G * hi, s2d = s1d * hi;
+    // scale factors in the accumulators' type (converted once per item)
+    const T s1 = T(s1d), s2 = T(s2d), s3 = T(s2d * hi), s4 = T(s2d * hi * hi);
     double* loc = t.loc;
-    atomicAdd(loc + cell, scaled(A.L0, s1) + s1 * n0);
-    atomicAdd(loc + N + cell, scaled(A.L1[0], s2) + s2 * n1);
-    atomicAdd(loc + 2 * N + cell, scaled(A.L1[1], s2) + s2 * n2);
-    atomicAdd(loc + 3 * N + cell, scaled(A.L1[2], s2) + s2 * n3);
+    atomicAdd(loc + cell, scaled(A.L0, s1) + s1d * n0);
+    atomicAdd(loc + N + cell, scaled(A.L1[0], s2) + s2d * n1);
+    atomicAdd(loc + 2 * N + cell, scaled(A.L1[1], s2) + s2d * n2);
+    atomicAdd(loc + 3 * N + cell, scaled(A.L1[2], s2) + s2d * n3);
     if (FULL) {
         const T d1 = A.d1;
         atomicAdd(loc + 4 * N + cell, scaled(A.L2[0] + d1, s3));
@@ -177,7 +179,7 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
         for (int r = 0; r < 10; r++) atomicAdd(loc + (10 + r) * N + cell, scaled(A.L3[r] + k3[r], s4));
     }
     if (AM) {
-        const double sa = -(G / 6.0) * hi * hi;
+        const T sa = T(-(G / 6.0) * hi * hi);
 #pragma unroll
         for (int a = 0; a < 3; a++) atomicAdd(loc + (20 + a) * N + cell, scaled(A.S[a], sa));
     }

@@ -13,7 +13,8 @@
 // around it are staged once in shared memory (parity-split, padded so a warp
 // reads 32 banks); cells of absent or interior neighbours are stored as zero
 // mass, so the inner loop has no branches: per stencil entry one broadcast
-// load of the table and the halo offset, two shared loads, eight FMAs.
+// load of the table and the halo offset, two shared loads, eight FMAs (the
+// near entries in (d, -d) pairs, fewer).
 // FP64 form: one FP64 halo for every pair.  FP32-bulk form: far pairs from an
 // FP32 halo with FP32 arithmetic, near pairs from an FP64 halo of width
 // floor(1/theta) in FP64; both accumulated and flushed in FP64.
@@ -23,17 +24,13 @@ namespace otfmm {
 
 namespace {
 
-template <class T> __device__ __forceinline__ const T* lat_mom(const DevTree& t);
-template <> __device__ __forceinline__ const double* lat_mom<double>(const DevTree& t) { return t.mom64; }
-template <> __device__ __forceinline__ const float* lat_mom<float>(const DevTree& t) { return t.mom32; }
-
 // Fills a parity-split halo of width w with the masses of the leaf cells
 // around `node` (zero where there is no leaf cell at this level): one warp
-// per row of the halo, lanes along x.  `stride` is the distance between two
-// cells' masses in `mass` (1 for the FP64 arrays, 20 for the FP32 records).
+// per row of the halo, lanes along x.  The masses are read from the
+// contiguous FP64 array (coalesced) and stored as T.
 template <class T>
-__device__ __forceinline__ void fill_halo(const DevTree& t, int node, int w, T* halo,
-                                          const T* __restrict__ mass, int stride) {
+__device__ __forceinline__ void fill_halo(const DevTree& t, int node, int w, T* halo) {
+    const double* __restrict__ mass = t.mom64;
     const int hw = 8 + 2 * w;
     const int* nbr = t.nbr + (long long)node * 27;
     const int lane = threadIdx.x & 31;
@@ -46,7 +43,7 @@ __device__ __forceinline__ void fill_halo(const DevTree& t, int node, int w, T* 
         const int nb = __ldg(nbr + slot);
         T v = T(0.0);
         if (nb >= 0 && __ldg(t.node_leaf + nb) >= 0)
-            v = mass[((long long)nb * kCells + (x & 7) + 8 * (y & 7) + 64 * (z & 7)) * stride];
+            v = (T)mass[(long long)nb * kCells + (x & 7) + 8 * (y & 7) + 64 * (z & 7)];
         halo[halo_index(x, y, z, w)] = v;
     }
 }
@@ -58,8 +55,8 @@ __global__ void __launch_bounds__(256) k_lattice(DevTree t, DevPlan p, DevLattic
     const int wf = lp.w_far, wn = lp.w_near;
     T* hfar = reinterpret_cast<T*>(smem);
     double* hnear = reinterpret_cast<double*>(smem + sizeof(T) * 8 * halo_sub(wf));
-    fill_halo<T>(t, node, wf, hfar, lat_mom<T>(t), sizeof(T) == 4 ? kMom : 1);
-    if (sizeof(T) == 4) fill_halo<double>(t, node, wn, hnear, t.mom64, 1);
+    fill_halo<T>(t, node, wf, hfar);
+    if (sizeof(T) == 4) fill_halo<double>(t, node, wn, hnear);
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
@@ -72,39 +69,55 @@ __global__ void __launch_bounds__(256) k_lattice(DevTree t, DevPlan p, DevLattic
     const int tf2 = 2 * halo_pz(wf);                    // second target: 4 cells up in z
     double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;     // FP64 sums, target 1
     double e0 = 0.0, e1 = 0.0, e2 = 0.0, e3 = 0.0;     // FP64 sums, target 2
-    int q0 = 0;
+    // Near entries come in (d, -d) pairs: entry q and entry n_near - 1 - q
+    // (the near set is centrally symmetric and sorted).  With D0 even and D1
+    // odd, a pair costs 6 FP64 operations per target instead of 8:
+    //   L0 += D0(d) (m(t+d) + m(t-d)),  L1 += D1(d) (m(t+d) - m(t-d)).
+    const int npair = lp.n_near >> 1;
+    const int* hn = sizeof(T) == 4 ? lp.hoff_near : lp.hoff_far;
+    const int tn = sizeof(T) == 4 ? a + kHaloPy * b + halo_pz(wn) * c : tf;
+    const int tn2 = sizeof(T) == 4 ? 2 * halo_pz(wn) : tf2;
+    const double* hd = sizeof(T) == 4 ? hnear : reinterpret_cast<const double*>(hfar);
+    auto near_pair = [&](int q) {
+        const int o1 = __ldg(hn + base + q) + tn;
+        const int o2 = __ldg(hn + base + lp.n_near - 1 - q) + tn;
+        const double2 k0 = __ldg(p.tab64 + 2 * (base + q)), k1 = __ldg(p.tab64 + 2 * (base + q) + 1);
+        const double p1 = hd[o1], q1 = hd[o2], p2 = hd[o1 + tn2], q2 = hd[o2 + tn2];
+        const double s1 = p1 + q1, r1 = p1 - q1, s2 = p2 + q2, r2 = p2 - q2;
+        d0 = fma(s1, k0.x, d0); d1 = fma(r1, k0.y, d1); d2 = fma(r1, k1.x, d2); d3 = fma(r1, k1.y, d3);
+        e0 = fma(s2, k0.x, e0); e1 = fma(r2, k0.y, e1); e2 = fma(r2, k1.x, e2); e3 = fma(r2, k1.y, e3);
+    };
     if (sizeof(T) == 4) {
-        // near pairs in FP64 from the FP64 halo
-        const int tn = a + kHaloPy * b + halo_pz(wn) * c;
-        const int tn2 = 2 * halo_pz(wn);
-#pragma unroll 4
-        for (int q = 0; q < lp.n_near; q++) {
-            const int o = __ldg(lp.hoff_near + base + q) + tn;
-            const double2 k0 = __ldg(p.tab64 + 2 * (base + q)), k1 = __ldg(p.tab64 + 2 * (base + q) + 1);
-            const double m1 = hnear[o], m2 = hnear[o + tn2];
-            d0 = fma(m1, k0.x, d0); d1 = fma(m1, k0.y, d1); d2 = fma(m1, k1.x, d2); d3 = fma(m1, k1.y, d3);
-            e0 = fma(m2, k0.x, e0); e1 = fma(m2, k0.y, e1); e2 = fma(m2, k1.x, e2); e3 = fma(m2, k1.y, e3);
-        }
-        q0 = lp.n_near;
+        // far pairs in FP32 from the FP32 halo, with the FP64 near pairs spread
+        // evenly through the loop so the FP32 and FP64 pipes work together
         float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
         const float* hf = reinterpret_cast<const float*>(hfar);
-#pragma unroll 4
-        for (int q = q0; q < len; q++) {
+        const int nfar = len - lp.n_near;
+        const int every = npair > 0 ? (nfar + npair - 1) / npair : nfar + 1;
+        int jn = 0, tick = 0;
+#pragma unroll 2
+        for (int q = lp.n_near; q < len; q++) {
             const int o = __ldg(lp.hoff_far + base + q) + tf;
             const float4 k = __ldg(p.tab32 + base + q);
             const float m1 = hf[o], m2 = hf[o + tf2];
             f0 = fmaf(m1, k.x, f0); f1 = fmaf(m1, k.y, f1); f2 = fmaf(m1, k.z, f2); f3 = fmaf(m1, k.w, f3);
             g0 = fmaf(m2, k.x, g0); g1 = fmaf(m2, k.y, g1); g2 = fmaf(m2, k.z, g2); g3 = fmaf(m2, k.w, g3);
+            if (++tick == every) {
+                tick = 0;
+                if (jn < npair) near_pair(jn++);
+            }
         }
+        for (; jn < npair; jn++) near_pair(jn);
         d0 += f0; d1 += f1; d2 += f2; d3 += f3;
         e0 += g0; e1 += g1; e2 += g2; e3 += g3;
     } else {
-        const double* hd = reinterpret_cast<const double*>(hfar);
+        for (int q = 0; q < npair; q++) near_pair(q);
+        const double* hdf = reinterpret_cast<const double*>(hfar);
 #pragma unroll 4
-        for (int q = 0; q < len; q++) {
+        for (int q = lp.n_near; q < len; q++) {
             const int o = __ldg(lp.hoff_far + base + q) + tf;
             const double2 k0 = __ldg(p.tab64 + 2 * (base + q)), k1 = __ldg(p.tab64 + 2 * (base + q) + 1);
-            const double m1 = hd[o], m2 = hd[o + tf2];
+            const double m1 = hdf[o], m2 = hdf[o + tf2];
             d0 = fma(m1, k0.x, d0); d1 = fma(m1, k0.y, d1); d2 = fma(m1, k1.x, d2); d3 = fma(m1, k1.y, d3);
             e0 = fma(m2, k0.x, e0); e1 = fma(m2, k0.y, e1); e2 = fma(m2, k1.x, e2); e3 = fma(m2, k1.y, e3);
         }
