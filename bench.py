@@ -138,22 +138,32 @@ def barrier(world):
         torch.distributed.barrier()
 
 
-def max_over_ranks(world, x: float) -> float:
+def _reduce(world, x: float, op) -> float:
     import torch
     if world == 1:
         return x
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    # NCCL reduces device tensors, gloo host tensors
+    dev = "cuda" if torch.distributed.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    torch.distributed.all_reduce(t, op=op)
     return float(t.item())
+
+
+def max_over_ranks(world, x: float) -> float:
+    import torch
+    return _reduce(world, x, torch.distributed.ReduceOp.MAX if world > 1 else None)
 
 
 def sum_over_ranks(world, x: float) -> float:
     import torch
-    if world == 1:
-        return x
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(world, x, torch.distributed.ReduceOp.SUM if world > 1 else None)
+
+
+def aggregate(world, per_rank_ms: float, per_rank_units: float):
+    """Whole-job throughput of weak-scaled replicas: the slowest rank's time
+    and the units every rank processed."""
+    total_ms = max_over_ranks(world, per_rank_ms)
+    return total_ms, sum_over_ranks(world, per_rank_units) / (total_ms / 1e3)
 
 
 def time_steps(tree, rho, phi, g, opts, steps, flush, per_step_times=True):
@@ -284,9 +294,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop()
-    total_ms = max_over_ranks(world, sum(solve_ms))
+    total_ms, value = aggregate(world, sum(solve_ms), n_int * args.steps)
     ms_per_step = total_ms / args.steps
-    value = sum_over_ranks(world, n_int * args.steps) / (total_ms / 1e3)
     subgrids = sum_over_ranks(world, leaves.shape[0] * args.steps) / (total_ms / 1e3)
 
     # roofline of the interaction launch
@@ -332,8 +341,7 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
-    e2e_total = max_over_ranks(world, sum(e2e_ms))
-    e2e_value = sum_over_ranks(world, n_int * args.steps) / (e2e_total / 1e3)
+    _, e2e_value = aggregate(world, sum(e2e_ms), n_int * args.steps)
     n_cells = leaves.shape[0] * 512
     extra = {}
     if rank == 0 and world == 1 and not args.no_extra:
