@@ -182,7 +182,7 @@ int ot_tree_info(ot_tree* tree, ot_tree_stats* stats);
  * counterpart; it is the same solve as ot_solve_gravity (same kernels, same
  * results to rounding) for small trees, without a tree handle: every piece of
  * scratch (node tables, moments, expansions, stencil tables, work items) lives
- * in one fixed 3 MiB device array inside the library, held by every GPU that
+ * in one fixed 4 MiB device array inside the library, held by every GPU that
  * loads it until the process exits.  desc: host leaf list as for
  * ot_build_tree, at most 9 nodes (the root leaf alone, or the root and its 8
  * leaf children: 4,096 cells); rho, phi, g: device buffers on the CURRENT

@@ -55,6 +55,7 @@ struct ot_tree {
     int *d_level = nullptr, *d_leaf = nullptr, *d_parent = nullptr, *d_child = nullptr;
     int *d_xyz = nullptr, *d_nbr = nullptr, *d_level_first = nullptr, *d_leaf_node = nullptr;
     double* d_mom64 = nullptr;
+    double* d_rec64 = nullptr;
     float* d_mom32 = nullptr;
     double* d_loc = nullptr;
     int* d_status = nullptr;
@@ -62,6 +63,8 @@ struct ot_tree {
     int* d_entries = nullptr;
     double2* d_tab64 = nullptr;
     float4* d_tab32 = nullptr;
+    double2* d_off64 = nullptr;
+    float4* d_off32 = nullptr;
     int* d_list_first = nullptr;
     int* d_list_len = nullptr;
     int4* d_items = nullptr;
@@ -142,6 +145,7 @@ DevTree dev_tree(const ot_tree* t) {
     d.level_first = t->d_level_first;
     d.mom64 = t->d_mom64;
     d.mom32 = t->d_mom32;
+    d.rec64 = t->d_rec64;
     d.inv_side8 = 8.0 / t->h.size;
     d.loc = t->d_loc;
     d.status = t->d_status;
@@ -153,6 +157,8 @@ DevPlan dev_plan(const ot_tree* t) {
     p.entries = t->d_entries;
     p.tab64 = t->d_tab64;
     p.tab32 = t->d_tab32;
+    p.off64 = t->d_off64;
+    p.off32 = t->d_off32;
     p.list_first = t->d_list_first;
     p.list_len = t->d_list_len;
     p.items = t->d_items;
@@ -190,12 +196,16 @@ int ensure_plan(ot_tree* t, double theta) {
         cudaFree(t->d_tab32);
         cudaFree(t->d_hoff_far);
         cudaFree(t->d_hoff_near);
+        cudaFree(t->d_off64);
+        cudaFree(t->d_off32);
         t->entries_cap = p.entries.size();
         TRY(dalloc(t, &t->d_entries, t->entries_cap));
         TRY(dalloc(t, &t->d_tab64, 2 * t->entries_cap));
         TRY(dalloc(t, &t->d_tab32, t->entries_cap));
         TRY(dalloc(t, &t->d_hoff_far, t->entries_cap));
         TRY(dalloc(t, &t->d_hoff_near, t->entries_cap));
+        TRY(dalloc(t, &t->d_off64, 2 * t->entries_cap));
+        TRY(dalloc(t, &t->d_off32, t->entries_cap));
     }
     if (!t->d_lattice_nodes) TRY(dalloc(t, &t->d_lattice_nodes, (size_t)t->h.n_leaf));
     if (p.items.size() > t->items_cap) {
@@ -215,6 +225,10 @@ int ensure_plan(ot_tree* t, double theta) {
     TRYC(cudaMemcpy(t->d_tab64, p.tab64.data(), p.tab64.size() * 2 * sizeof(double2),
                     cudaMemcpyHostToDevice));
     TRYC(cudaMemcpy(t->d_tab32, p.tab32.data(), p.tab32.size() * sizeof(float4),
+                    cudaMemcpyHostToDevice));
+    TRYC(cudaMemcpy(t->d_off64, p.off64.data(), p.off64.size() * 2 * sizeof(double2),
+                    cudaMemcpyHostToDevice));
+    TRYC(cudaMemcpy(t->d_off32, p.off32.data(), p.off32.size() * sizeof(float4),
                     cudaMemcpyHostToDevice));
     TRYC(cudaMemcpy(t->d_list_first, p.list_first, sizeof(p.list_first), cudaMemcpyHostToDevice));
     TRYC(cudaMemcpy(t->d_list_len, p.list_len, sizeof(p.list_len), cudaMemcpyHostToDevice));
@@ -401,7 +415,7 @@ int ot_build_tree(const ot_tree_desc* desc, int device, ot_tree** out) {
         (e = dalloc(t, &t->d_xyz, 3 * N)) || (e = dalloc(t, &t->d_nbr, 27 * N)) ||
         (e = dalloc(t, &t->d_level_first, h.level_first.size())) ||
         (e = dalloc(t, &t->d_leaf_node, (size_t)h.n_leaf)) || (e = dalloc(t, &t->d_mom64, kMom * C)) ||
-        (e = dalloc(t, &t->d_mom32, kMom * C)) || (e = dalloc(t, &t->d_loc, kLoc * C)) ||
+        (e = dalloc(t, &t->d_mom32, kMom * C)) || (e = dalloc(t, &t->d_rec64, kRec * C)) || (e = dalloc(t, &t->d_loc, kLoc * C)) ||
         (e = dalloc(t, &t->d_status, 1)) || (e = dalloc(t, &t->d_list_first, kNumLists)) ||
         (e = dalloc(t, &t->d_list_len, kNumLists)) || (e = dalloc(t, &t->d_counter, 1)) ||
         (e = dalloc(t, &t->d_rho_in, (size_t)h.n_leaf * kCells)) ||
@@ -416,6 +430,7 @@ int ot_build_tree(const ot_tree_desc* desc, int device, ot_tree** out) {
     // leaf cells keep dX = M2 = M3 = 0 for the life of the tree
     if (cudaMemset(t->d_mom64, 0, sizeof(double) * kMom * C) != cudaSuccess ||
         cudaMemset(t->d_mom32, 0, sizeof(float) * kMom * C) != cudaSuccess ||
+        cudaMemset(t->d_rec64, 0, sizeof(double) * kRec * C) != cudaSuccess ||
         cudaMemset(t->d_status, 0, sizeof(int)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&t->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&t->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -445,10 +460,11 @@ void ot_destroy_tree(ot_tree* t) {
         for (cudaEvent_t e : t->ev)
             if (e) cudaEventDestroy(e);
         void* ptrs[] = {t->d_level, t->d_leaf, t->d_parent, t->d_child, t->d_xyz, t->d_nbr,
-                        t->d_level_first, t->d_leaf_node, t->d_mom64, t->d_mom32, t->d_loc,
+                        t->d_level_first, t->d_leaf_node, t->d_mom64, t->d_mom32, t->d_rec64, t->d_loc,
                         t->d_status, t->d_entries, t->d_tab64, t->d_tab32, t->d_list_first,
                         t->d_list_len, t->d_items, t->d_counter, t->d_rho_in, t->d_phi_out,
                         t->d_hoff_far, t->d_hoff_near, t->d_lattice_nodes, t->d_items_adj,
+                        t->d_off64, t->d_off32,
                         t->d_g_out, t->d_locbar, t->d_mombar};
         for (void* p : ptrs)
             if (p) cudaFree(p);

@@ -8,9 +8,11 @@
 //                                        + i + 8 j + 64 k
 //   moments       20 components: m, dX(3), M2(6), M3(10) in units of the cell's
 //                 own side h (dX = centre of mass - cell centre, M2 / h^2,
-//                 M3 / h^3); FP64 structure of arrays [20][n_cells], and an
-//                 FP32 copy as an array of 80-byte records [n_cells][20] (one
-//                 source cell = five 16-byte loads)
+//                 M3 / h^3); FP64 structure of arrays [20][n_cells]; FP64
+//                 per-cell records [n_cells][24] (the 20 moments, the M3
+//                 trace vector t_i = M3_ijj and trace(M2)) and FP32 records
+//                 [n_cells][20], read by the interaction kernels (a source is
+//                 a few 16-byte loads)
 //   expansions    23 components: L0, L1(3), L2(6), L3(10), ac(3), physical
 //                 units, FP64
 // Packed symmetric index orders: M2/L2 = xx xy xz yy yz zz;
@@ -24,6 +26,7 @@ namespace otfmm {
 
 constexpr int kCells = 512;      // 8^3 cells per node (Sec. 4.3.2)
 constexpr int kMom = 20;         // moment components per cell
+constexpr int kRec = 24;         // per-cell record: 20 moments, M3 trace vector, M2 trace
 constexpr int kLoc = 23;         // expansion components per cell (+ correction)
 
 // Status word codes latched by kernels (never trapped).
@@ -45,6 +48,7 @@ struct DevTree {
     const int* nbr;             // [n_nodes][27] neighbour node or -1
     const int* level_first;     // [n_levels + 1] first node of each level
     double* mom64;              // [20][n_cells]
+    double* rec64;              // [n_cells][24]
     float* mom32;               // [n_cells][20]
     double inv_side8;           // 8 / size: 1/h at level 0
     double* loc;                // [23][n_cells]
@@ -57,6 +61,8 @@ struct DevPlan {
     const int* entries;         // [n_entries]
     const double2* tab64;       // [2 n_entries] (D0, D1x), (D1y, D1z) of the lattice offset
     const float4* tab32;        // [n_entries]
+    const double2* off64;       // [2 n_entries] (dx, dy), (dz, 0) of each entry
+    const float4* off32;        // [n_entries] (dx, dy, dz, 0)
     const int* list_first;      // [9] first entry of list 0..8 (8 = level 0)
     const int* list_len;        // [9]
     const int4* items;          // [n_items]

@@ -41,15 +41,17 @@ __device__ __forceinline__ void tab_of(const DevPlan& p, int k, float& a, float&
 
 constexpr int kMaxWarps = 16;
 
-// Source/target moment loads: FP64 from the structure of arrays, FP32 from
-// the 80-byte records (head = m, dX; tail = M2, M3).
+// Source/target loads from the per-cell records (head = m, dX; tail = M2,
+// M3, the M3 trace vector and trace(M2)): FP64 records of 24 doubles hold the
+// traces, FP32 records of 20 floats do not.
 __device__ __forceinline__ void load_head(const DevTree& t, long long c, double& m, double& x,
                                           double& y, double& z) {
-    const long long N = t.n_cells;
-    m = t.mom64[c];
-    x = t.mom64[N + c];
-    y = t.mom64[2 * N + c];
-    z = t.mom64[3 * N + c];
+    const double2* p = reinterpret_cast<const double2*>(t.rec64 + c * kRec);
+    const double2 a = __ldg(p), b = __ldg(p + 1);
+    m = a.x;
+    x = a.y;
+    y = b.x;
+    z = b.y;
 }
 __device__ __forceinline__ void load_head(const DevTree& t, long long c, float& m, float& x,
                                           float& y, float& z) {
@@ -59,19 +61,47 @@ __device__ __forceinline__ void load_head(const DevTree& t, long long c, float& 
     y = v.z;
     z = v.w;
 }
-__device__ __forceinline__ void load_tail(const DevTree& t, long long c, double* b2, double* b3) {
-    const long long N = t.n_cells;
+__device__ __forceinline__ void load_tail(const DevTree& t, long long c, double* b2, double* b3,
+                                          double* bt) {
+    const double2* p = reinterpret_cast<const double2*>(t.rec64 + c * kRec);
+    double v[20];
 #pragma unroll
-    for (int r = 0; r < 6; r++) b2[r] = t.mom64[(4 + r) * N + c];
+    for (int r = 0; r < 10; r++) {
+        const double2 q = __ldg(p + 2 + r);
+        v[2 * r] = q.x;
+        v[2 * r + 1] = q.y;
+    }
 #pragma unroll
-    for (int r = 0; r < 10; r++) b3[r] = t.mom64[(10 + r) * N + c];
+    for (int r = 0; r < 6; r++) b2[r] = v[r];
+#pragma unroll
+    for (int r = 0; r < 10; r++) b3[r] = v[6 + r];
+#pragma unroll
+    for (int r = 0; r < 4; r++) bt[r] = v[16 + r];
 }
-__device__ __forceinline__ void load_tail(const DevTree& t, long long c, float* b2, float* b3) {
+__device__ __forceinline__ void load_tail(const DevTree& t, long long c, float* b2, float* b3,
+                                          float* bt) {
+    // 80-byte FP32 records: the traces are cheaper to form here than to load
     const float4* p = reinterpret_cast<const float4*>(t.mom32 + c * kMom);
     const float4 v1 = __ldg(p + 1), v2 = __ldg(p + 2), v3 = __ldg(p + 3), v4 = __ldg(p + 4);
     b2[0] = v1.x; b2[1] = v1.y; b2[2] = v1.z; b2[3] = v1.w; b2[4] = v2.x; b2[5] = v2.y;
     b3[0] = v2.z; b3[1] = v2.w; b3[2] = v3.x; b3[3] = v3.y; b3[4] = v3.z; b3[5] = v3.w;
     b3[6] = v4.x; b3[7] = v4.y; b3[8] = v4.z; b3[9] = v4.w;
+    bt[0] = b3[0] + b3[3] + b3[5];
+    bt[1] = b3[1] + b3[6] + b3[8];
+    bt[2] = b3[2] + b3[7] + b3[9];
+    bt[3] = b2[0] + b2[3] + b2[5];
+}
+__device__ __forceinline__ void load_off(const DevPlan& p, int k, double& x, double& y, double& z) {
+    const double2 a = __ldg(p.off64 + 2 * k), b = __ldg(p.off64 + 2 * k + 1);
+    x = a.x;
+    y = a.y;
+    z = b.x;
+}
+__device__ __forceinline__ void load_off(const DevPlan& p, int k, float& x, float& y, float& z) {
+    const float4 a = __ldg(p.off32 + k);
+    x = a.x;
+    y = a.y;
+    z = a.z;
 }
 
 // Scales a partial sum to physical units and widens it: the FP64 form
@@ -93,14 +123,11 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
     const long long cell = (long long)node * kCells + i + 8 * j + 64 * k;
     T ma, dax, day, daz;
     load_head(t, cell, ma, dax, day, daz);
-    T inv_ma = T(0.0), a3[10], ta[3];
+    T inv_ma = T(0.0), a3[10], ta[4];
     if (FULL && AM) {
         T a2[6];
         inv_ma = T(1.0) / ma;
-        load_tail(t, cell, a2, a3);
-        ta[0] = a3[0] + a3[3] + a3[5];
-        ta[1] = a3[1] + a3[6] + a3[8];
-        ta[2] = a3[2] + a3[7] + a3[9];
+        load_tail(t, cell, a2, a3, ta);
     }
     Acc<T> A;
     acc_zero(A);
@@ -140,18 +167,19 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
             continue;
         }
         if (FULL && !sleaf && entry_near(e)) continue;  // resolved at the next level
-        T m, bx, by, bz;
+        T m, bx, by, bz, ox, oy, oz;
         load_head(t, sc, m, bx, by, bz);
+        load_off(p, base + q, ox, oy, oz);
         // R' = X_A - X_B in cell units: the source sits at offset d from the target
-        const T x = (dax - bx) - T(dx);
-        const T y = (day - by) - T(dy);
-        const T z = (daz - bz) - T(dz);
+        const T x = (dax - bx) - ox;
+        const T y = (day - by) - oy;
+        const T z = (daz - bz) - oz;
         if (sleaf) {
-            m2l_pair<T, FULL, false, AM>(x, y, z, m, nullptr, nullptr, m * inv_ma, a3, ta, A);
+            m2l_pair<T, FULL, false, AM>(x, y, z, m, nullptr, nullptr, nullptr, m * inv_ma, a3, ta, A);
         } else {
-            T b2[6], b3[10];
-            load_tail(t, sc, b2, b3);
-            m2l_pair<T, FULL, true, AM>(x, y, z, m, b2, b3, m * inv_ma, a3, ta, A);
+            T b2[6], b3[10], bt[4];
+            load_tail(t, sc, b2, b3, bt);
+            m2l_pair<T, FULL, true, AM>(x, y, z, m, b2, b3, bt, m * inv_ma, a3, ta, A);
         }
     }
     // scale to physical units: L^(n) * (-G h^-(n+1)), correction * -(G/6) h^-2
@@ -165,18 +193,11 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
     atomicAdd(loc + 2 * N + cell, scaled(A.L1[1], s2) + s2d * n2);
     atomicAdd(loc + 3 * N + cell, scaled(A.L1[2], s2) + s2d * n3);
     if (FULL) {
-        const T d1 = A.d1;
-        atomicAdd(loc + 4 * N + cell, scaled(A.L2[0] + d1, s3));
-        atomicAdd(loc + 5 * N + cell, scaled(A.L2[1], s3));
-        atomicAdd(loc + 6 * N + cell, scaled(A.L2[2], s3));
-        atomicAdd(loc + 7 * N + cell, scaled(A.L2[3] + d1, s3));
-        atomicAdd(loc + 8 * N + cell, scaled(A.L2[4], s3));
-        atomicAdd(loc + 9 * N + cell, scaled(A.L2[5] + d1, s3));
-        const T Vx = A.V[0], Vy = A.V[1], Vz = A.V[2];
-        // Kronecker part of L3: delta_ij V_k + delta_ik V_j + delta_jk V_i
-        const T k3[10] = {T(3.0) * Vx, Vy, Vz, Vx, T(0.0), Vx, T(3.0) * Vy, Vz, Vy, T(3.0) * Vz};
+        finish_acc(A);  // Kronecker parts of L2 and L3 from their traces
 #pragma unroll
-        for (int r = 0; r < 10; r++) atomicAdd(loc + (10 + r) * N + cell, scaled(A.L3[r] + k3[r], s4));
+        for (int r = 0; r < 6; r++) atomicAdd(loc + (4 + r) * N + cell, scaled(A.L2[r], s3));
+#pragma unroll
+        for (int r = 0; r < 10; r++) atomicAdd(loc + (10 + r) * N + cell, scaled(A.L3[r], s4));
     }
     if (AM) {
         const T sa = T(-(G / 6.0) * hi * hi);

@@ -34,6 +34,7 @@ __global__ void __launch_bounds__(256) k_leaf_moments(DevTree t, const int* __re
         const double m = rho[(long long)leaf * kCells + c] * h3;
         const long long cell = (long long)node * kCells + c;
         t.mom64[cell] = m;
+        t.rec64[cell * kRec] = m;
         t.mom32[cell * kMom] = (float)m;
         // a leaf cell's expansion: L0, L1 and the correction acceleration
         t.loc[cell] = 0.0;
@@ -108,19 +109,28 @@ __global__ void __launch_bounds__(256) k_m2m(DevTree t, int first) {
 #pragma unroll
     for (int r = 0; r < 16; r++) S[r] = sum8(S[r]);
     const long long cell = (long long)node * kCells + c;
-    // lane q writes the components it owns: 20 moments, 23 zeroed expansions
-    double vals[20];
+    // lane q writes the components it owns: 20 moments (+ the record's two
+    // traces), 23 zeroed expansions
+    double vals[kRec];
     vals[0] = M;
     vals[1] = X[0];
     vals[2] = X[1];
     vals[3] = X[2];
 #pragma unroll
     for (int r = 0; r < 16; r++) vals[4 + r] = S[r];
+    // M3 trace vector t_i = M3_ijj and trace(M2)
+    vals[20] = S[6 + 0] + S[6 + 3] + S[6 + 5];
+    vals[21] = S[6 + 1] + S[6 + 6] + S[6 + 8];
+    vals[22] = S[6 + 2] + S[6 + 7] + S[6 + 9];
+    vals[23] = S[0] + S[3] + S[5];
 #pragma unroll
-    for (int r = 0; r < 20; r++) {
+    for (int r = 0; r < kRec; r++) {
         if ((r & 7) == q) {
-            t.mom64[r * N + cell] = vals[r];
-            t.mom32[cell * kMom + r] = (float)vals[r];
+            if (r < kMom) {
+                t.mom64[r * N + cell] = vals[r];
+                t.mom32[cell * kMom + r] = (float)vals[r];
+            }
+            t.rec64[cell * kRec + r] = vals[r];
         }
     }
 #pragma unroll
@@ -184,19 +194,27 @@ __global__ void __launch_bounds__(256) k_m2m_leafkids(DevTree t, int first) {
                 2.0 * MX[ii] * X[jj] * X[kk];
     }
     const long long cell = (long long)node * kCells + c;
-    float4* m32 = reinterpret_cast<float4*>(t.mom32 + cell * kMom);
-    t.mom64[cell] = M;
+    double v[kRec];
+    v[0] = M;
 #pragma unroll
-    for (int s = 0; s < 3; s++) t.mom64[(1 + s) * N + cell] = X[s];
+    for (int s = 0; s < 3; s++) v[1 + s] = X[s];
 #pragma unroll
-    for (int r = 0; r < 6; r++) t.mom64[(4 + r) * N + cell] = S2[r];
+    for (int r = 0; r < 6; r++) v[4 + r] = S2[r];
 #pragma unroll
-    for (int r = 0; r < 10; r++) t.mom64[(10 + r) * N + cell] = S3[r];
-    m32[0] = make_float4((float)M, (float)X[0], (float)X[1], (float)X[2]);
-    m32[1] = make_float4((float)S2[0], (float)S2[1], (float)S2[2], (float)S2[3]);
-    m32[2] = make_float4((float)S2[4], (float)S2[5], (float)S3[0], (float)S3[1]);
-    m32[3] = make_float4((float)S3[2], (float)S3[3], (float)S3[4], (float)S3[5]);
-    m32[4] = make_float4((float)S3[6], (float)S3[7], (float)S3[8], (float)S3[9]);
+    for (int r = 0; r < 10; r++) v[10 + r] = S3[r];
+    v[20] = S3[0] + S3[3] + S3[5];
+    v[21] = S3[1] + S3[6] + S3[8];
+    v[22] = S3[2] + S3[7] + S3[9];
+    v[23] = S2[0] + S2[3] + S2[5];
+#pragma unroll
+    for (int r = 0; r < kMom; r++) t.mom64[r * N + cell] = v[r];
+    double2* r64 = reinterpret_cast<double2*>(t.rec64 + cell * kRec);
+    float4* r32 = reinterpret_cast<float4*>(t.mom32 + cell * kMom);
+#pragma unroll
+    for (int r = 0; r < kRec / 2; r++) r64[r] = make_double2(v[2 * r], v[2 * r + 1]);
+#pragma unroll
+    for (int r = 0; r < kMom / 4; r++)
+        r32[r] = make_float4((float)v[4 * r], (float)v[4 * r + 1], (float)v[4 * r + 2], (float)v[4 * r + 3]);
 #pragma unroll
     for (int r = 0; r < kLoc; r++) t.loc[r * N + cell] = 0.0;
 }

@@ -26,24 +26,45 @@ namespace otfmm {
 
 template <class T> struct Acc {
     T L0, L1[3], L2[6], L3[10];
-    T d1;    // sum of m f1: the Kronecker part of L2 (added to xx, yy, zz)
-    T V[3];  // sum of m f2 R: the Kronecker part of L3
     T S[3];  // correction sum
 };
+// The Kronecker parts of L2 and L3 are not accumulated: D2 and D3 are
+// traceless, so per pair sum m f1 = -trace(m f2 R R) / 3 and
+// sum m f2 R = -trace(m f3 R R R) / 5; finish_acc restores them from the
+// accumulated R R and R R R parts once per target.
 
 template <class T> __host__ __device__ __forceinline__ void acc_zero(Acc<T>& A) {
     A.L0 = T(0.0);
-    A.d1 = T(0.0);
 #pragma unroll
     for (int i = 0; i < 3; i++) {
         A.L1[i] = T(0.0);
-        A.V[i] = T(0.0);
         A.S[i] = T(0.0);
     }
 #pragma unroll
     for (int i = 0; i < 6; i++) A.L2[i] = T(0.0);
 #pragma unroll
     for (int i = 0; i < 10; i++) A.L3[i] = T(0.0);
+}
+
+// Adds the Kronecker parts to L2 (d1 on the diagonal) and L3 (delta_ij V_k
+// + delta_ik V_j + delta_jk V_i), d1 and V taken from the traces.
+template <class T> __host__ __device__ __forceinline__ void finish_acc(Acc<T>& A) {
+    const T d1 = T(-1.0 / 3.0) * (A.L2[0] + A.L2[3] + A.L2[5]);
+    const T Vx = T(-0.2) * (A.L3[0] + A.L3[3] + A.L3[5]);
+    const T Vy = T(-0.2) * (A.L3[1] + A.L3[6] + A.L3[8]);
+    const T Vz = T(-0.2) * (A.L3[2] + A.L3[7] + A.L3[9]);
+    A.L2[0] += d1;
+    A.L2[3] += d1;
+    A.L2[5] += d1;
+    A.L3[0] += T(3.0) * Vx;
+    A.L3[1] += Vy;
+    A.L3[2] += Vz;
+    A.L3[3] += Vx;
+    A.L3[5] += Vx;
+    A.L3[6] += T(3.0) * Vy;
+    A.L3[7] += Vz;
+    A.L3[8] += Vy;
+    A.L3[9] += T(3.0) * Vz;
 }
 
 __host__ __device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
@@ -69,46 +90,57 @@ __host__ __device__ __forceinline__ void contract_rr(const T* c, T xx, T yy, T z
 // TGT_FULL: the target is an interior cell (needs L2, L3 and the target part
 // of the correction).  SRC_MULTI: the source is an interior cell (has M2, M3).
 // AM: the correction is on.  (x, y, z) = R', m = source mass, b2/b3 = source
-// M2'/M3', ratio = m_B / m_A, a3/ta = target M3' and its trace vector.
+// M2'/M3', bt = the source's M3 trace vector (t_i = M3_ijj) and trace of M2
+// (bt[3]), ratio = m_B / m_A, a3/ta = target M3' and its trace vector.
 template <class T, bool TGT_FULL, bool SRC_MULTI, bool AM>
 __host__ __device__ __forceinline__ void m2l_pair(T x, T y, T z, T m, const T* b2, const T* b3,
-                                                  T ratio, const T* a3, const T* ta, Acc<T>& A) {
+                                                  const T* bt, T ratio, const T* a3, const T* ta,
+                                                  Acc<T>& A) {
     const T r2 = fma_(x, x, fma_(y, y, z * z));
     const T f0 = rsqrt_(r2);
     const T ri2 = f0 * f0;
     const T f1 = -(f0 * ri2);
-    const T f2 = T(-3.0) * (f1 * ri2);
-    const T f3 = T(-5.0) * (f2 * ri2);
+    const T f2 = f1 * (T(-3.0) * ri2);
+    const T f3 = f2 * (T(-5.0) * ri2);
     const T c1 = m * f1;
     T f4 = T(0.0);
-    if (AM) f4 = T(-7.0) * (f3 * ri2);
+    if (AM) f4 = f3 * (T(-7.0) * ri2);
     const T xx = x * x, yy = y * y, zz = z * z;
     const T xy = x * y, xz = x * z, yz = y * z;
+    T xy2 = T(0.0), xz2 = T(0.0), yz2 = T(0.0), u = T(0.0), w = T(0.0);
+    if (SRC_MULTI || (TGT_FULL && AM)) {
+        xy2 = xy + xy;
+        xz2 = xz + xz;
+        yz2 = yz + yz;
+    }
+    if (AM) {
+        u = T(3.0) * f3;
+        w = T(3.0) * f2;
+    }
     if (SRC_MULTI) {
         const T Mx = fma_(b2[0], x, fma_(b2[1], y, b2[2] * z));
         const T My = fma_(b2[1], x, fma_(b2[3], y, b2[4] * z));
         const T Mz = fma_(b2[2], x, fma_(b2[4], y, b2[5] * z));
         const T xMx = fma_(x, Mx, fma_(y, My, z * Mz));
-        const T tr = b2[0] + b2[3] + b2[5];
+        const T tr = bt[3];
         T qx, qy, qz;
-        contract_rr(b3, xx, yy, zz, xy + xy, xz + xz, yz + yz, qx, qy, qz);
+        contract_rr(b3, xx, yy, zz, xy2, xz2, yz2, qx, qy, qz);
         const T q3 = fma_(x, qx, fma_(y, qy, z * qz));
-        const T tx = b3[0] + b3[3] + b3[5];
-        const T ty = b3[1] + b3[6] + b3[8];
-        const T tz = b3[2] + b3[7] + b3[9];
-        const T Rt = fma_(x, tx, fma_(y, ty, z * tz));
+        const T Rt = fma_(x, bt[0], fma_(y, bt[1], z * bt[2]));
+        const T h2 = T(0.5) * f2;
         // L0 += m f0 + (f2 xMx + f1 tr) / 2 - (f3 q3 + 3 f2 Rt) / 6
-        A.L0 += fma_(m, f0, fma_(T(0.5) * f1, tr, fma_(T(0.5) * f2, xMx - Rt, T(-1.0 / 6.0) * (f3 * q3))));
+        A.L0 = fma_(m, f0, fma_(T(0.5) * f1, tr, fma_(h2, xMx - Rt, fma_(T(-1.0 / 6.0) * f3, q3, A.L0))));
         // L1 += R (m f1 + (f3 xMx + f2 tr) / 2) + f2 M2 R
-        const T g1 = fma_(T(0.5), fma_(f3, xMx, f2 * tr), c1);
+        const T g1 = fma_(T(0.5) * f3, xMx, fma_(h2, tr, c1));
         A.L1[0] = fma_(g1, x, fma_(f2, Mx, A.L1[0]));
         A.L1[1] = fma_(g1, y, fma_(f2, My, A.L1[1]));
         A.L1[2] = fma_(g1, z, fma_(f2, Mz, A.L1[2]));
         if (AM) {
-            const T u = T(3.0) * f3, w = T(3.0) * f2, v = f4 * q3;
-            A.S[0] += fma_(v, x, fma_(u, fma_(x, Rt, qx), w * tx));
-            A.S[1] += fma_(v, y, fma_(u, fma_(y, Rt, qy), w * ty));
-            A.S[2] += fma_(v, z, fma_(u, fma_(z, Rt, qz), w * tz));
+            // S += f4 R q3 + 3 f3 (q2 + R Rt) + 3 f2 t = R k + u q2 + w t
+            const T k = fma_(u, Rt, f4 * q3);
+            A.S[0] = fma_(k, x, fma_(u, qx, fma_(w, bt[0], A.S[0])));
+            A.S[1] = fma_(k, y, fma_(u, qy, fma_(w, bt[1], A.S[1])));
+            A.S[2] = fma_(k, z, fma_(u, qz, fma_(w, bt[2], A.S[2])));
         }
     } else {
         A.L0 = fma_(m, f0, A.L0);
@@ -124,7 +156,6 @@ __host__ __device__ __forceinline__ void m2l_pair(T x, T y, T z, T m, const T* b
         A.L2[3] = fma_(s2, yy, A.L2[3]);
         A.L2[4] = fma_(s2, yz, A.L2[4]);
         A.L2[5] = fma_(s2, zz, A.L2[5]);
-        A.d1 += c1;
         const T s3 = m * f3;
         const T tx3 = s3 * x, ty3 = s3 * y, tz3 = s3 * z;
         A.L3[0] = fma_(tx3, xx, A.L3[0]);
@@ -137,20 +168,17 @@ __host__ __device__ __forceinline__ void m2l_pair(T x, T y, T z, T m, const T* b
         A.L3[7] = fma_(ty3, yz, A.L3[7]);
         A.L3[8] = fma_(ty3, zz, A.L3[8]);
         A.L3[9] = fma_(tz3, zz, A.L3[9]);
-        A.V[0] = fma_(s2, x, A.V[0]);
-        A.V[1] = fma_(s2, y, A.V[1]);
-        A.V[2] = fma_(s2, z, A.V[2]);
         if (AM) {
-            // - (m_B / m_A) D4 : M3_A
+            // - (m_B / m_A) D4 : M3_A = -ratio (R k' + u q2_A + w t_A)
             T qx, qy, qz;
-            contract_rr(a3, xx, yy, zz, xy + xy, xz + xz, yz + yz, qx, qy, qz);
+            contract_rr(a3, xx, yy, zz, xy2, xz2, yz2, qx, qy, qz);
             const T q3 = fma_(x, qx, fma_(y, qy, z * qz));
             const T Rt = fma_(x, ta[0], fma_(y, ta[1], z * ta[2]));
-            const T u = T(3.0) * f3, w = T(3.0) * f2, v = f4 * q3;
             const T nr = -ratio;
-            A.S[0] = fma_(nr, fma_(v, x, fma_(u, fma_(x, Rt, qx), w * ta[0])), A.S[0]);
-            A.S[1] = fma_(nr, fma_(v, y, fma_(u, fma_(y, Rt, qy), w * ta[1])), A.S[1]);
-            A.S[2] = fma_(nr, fma_(v, z, fma_(u, fma_(z, Rt, qz), w * ta[2])), A.S[2]);
+            const T nk = nr * fma_(u, Rt, f4 * q3), nu = nr * u, nw = nr * w;
+            A.S[0] = fma_(nk, x, fma_(nu, qx, fma_(nw, ta[0], A.S[0])));
+            A.S[1] = fma_(nk, y, fma_(nu, qy, fma_(nw, ta[1], A.S[1])));
+            A.S[2] = fma_(nk, z, fma_(nu, qz, fma_(nw, ta[2], A.S[2])));
         }
     }
 }

@@ -8,7 +8,7 @@
 // cannot use ot_solve_gravity.  ot_solve_gravity_static runs the same kernels
 // as ot_solve_gravity, but every piece of scratch memory -- node tables,
 // moments, expansions, stencil tables, work items, the item counter -- lives
-// in one file-scope device array of fixed size (kStaticBytes, 3 MiB), which
+// in one file-scope device array of fixed size (kStaticBytes, 4 MiB), which
 // every GPU that loads the library holds until the process exits.  The caller
 // passes only the inputs (leaf list on the host, densities on the device) and
 // the outputs (phi, g on the device).  The library allocates no device memory
@@ -42,10 +42,10 @@ namespace otfmm {
 namespace {
 
 constexpr int kMaxNodes = 9;
-constexpr int kMaxEntries = 14336;
+constexpr int kMaxEntries = 5632;  // 8 parity lists of <= 263 entries and the level-0 list of 3374 (theta >= 0.5)
 constexpr int kMaxItems = 2048;
 constexpr int kMaxDevices = 64;
-constexpr size_t kStaticBytes = 3u << 20;
+constexpr size_t kStaticBytes = 4u << 20;
 
 static __device__ __align__(256) unsigned char g_scratch[kStaticBytes];
 
@@ -57,9 +57,9 @@ inline size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Byte offsets of every array inside the static scratch.
 struct Layout {
     size_t level, leaf, parent, child, xyz, nbr, level_first, leaf_node;
-    size_t mom64, mom32, loc, status, counter;
+    size_t mom64, mom32, rec64, loc, status, counter;
     size_t entries, tab64, tab32, list_first, list_len, items;
-    size_t hoff_far, hoff_near, lattice_nodes;
+    size_t hoff_far, hoff_near, lattice_nodes, off64, off32;
     size_t end;
 };
 
@@ -82,6 +82,7 @@ Layout make_layout() {
     l.leaf_node = take(sizeof(int) * kMaxNodes);
     l.mom64 = take(sizeof(double) * kMom * cells);
     l.mom32 = take(sizeof(float) * kMom * cells);
+    l.rec64 = take(sizeof(double) * kRec * cells);
     l.loc = take(sizeof(double) * kLoc * cells);
     l.status = take(sizeof(int));
     l.counter = take(sizeof(int));
@@ -94,6 +95,8 @@ Layout make_layout() {
     l.hoff_far = take(sizeof(int) * kMaxEntries);
     l.hoff_near = take(sizeof(int) * kMaxEntries);
     l.lattice_nodes = take(sizeof(int) * kMaxNodes);
+    l.off64 = take(sizeof(double) * 4 * kMaxEntries);
+    l.off32 = take(sizeof(float) * 4 * kMaxEntries);
     l.end = o;
     return l;
 }
@@ -185,6 +188,8 @@ extern "C" int ot_solve_gravity_static(const ot_tree_desc* desc, const double* r
         (e = put(base, l.entries, p.entries.data(), p.entries.size(), s)) ||
         (e = put(base, l.tab64, &p.tab64[0].x, 4 * p.tab64.size(), s)) ||
         (e = put(base, l.tab32, &p.tab32[0].x, 4 * p.tab32.size(), s)) ||
+        (e = put(base, l.off64, &p.off64[0].x, 4 * p.off64.size(), s)) ||
+        (e = put(base, l.off32, &p.off32[0].x, 4 * p.off32.size(), s)) ||
         (e = put(base, l.list_first, p.list_first, kNumLists, s)) ||
         (e = put(base, l.list_len, p.list_len, kNumLists, s)) ||
         (e = put(base, l.hoff_far, p.hoff_far.data(), p.hoff_far.size(), s)) ||
@@ -196,6 +201,7 @@ extern "C" int ot_solve_gravity_static(const ot_tree_desc* desc, const double* r
     // the item counter and the status word
     if (cudaMemsetAsync(base + l.mom64, 0, sizeof(double) * kMom * cells, s) != cudaSuccess ||
         cudaMemsetAsync(base + l.mom32, 0, sizeof(float) * kMom * cells, s) != cudaSuccess ||
+        cudaMemsetAsync(base + l.rec64, 0, sizeof(double) * kRec * cells, s) != cudaSuccess ||
         cudaMemsetAsync(base + l.loc, 0, sizeof(double) * kLoc * cells, s) != cudaSuccess ||
         cudaMemsetAsync(base + l.status, 0, sizeof(int), s) != cudaSuccess ||
         cudaMemsetAsync(base + l.counter, 0, sizeof(int), s) != cudaSuccess) {
@@ -217,6 +223,7 @@ extern "C" int ot_solve_gravity_static(const ot_tree_desc* desc, const double* r
     d.level_first = (const int*)(base + l.level_first);
     d.mom64 = (double*)(base + l.mom64);
     d.mom32 = (float*)(base + l.mom32);
+    d.rec64 = (double*)(base + l.rec64);
     d.inv_side8 = 8.0 / h.size;
     d.loc = (double*)(base + l.loc);
     d.status = (int*)(base + l.status);
@@ -224,6 +231,8 @@ extern "C" int ot_solve_gravity_static(const ot_tree_desc* desc, const double* r
     dp.entries = (const int*)(base + l.entries);
     dp.tab64 = (const double2*)(base + l.tab64);
     dp.tab32 = (const float4*)(base + l.tab32);
+    dp.off64 = (const double2*)(base + l.off64);
+    dp.off32 = (const float4*)(base + l.off32);
     dp.list_first = (const int*)(base + l.list_first);
     dp.list_len = (const int*)(base + l.list_len);
     dp.items = (const int4*)(base + l.items);

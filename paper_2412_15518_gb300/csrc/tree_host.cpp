@@ -155,6 +155,8 @@ int build_stencil(const HostTree& t, double theta, HostPlan& p) {
         p.tab64.push_back({1.0 / r, d[0] / r3, d[1] / r3, d[2] / r3});
         p.tab32.push_back({(float)(1.0 / r), (float)(d[0] / r3), (float)(d[1] / r3),
                            (float)(d[2] / r3)});
+        p.off64.push_back({(double)d[0], (double)d[1], (double)d[2], 0.0});
+        p.off32.push_back({(float)d[0], (float)d[1], (float)d[2], 0.0f});
     };
     for (int par = 0; par < 8; par++) {
         int pp[3] = {par & 1, (par >> 1) & 1, par >> 2};

@@ -49,6 +49,8 @@ struct HostPlan {
     std::vector<int> entries;         // packed offsets (see pack_entry)
     std::vector<Tab4d> tab64;         // (1/|d|, d/|d|^3) per entry, cell units
     std::vector<Tab4f> tab32;
+    std::vector<Tab4d> off64;         // (dx, dy, dz, 0) per entry
+    std::vector<Tab4f> off32;
     int list_first[kNumLists] = {0};
     int list_len[kNumLists] = {0};
     int n_near = 0;                   // near offsets (first entries of every list)
