@@ -184,7 +184,9 @@ void m2l(const Mom<T>& A, const Mom<T>& B, double G, int am, Loc<T>& out) {
             for (int k = 0; k < 3; k++) out.L3[i][j][k] += T(-G) * B.m * D.D3[i][j][k];
         }
     if (am) {
-        T ratio = B.m / A.m;
+        // A cell of zero mass has M3 = 0 for non-negative densities; the
+        // product of its undefined mass ratio and that zero tensor is taken as 0.
+        T ratio = val(A.m) != 0.0 ? B.m / A.m : T(0.0);
         for (int i = 0; i < 3; i++) {
             T t = T(0.0);
             for (int j = 0; j < 3; j++)
@@ -197,13 +199,23 @@ void m2l(const Mom<T>& A, const Mom<T>& B, double G, int am, Loc<T>& out) {
 }
 
 // U2: moments of a parent from its children (exact shift to the parent COM).
-template <class T> void m2m(const Mom<T>* ch, int n, Mom<T>& P) {
+// A parent of zero mass has no centre of mass; its moments are taken about
+// `centre` (its geometric centre), or about the mean of the children's
+// positions when no centre is given.
+template <class T> void m2m(const Mom<T>* ch, int n, Mom<T>& P, const double* centre = nullptr) {
     zero_mom(P);
     for (int c = 0; c < n; c++) P.m += ch[c].m;
     for (int i = 0; i < 3; i++) {
         T s = T(0.0);
-        for (int c = 0; c < n; c++) s += ch[c].m * ch[c].X[i];
-        P.X[i] = s / P.m;
+        if (val(P.m) != 0.0) {
+            for (int c = 0; c < n; c++) s += ch[c].m * ch[c].X[i];
+            P.X[i] = s / P.m;
+        } else if (centre) {
+            P.X[i] = T(centre[i]);
+        } else {
+            for (int c = 0; c < n; c++) s += ch[c].X[i];
+            P.X[i] = s / T((double)n);
+        }
     }
     for (int c = 0; c < n; c++) {
         T d[3];
@@ -379,7 +391,10 @@ template <class T> void upward(const Tree& t, const T* rho, Work<T>& w) {
                                                  2 * cz + ((c >> 2) & 1));
                                 ch[c] = w.mom[L + 1][ci];
                             }
-                            m2m(ch, 8, M);
+                            const double ctr[3] = {t.origin[0] + (cx + 0.5) * h,
+                                                   t.origin[1] + (cy + 0.5) * h,
+                                                   t.origin[2] + (cz + 0.5) * h};
+                            m2m(ch, 8, M, ctr);
                         }
                     }
         }
@@ -692,7 +707,9 @@ void m2l_reverse(const Mom<double>& A, const Mom<double>& B, double G, int am,
                 b3[i][j][k] = -G * (-(1.0 / 6.0) * E.L0 * B.M3[i][j][k] +
                                     0.5 * E.L1[i] * B.M2[j][k] + E.L3[i][j][k] * B.m);
         }
-    double ratio = B.m / A.m;
+    // zero-mass target: ratio term taken as 0 (and not differentiated)
+    const bool live_A = A.m != 0.0;
+    double ratio = live_A ? B.m / A.m : 0.0;
     for (int i = 0; i < 3; i++)
         for (int j = 0; j < 3; j++)
             for (int k = 0; k < 3; k++)
@@ -730,7 +747,7 @@ void m2l_reverse(const Mom<double>& A, const Mom<double>& B, double G, int am,
                             bA->M3[j][k][l] += t * (-ratio);
                             s += t * A.M3[j][k][l];
                         }
-            bA->m += s * (B.m / (A.m * A.m));
+            if (live_A) bA->m += s * (B.m / (A.m * A.m));
         }
     }
     if (bB) {
@@ -761,7 +778,7 @@ void m2l_reverse(const Mom<double>& A, const Mom<double>& B, double G, int am,
                             bB->M3[j][k][l] += t;
                             s += t * A.M3[j][k][l];
                         }
-            bB->m += s * (-1.0 / A.m);
+            if (live_A) bB->m += s * (-1.0 / A.m);
         }
     }
 }
@@ -836,10 +853,10 @@ void m2m_reverse(const Mom<double>* ch, int n, const Mom<double>& P, const MomBa
             Xb[i] -= dbar[i];
         }
     }
-    // X_P = sum m_k X_k / M,  M = sum m_k
+    // X_P = sum m_k X_k / M,  M = sum m_k (a constant centre when M = 0)
     for (int c = 0; c < n; c++) {
         double s = 0.0;
-        for (int i = 0; i < 3; i++) {
+        for (int i = 0; i < 3 && P.m != 0.0; i++) {
             cb[c].X[i] += Xb[i] * ch[c].m / P.m;
             s += Xb[i] * (ch[c].X[i] - P.X[i]) / P.m;
         }

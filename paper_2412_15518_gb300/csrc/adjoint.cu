@@ -392,6 +392,8 @@ __global__ void __launch_bounds__(128) k_m2m_reverse(DevTree t, int first, doubl
             for (int n = 0; n < 10; n++) mombar[(10 + n) * N + cc] += B3[n];
         }
         // second pass: the centre of mass X_P = sum m_k X_k / M and M = sum m_k
+        // (the geometric centre, a constant, when M = 0)
+        const double iM = M != 0.0 ? 1.0 / M : 0.0;
 #pragma unroll 1
         for (int q = 0; q < 8; q++) {
             const long long cc = cix[q];
@@ -399,8 +401,8 @@ __global__ void __launch_bounds__(128) k_m2m_reverse(DevTree t, int first, doubl
             double s = 0.0;
 #pragma unroll
             for (int p = 0; p < 3; p++) {
-                mombar[(1 + p) * N + cc] += Xtot[p] * m / M;
-                s += Xtot[p] * dk[q][p] / M;
+                mombar[(1 + p) * N + cc] += Xtot[p] * m * iM;
+                s += Xtot[p] * dk[q][p] * iM;
             }
             mombar[cc] += s + Bm;
         }

@@ -121,8 +121,10 @@ __host__ __device__ inline void m2l_pair_reverse(
     const double f4 = -7.0 * f3 * ri2;
     const double f5 = -9.0 * f4 * ri2;
     const double R[3] = {x, y, z};
-    const double ratio = mB / mA;
-    const bool useA = am && multiA;  // the target's M3 enters only through the correction
+    // the target's M3 enters only through the correction's mass-ratio term,
+    // which is taken as zero (and has no derivative) for a target of zero mass
+    const bool useA = am && multiA && mA != 0.0;
+    const double ratio = useA ? mB / mA : 0.0;
 
     // contractions of the adjoints with R
     const double E1R = E1[0] * x + E1[1] * y + E1[2] * z;

@@ -91,6 +91,26 @@ __device__ __forceinline__ void load_tail(const DevTree& t, long long c, float* 
     bt[2] = b3[2] + b3[7] + b3[9];
     bt[3] = b2[0] + b2[3] + b2[5];
 }
+// The target's octupole per unit mass, M3_A / m_A, and its trace vector,
+// formed in FP64 once per target (the correction's mass ratio); zero for a
+// target of zero mass (whose M3 is zero for non-negative densities).
+template <class T>
+__device__ __forceinline__ void load_octupole_per_mass(const DevTree& t, long long c, T* a3, T* ta) {
+    const double2* p = reinterpret_cast<const double2*>(t.rec64 + c * kRec);
+    const double m = __ldg(t.rec64 + c * kRec);
+    const double r = m != 0.0 ? 1.0 / m : 0.0;
+    double v[14];
+#pragma unroll
+    for (int q = 0; q < 7; q++) {
+        const double2 w = __ldg(p + 5 + q);
+        v[2 * q] = w.x;
+        v[2 * q + 1] = w.y;
+    }
+#pragma unroll
+    for (int q = 0; q < 10; q++) a3[q] = T(r * v[q]);
+#pragma unroll
+    for (int q = 0; q < 3; q++) ta[q] = T(r * v[10 + q]);
+}
 __device__ __forceinline__ void load_off(const DevPlan& p, int k, double& x, double& y, double& z) {
     const double2 a = __ldg(p.off64 + 2 * k), b = __ldg(p.off64 + 2 * k + 1);
     x = a.x;
@@ -123,12 +143,8 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
     const long long cell = (long long)node * kCells + i + 8 * j + 64 * k;
     T ma, dax, day, daz;
     load_head(t, cell, ma, dax, day, daz);
-    T inv_ma = T(0.0), a3[10], ta[4];
-    if (FULL && AM) {
-        T a2[6];
-        inv_ma = T(1.0) / ma;
-        load_tail(t, cell, a2, a3, ta);
-    }
+    T a3[10], ta[4];
+    if (FULL && AM) load_octupole_per_mass(t, cell, a3, ta);
     Acc<T> A;
     acc_zero(A);
     double n0 = 0.0, n1 = 0.0, n2 = 0.0, n3 = 0.0;  // FP64 near leaf pairs (bulk form)
@@ -175,11 +191,11 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
         const T y = (day - by) - oy;
         const T z = (daz - bz) - oz;
         if (sleaf) {
-            m2l_pair<T, FULL, false, AM>(x, y, z, m, nullptr, nullptr, nullptr, m * inv_ma, a3, ta, A);
+            m2l_pair<T, FULL, false, AM>(x, y, z, m, nullptr, nullptr, nullptr, a3, ta, A);
         } else {
             T b2[6], b3[10], bt[4];
             load_tail(t, sc, b2, b3, bt);
-            m2l_pair<T, FULL, true, AM>(x, y, z, m, b2, b3, bt, m * inv_ma, a3, ta, A);
+            m2l_pair<T, FULL, true, AM>(x, y, z, m, b2, b3, bt, a3, ta, A);
         }
     }
     // scale to physical units: L^(n) * (-G h^-(n+1)), correction * -(G/6) h^-2
@@ -200,9 +216,11 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
         for (int r = 0; r < 10; r++) atomicAdd(loc + (10 + r) * N + cell, scaled(A.L3[r], s4));
     }
     if (AM) {
+        // a_c = -(G/6) h^-2 (S - P)
         const T sa = T(-(G / 6.0) * hi * hi);
 #pragma unroll
-        for (int a = 0; a < 3; a++) atomicAdd(loc + (20 + a) * N + cell, scaled(A.S[a], sa));
+        for (int a = 0; a < 3; a++)
+            atomicAdd(loc + (20 + a) * N + cell, scaled(FULL ? A.S[a] - A.P[a] : A.S[a], sa));
     }
 }
 

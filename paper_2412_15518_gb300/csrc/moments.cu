@@ -92,7 +92,10 @@ __global__ void __launch_bounds__(256) k_m2m(DevTree t, int first) {
     const double M = sum8(m);
     double X[3];
 #pragma unroll
-    for (int s = 0; s < 3; s++) X[s] = sum8(m * pos[s]) / M;
+    for (int s = 0; s < 3; s++) X[s] = sum8(m * pos[s]);  // shuffles: every lane takes part
+    const double iM = M != 0.0 ? 1.0 / M : 0.0;               // zero mass: moments about the centre
+#pragma unroll
+    for (int s = 0; s < 3; s++) X[s] *= iM;
     const double d[3] = {pos[0] - X[0], pos[1] - X[1], pos[2] - X[2]};
     double c2[6], S[16];
 #pragma unroll
@@ -176,7 +179,7 @@ __global__ void __launch_bounds__(256) k_m2m_leafkids(DevTree t, int first) {
     const double M = w[0];
     const double Sx = -w[1], Sy = -w[2], Sz = -w[4];
     const double Sxy = w[3], Sxz = w[5], Syz = w[6], Sxyz = -w[7];
-    const double iM = 1.0 / M;
+    const double iM = M != 0.0 ? 1.0 / M : 0.0;  // zero mass: moments about the centre
     const double X[3] = {0.25 * Sx * iM, 0.25 * Sy * iM, 0.25 * Sz * iM};
     // raw moments about the parent centre (packed xx xy xz yy yz zz, ...)
     const double P2[6] = {0.0625 * M, 0.0625 * Sxy, 0.0625 * Sxz, 0.0625 * M, 0.0625 * Syz, 0.0625 * M};

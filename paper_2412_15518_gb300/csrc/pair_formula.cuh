@@ -8,6 +8,9 @@
 //   R = X_A - X_B, D^(n) = grad^n (1/|R|);
 //   L^(n)_A += -G sum_{m <= 3-n} (-1)^m / m!  M^(m)_B ._m D^(n+m)(R)
 //   a_c,A   += -(G/6) D^(4)(R) ._3 [M3_B - (m_B / m_A) M3_A]
+//            = -(G/6) [S - P],  S = sum_B D4 ._3 M3_B,
+//                               P = sum_B m_B D4 ._3 (M3_A / m_A)
+// (the caller divides the target octupole by m_A once per target, in FP64)
 // With f_k = (-1)^k (2k-1)!! / r^(2k+1), every contraction of a symmetric
 // tensor with D^(n) reduces to a few scalars: for S = M2 (Mx = M2 R,
 // xMx = R.M2.R, tr = trace) and T = M3 (q2 = T:RR, q3 = R.q2, t_i = T_ijj,
@@ -18,15 +21,16 @@
 //   (D4 : M3)_i    = f4 R_i q3 + 3 f3 (q2_i + R_i Rt) + 3 f2 t_i
 // so no D tensor is ever formed.  Everything here is in units of the cell
 // side h (R' = R / h, M2' = M2 / h^2, M3' = M3 / h^3) and without the -G
-// factor; the caller scales L^(n) by -G h^-(n+1) and the correction sum S by
-// -(G/6) h^-2 once per target.
+// factor; the caller scales L^(n) by -G h^-(n+1) and the correction sums S
+// and P by -(G/6) h^-2 once per target.
 #pragma once
 
 namespace otfmm {
 
 template <class T> struct Acc {
     T L0, L1[3], L2[6], L3[10];
-    T S[3];  // correction sum
+    T S[3];  // correction sum of the source octupoles
+    T P[3];  // correction sum of the target octupole per unit mass
 };
 // The Kronecker parts of L2 and L3 are not accumulated: D2 and D3 are
 // traceless, so per pair sum m f1 = -trace(m f2 R R) / 3 and
@@ -39,6 +43,7 @@ template <class T> __host__ __device__ __forceinline__ void acc_zero(Acc<T>& A) 
     for (int i = 0; i < 3; i++) {
         A.L1[i] = T(0.0);
         A.S[i] = T(0.0);
+        A.P[i] = T(0.0);
     }
 #pragma unroll
     for (int i = 0; i < 6; i++) A.L2[i] = T(0.0);
@@ -91,10 +96,10 @@ __host__ __device__ __forceinline__ void contract_rr(const T* c, T xx, T yy, T z
 // of the correction).  SRC_MULTI: the source is an interior cell (has M2, M3).
 // AM: the correction is on.  (x, y, z) = R', m = source mass, b2/b3 = source
 // M2'/M3', bt = the source's M3 trace vector (t_i = M3_ijj) and trace of M2
-// (bt[3]), ratio = m_B / m_A, a3/ta = target M3' and its trace vector.
+// (bt[3]), a3/ta = target M3' / m_A and its trace vector.
 template <class T, bool TGT_FULL, bool SRC_MULTI, bool AM>
 __host__ __device__ __forceinline__ void m2l_pair(T x, T y, T z, T m, const T* b2, const T* b3,
-                                                  const T* bt, T ratio, const T* a3, const T* ta,
+                                                  const T* bt, const T* a3, const T* ta,
                                                   Acc<T>& A) {
     const T r2 = fma_(x, x, fma_(y, y, z * z));
     const T f0 = rsqrt_(r2);
@@ -169,16 +174,15 @@ __host__ __device__ __forceinline__ void m2l_pair(T x, T y, T z, T m, const T* b
         A.L3[8] = fma_(ty3, zz, A.L3[8]);
         A.L3[9] = fma_(tz3, zz, A.L3[9]);
         if (AM) {
-            // - (m_B / m_A) D4 : M3_A = -ratio (R k' + u q2_A + w t_A)
+            // P += m_B D4 : (M3_A / m_A) = m_B (R k' + u q2_A + w t_A)
             T qx, qy, qz;
             contract_rr(a3, xx, yy, zz, xy2, xz2, yz2, qx, qy, qz);
             const T q3 = fma_(x, qx, fma_(y, qy, z * qz));
             const T Rt = fma_(x, ta[0], fma_(y, ta[1], z * ta[2]));
-            const T nr = -ratio;
-            const T nk = nr * fma_(u, Rt, f4 * q3), nu = nr * u, nw = nr * w;
-            A.S[0] = fma_(nk, x, fma_(nu, qx, fma_(nw, ta[0], A.S[0])));
-            A.S[1] = fma_(nk, y, fma_(nu, qy, fma_(nw, ta[1], A.S[1])));
-            A.S[2] = fma_(nk, z, fma_(nu, qz, fma_(nw, ta[2], A.S[2])));
+            const T mk = m * fma_(u, Rt, f4 * q3), mu = m * u, mw = m * w;
+            A.P[0] = fma_(mk, x, fma_(mu, qx, fma_(mw, ta[0], A.P[0])));
+            A.P[1] = fma_(mk, y, fma_(mu, qy, fma_(mw, ta[1], A.P[1])));
+            A.P[2] = fma_(mk, z, fma_(mu, qz, fma_(mw, ta[2], A.P[2])));
         }
     }
 }

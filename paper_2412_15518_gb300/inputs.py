@@ -46,20 +46,21 @@ def cell_centres(leaves, origin=(0.0, 0.0, 0.0), size=1.0) -> np.ndarray:
     return np.asarray(origin) + (base[:, None, :] + loc[None] + 0.5) * h[:, None, None]
 
 
-def star_density(x: np.ndarray, stars) -> np.ndarray:
+def star_density(x: np.ndarray, stars, atmosphere: float = ATMOSPHERE) -> np.ndarray:
     """max(atmosphere, sum_s rho_s (1 - |x - c_s|^2 / R_s^2)_+^1.5) at points x [..., 3]."""
     rho = np.zeros(x.shape[:-1])
     for c, rc, R in stars:
         q = 1.0 - np.sum((x - np.asarray(c)) ** 2, -1) / (R * R)
         rho += rc * np.clip(q, 0.0, None) ** 1.5
-    return np.maximum(rho, ATMOSPHERE)
+    return np.maximum(rho, atmosphere)
 
 
 def density(leaves, stars, seed: int = 0, noise: float = 1e-3, origin=(0.0, 0.0, 0.0),
-            size=1.0) -> np.ndarray:
+            size=1.0, atmosphere: float = ATMOSPHERE) -> np.ndarray:
     """Star densities at cell centres times (1 + noise * u), u ~ U[-1, 1] drawn
-    from PCG64(seed) in leaf order."""
-    rho = star_density(cell_centres(leaves, origin, size), stars)
+    from PCG64(seed) in leaf order.  atmosphere = 0 leaves the space outside
+    the stars empty (cells of exactly zero mass)."""
+    rho = star_density(cell_centres(leaves, origin, size), stars, atmosphere)
     u = np.random.Generator(np.random.PCG64(seed)).uniform(-1.0, 1.0, size=rho.shape)
     return np.ascontiguousarray(rho * (1.0 + noise * u))
 

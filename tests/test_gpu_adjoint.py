@@ -46,6 +46,11 @@ CASES = {
         I.amr_leaves(3, 2e-4, I.BINARY)),
     "amr_l2_ragged": lambda: (lambda lv: (lv, I.density(lv, I.BINARY, 4)))(
         I.amr_leaves(2, 5e-4, I.BINARY, lmin=1)),
+    # empty space outside the stars: cells and whole interior cells of zero mass
+    "sphere_l1_empty": lambda: (lambda lv: (lv, I.density(lv, I.SPHERE, 0, atmosphere=0.0)))(
+        I.uniform_leaves(1, seed=3)),
+    "amr_l3_empty": lambda: (lambda lv: (lv, I.density(lv, I.BINARY, 5, atmosphere=0.0)))(
+        I.amr_leaves(3, 2e-4, I.BINARY)),
     "root_leaf": lambda: (np.array([[0, 0, 0, 0]], np.int32),
                           I.density(np.array([[0, 0, 0, 0]], np.int32), I.SPHERE, 2)),
 }

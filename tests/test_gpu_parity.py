@@ -50,6 +50,11 @@ CASES = {
     "sphere_l1_shuffled": lambda: (lambda lv: (lv, I.density(lv, I.SPHERE, 0)))(
         I.uniform_leaves(1, seed=3)),
     "amr_l3_seams": small_amr,
+    # empty space outside the stars: cells and whole interior cells of zero mass
+    "sphere_l1_empty": lambda: (lambda lv: (lv, I.density(lv, I.SPHERE, 0, atmosphere=0.0)))(
+        I.uniform_leaves(1, seed=3)),
+    "amr_l3_empty": lambda: (lambda lv: (lv, I.density(lv, I.BINARY, 5, atmosphere=0.0)))(
+        I.amr_leaves(3, 2e-4, I.BINARY)),
     "root_leaf": lambda: (np.array([[0, 0, 0, 0]], np.int32),
                           I.density(np.array([[0, 0, 0, 0]], np.int32), I.SPHERE, 2)),
     "amr_l2_ragged": lambda: (lambda lv: (lv, I.density(lv, I.BINARY, 4)))(
@@ -112,7 +117,8 @@ def test_fp32_bulk_binary_l3(fmm, binary_l3):
     assert rel(g, g_o) < TOL32
 
 
-@pytest.mark.parametrize("case", ["sphere_l1_shuffled", "amr_l3_seams", "amr_l2_ragged"])
+@pytest.mark.parametrize("case", ["sphere_l1_shuffled", "amr_l3_seams", "amr_l2_ragged",
+                                  "amr_l3_empty"])
 def test_fp32_bulk_matches_oracle(fmm, case):
     lv, rho = CASES[case]()
     phi, g = gpu_solve(fmm, lv, rho, precision=fmm.OT_PRECISION_FP32_BULK)

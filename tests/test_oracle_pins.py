@@ -495,3 +495,79 @@ def test_gradient_self_term(sphere):
     g1 = O.gradient(lv, rho, w1, w2, self_term=True)
     C = 3 * (np.log(2 + np.sqrt(3)) - np.pi / 6)
     assert np.abs(g1 - g0 + w1 * (1.0 / 16) ** 2 * C).max() < 1e-12 * np.abs(g0).max()
+
+
+# --------------------------------------------------------------------------
+# Empty space.  A cell of zero total mass has no centre of mass and no mass
+# ratio; the readings are: its moments are taken about its geometric centre,
+# and the correction's target term -(m_B / m_A) M3_A (M3_A = 0 for
+# non-negative densities) is zero.  Both must be the limit of a vanishing
+# uniform atmosphere, where every quantity is defined.
+EPS_ATM = 1e-150
+
+
+def empty_and_limit(lv, stars, seed):
+    rho0 = I.density(lv, stars, seed, atmosphere=0.0)
+    rho_eps = np.where(rho0 == 0.0, EPS_ATM, rho0)   # uniform: no noise outside the stars
+    return rho0, rho_eps
+
+
+@pytest.fixture(scope="module")
+def empty_sphere():
+    lv = I.uniform_leaves(1)
+    rho0, rho_eps = empty_and_limit(lv, I.SPHERE, 0)
+    assert (rho0 == 0.0).mean() > 0.4      # most of the cube is empty
+    return lv, rho0, rho_eps
+
+
+@pytest.fixture(scope="module")
+def empty_amr():
+    lv = I.amr_leaves(3, 2e-4, I.BINARY)
+    rho0, rho_eps = empty_and_limit(lv, I.BINARY, 5)
+    return lv, rho0, rho_eps
+
+
+@pytest.mark.parametrize("which", ["empty_sphere", "empty_amr"])
+@pytest.mark.parametrize("am", [True, False])
+def test_zero_mass_cells_are_the_vanishing_atmosphere_limit(which, am, request):
+    lv, rho0, rho_eps = request.getfixturevalue(which)
+    phi0, g0 = O.solve(lv, rho0, am_correction=am)
+    phie, ge = O.solve(lv, rho_eps, am_correction=am)
+    assert np.isfinite(phi0).all() and np.isfinite(g0).all()
+    assert rel(phi0, phie) < 1e-13
+    assert rel(g0, ge) < 1e-13
+
+
+def test_zero_mass_cells_theta_to_zero_equals_direct_sum(empty_sphere):
+    lv, rho0, _ = empty_sphere
+    phi_d, g_d = O.direct(lv, rho0)
+    phi, g = O.solve(lv, rho0, theta=0.03)
+    assert rel(phi, phi_d) < 1e-13
+    assert rel(g, g_d) < 1e-13
+
+
+@pytest.mark.parametrize("which", ["empty_sphere", "empty_amr"])
+def test_zero_mass_cells_conserve_momentum_and_angular_momentum(which, request):
+    lv, rho0, _ = request.getfixturevalue(which)
+    _, g = O.solve(lv, rho0)
+    mom, ang = residuals(lv, rho0, g)
+    assert mom < 1e-14
+    assert ang < 1e-12
+
+
+@pytest.mark.parametrize("which", ["empty_sphere", "empty_amr"])
+def test_zero_mass_gradient(which, request):
+    """The gradient is finite; on cells inside the stars it equals the
+    gradient of the vanishing-atmosphere field, and it agrees with the
+    forward-mode derivative along directions inside the stars."""
+    lv, rho0, rho_eps = request.getfixturevalue(which)
+    w1, w2 = I.weights(lv.shape[0])
+    gr0 = O.gradient(lv, rho0, w1, w2)
+    assert np.isfinite(gr0).all()
+    star = rho0 > 0.0
+    gre = O.gradient(lv, rho_eps, w1, w2)
+    assert np.abs(gr0 - gre)[star].max() < 1e-12 * np.abs(gre[star]).max()
+    v = np.random.default_rng(3).normal(size=rho0.shape) * rho0
+    _, _, dphi, dg = O.solve_jvp(lv, rho0, v)
+    jvp = (w1 * dphi).sum() + (w2 * dg).sum()
+    assert abs((gr0 * v).sum() - jvp) < 1e-12 * abs(jvp)
