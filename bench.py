@@ -369,6 +369,10 @@ def run_ours(args):
                 "interact_fp32_tflops": a32, "frac_of_fp32_peak": a32 / PEAK_FP32_TFLOPS,
                 "mixed_bound_ms": mixed_ms,
                 "frac_of_mixed_bound": mixed_ms / statistics.mean(int32)}
+            i32 = tree.info()
+            extra["fp32_bulk"]["tuned"] = {"chunk": i32["tuned_chunk"],
+                                           "ctas_per_sm": i32["tuned_ctas_per_sm"],
+                                           "work_items": i32["n_work_items"]}
             # the adjoint (FP64): dJ/drho for J = sum(w1 phi + w2 . g)
             w1n, w2n = inputs.weights(leaves.shape[0])
             w1, w2 = torch.from_numpy(w1n).cuda(), torch.from_numpy(w2n).cuda()

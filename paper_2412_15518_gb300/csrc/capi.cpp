@@ -57,6 +57,8 @@ struct ot_tree {
     double* d_mom64 = nullptr;
     double* d_rec64 = nullptr;
     float* d_mom32 = nullptr;
+    float* d_m32 = nullptr;
+    float* d_oct32 = nullptr;
     double* d_loc = nullptr;
     int* d_status = nullptr;
     // device arrays of the plan
@@ -68,6 +70,8 @@ struct ot_tree {
     int* d_list_first = nullptr;
     int* d_list_len = nullptr;
     int4* d_items = nullptr;
+    int* d_item_entries = nullptr;
+    size_t item_entries_cap = 0;
     int4* d_items_adj = nullptr;
     size_t items_adj_cap = 0;
     int* d_hoff_far = nullptr;
@@ -89,7 +93,8 @@ struct ot_tree {
     // graphs
     cudaStream_t cap_stream = nullptr;
     cudaStream_t side_stream = nullptr;      // second branch: the lattice kernel
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t far_stream = nullptr;       // third branch (FP32 form): FP32 far lattice pairs
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join_far = nullptr;
     std::vector<GraphEntry> graphs;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // solve start, interact start/end, solve end
     int64_t workspace_bytes = 0;
@@ -145,6 +150,8 @@ DevTree dev_tree(const ot_tree* t) {
     d.level_first = t->d_level_first;
     d.mom64 = t->d_mom64;
     d.mom32 = t->d_mom32;
+    d.m32 = t->d_m32;
+    d.oct32 = t->d_oct32;
     d.rec64 = t->d_rec64;
     d.inv_side8 = 8.0 / t->h.size;
     d.loc = t->d_loc;
@@ -162,8 +169,10 @@ DevPlan dev_plan(const ot_tree* t) {
     p.list_first = t->d_list_first;
     p.list_len = t->d_list_len;
     p.items = t->d_items;
+    p.item_entries = t->d_item_entries;
     p.n_items = (int)t->plan.items.size();
     p.counter = t->d_counter;
+    p.near_d2 = t->plan.near_d2;
     return p;
 }
 
@@ -213,12 +222,18 @@ int ensure_plan(ot_tree* t, double theta) {
         t->items_cap = p.items.size();
         TRY(dalloc(t, &t->d_items, t->items_cap));
     }
+    if (p.item_entries.size() > t->item_entries_cap || !t->d_item_entries) {
+        cudaFree(t->d_item_entries);
+        t->item_entries_cap = std::max<size_t>(1, p.item_entries.size());
+        TRY(dalloc(t, &t->d_item_entries, t->item_entries_cap));
+    }
     if (p.items_adj.size() > t->items_adj_cap) {
         cudaFree(t->d_items_adj);
         t->items_adj_cap = p.items_adj.size();
         TRY(dalloc(t, &t->d_items_adj, t->items_adj_cap));
     }
     TRY(upload(t->d_entries, p.entries));
+    TRY(upload(t->d_item_entries, p.item_entries));
     TRY(upload(t->d_hoff_far, p.hoff_far));
     TRY(upload(t->d_hoff_near, p.hoff_near));
     TRY(upload(t->d_lattice_nodes, p.lattice_nodes));
@@ -286,19 +301,24 @@ void enqueue_moments(ot_tree* t, const double* rho, cudaStream_t s) {
 int enqueue_interact(ot_tree* t, const ot_solve_opts& o, cudaStream_t s) {
     DevTree d = dev_tree(t);
     // the expansions were zeroed by the upward pass (leaf and M2M kernels).
-    // The lattice kernel (leaf-leaf pairs) and the general kernel (pairs with
-    // an interior cell) only add into the expansions with atomics, so they
-    // run as two concurrent branches: in the bulk form one is mostly FP64 and
-    // the other mostly FP32 work, and the two pipes overlap.
+    // The lattice kernels (leaf-leaf pairs) and the general kernel (pairs
+    // with an interior cell) only add into the expansions with atomics, so
+    // they run as concurrent branches: in the bulk form the near-pair lattice
+    // kernel is FP64 work and the other two FP32 work, and the pipes overlap.
+    const bool bulk = o.precision == OT_PRECISION_FP32_BULK;
     TRYC(cudaEventRecord(t->ev_fork, s));
     TRYC(cudaStreamWaitEvent(t->side_stream, t->ev_fork, 0));
-    launch_lattice(d, dev_plan(t), dev_lattice(t), o.precision, o.G, t->side_stream);
+    if (bulk) TRYC(cudaStreamWaitEvent(t->far_stream, t->ev_fork, 0));
+    launch_lattice(d, dev_plan(t), dev_lattice(t), o.precision, o.G, t->side_stream,
+                   bulk ? t->far_stream : nullptr);
     TRYC(cudaEventRecord(t->ev_join, t->side_stream));
+    if (bulk) TRYC(cudaEventRecord(t->ev_join_far, t->far_stream));
     TRYC(cudaMemsetAsync(t->d_counter, 0, sizeof(int), s));
     int ctas = std::max(1, t->num_sms * t->ctas_per_sm);
     launch_interact(d, dev_plan(t), o.precision, o.G, o.am_correction ? 1 : 0, ctas,
                     t->warps_per_cta, s);
     TRYC(cudaStreamWaitEvent(s, t->ev_join, 0));
+    if (bulk) TRYC(cudaStreamWaitEvent(s, t->ev_join_far, 0));
     TRYC(cudaGetLastError());
     return OT_OK;
 }
@@ -415,7 +435,9 @@ int ot_build_tree(const ot_tree_desc* desc, int device, ot_tree** out) {
         (e = dalloc(t, &t->d_xyz, 3 * N)) || (e = dalloc(t, &t->d_nbr, 27 * N)) ||
         (e = dalloc(t, &t->d_level_first, h.level_first.size())) ||
         (e = dalloc(t, &t->d_leaf_node, (size_t)h.n_leaf)) || (e = dalloc(t, &t->d_mom64, kMom * C)) ||
-        (e = dalloc(t, &t->d_mom32, kMom * C)) || (e = dalloc(t, &t->d_rec64, kRec * C)) || (e = dalloc(t, &t->d_loc, kLoc * C)) ||
+        (e = dalloc(t, &t->d_mom32, kMom * C)) || (e = dalloc(t, &t->d_rec64, kRec * C)) ||
+        (e = dalloc(t, &t->d_m32, C)) || (e = dalloc(t, &t->d_oct32, kOct * C)) ||
+        (e = dalloc(t, &t->d_loc, kLoc * C)) ||
         (e = dalloc(t, &t->d_status, 1)) || (e = dalloc(t, &t->d_list_first, kNumLists)) ||
         (e = dalloc(t, &t->d_list_len, kNumLists)) || (e = dalloc(t, &t->d_counter, 1)) ||
         (e = dalloc(t, &t->d_rho_in, (size_t)h.n_leaf * kCells)) ||
@@ -430,12 +452,16 @@ int ot_build_tree(const ot_tree_desc* desc, int device, ot_tree** out) {
     // leaf cells keep dX = M2 = M3 = 0 for the life of the tree
     if (cudaMemset(t->d_mom64, 0, sizeof(double) * kMom * C) != cudaSuccess ||
         cudaMemset(t->d_mom32, 0, sizeof(float) * kMom * C) != cudaSuccess ||
+        cudaMemset(t->d_m32, 0, sizeof(float) * C) != cudaSuccess ||
+        cudaMemset(t->d_oct32, 0, sizeof(float) * kOct * C) != cudaSuccess ||
         cudaMemset(t->d_rec64, 0, sizeof(double) * kRec * C) != cudaSuccess ||
         cudaMemset(t->d_status, 0, sizeof(int)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&t->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&t->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&t->far_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&t->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&t->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&t->ev_join_far, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreate(&t->ev[0]) != cudaSuccess || cudaEventCreate(&t->ev[1]) != cudaSuccess ||
         cudaEventCreate(&t->ev[2]) != cudaSuccess || cudaEventCreate(&t->ev[3]) != cudaSuccess) {
         cudaGetLastError();
@@ -455,15 +481,18 @@ void ot_destroy_tree(ot_tree* t) {
         destroy_graphs(t);
         if (t->cap_stream) cudaStreamDestroy(t->cap_stream);
         if (t->side_stream) cudaStreamDestroy(t->side_stream);
+        if (t->far_stream) cudaStreamDestroy(t->far_stream);
         if (t->ev_fork) cudaEventDestroy(t->ev_fork);
         if (t->ev_join) cudaEventDestroy(t->ev_join);
+        if (t->ev_join_far) cudaEventDestroy(t->ev_join_far);
         for (cudaEvent_t e : t->ev)
             if (e) cudaEventDestroy(e);
         void* ptrs[] = {t->d_level, t->d_leaf, t->d_parent, t->d_child, t->d_xyz, t->d_nbr,
                         t->d_level_first, t->d_leaf_node, t->d_mom64, t->d_mom32, t->d_rec64, t->d_loc,
+                        t->d_m32, t->d_oct32,
                         t->d_status, t->d_entries, t->d_tab64, t->d_tab32, t->d_list_first,
                         t->d_list_len, t->d_items, t->d_counter, t->d_rho_in, t->d_phi_out,
-                        t->d_hoff_far, t->d_hoff_near, t->d_lattice_nodes, t->d_items_adj,
+                        t->d_hoff_far, t->d_hoff_near, t->d_lattice_nodes, t->d_items_adj, t->d_item_entries,
                         t->d_off64, t->d_off32,
                         t->d_g_out, t->d_locbar, t->d_mombar};
         for (void* p : ptrs)
@@ -556,6 +585,7 @@ int ot_gravity_backward(ot_tree* t, const double* rho, const double* w1, const d
     TRYC(cudaMemsetAsync(t->d_counter, 0, sizeof(int), s));
     DevPlan pa = dev_plan(t);
     pa.items = t->d_items_adj;
+    pa.item_entries = nullptr;  // the adjoint's items range over the lists
     pa.n_items = (int)t->plan.items_adj.size();
     launch_m2l_reverse(d, pa, t->d_locbar, t->d_mombar, o.G, o.am_correction ? 1 : 0,
                        std::max(1, t->num_sms * 4), s);
@@ -583,7 +613,7 @@ int ot_autotune(ot_tree* t, const double* rho, double* phi, double* g, const ot_
     TRYC(cudaEventCreate(&e0));
     TRYC(cudaEventCreate(&e1));
     const int chunks[] = {32, 64, 128, 263};
-    const int cps[] = {2, 4, 8};
+    const int cps[] = {1, 2, 4, 8};
     float best = 1e30f;
     int bc = t->chunk, bp = t->ctas_per_sm;
     int err = OT_OK;

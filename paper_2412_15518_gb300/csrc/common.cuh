@@ -12,7 +12,10 @@
 //                 per-cell records [n_cells][24] (the 20 moments, the M3
 //                 trace vector t_i = M3_ijj and trace(M2)) and FP32 records
 //                 [n_cells][20], read by the interaction kernels (a source is
-//                 a few 16-byte loads)
+//                 a few 16-byte loads); FP32 leaf masses [n_cells] (the
+//                 lattice kernel's halo); FP32 octupole per unit mass
+//                 [n_cells][16] of interior cells (M3 / m, its trace vector;
+//                 the correction's target term)
 //   expansions    23 components: L0, L1(3), L2(6), L3(10), ac(3), physical
 //                 units, FP64
 // Packed symmetric index orders: M2/L2 = xx xy xz yy yz zz;
@@ -20,6 +23,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cstring>
 #include <cuda_runtime.h>
 
 namespace otfmm {
@@ -28,6 +32,8 @@ constexpr int kCells = 512;      // 8^3 cells per node (Sec. 4.3.2)
 constexpr int kMom = 20;         // moment components per cell
 constexpr int kRec = 24;         // per-cell record: 20 moments, M3 trace vector, M2 trace
 constexpr int kLoc = 23;         // expansion components per cell (+ correction)
+constexpr int kOct = 16;         // per-cell FP32 octupole record: M3 / m (10), trace vector (3), pad
+constexpr int kMaxLevels = 16;   // levels 0..15
 
 // Status word codes latched by kernels (never trapped).
 constexpr int kStatusBadIndex = 1;
@@ -50,10 +56,81 @@ struct DevTree {
     double* mom64;              // [20][n_cells]
     double* rec64;              // [n_cells][24]
     float* mom32;               // [n_cells][20]
+    float* m32;                 // [n_cells] leaf masses (FP32)
+    float* oct32;               // [n_cells][16] interior cells: M3 / m, trace vector
     double inv_side8;           // 8 / size: 1/h at level 0
     double* loc;                // [23][n_cells]
     int* status;                // device status word
 };
+
+// Per-level factors from cell units to physical units, computed on the host
+// for each solve (they hold G): s[L][n] = -G h_L^-(n+1) for the expansion
+// orders n = 0..3, s[L][4] = -(G/6) h_L^-2 for the correction.
+struct LevelScales {
+    double s64[kMaxLevels][5];
+    float s32[kMaxLevels][5];
+};
+
+inline LevelScales level_scales(double inv_side8, double G) {
+    LevelScales r;
+    for (int L = 0; L < kMaxLevels; L++) {
+        const double hi = inv_side8 * (double)(1 << L);
+        const double s1 = -G * hi, s2 = s1 * hi;
+        const double v[5] = {s1, s2, s2 * hi, s2 * hi * hi, -(G / 6.0) * hi * hi};
+        for (int n = 0; n < 5; n++) {
+            r.s64[L][n] = v[n];
+            r.s32[L][n] = (float)v[n];
+        }
+    }
+    return r;
+}
+
+// Exact IEEE-754 binary32 -> binary64 widening by integer operations only
+// (on this GPU the hardware conversion issues on the FP64 pipe, at 1/64 of
+// the FP32 rate).  Normal numbers: the exponent is rebiased (127 -> 1023) and
+// the 23-bit fraction moved to the top of the 52-bit one.  Subnormals
+// (e = 0, f != 0): the fraction is shifted until its leading one reaches the
+// implicit bit, and the exponent lowered by the shift.  Zeros keep their
+// sign; infinities and NaNs get the all-ones exponent (a NaN keeps its
+// payload with the quiet bit set).
+__host__ __device__ __forceinline__ unsigned clz32(unsigned x) {
+#ifdef __CUDA_ARCH__
+    return (unsigned)__clz((int)x);
+#else
+    return x ? (unsigned)__builtin_clz(x) : 32u;
+#endif
+}
+__host__ __device__ __forceinline__ double widen(float f) {
+    unsigned u;
+#ifdef __CUDA_ARCH__
+    u = __float_as_uint(f);
+#else
+    std::memcpy(&u, &f, sizeof u);
+#endif
+    const unsigned sign = u & 0x80000000u;
+    const unsigned e = (u >> 23) & 0xffu;
+    unsigned m = u & 0x7fffffu;
+    unsigned E = e + 896u;                          // normal: rebias
+    if (e == 0u) {                                  // zero or subnormal
+        const unsigned sh = clz32(m) - 8u;          // leading one to bit 23
+        m = (m << sh) & 0x7fffffu;
+        E = m == 0u && sh == 24u ? 0u : 897u - sh;  // a zero keeps E = 0
+    }
+    if (e == 0xffu) {                               // infinity or NaN
+        E = 0x7ffu;
+        if (m) m |= 0x400000u;                      // quiet NaN
+    }
+    const unsigned hi = sign | (E << 20) | (m >> 3);
+    const unsigned lo = m << 29;
+#ifdef __CUDA_ARCH__
+    return __hiloint2double((int)hi, (int)lo);
+#else
+    const unsigned long long b = ((unsigned long long)hi << 32) | lo;
+    double d;
+    std::memcpy(&d, &b, sizeof d);
+    return d;
+#endif
+}
 
 // Stencil entries of a plan: int code = (dx+16) | (dy+16)<<5 | (dz+16)<<10 |
 // near<<15; lists are contiguous ranges of the entry array.
@@ -66,9 +143,15 @@ struct DevPlan {
     const int* list_first;      // [9] first entry of list 0..8 (8 = level 0)
     const int* list_len;        // [9]
     const int4* items;          // [n_items]
+    const int* item_entries;    // forward items: list positions of their ranges
     int n_items;
     int* counter;               // dynamic item counter of the persistent launch
+    int near_d2;                // largest |d|^2 (cell units) of a near pair
 };
+
+// List id of the items of an interior root: their range runs over the
+// root's own 512 cells as sources instead of over stencil entries.
+constexpr int kRootList = 9;
 
 __host__ __device__ inline int pack_entry(int dx, int dy, int dz, int near) {
     return (dx + 16) | ((dy + 16) << 5) | ((dz + 16) << 10) | (near << 15);
@@ -111,7 +194,9 @@ struct DevLattice {
 };
 
 // Work item: x = target node; y = level | parity << 8 | half << 11 | list << 12;
-// z, w = entry range [k0, k1) of that list.  32 target cells per item: the
+// z, w = range [k0, k1): of item_entries, whose values are positions in the
+// list (forward launch); of the list itself (adjoint); of the root's cells
+// (kRootList).  32 target cells per item: the
 // cells of one parity class (px, py, pz) with z-index 2 (2 half + q) + pz,
 // q in {0, 1}.
 __host__ __device__ inline int item_level(int4 it) { return it.y & 0xff; }

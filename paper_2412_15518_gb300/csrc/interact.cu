@@ -20,6 +20,8 @@
 // Each lane accumulates in registers (FP64, or FP32 for the bulk form with
 // the near leaf pairs kept in FP64) and adds its sums once per item into the
 // cell's FP64 expansion with atomics, scaled to physical units.
+#include <type_traits>
+
 #include "kernels.hpp"
 #include "pair_formula.cuh"
 
@@ -91,11 +93,13 @@ __device__ __forceinline__ void load_tail(const DevTree& t, long long c, float* 
     bt[2] = b3[2] + b3[7] + b3[9];
     bt[3] = b2[0] + b2[3] + b2[5];
 }
-// The target's octupole per unit mass, M3_A / m_A, and its trace vector,
-// formed in FP64 once per target (the correction's mass ratio); zero for a
-// target of zero mass (whose M3 is zero for non-negative densities).
-template <class T>
-__device__ __forceinline__ void load_octupole_per_mass(const DevTree& t, long long c, T* a3, T* ta) {
+// The target's octupole per unit mass, M3_A / m_A, and its trace vector
+// (the correction's mass ratio, applied once per target in FP64); zero for a
+// target of zero mass (whose M3 is zero for non-negative densities).  The
+// FP64 form divides here; the FP32 form reads the FP32 records that the
+// upward pass formed in FP64.
+__device__ __forceinline__ void load_octupole_per_mass(const DevTree& t, long long c, double* a3,
+                                                       double* ta) {
     const double2* p = reinterpret_cast<const double2*>(t.rec64 + c * kRec);
     const double m = __ldg(t.rec64 + c * kRec);
     const double r = m != 0.0 ? 1.0 / m : 0.0;
@@ -107,9 +111,17 @@ __device__ __forceinline__ void load_octupole_per_mass(const DevTree& t, long lo
         v[2 * q + 1] = w.y;
     }
 #pragma unroll
-    for (int q = 0; q < 10; q++) a3[q] = T(r * v[q]);
+    for (int q = 0; q < 10; q++) a3[q] = r * v[q];
 #pragma unroll
-    for (int q = 0; q < 3; q++) ta[q] = T(r * v[10 + q]);
+    for (int q = 0; q < 3; q++) ta[q] = r * v[10 + q];
+}
+__device__ __forceinline__ void load_octupole_per_mass(const DevTree& t, long long c, float* a3,
+                                                       float* ta) {
+    const float4* p = reinterpret_cast<const float4*>(t.oct32 + c * kOct);
+    const float4 v0 = __ldg(p), v1 = __ldg(p + 1), v2 = __ldg(p + 2), v3 = __ldg(p + 3);
+    a3[0] = v0.x; a3[1] = v0.y; a3[2] = v0.z; a3[3] = v0.w; a3[4] = v1.x;
+    a3[5] = v1.y; a3[6] = v1.z; a3[7] = v1.w; a3[8] = v2.x; a3[9] = v2.y;
+    ta[0] = v2.z; ta[1] = v2.w; ta[2] = v3.x;
 }
 __device__ __forceinline__ void load_off(const DevPlan& p, int k, double& x, double& y, double& z) {
     const double2 a = __ldg(p.off64 + 2 * k), b = __ldg(p.off64 + 2 * k + 1);
@@ -126,14 +138,74 @@ __device__ __forceinline__ void load_off(const DevPlan& p, int k, float& x, floa
 
 // Scales a partial sum to physical units and widens it: the FP64 form
 // multiplies in FP64; the FP32 form multiplies by the scale rounded to FP32
-// (one more rounding of the size of the sum's own) and converts once.
+// (one more rounding of the size of the sum's own) and widens exactly.
 __device__ __forceinline__ double scaled(double v, double s) { return s * v; }
-__device__ __forceinline__ double scaled(float v, float s) { return (double)(v * s); }
+__device__ __forceinline__ double scaled(float v, float s) { return widen(v * s); }
+__device__ __forceinline__ const double* scales_of(const LevelScales& sc, int L, double) { return sc.s64[L]; }
+__device__ __forceinline__ const float* scales_of(const LevelScales& sc, int L, float) { return sc.s32[L]; }
+
+// Small non-negative integer (< 2^22) to T without a conversion
+// instruction: for FP32, 2^23 + n is the float whose fraction bits are n.
+__device__ __forceinline__ double small_int(int n, double) { return (double)n; }
+__device__ __forceinline__ float small_int(int n, float) {
+    return __int_as_float(0x4b000000 | n) - 8388608.0f;
+}
+
+// Asynchronous global -> shared copies (cp.async, 16 bytes, through L1):
+// the FP32 loop stages the next pair's source record in shared memory while
+// the current pair is computed, without holding it in registers.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Per-warp shared staging of the FP32 loop: the item's stencil entries and
+// two stages of 32 source records (5 float4 each, component-major so that a
+// warp's 16-byte accesses are consecutive).
+constexpr int kMaxChunk = 264;
+struct WarpStage32 {
+    int entries[kMaxChunk];
+    float4 rec[2][5][32];
+};
+
+// Starts the copy of pair q's source into stage st and returns its kind:
+// 0 = no pair, 1 = leaf cell (monopole), 2 = interior cell (multipole).
+template <bool FULL>
+__device__ __forceinline__ int issue32(const DevTree& t, WarpStage32& ws, int q, int q0, int qend,
+                                       int i, int j, int k, int lane, const int* s_nb,
+                                       const int* s_lf, int st) {
+    if (q >= qend) return 0;
+    const int e = ws.entries[q - q0];
+    const int sx = i + entry_dx(e), sy = j + entry_dy(e), sz = k + entry_dz(e);
+    const int slot = ((sx >> 3) + 1) + 3 * ((sy >> 3) + 1) + 9 * ((sz >> 3) + 1);
+    const int nb = s_nb[slot];
+    if (nb < 0) return 0;  // outside the domain, or covered by a coarser leaf
+    const bool sleaf = s_lf[slot] != 0;
+    if (!FULL && sleaf) return 0;                   // leaf-leaf pairs of level >= 1: lattice kernel
+    if (FULL && !sleaf && entry_near(e)) return 0;  // resolved at the next level
+    const long long sc = (long long)nb * kCells + (sx & 7) + 8 * (sy & 7) + 64 * (sz & 7);
+    const float4* g = reinterpret_cast<const float4*>(t.mom32 + sc * kMom);
+    cp_async16(&ws.rec[st][0][lane], g);
+    if (!sleaf)
+#pragma unroll
+        for (int r = 1; r < 5; r++) cp_async16(&ws.rec[st][r][lane], g + r);
+    return sleaf ? 1 : 2;
+}
+
+// Small signed integer (|n| < 2^21) to float without a conversion
+// instruction: 2^23 + 2^21 + n is the float whose fraction bits are
+// 2^21 + n.
+__device__ __forceinline__ float small_sint(int n) {
+    return __int_as_float(0x4b000000 | (n + (1 << 21))) - 10485760.0f;
+}
 
 template <class T, bool FULL, bool AM>
 __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, const int4 it,
                                          const int lane, const int* s_nb, const int* s_lf,
-                                         double G) {
+                                         const LevelScales& sc, WarpStage32* ws) {
     const int node = it.x;
     const int L = item_level(it), par = item_parity(it), half = item_half(it);
     const int i = 2 * (lane & 3) + (par & 1);
@@ -148,9 +220,73 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
     Acc<T> A;
     acc_zero(A);
     double n0 = 0.0, n1 = 0.0, n2 = 0.0, n3 = 0.0;  // FP64 near leaf pairs (bulk form)
+    if (FULL && item_list(it) == kRootList) {
+        // the interior root: sources are the root's own cells [z, w), the
+        // same cell for every lane (a broadcast load); a pair is far iff
+        // |d|^2 > near_d2, and near pairs of two interior cells descend
+        const int root = it.x;
+        const T fi = small_int(i, T(0)), fj = small_int(j, T(0)), fk = small_int(k, T(0));
+#pragma unroll 1
+        for (int s = it.z; s < it.w; s++) {
+            const int sx = s & 7, sy = (s >> 3) & 7, sz = s >> 6;
+            const int dx = sx - i, dy = sy - j, dz = sz - k;
+            T m, bx, by, bz, b2[6], b3[10], bt[4];
+            const long long sc = (long long)root * kCells + s;
+            load_head(t, sc, m, bx, by, bz);
+            load_tail(t, sc, b2, b3, bt);
+            if (dx * dx + dy * dy + dz * dz <= p.near_d2) continue;
+            // R' = (t + dX_A) - (s + dX_B) in cell units
+            const T x = (fi + dax) - (small_int(sx, T(0)) + bx);
+            const T y = (fj + day) - (small_int(sy, T(0)) + by);
+            const T z = (fk + daz) - (small_int(sz, T(0)) + bz);
+            m2l_pair<T, FULL, true, AM>(x, y, z, m, b2, b3, bt, a3, ta, A);
+        }
+    } else if (std::is_same<T, float>::value && L > 0) {
+        // FP32 form, levels >= 1: the next source's loads are issued before
+        // the current pair is computed, so their latency overlaps the math
+        if constexpr (std::is_same<T, float>::value) {
+            const int base = p.list_first[item_list(it)];
+            const int q0 = it.z, q1 = it.w;
+            for (int q = q0 + lane; q < q1; q += 32)
+                ws->entries[q - q0] = __ldg(p.entries + base + __ldg(p.item_entries + q));
+            __syncwarp();
+            int kind = issue32<FULL>(t, *ws, q0, q0, q1, i, j, k, lane, s_nb, s_lf, 0);
+            cp_async_commit();
+#pragma unroll 1
+            for (int q = q0; q < q1; q++) {
+                const int st = (q - q0) & 1;
+                const int kind_next = issue32<FULL>(t, *ws, q + 1, q0, q1, i, j, k, lane, s_nb, s_lf, st ^ 1);
+                cp_async_commit();
+                cp_async_wait1();  // this lane's copies of pair q are done
+                if (kind) {
+                    const int e = ws->entries[q - q0];
+                    const float4 h = ws->rec[st][0][lane];
+                    // R' = X_A - X_B in cell units: the source sits at offset d
+                    const float x = (dax - h.y) - small_sint(entry_dx(e));
+                    const float y = (day - h.z) - small_sint(entry_dy(e));
+                    const float z = (daz - h.w) - small_sint(entry_dz(e));
+                    if (kind == 1) {
+                        m2l_pair<float, FULL, false, AM>(x, y, z, h.x, nullptr, nullptr, nullptr, a3, ta, A);
+                    } else {
+                        const float4 v1 = ws->rec[st][1][lane], v2 = ws->rec[st][2][lane],
+                                     v3 = ws->rec[st][3][lane], v4 = ws->rec[st][4][lane];
+                        const float b2[6] = {v1.x, v1.y, v1.z, v1.w, v2.x, v2.y};
+                        const float b3[10] = {v2.z, v2.w, v3.x, v3.y, v3.z, v3.w, v4.x, v4.y, v4.z, v4.w};
+                        const float bt[4] = {b3[0] + b3[3] + b3[5], b3[1] + b3[6] + b3[8],
+                                             b3[2] + b3[7] + b3[9], b2[0] + b2[3] + b2[5]};
+                        m2l_pair<float, FULL, true, AM>(x, y, z, h.x, b2, b3, bt, a3, ta, A);
+                    }
+                }
+                kind = kind_next;
+            }
+            cp_async_wait0();
+            __syncwarp();  // the stage and entry buffers are reused by the next item
+        }
+    } else {
     const int base = p.list_first[item_list(it)];
 #pragma unroll 1
-    for (int q = it.z; q < it.w; q++) {
+    for (int pos = it.z; pos < it.w; pos++) {
+        const int q = __ldg(p.item_entries + pos);
         const int e = __ldg(p.entries + base + q);
         const int dx = entry_dx(e), dy = entry_dy(e), dz = entry_dz(e);
         const int sx = i + dx, sy = j + dy, sz = k + dz;
@@ -198,16 +334,25 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
             m2l_pair<T, FULL, true, AM>(x, y, z, m, b2, b3, bt, a3, ta, A);
         }
     }
-    // scale to physical units: L^(n) * (-G h^-(n+1)), correction * -(G/6) h^-2
-    const double hi = t.inv_side8 * (double)(1 << L);
-    const double s1d = -G * hi, s2d = s1d * hi;
-    // scale factors in the accumulators' type (converted once per item)
-    const T s1 = T(s1d), s2 = T(s2d), s3 = T(s2d * hi), s4 = T(s2d * hi * hi);
+    }
+    // scale to physical units: L^(n) * (-G h^-(n+1)), correction * -(G/6) h^-2,
+    // with the level's factors in the accumulators' type
+    const T* sl = scales_of(sc, L, T(0));
+    const T s1 = sl[0], s2 = sl[1], s3 = sl[2], s4 = sl[3];
     double* loc = t.loc;
-    atomicAdd(loc + cell, scaled(A.L0, s1) + s1d * n0);
-    atomicAdd(loc + N + cell, scaled(A.L1[0], s2) + s2d * n1);
-    atomicAdd(loc + 2 * N + cell, scaled(A.L1[1], s2) + s2d * n2);
-    atomicAdd(loc + 3 * N + cell, scaled(A.L1[2], s2) + s2d * n3);
+    if (sizeof(T) == 4 && L == 0 && !FULL) {
+        // a leaf root: its near pairs were summed in FP64
+        const double s1d = sc.s64[0][0], s2d = sc.s64[0][1];
+        atomicAdd(loc + cell, scaled(A.L0, s1) + s1d * n0);
+        atomicAdd(loc + N + cell, scaled(A.L1[0], s2) + s2d * n1);
+        atomicAdd(loc + 2 * N + cell, scaled(A.L1[1], s2) + s2d * n2);
+        atomicAdd(loc + 3 * N + cell, scaled(A.L1[2], s2) + s2d * n3);
+    } else {
+        atomicAdd(loc + cell, scaled(A.L0, s1));
+        atomicAdd(loc + N + cell, scaled(A.L1[0], s2));
+        atomicAdd(loc + 2 * N + cell, scaled(A.L1[1], s2));
+        atomicAdd(loc + 3 * N + cell, scaled(A.L1[2], s2));
+    }
     if (FULL) {
         finish_acc(A);  // Kronecker parts of L2 and L3 from their traces
 #pragma unroll
@@ -217,7 +362,7 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
     }
     if (AM) {
         // a_c = -(G/6) h^-2 (S - P)
-        const T sa = T(-(G / 6.0) * hi * hi);
+        const T sa = sl[4];
 #pragma unroll
         for (int a = 0; a < 3; a++)
             atomicAdd(loc + (20 + a) * N + cell, scaled(FULL ? A.S[a] - A.P[a] : A.S[a], sa));
@@ -225,11 +370,14 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
 }
 
 template <class T>
-__global__ void __launch_bounds__(128) k_interact(DevTree t, DevPlan p, double G, int am) {
+__global__ void __launch_bounds__(128, std::is_same<T, double>::value ? 3 : 1)
+    k_interact(DevTree t, DevPlan p, LevelScales sc, int am) {
     __shared__ int s_nb[kMaxWarps][28];
     __shared__ int s_lf[kMaxWarps][28];
+    extern __shared__ __align__(16) unsigned char s_dyn[];  // FP32 form: one WarpStage32 per warp
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
+    WarpStage32* ws = std::is_same<T, float>::value ? reinterpret_cast<WarpStage32*>(s_dyn) + w : nullptr;
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(p.counter, 1);
@@ -242,13 +390,18 @@ __global__ void __launch_bounds__(128) k_interact(DevTree t, DevPlan p, double G
             s_lf[w][lane] = nb >= 0 ? (t.node_leaf[nb] >= 0) : 0;
         }
         __syncwarp();
+        if (it.w - it.z > kMaxChunk && item_list(it) != kRootList) {
+            // longer than the staging buffer: a plan error, latched and skipped
+            if (lane == 0) atomicOr(t.status, kStatusBadItem);
+            continue;
+        }
         const bool full = t.node_leaf[it.x] < 0;
         if (full) {
-            if (am) run_item<T, true, true>(t, p, it, lane, s_nb[w], s_lf[w], G);
-            else run_item<T, true, false>(t, p, it, lane, s_nb[w], s_lf[w], G);
+            if (am) run_item<T, true, true>(t, p, it, lane, s_nb[w], s_lf[w], sc, ws);
+            else run_item<T, true, false>(t, p, it, lane, s_nb[w], s_lf[w], sc, ws);
         } else {
-            if (am) run_item<T, false, true>(t, p, it, lane, s_nb[w], s_lf[w], G);
-            else run_item<T, false, false>(t, p, it, lane, s_nb[w], s_lf[w], G);
+            if (am) run_item<T, false, true>(t, p, it, lane, s_nb[w], s_lf[w], sc, ws);
+            else run_item<T, false, false>(t, p, it, lane, s_nb[w], s_lf[w], sc, ws);
         }
         __syncwarp();
     }
@@ -259,10 +412,11 @@ __global__ void __launch_bounds__(128) k_interact(DevTree t, DevPlan p, double G
 void launch_interact(const DevTree& t, const DevPlan& p, int precision, double G, int am,
                      int ctas, int warps_per_cta, cudaStream_t s) {
     if (warps_per_cta > 4) warps_per_cta = 4;
+    const LevelScales sc = level_scales(t.inv_side8, G);
     if (precision == 1)
-        k_interact<float><<<ctas, 32 * warps_per_cta, 0, s>>>(t, p, G, am);
+        k_interact<float><<<ctas, 32 * warps_per_cta, warps_per_cta * sizeof(WarpStage32), s>>>(t, p, sc, am);
     else
-        k_interact<double><<<ctas, 32 * warps_per_cta, 0, s>>>(t, p, G, am);
+        k_interact<double><<<ctas, 32 * warps_per_cta, 0, s>>>(t, p, sc, am);
 }
 
 }  // namespace otfmm

@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(256) k_leaf_moments(DevTree t, const int* __re
         t.mom64[cell] = m;
         t.rec64[cell * kRec] = m;
         t.mom32[cell * kMom] = (float)m;
+        t.m32[cell] = (float)m;
         // a leaf cell's expansion: L0, L1 and the correction acceleration
         t.loc[cell] = 0.0;
         t.loc[N + cell] = 0.0;
@@ -136,6 +137,15 @@ __global__ void __launch_bounds__(256) k_m2m(DevTree t, int first) {
             t.rec64[cell * kRec + r] = vals[r];
         }
     }
+    // FP32 octupole per unit mass (M3 / m and its trace vector) for the
+    // correction's target term, the division done here in FP64
+#pragma unroll
+    for (int r = 0; r < kOct; r++) {
+        if ((r & 7) == q) {
+            const double v = r < 13 ? vals[10 + r] : 0.0;
+            t.oct32[cell * kOct + r] = (float)(v * iM);
+        }
+    }
 #pragma unroll
     for (int r = q; r < kLoc; r += 8) t.loc[r * N + cell] = 0.0;
 }
@@ -218,6 +228,12 @@ __global__ void __launch_bounds__(256) k_m2m_leafkids(DevTree t, int first) {
 #pragma unroll
     for (int r = 0; r < kMom / 4; r++)
         r32[r] = make_float4((float)v[4 * r], (float)v[4 * r + 1], (float)v[4 * r + 2], (float)v[4 * r + 3]);
+    // FP32 octupole per unit mass: M3 / m (v[10..19]) and its trace vector (v[20..22])
+    float4* o32 = reinterpret_cast<float4*>(t.oct32 + cell * kOct);
+    o32[0] = make_float4((float)(v[10] * iM), (float)(v[11] * iM), (float)(v[12] * iM), (float)(v[13] * iM));
+    o32[1] = make_float4((float)(v[14] * iM), (float)(v[15] * iM), (float)(v[16] * iM), (float)(v[17] * iM));
+    o32[2] = make_float4((float)(v[18] * iM), (float)(v[19] * iM), (float)(v[20] * iM), (float)(v[21] * iM));
+    o32[3] = make_float4((float)(v[22] * iM), 0.f, 0.f, 0.f);
 #pragma unroll
     for (int r = 0; r < kLoc; r++) t.loc[r * N + cell] = 0.0;
 }

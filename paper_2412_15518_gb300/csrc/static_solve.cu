@@ -44,6 +44,7 @@ namespace {
 constexpr int kMaxNodes = 9;
 constexpr int kMaxEntries = 5632;  // 8 parity lists of <= 263 entries and the level-0 list of 3374 (theta >= 0.5)
 constexpr int kMaxItems = 2048;
+constexpr int kMaxItemEntries = 16 * 3374;  // a leaf root: 16 target groups x its level-0 list
 constexpr int kMaxDevices = 64;
 constexpr size_t kStaticBytes = 4u << 20;
 
@@ -57,8 +58,8 @@ inline size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Byte offsets of every array inside the static scratch.
 struct Layout {
     size_t level, leaf, parent, child, xyz, nbr, level_first, leaf_node;
-    size_t mom64, mom32, rec64, loc, status, counter;
-    size_t entries, tab64, tab32, list_first, list_len, items;
+    size_t mom64, mom32, m32, oct32, rec64, loc, status, counter;
+    size_t entries, tab64, tab32, list_first, list_len, items, item_entries;
     size_t hoff_far, hoff_near, lattice_nodes, off64, off32;
     size_t end;
 };
@@ -82,6 +83,8 @@ Layout make_layout() {
     l.leaf_node = take(sizeof(int) * kMaxNodes);
     l.mom64 = take(sizeof(double) * kMom * cells);
     l.mom32 = take(sizeof(float) * kMom * cells);
+    l.m32 = take(sizeof(float) * cells);
+    l.oct32 = take(sizeof(float) * kOct * cells);
     l.rec64 = take(sizeof(double) * kRec * cells);
     l.loc = take(sizeof(double) * kLoc * cells);
     l.status = take(sizeof(int));
@@ -92,6 +95,7 @@ Layout make_layout() {
     l.list_first = take(sizeof(int) * kNumLists);
     l.list_len = take(sizeof(int) * kNumLists);
     l.items = take(sizeof(int) * 4 * kMaxItems);
+    l.item_entries = take(sizeof(int) * kMaxItemEntries);
     l.hoff_far = take(sizeof(int) * kMaxEntries);
     l.hoff_near = take(sizeof(int) * kMaxEntries);
     l.lattice_nodes = take(sizeof(int) * kMaxNodes);
@@ -167,7 +171,8 @@ extern "C" int ot_solve_gravity_static(const ot_tree_desc* desc, const double* r
     HostPlan p;
     if ((e = build_stencil(h, o.theta, p))) return e;
     build_items(h, 64, p);
-    if ((int)p.entries.size() > kMaxEntries || (int)p.items.size() > kMaxItems)
+    if ((int)p.entries.size() > kMaxEntries || (int)p.items.size() > kMaxItems ||
+        (int)p.item_entries.size() > kMaxItemEntries)
         return OT_ERR_TOO_LARGE;
     const Layout l = make_layout();
     if (l.end > kStaticBytes) return OT_ERR_TOO_LARGE;
@@ -195,12 +200,15 @@ extern "C" int ot_solve_gravity_static(const ot_tree_desc* desc, const double* r
         (e = put(base, l.hoff_far, p.hoff_far.data(), p.hoff_far.size(), s)) ||
         (e = put(base, l.hoff_near, p.hoff_near.data(), p.hoff_near.size(), s)) ||
         (e = put(base, l.lattice_nodes, p.lattice_nodes.data(), p.lattice_nodes.size(), s)) ||
-        (p.items.size() && (e = put(base, l.items, &p.items[0].x, 4 * p.items.size(), s))))
+        (p.items.size() && (e = put(base, l.items, &p.items[0].x, 4 * p.items.size(), s))) ||
+        (p.item_entries.size() &&
+         (e = put(base, l.item_entries, p.item_entries.data(), p.item_entries.size(), s))))
         return e;
     // what must start at zero: leaf offsets and higher moments, expansions,
     // the item counter and the status word
     if (cudaMemsetAsync(base + l.mom64, 0, sizeof(double) * kMom * cells, s) != cudaSuccess ||
         cudaMemsetAsync(base + l.mom32, 0, sizeof(float) * kMom * cells, s) != cudaSuccess ||
+        cudaMemsetAsync(base + l.oct32, 0, sizeof(float) * kOct * cells, s) != cudaSuccess ||
         cudaMemsetAsync(base + l.rec64, 0, sizeof(double) * kRec * cells, s) != cudaSuccess ||
         cudaMemsetAsync(base + l.loc, 0, sizeof(double) * kLoc * cells, s) != cudaSuccess ||
         cudaMemsetAsync(base + l.status, 0, sizeof(int), s) != cudaSuccess ||
@@ -223,6 +231,8 @@ extern "C" int ot_solve_gravity_static(const ot_tree_desc* desc, const double* r
     d.level_first = (const int*)(base + l.level_first);
     d.mom64 = (double*)(base + l.mom64);
     d.mom32 = (float*)(base + l.mom32);
+    d.m32 = (float*)(base + l.m32);
+    d.oct32 = (float*)(base + l.oct32);
     d.rec64 = (double*)(base + l.rec64);
     d.inv_side8 = 8.0 / h.size;
     d.loc = (double*)(base + l.loc);
@@ -236,8 +246,10 @@ extern "C" int ot_solve_gravity_static(const ot_tree_desc* desc, const double* r
     dp.list_first = (const int*)(base + l.list_first);
     dp.list_len = (const int*)(base + l.list_len);
     dp.items = (const int4*)(base + l.items);
+    dp.item_entries = (const int*)(base + l.item_entries);
     dp.n_items = (int)p.items.size();
     dp.counter = (int*)(base + l.counter);
+    dp.near_d2 = p.near_d2;
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
         cudaGetLastError();

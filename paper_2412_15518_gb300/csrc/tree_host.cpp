@@ -146,6 +146,7 @@ int build_stencil(const HostTree& t, double theta, HostPlan& p) {
                 if ((double)(dx * dx + dy * dy + dz * dz) <= it2) near.push_back(pack_entry(dx, dy, dz, 1));
             }
     p.n_near = (int)near.size();
+    while ((double)(p.near_d2 + 1) <= it2) p.near_d2++;  // the same test as the lists
     auto push = [&](int e) {
         p.entries.push_back(e);
         int d[3] = {entry_dx(e), entry_dy(e), entry_dz(e)};
@@ -262,35 +263,84 @@ int build_stencil(const HostTree& t, double theta, HostPlan& p) {
 
 namespace {
 
-// Items of every node that needs the general kernel; with `all`, leaf nodes
-// of level >= 1 without interior neighbours get one item per parity half
-// covering their whole list (their pairs are all lattice pairs).
+// Neighbour slots (bit s = slot s of the 27) that the 32 targets of one item
+// group (parity par, half) reach through entry e.
+uint32_t slot_mask(int par, int half, int e) {
+    uint32_t m = 0;
+    for (int lane = 0; lane < 32; lane++) {
+        const int i = 2 * (lane & 3) + (par & 1);
+        const int j = 2 * ((lane >> 2) & 3) + ((par >> 1) & 1);
+        const int k = 2 * (2 * half + (lane >> 4)) + (par >> 2);
+        const int sx = i + entry_dx(e), sy = j + entry_dy(e), sz = k + entry_dz(e);
+        m |= 1u << (((sx >> 3) + 1) + 3 * ((sy >> 3) + 1) + 9 * ((sz >> 3) + 1));
+    }
+    return m;
+}
+
+// Items of every node that needs the general kernel.  Forward items (kept !=
+// null) range over a compacted array of list positions: for each node and
+// 32-target group only the entries for which some target has a pair to
+// compute (a source exists; a near source of an interior target is a leaf;
+// the source of a leaf target is interior) are kept, so whole-warp skips at
+// domain boundaries and the descending near pairs of interior cells cost no
+// iterations.  With `all` (the adjoint's items), every node gets items over
+// its whole list, leaf nodes of level >= 1 without interior neighbours one
+// item per parity half (their pairs are all lattice pairs).
 std::vector<Item> make_items(const HostTree& t, int chunk, const HostPlan& p, bool all,
-                             std::vector<int>* lattice_nodes) {
+                             std::vector<int>* lattice_nodes, std::vector<int>* kept) {
     std::vector<Item> items;
     std::vector<int64_t> cost;
+    // slot masks per list, parity and half (list 8: the leaf root)
+    std::vector<uint32_t> masks[kNumLists][8][2];
+    auto masks_of = [&](int list, int par, int half) -> const std::vector<uint32_t>& {
+        std::vector<uint32_t>& m = masks[list][par][half];
+        if (m.empty())
+            for (int q = 0; q < p.list_len[list]; q++)
+                m.push_back(slot_mask(par, half, p.entries[p.list_first[list] + q]));
+        return m;
+    };
     for (int v = 0; v < t.n_nodes(); v++) {
         int L = t.node_level[v];
         bool tl = t.node_leaf[v] >= 0;
         bool seam = false;
-        if (tl)
-            for (int s = 0; s < 27; s++) {
-                int nb = t.nbr[(size_t)v * 27 + s];
-                if (nb >= 0 && t.node_leaf[nb] < 0) seam = true;
-            }
+        uint32_t exist = 0, leafm = 0;
+        for (int s = 0; s < 27; s++) {
+            int nb = t.nbr[(size_t)v * 27 + s];
+            if (nb < 0) continue;
+            exist |= 1u << s;
+            if (t.node_leaf[nb] >= 0) leafm |= 1u << s;
+            else if (tl) seam = true;
+        }
+        const uint32_t inner = exist & ~leafm;
         bool lattice_only = tl && L > 0 && !seam;
         if (tl && L > 0 && lattice_nodes) lattice_nodes->push_back(v);
         if (lattice_only && !all) continue;
+        const bool root_cells = L == 0 && !tl && !all;  // an interior root, forward launch
         for (int par = 0; par < 8; par++) {
-            int list = L == 0 ? 8 : par;
-            int len = p.list_len[list];
+            int list = root_cells ? kRootList : (L == 0 ? 8 : par);
+            int len = root_cells ? kCells : p.list_len[list];
             int step = lattice_only ? len : std::max(1, chunk);
-            for (int half = 0; half < 2; half++)
-                for (int k0 = 0; k0 < len; k0 += step) {
-                    int k1 = std::min(len, k0 + step);
-                    items.push_back({v, L | (par << 8) | (half << 11) | (list << 12), k0, k1});
+            for (int half = 0; half < 2; half++) {
+                int start = 0, n = len;
+                if (kept && !root_cells) {
+                    const std::vector<uint32_t>& m = masks_of(list, par, half);
+                    start = (int)kept->size();
+                    for (int q = 0; q < len; q++) {
+                        const bool near = entry_near(p.entries[p.list_first[list] + q]) != 0;
+                        bool keep;
+                        if (tl && L == 0) keep = (m[q] & exist) != 0;  // leaf root: lattice pairs here
+                        else if (tl) keep = (m[q] & inner) != 0;
+                        else keep = (m[q] & (near ? leafm : exist)) != 0;
+                        if (keep) kept->push_back(q);
+                    }
+                    n = (int)kept->size() - start;
+                }
+                for (int k0 = 0; k0 < n; k0 += step) {
+                    int k1 = std::min(n, k0 + step);
+                    items.push_back({v, L | (par << 8) | (half << 11) | (list << 12), start + k0, start + k1});
                     cost.push_back((int64_t)(k1 - k0) * (lattice_only ? 1 : (tl ? 4 : 24)));
                 }
+            }
         }
     }
     // longest items first; ties keep the breadth-first node order
@@ -307,8 +357,9 @@ std::vector<Item> make_items(const HostTree& t, int chunk, const HostPlan& p, bo
 void build_items(const HostTree& t, int chunk, HostPlan& p) {
     p.chunk = chunk;
     p.lattice_nodes.clear();
-    p.items = make_items(t, chunk, p, false, &p.lattice_nodes);
-    p.items_adj = make_items(t, chunk, p, true, nullptr);
+    p.item_entries.clear();
+    p.items = make_items(t, chunk, p, false, &p.lattice_nodes, &p.item_entries);
+    p.items_adj = make_items(t, chunk, p, true, nullptr, nullptr);
 }
 
 }  // namespace otfmm

@@ -54,11 +54,13 @@ struct HostPlan {
     int list_first[kNumLists] = {0};
     int list_len[kNumLists] = {0};
     int n_near = 0;                   // near offsets (first entries of every list)
+    int near_d2 = 0;                  // largest integer |d|^2 classified near
     int w_far = 0, w_near = 0;        // halo widths of the lattice kernel
     std::vector<int> hoff_far, hoff_near;  // halo offsets per entry (parity lists)
     std::vector<int> lattice_nodes;   // leaf nodes of level >= 1
-    std::vector<Item> items;
-    std::vector<Item> items_adj;      // every node (the adjoint has no lattice kernel)
+    std::vector<Item> items;          // ranges over item_entries (kRootList: over root cells)
+    std::vector<int> item_entries;    // list positions kept per node and target group
+    std::vector<Item> items_adj;      // every node, ranges over the lists themselves
     int64_t n_m2l = 0, n_p2p = 0, n_seam = 0, n_lattice = 0;
     int64_t n_class[PairClasses] = {0, 0, 0, 0, 0};
     double flops_am = 0.0, flops_noam = 0.0;  // one interaction launch
@@ -70,9 +72,11 @@ struct HostPlan {
 int build_stencil(const HostTree& t, double theta, HostPlan& p);
 
 // Work items of the persistent launch for a given chunk length: interior
-// targets (chunked), leaf targets that border interior cells (their pairs
-// with interior cells), and a leaf root; the leaf-leaf pairs of leaf nodes
-// of level >= 1 go to the lattice kernel (lattice_nodes).
+// targets (chunked; an interior root's items range over its 512 cells as
+// sources), leaf targets that border interior cells (their pairs with
+// interior cells), and a leaf root; the leaf-leaf pairs of leaf nodes of
+// level >= 1 go to the lattice kernel (lattice_nodes).  The adjoint's items
+// (items_adj) cover every node and use the stencil lists at every level.
 void build_items(const HostTree& t, int chunk, HostPlan& p);
 
 }  // namespace otfmm
