@@ -372,6 +372,7 @@ def run_ours(args):
             i32 = tree.info()
             extra["fp32_bulk"]["tuned"] = {"chunk": i32["tuned_chunk"],
                                            "ctas_per_sm": i32["tuned_ctas_per_sm"],
+                                           "lattice_ctas_per_sm": i32["tuned_lattice_ctas_per_sm"],
                                            "work_items": i32["n_work_items"]}
             # the adjoint (FP64): dJ/drho for J = sum(w1 phi + w2 . g)
             w1n, w2n = inputs.weights(leaves.shape[0])

@@ -118,6 +118,9 @@ typedef struct {
     int32_t tuned_chunk;                       /* stencil entries per work item     */
     int32_t tuned_ctas_per_sm;                 /* persistent CTAs per SM            */
     int32_t tuned_warps_per_cta;
+    int32_t tuned_lattice_ctas_per_sm;         /* FP32-bulk form: persistent CTAs per
+                                                  SM of each lattice kernel (0: one
+                                                  CTA per leaf node)                 */
     int32_t device_status;                     /* latched device error, 0 = none    */
     int64_t workspace_bytes;                   /* device memory held by the tree    */
 } ot_tree_stats;

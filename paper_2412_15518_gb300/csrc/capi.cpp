@@ -88,6 +88,7 @@ struct ot_tree {
     // tuning of the persistent launch
     int chunk = 64;
     int ctas_per_sm = 4;
+    int lattice_ctas_per_sm = 0;   // bulk form: persistent lattice CTAs per SM (0: one per node)
     int warps_per_cta = 4;
     bool tuned = false;
     // graphs
@@ -135,7 +136,7 @@ template <class T> int upload(T* d, const std::vector<T>& v) {
     } while (0)
 
 DevTree dev_tree(const ot_tree* t) {
-    DevTree d;
+    DevTree d = {};
     d.n_levels = t->h.n_levels;
     d.n_nodes = t->h.n_nodes();
     d.n_leaf = t->h.n_leaf;
@@ -160,7 +161,7 @@ DevTree dev_tree(const ot_tree* t) {
 }
 
 DevPlan dev_plan(const ot_tree* t) {
-    DevPlan p;
+    DevPlan p = {};
     p.entries = t->d_entries;
     p.tab64 = t->d_tab64;
     p.tab32 = t->d_tab32;
@@ -177,7 +178,7 @@ DevPlan dev_plan(const ot_tree* t) {
 }
 
 DevLattice dev_lattice(const ot_tree* t) {
-    DevLattice l;
+    DevLattice l = {};
     l.hoff_far = t->d_hoff_far;
     l.hoff_near = t->d_hoff_near;
     l.nodes = t->d_lattice_nodes;
@@ -185,6 +186,8 @@ DevLattice dev_lattice(const ot_tree* t) {
     l.w_far = t->plan.w_far;
     l.w_near = t->plan.w_near;
     l.n_near = t->plan.n_near;
+    l.counter = t->d_counter + 1;
+    lattice_far_table_plan(l, t->plan.list_len);
     return l;
 }
 
@@ -306,14 +309,18 @@ int enqueue_interact(ot_tree* t, const ot_solve_opts& o, cudaStream_t s) {
     // they run as concurrent branches: in the bulk form the near-pair lattice
     // kernel is FP64 work and the other two FP32 work, and the pipes overlap.
     const bool bulk = o.precision == OT_PRECISION_FP32_BULK;
+    // work counters: [0] general kernel, [1] near (or all) lattice, [2] far lattice
+    TRYC(cudaMemsetAsync(t->d_counter, 0, 4 * sizeof(int), s));
     TRYC(cudaEventRecord(t->ev_fork, s));
     TRYC(cudaStreamWaitEvent(t->side_stream, t->ev_fork, 0));
     if (bulk) TRYC(cudaStreamWaitEvent(t->far_stream, t->ev_fork, 0));
-    launch_lattice(d, dev_plan(t), dev_lattice(t), o.precision, o.G, t->side_stream,
+    // bulk form: a bounded number of persistent lattice CTAs per SM (tuned)
+    // leaves room for the general kernel, so the kernels share the SMs
+    launch_lattice(d, dev_plan(t), dev_lattice(t), o.precision, o.G,
+                   bulk ? t->num_sms * t->lattice_ctas_per_sm : 0, t->side_stream,
                    bulk ? t->far_stream : nullptr);
     TRYC(cudaEventRecord(t->ev_join, t->side_stream));
     if (bulk) TRYC(cudaEventRecord(t->ev_join_far, t->far_stream));
-    TRYC(cudaMemsetAsync(t->d_counter, 0, sizeof(int), s));
     int ctas = std::max(1, t->num_sms * t->ctas_per_sm);
     launch_interact(d, dev_plan(t), o.precision, o.G, o.am_correction ? 1 : 0, ctas,
                     t->warps_per_cta, s);
@@ -439,7 +446,7 @@ int ot_build_tree(const ot_tree_desc* desc, int device, ot_tree** out) {
         (e = dalloc(t, &t->d_m32, C)) || (e = dalloc(t, &t->d_oct32, kOct * C)) ||
         (e = dalloc(t, &t->d_loc, kLoc * C)) ||
         (e = dalloc(t, &t->d_status, 1)) || (e = dalloc(t, &t->d_list_first, kNumLists)) ||
-        (e = dalloc(t, &t->d_list_len, kNumLists)) || (e = dalloc(t, &t->d_counter, 1)) ||
+        (e = dalloc(t, &t->d_list_len, kNumLists)) || (e = dalloc(t, &t->d_counter, 4)) ||
         (e = dalloc(t, &t->d_rho_in, (size_t)h.n_leaf * kCells)) ||
         (e = dalloc(t, &t->d_phi_out, (size_t)h.n_leaf * kCells)) ||
         (e = dalloc(t, &t->d_g_out, (size_t)h.n_leaf * 3 * kCells)))
@@ -614,31 +621,40 @@ int ot_autotune(ot_tree* t, const double* rho, double* phi, double* g, const ot_
     TRYC(cudaEventCreate(&e1));
     const int chunks[] = {32, 64, 128, 263};
     const int cps[] = {1, 2, 4, 8};
+    const bool bulk = o.precision == OT_PRECISION_FP32_BULK;
+    const int lcps_bulk[] = {1, 2, 4, 0};
+    const int lcps_fp64[] = {0};
+    const int* lcps = bulk ? lcps_bulk : lcps_fp64;
+    const int n_lcps = bulk ? 4 : 1;
     float best = 1e30f;
-    int bc = t->chunk, bp = t->ctas_per_sm;
+    int bc = t->chunk, bp = t->ctas_per_sm, bl = t->lattice_ctas_per_sm;
     int err = OT_OK;
     for (int c : chunks) {
         t->chunk = c;
         if ((err = ensure_plan(t, o.theta))) break;
         enqueue_moments(t, rho, s);
         for (int p : cps) {
-            t->ctas_per_sm = p;
-            float ms_sum = 0.0f;
-            for (int rep = 0; rep < 4 && err == OT_OK; rep++) {
-                cudaEventRecord(e0, s);
-                err = enqueue_interact(t, o, s);
-                cudaEventRecord(e1, s);
-                cudaEventSynchronize(e1);
-                float ms = 0.0f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (rep > 0) ms_sum += ms;  // first run warms the plan
+            for (int li = 0; li < n_lcps && err == OT_OK; li++) {
+                t->ctas_per_sm = p;
+                t->lattice_ctas_per_sm = lcps[li];
+                float ms_sum = 0.0f;
+                for (int rep = 0; rep < 4 && err == OT_OK; rep++) {
+                    cudaEventRecord(e0, s);
+                    err = enqueue_interact(t, o, s);
+                    cudaEventRecord(e1, s);
+                    cudaEventSynchronize(e1);
+                    float ms = 0.0f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep > 0) ms_sum += ms;  // first run warms the plan
+                }
+                if (err == OT_OK && ms_sum < best) {
+                    best = ms_sum;
+                    bc = c;
+                    bp = p;
+                    bl = lcps[li];
+                }
             }
             if (err) break;
-            if (ms_sum < best) {
-                best = ms_sum;
-                bc = c;
-                bp = p;
-            }
         }
         if (err) break;
     }
@@ -646,6 +662,7 @@ int ot_autotune(ot_tree* t, const double* rho, double* phi, double* g, const ot_
     cudaEventDestroy(e1);
     t->chunk = bc;
     t->ctas_per_sm = bp;
+    t->lattice_ctas_per_sm = bl;
     TRY(err);
     TRY(ensure_plan(t, o.theta));
     t->tuned = true;
@@ -691,6 +708,7 @@ int ot_tree_info(ot_tree* t, ot_tree_stats* st) {
     st->tuned_chunk = t->chunk;
     st->tuned_ctas_per_sm = t->ctas_per_sm;
     st->tuned_warps_per_cta = t->warps_per_cta;
+    st->tuned_lattice_ctas_per_sm = t->lattice_ctas_per_sm;
     st->workspace_bytes = t->workspace_bytes;
     if (t->device >= 0) {
         DeviceGuard guard(t->device);

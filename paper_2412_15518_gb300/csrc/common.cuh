@@ -132,6 +132,23 @@ __host__ __device__ __forceinline__ double widen(float f) {
 #endif
 }
 
+#if defined(__CUDACC__)
+// Asynchronous global -> shared copies (cp.async, through L1; 4, 8 or 16
+// bytes, both addresses aligned to the size): the copy needs no register and
+// nothing waits for it until cp.async.wait_group, so a thread can keep many
+// in flight.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(a), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) { cp_async<16>(smem, gmem); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+#endif
+
 // Stencil entries of a plan: int code = (dx+16) | (dy+16)<<5 | (dz+16)<<10 |
 // near<<15; lists are contiguous ranges of the entry array.
 struct DevPlan {
@@ -191,6 +208,9 @@ struct DevLattice {
     int n_nodes;
     int w_far, w_near;
     int n_near;
+    int* counter;               // [2] node counters of the persistent CTAs (near/all, far)
+    int n_far_max;              // largest far part of the 8 parity lists
+    int far_table_smem;         // 1: the FP32 far kernel stages its tables in shared memory
 };
 
 // Work item: x = target node; y = level | parity << 8 | half << 11 | list << 12;

@@ -151,17 +151,6 @@ __device__ __forceinline__ float small_int(int n, float) {
     return __int_as_float(0x4b000000 | n) - 8388608.0f;
 }
 
-// Asynchronous global -> shared copies (cp.async, 16 bytes, through L1):
-// the FP32 loop stages the next pair's source record in shared memory while
-// the current pair is computed, without holding it in registers.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
 // Per-warp shared staging of the FP32 loop: the item's stencil entries and
 // two stages of 32 source records (5 float4 each, component-major so that a
 // warp's 16-byte accesses are consecutive).
@@ -171,15 +160,25 @@ struct WarpStage32 {
     float4 rec[2][5][32];
 };
 
+// Small signed integer (|n| < 2^21) to float without a conversion
+// instruction: 2^23 + 2^21 + n is the float whose fraction bits are
+// 2^21 + n.
+__device__ __forceinline__ float small_sint(int n) {
+    return __int_as_float(0x4b000000 | (n + (1 << 21))) - 10485760.0f;
+}
+
 // Starts the copy of pair q's source into stage st and returns its kind:
-// 0 = no pair, 1 = leaf cell (monopole), 2 = interior cell (multipole).
+// 0 = no pair, 1 = leaf cell (monopole), 2 = interior cell (multipole); d
+// receives the entry's offset as floats.
 template <bool FULL>
 __device__ __forceinline__ int issue32(const DevTree& t, WarpStage32& ws, int q, int q0, int qend,
                                        int i, int j, int k, int lane, const int* s_nb,
-                                       const int* s_lf, int st) {
+                                       const int* s_lf, int st, float3& d) {
     if (q >= qend) return 0;
     const int e = ws.entries[q - q0];
-    const int sx = i + entry_dx(e), sy = j + entry_dy(e), sz = k + entry_dz(e);
+    const int dx = entry_dx(e), dy = entry_dy(e), dz = entry_dz(e);
+    d = make_float3(small_sint(dx), small_sint(dy), small_sint(dz));
+    const int sx = i + dx, sy = j + dy, sz = k + dz;
     const int slot = ((sx >> 3) + 1) + 3 * ((sy >> 3) + 1) + 9 * ((sz >> 3) + 1);
     const int nb = s_nb[slot];
     if (nb < 0) return 0;  // outside the domain, or covered by a coarser leaf
@@ -193,13 +192,6 @@ __device__ __forceinline__ int issue32(const DevTree& t, WarpStage32& ws, int q,
 #pragma unroll
         for (int r = 1; r < 5; r++) cp_async16(&ws.rec[st][r][lane], g + r);
     return sleaf ? 1 : 2;
-}
-
-// Small signed integer (|n| < 2^21) to float without a conversion
-// instruction: 2^23 + 2^21 + n is the float whose fraction bits are
-// 2^21 + n.
-__device__ __forceinline__ float small_sint(int n) {
-    return __int_as_float(0x4b000000 | (n + (1 << 21))) - 10485760.0f;
 }
 
 template <class T, bool FULL, bool AM>
@@ -250,21 +242,22 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
             for (int q = q0 + lane; q < q1; q += 32)
                 ws->entries[q - q0] = __ldg(p.entries + base + __ldg(p.item_entries + q));
             __syncwarp();
-            int kind = issue32<FULL>(t, *ws, q0, q0, q1, i, j, k, lane, s_nb, s_lf, 0);
+            float3 d = make_float3(0.f, 0.f, 0.f), d_next = d;
+            int kind = issue32<FULL>(t, *ws, q0, q0, q1, i, j, k, lane, s_nb, s_lf, 0, d);
             cp_async_commit();
 #pragma unroll 1
             for (int q = q0; q < q1; q++) {
                 const int st = (q - q0) & 1;
-                const int kind_next = issue32<FULL>(t, *ws, q + 1, q0, q1, i, j, k, lane, s_nb, s_lf, st ^ 1);
+                const int kind_next =
+                    issue32<FULL>(t, *ws, q + 1, q0, q1, i, j, k, lane, s_nb, s_lf, st ^ 1, d_next);
                 cp_async_commit();
                 cp_async_wait1();  // this lane's copies of pair q are done
                 if (kind) {
-                    const int e = ws->entries[q - q0];
                     const float4 h = ws->rec[st][0][lane];
                     // R' = X_A - X_B in cell units: the source sits at offset d
-                    const float x = (dax - h.y) - small_sint(entry_dx(e));
-                    const float y = (day - h.z) - small_sint(entry_dy(e));
-                    const float z = (daz - h.w) - small_sint(entry_dz(e));
+                    const float x = (dax - h.y) - d.x;
+                    const float y = (day - h.z) - d.y;
+                    const float z = (daz - h.w) - d.z;
                     if (kind == 1) {
                         m2l_pair<float, FULL, false, AM>(x, y, z, h.x, nullptr, nullptr, nullptr, a3, ta, A);
                     } else {
@@ -278,6 +271,7 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
                     }
                 }
                 kind = kind_next;
+                d = d_next;
             }
             cp_async_wait0();
             __syncwarp();  // the stage and entry buffers are reused by the next item

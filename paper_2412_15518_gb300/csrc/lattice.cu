@@ -8,8 +8,8 @@
 // two terms at a leaf target.  Over one leaf node this is a small 3-D
 // convolution of the masses with a parity-dependent stencil.
 //
-// One CTA per leaf node, 8 warps (one per parity class of targets), each lane
-// 2 targets 4 cells apart in z.  The masses of the node and of a margin w
+// A CTA of 8 warps handles one leaf node at a time (one warp per parity
+// class of targets, each lane 2 targets 4 cells apart in z).  The masses of the node and of a margin w
 // around it are staged once in shared memory (parity-split, padded so a warp
 // reads 32 banks); cells of absent or interior neighbours are stored as zero
 // mass, so the inner loop has no branches: per stencil entry one broadcast
@@ -25,29 +25,42 @@ namespace otfmm {
 namespace {
 
 // Fills a parity-split halo of width w with the masses of the leaf cells
-// around `node` (zero where there is no leaf cell at this level): one warp
-// per row of the halo, lanes along x.  The masses are read from the
-// contiguous FP64 or FP32 array (coalesced), so no conversion is needed.
+// around `node` (zero where there is no leaf cell at this level).  The 27
+// neighbours are resolved once into shared memory (s_nbl: the neighbour node
+// if it is a leaf, else -1); then one warp per halo row, lanes along x, each
+// mass copied by cp.async straight into its halo slot (coalesced reads of
+// the contiguous FP64 or FP32 mass array, no conversion, and nothing waits
+// per element).  The caller waits (cp.async.wait_all) and synchronises.
 __device__ __forceinline__ const double* mass_array(const DevTree& t, double) { return t.mom64; }
 __device__ __forceinline__ const float* mass_array(const DevTree& t, float) { return t.m32; }
 
 template <class T>
-__device__ __forceinline__ void fill_halo(const DevTree& t, int node, int w, T* halo) {
+__device__ __forceinline__ void fill_halo(const DevTree& t, int node, int w, T* halo, int* s_nbl) {
+    if (threadIdx.x < 27) {
+        const int nb = __ldg(t.nbr + (long long)node * 27 + threadIdx.x);
+        s_nbl[threadIdx.x] = nb >= 0 && __ldg(t.node_leaf + nb) >= 0 ? nb : -1;
+    }
+    __syncthreads();
     const T* __restrict__ mass = mass_array(t, T(0));
     const int hw = 8 + 2 * w;
-    const int* nbr = t.nbr + (long long)node * 27;
     const int lane = threadIdx.x & 31;
     const int nwarp = blockDim.x >> 5;
+    const int x = lane - w;
+    if (lane >= hw) return;
+    const int sx = (x >> 3) + 1, lx = x & 7;
+    int y = (threadIdx.x >> 5) % hw - w, z = (threadIdx.x >> 5) / hw - w;
     for (int row = threadIdx.x >> 5; row < hw * hw; row += nwarp) {
-        const int y = row % hw - w, z = row / hw - w;
-        const int x = lane - w;
-        if (lane >= hw) continue;
-        const int slot = ((x >> 3) + 1) + 3 * ((y >> 3) + 1) + 9 * ((z >> 3) + 1);
-        const int nb = __ldg(nbr + slot);
-        T v = T(0.0);
-        if (nb >= 0 && __ldg(t.node_leaf + nb) >= 0)
-            v = mass[(long long)nb * kCells + (x & 7) + 8 * (y & 7) + 64 * (z & 7)];
-        halo[halo_index(x, y, z, w)] = v;
+        const int nb = s_nbl[sx + 3 * ((y >> 3) + 1) + 9 * ((z >> 3) + 1)];
+        T* dst = halo + halo_index(x, y, z, w);
+        if (nb >= 0)
+            cp_async<sizeof(T)>(dst, mass + (long long)nb * kCells + lx + 8 * (y & 7) + 64 * (z & 7));
+        else
+            *dst = T(0.0);
+        y += nwarp;  // next row of this warp: (y, z) advanced without a division
+        while (y >= hw - w) {
+            y -= hw;
+            z++;
+        }
     }
 }
 
@@ -58,15 +71,14 @@ __device__ __forceinline__ void fill_halo(const DevTree& t, int node, int w, T* 
 // kernel and of the FP32-pipe kernels share the SMs.
 enum LatticeMode { kAll = 0, kNear = 1, kFar = 2 };
 
+// One node of the lattice pairs, by a CTA of 8 warps (one per parity class).
 template <int MODE>
-__global__ void __launch_bounds__(256) k_lattice(DevTree t, DevPlan p, DevLattice lp, LevelScales sc) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int node = lp.nodes[blockIdx.x];
+__device__ __forceinline__ void lattice_node(const DevTree& t, const DevPlan& p, const DevLattice& lp,
+                                             const LevelScales& sc, int node,
+                                             unsigned char* smem, int* s_nbl) {
     const int w = MODE == kNear ? lp.w_near : lp.w_far;
-    if (MODE == kFar)
-        fill_halo<float>(t, node, w, reinterpret_cast<float*>(smem));
-    else
-        fill_halo<double>(t, node, w, reinterpret_cast<double*>(smem));
+    fill_halo<double>(t, node, w, reinterpret_cast<double*>(smem), s_nbl);
+    cp_async_wait_all();
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
@@ -109,21 +121,6 @@ __global__ void __launch_bounds__(256) k_lattice(DevTree t, DevPlan p, DevLattic
             e0 = fma(m2, k0.x, e0); e1 = fma(m2, k0.y, e1); e2 = fma(m2, k1.x, e2); e3 = fma(m2, k1.y, e3);
         }
     }
-    if (MODE == kFar) {
-        // far pairs in FP32, widened exactly to FP64 once per target
-        float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
-        const float* hf = reinterpret_cast<const float*>(smem);
-#pragma unroll 4
-        for (int q = lp.n_near; q < len; q++) {
-            const int o = __ldg(lp.hoff_far + base + q) + t1;
-            const float4 k = __ldg(p.tab32 + base + q);
-            const float m1 = hf[o], m2 = hf[o + t2];
-            f0 = fmaf(m1, k.x, f0); f1 = fmaf(m1, k.y, f1); f2 = fmaf(m1, k.z, f2); f3 = fmaf(m1, k.w, f3);
-            g0 = fmaf(m2, k.x, g0); g1 = fmaf(m2, k.y, g1); g2 = fmaf(m2, k.z, g2); g3 = fmaf(m2, k.w, g3);
-        }
-        d0 = widen(f0); d1 = widen(f1); d2 = widen(f2); d3 = widen(f3);
-        e0 = widen(g0); e1 = widen(g1); e2 = widen(g2); e3 = widen(g3);
-    }
     // to physical units: L0 * (-G / h), L1 * (-G / h^2)
     const int L = t.node_level[node];
     const double s1 = sc.s64[L][0], s2 = sc.s64[L][1];
@@ -141,16 +138,132 @@ __global__ void __launch_bounds__(256) k_lattice(DevTree t, DevPlan p, DevLattic
     atomicAdd(loc + 3 * N + c2, s2 * e3);
 }
 
+// Shared-memory layout of the FP32 far kernel: the FP32 halo, then (when it
+// fits) the far part of the 8 parity lists: coefficients float4 [8][n_far_max],
+// halo offsets int [8][n_far_max].
+__device__ __forceinline__ float4* far_coef(unsigned char* smem, const DevLattice& lp) {
+    return reinterpret_cast<float4*>(smem + sizeof(float) * 8 * (size_t)halo_sub(lp.w_far));
+}
+__device__ __forceinline__ int* far_hoff(unsigned char* smem, const DevLattice& lp) {
+    return reinterpret_cast<int*>(far_coef(smem, lp) + 8 * lp.n_far_max);
+}
+
+// Copies the far tables into shared memory (once per persistent CTA).
+__device__ __forceinline__ void lattice_far_tables(const DevPlan& p, const DevLattice& lp,
+                                                   unsigned char* smem) {
+    float4* kc = far_coef(smem, lp);
+    int* ho = far_hoff(smem, lp);
+    for (int par = 0; par < 8; par++) {
+        const int len = p.list_len[par] - lp.n_near;
+        const int at = p.list_first[par] + lp.n_near;
+        for (int q = threadIdx.x; q < len; q += blockDim.x) {
+            cp_async<16>(kc + par * lp.n_far_max + q, p.tab32 + at + q);
+            cp_async<4>(ho + par * lp.n_far_max + q, lp.hoff_far + at + q);
+        }
+    }
+    cp_async_wait_all();  // made visible to the CTA by the caller's next barrier
+}
+
+// FP32 far pairs of one node by a CTA of 4 warps: a half-warp per parity
+// class, each lane 4 targets along z (so one table entry feeds 16 FMAs);
+// FP32 sums widened exactly to FP64 once per target.
+__device__ __forceinline__ void lattice_far_node(const DevTree& t, const DevPlan& p,
+                                                 const DevLattice& lp, const LevelScales& sc,
+                                                 int node, unsigned char* smem, int* s_nbl) {
+    const int w = lp.w_far;
+    fill_halo<float>(t, node, w, reinterpret_cast<float*>(smem), s_nbl);
+    cp_async_wait_all();
+    __syncthreads();
+    const float* hf = reinterpret_cast<const float*>(smem);
+    const int lane = threadIdx.x & 31;
+    const int par = 2 * (threadIdx.x >> 5) + (lane >> 4);
+    const int a = lane & 3, b = (lane >> 2) & 3;
+    const int px = par & 1, py = (par >> 1) & 1, pz = par >> 2;
+    const int base = p.list_first[par];
+    const int len = p.list_len[par];
+    const int pzs = halo_pz(w);              // z stride of a parity sub-halo
+    const int t0 = a + kHaloPy * b;          // lane offset (first target) in the halo
+    float f[4][4];
+#pragma unroll
+    for (int c = 0; c < 4; c++)
+#pragma unroll
+        for (int r = 0; r < 4; r++) f[c][r] = 0.f;
+    auto entry = [&](int o, const float4 k) {
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            const float m = hf[o + c * pzs];
+            f[c][0] = fmaf(m, k.x, f[c][0]);
+            f[c][1] = fmaf(m, k.y, f[c][1]);
+            f[c][2] = fmaf(m, k.z, f[c][2]);
+            f[c][3] = fmaf(m, k.w, f[c][3]);
+        }
+    };
+    if (lp.far_table_smem) {
+        // tables staged in shared memory by the CTA (lattice_far_tables)
+        const float4* kc = far_coef(smem, lp) + par * lp.n_far_max;
+        const int* ho = far_hoff(smem, lp) + par * lp.n_far_max;
+        const int nf = len - lp.n_near;
+#pragma unroll 4
+        for (int q = 0; q < nf; q++) entry(ho[q] + t0, kc[q]);
+    } else {
+#pragma unroll 2
+        for (int q = lp.n_near; q < len; q++) entry(__ldg(lp.hoff_far + base + q) + t0, __ldg(p.tab32 + base + q));
+    }
+    const int L = t.node_level[node];
+    const double s1 = sc.s64[L][0], s2 = sc.s64[L][1];
+    const long long N = t.n_cells;
+    double* loc = t.loc;
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        const long long cell = (long long)node * kCells + (2 * a + px) + 8 * (2 * b + py) + 64 * (2 * c + pz);
+        atomicAdd(loc + cell, s1 * widen(f[c][0]));
+        atomicAdd(loc + N + cell, s2 * widen(f[c][1]));
+        atomicAdd(loc + 2 * N + cell, s2 * widen(f[c][2]));
+        atomicAdd(loc + 3 * N + cell, s2 * widen(f[c][3]));
+    }
+}
+
+// Persistent CTAs: each takes the next node from its mode's counter until
+// none are left, so a bounded number of CTAs per SM leaves room for the
+// kernels of the other graph branches on the same SMs.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_lattice(DevTree t, DevPlan p, DevLattice lp, LevelScales sc) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_task;
+    __shared__ int s_nbl[27];
+    int* counter = lp.counter + (MODE == kFar ? 1 : 0);
+    if (MODE == kFar && lp.far_table_smem) lattice_far_tables(p, lp, smem);  // visible after the next barrier
+    for (;;) {
+        if (threadIdx.x == 0) s_task = atomicAdd(counter, 1);
+        __syncthreads();
+        const int task = s_task;
+        if (task >= lp.n_nodes) break;
+        if (MODE == kFar)
+            lattice_far_node(t, p, lp, sc, lp.nodes[task], smem, s_nbl);
+        else
+            lattice_node<MODE>(t, p, lp, sc, lp.nodes[task], smem, s_nbl);
+        __syncthreads();  // the halo and s_task are rewritten for the next node
+    }
+}
+
 }  // namespace
 
-size_t lattice_smem_bytes(int mode, int w_far, int w_near) {
-    if (mode == kFar) return sizeof(float) * 8 * (size_t)halo_sub(w_far);
+size_t lattice_smem_bytes(int mode, int w_far, int w_near, int far_table_entries) {
+    if (mode == kFar)
+        return sizeof(float) * 8 * (size_t)halo_sub(w_far) + (size_t)far_table_entries * (16 + 4);
     if (mode == kNear) return sizeof(double) * 8 * (size_t)halo_sub(w_near);
     return sizeof(double) * 8 * (size_t)halo_sub(w_far);
 }
 
+void lattice_far_table_plan(DevLattice& lp, const int* list_len) {
+    int m = 0;
+    for (int par = 0; par < 8; par++) m = list_len[par] - lp.n_near > m ? list_len[par] - lp.n_near : m;
+    lp.n_far_max = m;
+    lp.far_table_smem = lattice_smem_bytes(kFar, lp.w_far, lp.w_near, 8 * m) <= kLatticeSmemMax ? 1 : 0;
+}
+
 int configure_lattice() {
-    const int bytes = 160 * 1024;
+    const int bytes = (int)kLatticeSmemMax;
     if (cudaFuncSetAttribute(k_lattice<kAll>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
             cudaSuccess ||
         cudaFuncSetAttribute(k_lattice<kNear>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
@@ -164,15 +277,17 @@ int configure_lattice() {
 }
 
 void launch_lattice(const DevTree& t, const DevPlan& p, const DevLattice& lp, int precision,
-                    double G, cudaStream_t s, cudaStream_t s_far) {
+                    double G, int ctas, cudaStream_t s, cudaStream_t s_far) {
     if (lp.n_nodes <= 0) return;
     const LevelScales sc = level_scales(t.inv_side8, G);
+    const int grid = ctas > 0 && ctas < lp.n_nodes ? ctas : lp.n_nodes;
     if (precision == 1) {
-        k_lattice<kNear><<<lp.n_nodes, 256, lattice_smem_bytes(kNear, lp.w_far, lp.w_near), s>>>(t, p, lp, sc);
-        k_lattice<kFar><<<lp.n_nodes, 256, lattice_smem_bytes(kFar, lp.w_far, lp.w_near),
-                          s_far ? s_far : s>>>(t, p, lp, sc);
+        const int tab = lp.far_table_smem ? 8 * lp.n_far_max : 0;
+        cudaStream_t sf = s_far ? s_far : s;
+        k_lattice<kNear><<<grid, 256, lattice_smem_bytes(kNear, lp.w_far, lp.w_near, 0), s>>>(t, p, lp, sc);
+        k_lattice<kFar><<<grid, 128, lattice_smem_bytes(kFar, lp.w_far, lp.w_near, tab), sf>>>(t, p, lp, sc);
     } else {
-        k_lattice<kAll><<<lp.n_nodes, 256, lattice_smem_bytes(kAll, lp.w_far, lp.w_near), s>>>(t, p, lp, sc);
+        k_lattice<kAll><<<grid, 256, lattice_smem_bytes(kAll, lp.w_far, lp.w_near, 0), s>>>(t, p, lp, sc);
     }
 }
 

@@ -88,7 +88,7 @@ Layout make_layout() {
     l.rec64 = take(sizeof(double) * kRec * cells);
     l.loc = take(sizeof(double) * kLoc * cells);
     l.status = take(sizeof(int));
-    l.counter = take(sizeof(int));
+    l.counter = take(4 * sizeof(int));
     l.entries = take(sizeof(int) * kMaxEntries);
     l.tab64 = take(sizeof(double) * 4 * kMaxEntries);
     l.tab32 = take(sizeof(float) * 4 * kMaxEntries);
@@ -212,11 +212,11 @@ extern "C" int ot_solve_gravity_static(const ot_tree_desc* desc, const double* r
         cudaMemsetAsync(base + l.rec64, 0, sizeof(double) * kRec * cells, s) != cudaSuccess ||
         cudaMemsetAsync(base + l.loc, 0, sizeof(double) * kLoc * cells, s) != cudaSuccess ||
         cudaMemsetAsync(base + l.status, 0, sizeof(int), s) != cudaSuccess ||
-        cudaMemsetAsync(base + l.counter, 0, sizeof(int), s) != cudaSuccess) {
+        cudaMemsetAsync(base + l.counter, 0, 4 * sizeof(int), s) != cudaSuccess) {
         cudaGetLastError();
         return OT_ERR_CUDA;
     }
-    DevTree d;
+    DevTree d = {};
     d.n_levels = h.n_levels;
     d.n_nodes = N;
     d.n_leaf = h.n_leaf;
@@ -237,7 +237,7 @@ extern "C" int ot_solve_gravity_static(const ot_tree_desc* desc, const double* r
     d.inv_side8 = 8.0 / h.size;
     d.loc = (double*)(base + l.loc);
     d.status = (int*)(base + l.status);
-    DevPlan dp;
+    DevPlan dp = {};
     dp.entries = (const int*)(base + l.entries);
     dp.tab64 = (const double2*)(base + l.tab64);
     dp.tab32 = (const float4*)(base + l.tab32);
@@ -258,7 +258,7 @@ extern "C" int ot_solve_gravity_static(const ot_tree_desc* desc, const double* r
     launch_leaf_moments(d, (const int*)(base + l.leaf_node), rho, s);
     for (int L = h.n_levels - 2; L >= 0; L--)
         launch_m2m(d, L, h.level_first[L], h.level_first[L + 1] - h.level_first[L], s);
-    DevLattice dl;
+    DevLattice dl = {};
     dl.hoff_far = (const int*)(base + l.hoff_far);
     dl.hoff_near = (const int*)(base + l.hoff_near);
     dl.nodes = (const int*)(base + l.lattice_nodes);
@@ -266,7 +266,9 @@ extern "C" int ot_solve_gravity_static(const ot_tree_desc* desc, const double* r
     dl.w_far = p.w_far;
     dl.w_near = p.w_near;
     dl.n_near = p.n_near;
-    launch_lattice(d, dp, dl, o.precision, o.G, s);
+    dl.counter = (int*)(base + l.counter) + 1;
+    lattice_far_table_plan(dl, p.list_len);
+    launch_lattice(d, dp, dl, o.precision, o.G, 0, s);
     launch_interact(d, dp, o.precision, o.G, o.am_correction ? 1 : 0, 4 * sms, 4, s);
     for (int L = 0; L < h.n_levels; L++)
         launch_l2l(d, L, h.level_first[L], h.level_first[L + 1] - h.level_first[L], rho, phi, g,

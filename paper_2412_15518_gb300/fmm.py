@@ -53,6 +53,7 @@ class ot_tree_stats(ctypes.Structure):
                 ("flops_near", ctypes.c_double),
                 ("n_work_items", ctypes.c_int64), ("tuned_chunk", ctypes.c_int32),
                 ("tuned_ctas_per_sm", ctypes.c_int32), ("tuned_warps_per_cta", ctypes.c_int32),
+                ("tuned_lattice_ctas_per_sm", ctypes.c_int32),
                 ("device_status", ctypes.c_int32), ("workspace_bytes", ctypes.c_int64)]
 
 
@@ -190,7 +191,8 @@ def ot_tree_info(tree) -> dict:
                 n_mm=st.n_mm, flops_am=st.flops_am, flops_noam=st.flops_noam,
                 flops_near=st.flops_near, n_work_items=st.n_work_items,
                 tuned_chunk=st.tuned_chunk, tuned_ctas_per_sm=st.tuned_ctas_per_sm,
-                tuned_warps_per_cta=st.tuned_warps_per_cta, device_status=st.device_status,
+                tuned_warps_per_cta=st.tuned_warps_per_cta,
+                tuned_lattice_ctas_per_sm=st.tuned_lattice_ctas_per_sm, device_status=st.device_status,
                 workspace_bytes=st.workspace_bytes)
     _check(code, "ot_tree_info")
     return info
