@@ -44,6 +44,13 @@ PEAK_FP64_TFLOPS = NUM_SMS * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
 PEAK_FP32_TFLOPS = NUM_SMS * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 
+# DRAM bytes (read + write) of one interaction phase, from the ncu capture of
+# the interaction kernels summarised in profiles/ (k_interact + the lattice
+# kernels of the form, per launch).  Valid for these kernels as captured; a
+# workload or form without a capture reports null.
+TRAFFIC_BYTES = {("binary_l3", "fp64"): 15.398e6 + 10.637e6,
+                 ("binary_l3", "fp32_bulk"): 13.435e6 + 10.566e6 + 9.563e6}
+
 WORKLOAD_TEXT = {
     "sphere_l1": "uniform level-1 octree, 8 leaves of 8^3 (4,096 cells), one polytrope",
     "binary_l3": "uniform level-3 octree, 512 leaves of 8^3 (262,144 cells), binary "
@@ -85,13 +92,19 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (FileNotFoundError, OSError):
             self.proc = None
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        # nvidia-smi takes a while to print its first row: start timing only
+        # once it samples, so the samples fall inside the timed region
+        t0 = time.time()
+        while not self.rows and time.time() - t0 < 3.0 and self.proc.poll() is None:
+            time.sleep(0.01)
+        self.rows.clear()
 
     def _read(self):
         for line in self.proc.stdout:
@@ -304,8 +317,9 @@ def run_ours(args):
     if prec == fmm.OT_PRECISION_FP64:
         achieved = flops / (inter_avg / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": PEAK_FP64_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / PEAK_FP64_TFLOPS, "traffic": None,
-                "kernel": "k_interact<double> + k_lattice<double> (concurrent)",
+                "unit": "TFLOP/s", "frac": achieved / PEAK_FP64_TFLOPS,
+                "traffic": TRAFFIC_BYTES.get((args.workload, "fp64")),
+                "kernel": "k_interact<double> + k_lattice<0> (concurrent graph branches)",
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz",
                 "flops_per_launch": flops, "launch_ms": inter_avg}
     else:
@@ -316,8 +330,9 @@ def run_ours(args):
         mixed_ms = 1e3 * max(f32 / (PEAK_FP32_TFLOPS * 1e12),
                              info["flops_near"] / (PEAK_FP64_TFLOPS * 1e12))
         roof = {"bound": "alu", "achieved": achieved, "peak": PEAK_FP32_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / PEAK_FP32_TFLOPS, "traffic": None,
-                "kernel": "k_interact<float> + k_lattice<float> (concurrent)",
+                "unit": "TFLOP/s", "frac": achieved / PEAK_FP32_TFLOPS,
+                "traffic": TRAFFIC_BYTES.get((args.workload, "fp32_bulk")),
+                "kernel": "k_interact<float> + k_lattice<1> + k_lattice<2> (concurrent graph branches)",
                 "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 flops x 2070 MHz",
                 "flops_per_launch": f32, "fp64_flops_per_launch": info["flops_near"],
                 "launch_ms": inter_avg, "mixed_bound_ms": mixed_ms,
