@@ -412,7 +412,13 @@ def run_ours(args):
         extra["cpu_baseline"] = cpu_baseline(leaves, rho_np)
     # leaf moments, 2 M2M kernels per interior level, lattice, interactions,
     # 2 L2L kernels per level
-    launches = (1 + 2 * (info["n_levels"] - 1) + 2 + 2 * info["n_levels"]) * args.steps
+    # library kernels of one solve: leaf moments, 2 M2M kernels per parent
+    # level, the general interaction kernel, the lattice kernels (1 in the
+    # FP64 form, near + far in the FP32-bulk form; none without leaf nodes
+    # below the root), 2 L2L kernels per level
+    lattice = sum(info["n_leaf_nodes"][1:info["n_levels"]]) > 0
+    n_lat = (2 if prec == fmm.OT_PRECISION_FP32_BULK else 1) if lattice else 0
+    launches = (1 + 2 * (info["n_levels"] - 1) + 1 + n_lat + 2 * info["n_levels"]) * args.steps
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,

@@ -619,9 +619,15 @@ int ot_autotune(ot_tree* t, const double* rho, double* phi, double* g, const ot_
     cudaEvent_t e0, e1;
     TRYC(cudaEventCreate(&e0));
     TRYC(cudaEventCreate(&e1));
-    const int chunks[] = {32, 64, 128, 263};
-    const int cps[] = {1, 2, 4, 8};
     const bool bulk = o.precision == OT_PRECISION_FP32_BULK;
+    // the FP32-bulk form flushes its FP32 partial sums every 64 pairs anyway
+    // (their rounding error grows with the summation length), so longer
+    // items buy it nothing
+    const int chunks_fp64[] = {32, 64, 128, 263};
+    const int chunks_bulk[] = {32, 64};
+    const int* chunks = bulk ? chunks_bulk : chunks_fp64;
+    const int n_chunks = bulk ? 2 : 4;
+    const int cps[] = {1, 2, 4, 8};
     const int lcps_bulk[] = {1, 2, 4, 0};
     const int lcps_fp64[] = {0};
     const int* lcps = bulk ? lcps_bulk : lcps_fp64;
@@ -629,7 +635,8 @@ int ot_autotune(ot_tree* t, const double* rho, double* phi, double* g, const ot_
     float best = 1e30f;
     int bc = t->chunk, bp = t->ctas_per_sm, bl = t->lattice_ctas_per_sm;
     int err = OT_OK;
-    for (int c : chunks) {
+    for (int ci = 0; ci < n_chunks; ci++) {
+        const int c = chunks[ci];
         t->chunk = c;
         if ((err = ensure_plan(t, o.theta))) break;
         enqueue_moments(t, rho, s);

@@ -155,6 +155,7 @@ __device__ __forceinline__ float small_int(int n, float) {
 // two stages of 32 source records (5 float4 each, component-major so that a
 // warp's 16-byte accesses are consecutive).
 constexpr int kMaxChunk = 264;
+constexpr int kFlush32 = 64;  // pairs per FP32 partial sum (a power of two)
 struct WarpStage32 {
     int entries[kMaxChunk];
     float4 rec[2][5][32];
@@ -212,6 +213,41 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
     Acc<T> A;
     acc_zero(A);
     double n0 = 0.0, n1 = 0.0, n2 = 0.0, n3 = 0.0;  // FP64 near leaf pairs (bulk form)
+    // Adds the partial sums into the cell's FP64 expansion with atomics,
+    // scaled to physical units: L^(n) * (-G h^-(n+1)), correction * -(G/6) h^-2,
+    // with the level's factors in the accumulators' type.
+    auto flush = [&]() {
+        const T* sl = scales_of(sc, L, T(0));
+        const T s1 = sl[0], s2 = sl[1], s3 = sl[2], s4 = sl[3];
+        double* loc = t.loc;
+        if (sizeof(T) == 4 && L == 0 && !FULL) {
+            // a leaf root: its near pairs were summed in FP64
+            const double s1d = sc.s64[0][0], s2d = sc.s64[0][1];
+            atomicAdd(loc + cell, scaled(A.L0, s1) + s1d * n0);
+            atomicAdd(loc + N + cell, scaled(A.L1[0], s2) + s2d * n1);
+            atomicAdd(loc + 2 * N + cell, scaled(A.L1[1], s2) + s2d * n2);
+            atomicAdd(loc + 3 * N + cell, scaled(A.L1[2], s2) + s2d * n3);
+        } else {
+            atomicAdd(loc + cell, scaled(A.L0, s1));
+            atomicAdd(loc + N + cell, scaled(A.L1[0], s2));
+            atomicAdd(loc + 2 * N + cell, scaled(A.L1[1], s2));
+            atomicAdd(loc + 3 * N + cell, scaled(A.L1[2], s2));
+        }
+        if (FULL) {
+            finish_acc(A);  // Kronecker parts of L2 and L3 from their traces
+#pragma unroll
+            for (int r = 0; r < 6; r++) atomicAdd(loc + (4 + r) * N + cell, scaled(A.L2[r], s3));
+#pragma unroll
+            for (int r = 0; r < 10; r++) atomicAdd(loc + (10 + r) * N + cell, scaled(A.L3[r], s4));
+        }
+        if (AM) {
+            // a_c = -(G/6) h^-2 (S - P)
+            const T sa = sl[4];
+#pragma unroll
+            for (int a = 0; a < 3; a++)
+                atomicAdd(loc + (20 + a) * N + cell, scaled(FULL ? A.S[a] - A.P[a] : A.S[a], sa));
+        }
+    };
     if (FULL && item_list(it) == kRootList) {
         // the interior root: sources are the root's own cells [z, w), the
         // same cell for every lane (a broadcast load); a pair is far iff
@@ -272,6 +308,12 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
                 }
                 kind = kind_next;
                 d = d_next;
+                // FP32 partial sums span at most kFlush32 pairs: their rounding
+                // error grows with the summation length
+                if (((q - q0) & (kFlush32 - 1)) == kFlush32 - 1 && q + 1 < q1) {
+                    flush();
+                    acc_zero(A);
+                }
             }
             cp_async_wait0();
             __syncwarp();  // the stage and entry buffers are reused by the next item
@@ -329,38 +371,7 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
         }
     }
     }
-    // scale to physical units: L^(n) * (-G h^-(n+1)), correction * -(G/6) h^-2,
-    // with the level's factors in the accumulators' type
-    const T* sl = scales_of(sc, L, T(0));
-    const T s1 = sl[0], s2 = sl[1], s3 = sl[2], s4 = sl[3];
-    double* loc = t.loc;
-    if (sizeof(T) == 4 && L == 0 && !FULL) {
-        // a leaf root: its near pairs were summed in FP64
-        const double s1d = sc.s64[0][0], s2d = sc.s64[0][1];
-        atomicAdd(loc + cell, scaled(A.L0, s1) + s1d * n0);
-        atomicAdd(loc + N + cell, scaled(A.L1[0], s2) + s2d * n1);
-        atomicAdd(loc + 2 * N + cell, scaled(A.L1[1], s2) + s2d * n2);
-        atomicAdd(loc + 3 * N + cell, scaled(A.L1[2], s2) + s2d * n3);
-    } else {
-        atomicAdd(loc + cell, scaled(A.L0, s1));
-        atomicAdd(loc + N + cell, scaled(A.L1[0], s2));
-        atomicAdd(loc + 2 * N + cell, scaled(A.L1[1], s2));
-        atomicAdd(loc + 3 * N + cell, scaled(A.L1[2], s2));
-    }
-    if (FULL) {
-        finish_acc(A);  // Kronecker parts of L2 and L3 from their traces
-#pragma unroll
-        for (int r = 0; r < 6; r++) atomicAdd(loc + (4 + r) * N + cell, scaled(A.L2[r], s3));
-#pragma unroll
-        for (int r = 0; r < 10; r++) atomicAdd(loc + (10 + r) * N + cell, scaled(A.L3[r], s4));
-    }
-    if (AM) {
-        // a_c = -(G/6) h^-2 (S - P)
-        const T sa = sl[4];
-#pragma unroll
-        for (int a = 0; a < 3; a++)
-            atomicAdd(loc + (20 + a) * N + cell, scaled(FULL ? A.S[a] - A.P[a] : A.S[a], sa));
-    }
+    flush();
 }
 
 template <class T>
