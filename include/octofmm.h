@@ -168,10 +168,13 @@ int ot_gravity_backward(ot_tree* tree, const double* rho, const double* w1, cons
 int ot_autotune(ot_tree* tree, const double* rho, double* phi, double* g,
                 const ot_solve_opts* opts, void* stream);
 
-/* Device time in milliseconds of the interaction launch (all levels) and of
- * the whole solve in the most recent ot_solve_gravity(_host) on this tree,
- * from CUDA events recorded around them inside the solve's CUDA graph.
- * Waits for those events.  Either pointer may be NULL. */
+/* Device time in milliseconds of the interaction phase and of the whole
+ * solve in the most recent ot_solve_gravity(_host) on this tree, from CUDA
+ * events recorded inside the solve's CUDA graph.  The interaction phase runs
+ * from the end of the leaf-moment kernel to the end of the last interaction
+ * kernel; the M2M kernels of the interior levels run inside it, concurrently
+ * with the leaf-leaf interactions.  Waits for those events.  Either pointer
+ * may be NULL. */
 int ot_last_solve_times(ot_tree* tree, float* interact_ms, float* solve_ms);
 
 /* Counts of the tree and of the current plan; synchronises the tree's last

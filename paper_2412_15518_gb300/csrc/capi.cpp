@@ -292,22 +292,29 @@ int check_dev_ptr(const ot_tree* t, const void* p) {
     return OT_OK;
 }
 
-// Enqueues the upward pass.
-void enqueue_moments(ot_tree* t, const double* rho, cudaStream_t s) {
+// Upward pass, in two parts: the leaf point masses, then M2M level by level.
+void enqueue_leaf_moments(ot_tree* t, const double* rho, cudaStream_t s) {
+    launch_leaf_moments(dev_tree(t), t->d_leaf_node, rho, s);
+}
+void enqueue_m2m(ot_tree* t, cudaStream_t s) {
     DevTree d = dev_tree(t);
-    launch_leaf_moments(d, t->d_leaf_node, rho, s);
     for (int L = t->h.n_levels - 2; L >= 0; L--)
         launch_m2m(d, L, t->h.level_first[L], t->h.level_first[L + 1] - t->h.level_first[L], s);
 }
+void enqueue_moments(ot_tree* t, const double* rho, cudaStream_t s) {
+    enqueue_leaf_moments(t, rho, s);
+    enqueue_m2m(t, s);
+}
 
-// Enqueues the interaction launch (expansions zeroed first).
-int enqueue_interact(ot_tree* t, const ot_solve_opts& o, cudaStream_t s) {
-    DevTree d = dev_tree(t);
-    // the expansions were zeroed by the upward pass (leaf and M2M kernels).
-    // The lattice kernels (leaf-leaf pairs) and the general kernel (pairs
-    // with an interior cell) only add into the expansions with atomics, so
-    // they run as concurrent branches: in the bulk form the near-pair lattice
-    // kernel is FP64 work and the other two FP32 work, and the pipes overlap.
+// The interaction kernels only add into the expansions with atomics, so they
+// run as concurrent graph branches: the lattice kernels (leaf-leaf pairs) on
+// side streams, the general kernel (pairs with an interior cell) on s.  The
+// lattice kernels read only the leaf masses and write only leaf cells'
+// expansions (both set by the leaf-moment kernel; no M2M kernel touches
+// them), so they may be forked before the M2M chain.  In the bulk form the
+// near-pair lattice kernel is FP64 work and the other two FP32 work, and the
+// pipes overlap.
+int fork_lattice(ot_tree* t, const ot_solve_opts& o, cudaStream_t s) {
     const bool bulk = o.precision == OT_PRECISION_FP32_BULK;
     // work counters: [0] general kernel, [1] near (or all) lattice, [2] far lattice
     TRYC(cudaMemsetAsync(t->d_counter, 0, 4 * sizeof(int), s));
@@ -316,18 +323,30 @@ int enqueue_interact(ot_tree* t, const ot_solve_opts& o, cudaStream_t s) {
     if (bulk) TRYC(cudaStreamWaitEvent(t->far_stream, t->ev_fork, 0));
     // bulk form: a bounded number of persistent lattice CTAs per SM (tuned)
     // leaves room for the general kernel, so the kernels share the SMs
-    launch_lattice(d, dev_plan(t), dev_lattice(t), o.precision, o.G,
+    launch_lattice(dev_tree(t), dev_plan(t), dev_lattice(t), o.precision, o.G,
                    bulk ? t->num_sms * t->lattice_ctas_per_sm : 0, t->side_stream,
                    bulk ? t->far_stream : nullptr);
     TRYC(cudaEventRecord(t->ev_join, t->side_stream));
     if (bulk) TRYC(cudaEventRecord(t->ev_join_far, t->far_stream));
-    int ctas = std::max(1, t->num_sms * t->ctas_per_sm);
-    launch_interact(d, dev_plan(t), o.precision, o.G, o.am_correction ? 1 : 0, ctas,
+    return OT_OK;
+}
+void launch_general(ot_tree* t, const ot_solve_opts& o, cudaStream_t s) {
+    const int ctas = std::max(1, t->num_sms * t->ctas_per_sm);
+    launch_interact(dev_tree(t), dev_plan(t), o.precision, o.G, o.am_correction ? 1 : 0, ctas,
                     t->warps_per_cta, s);
+}
+int join_lattice(ot_tree* t, const ot_solve_opts& o, cudaStream_t s) {
     TRYC(cudaStreamWaitEvent(s, t->ev_join, 0));
-    if (bulk) TRYC(cudaStreamWaitEvent(s, t->ev_join_far, 0));
+    if (o.precision == OT_PRECISION_FP32_BULK) TRYC(cudaStreamWaitEvent(s, t->ev_join_far, 0));
     TRYC(cudaGetLastError());
     return OT_OK;
+}
+
+// Enqueues all interactions after a complete upward pass.
+int enqueue_interact(ot_tree* t, const ot_solve_opts& o, cudaStream_t s) {
+    TRY(fork_lattice(t, o, s));
+    launch_general(t, o, s);
+    return join_lattice(t, o, s);
 }
 
 void enqueue_downward(ot_tree* t, const double* rho, double* phi, double* g,
@@ -344,10 +363,16 @@ void enqueue_downward(ot_tree* t, const double* rho, double* phi, double* g,
 int enqueue_solve(ot_tree* t, const double* rho, double* phi, double* g, const ot_solve_opts& o,
                   cudaStream_t s) {
     TRYC(cudaEventRecordWithFlags(t->ev[0], s, cudaEventRecordExternal));
-    enqueue_moments(t, rho, s);
+    enqueue_leaf_moments(t, rho, s);
     TRYC(cudaGetLastError());
+    // interaction window: from the leaf masses to the join of every
+    // interaction kernel; the M2M chain runs inside it, beside the lattice
+    // branches, before the general kernel
     TRYC(cudaEventRecordWithFlags(t->ev[1], s, cudaEventRecordExternal));
-    TRY(enqueue_interact(t, o, s));
+    TRY(fork_lattice(t, o, s));
+    enqueue_m2m(t, s);
+    launch_general(t, o, s);
+    TRY(join_lattice(t, o, s));
     TRYC(cudaEventRecordWithFlags(t->ev[2], s, cudaEventRecordExternal));
     enqueue_downward(t, rho, phi, g, o, s);
     TRYC(cudaGetLastError());
