@@ -202,16 +202,12 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
         // own moments (physical) and own expansion adjoints
         const double mC = t.mom64[cell];
         const double dC[3] = {t.mom64[N + cell], t.mom64[2 * N + cell], t.mom64[3 * N + cell]};
-        double M2C[6], M3C[10], EC[20], aC[3];
+        double M2C[6], M3C[10];
         if (!cleaf) {
 #pragma unroll
             for (int r = 0; r < 6; r++) M2C[r] = h2 * t.mom64[(4 + r) * N + cell];
 #pragma unroll
             for (int r = 0; r < 10; r++) M3C[r] = h3 * t.mom64[(10 + r) * N + cell];
-#pragma unroll
-            for (int r = 0; r < 20; r++) EC[r] = locbar[r * N + cell];
-#pragma unroll
-            for (int r = 0; r < 3; r++) aC[r] = locbar[(20 + r) * N + cell];
         } else {
 #pragma unroll
             for (int r = 0; r < 6; r++) M2C[r] = 0.0;
@@ -220,9 +216,11 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
         }
         PairAdjOut acc;
         adj_zero(acc);
-        double Xs[3] = {0.0, 0.0, 0.0};  // signed position adjoint of this cell
         double lat0 = 0.0, lat1 = 0.0;   // lattice pairs: dJ/dm of this leaf cell (h, h^2 parts)
         const int base = p.list_first[item_list(it)];
+        // Two passes over the partners, each holding only what its role needs.
+        // Pass 1: this cell as the source of its partners' expansions
+        // (R = X_P - X_C), and the transposed lattice pairs of a leaf cell.
 #pragma unroll 1
         for (int q = it.z; q < it.w; q++) {
             const int e = __ldg(p.entries + base + q);
@@ -241,65 +239,57 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
                 continue;
             }
             if (!cleaf && !pleaf && entry_near(e)) continue;
-            // partner moments (physical) and R = X_P - X_C
             const double mP = t.mom64[pc];
-            double R[3] = {h * ((double)dx + t.mom64[N + pc] - dC[0]),
-                           h * ((double)dy + t.mom64[2 * N + pc] - dC[1]),
-                           h * ((double)dz + t.mom64[3 * N + pc] - dC[2])};
-            double M2P[6], M3P[10];
-            if (!pleaf) {
+            const double R[3] = {h * ((double)dx + t.mom64[N + pc] - dC[0]),
+                                 h * ((double)dy + t.mom64[2 * N + pc] - dC[1]),
+                                 h * ((double)dz + t.mom64[3 * N + pc] - dC[2])};
+            double M3P[10], EP[20], aP[3];
 #pragma unroll
-                for (int r = 0; r < 6; r++) M2P[r] = h2 * t.mom64[(4 + r) * N + pc];
+            for (int r = 0; r < 10; r++) M3P[r] = pleaf ? 0.0 : h3 * t.mom64[(10 + r) * N + pc];
 #pragma unroll
-                for (int r = 0; r < 10; r++) M3P[r] = h3 * t.mom64[(10 + r) * N + pc];
-            } else {
+            for (int r = 0; r < 20; r++) EP[r] = (pleaf && r >= 4) ? 0.0 : locbar[r * N + pc];
 #pragma unroll
-                for (int r = 0; r < 6; r++) M2P[r] = 0.0;
+            for (int r = 0; r < 3; r++) aP[r] = locbar[(20 + r) * N + pc];
+            m2l_pair_reverse<true, false>(R, G, am, mC, M2C, M3C, !cleaf, mP, M3P, !pleaf, EP[0], EP + 1,
+                                          EP + 4, EP + 10, aP, !cleaf, -1.0, acc);
+        }
+        // Pass 2 (interior cells): this cell as the target of its partners
+        // (R = X_C - X_P): its centre of mass and the correction's mass ratio.
+        if (!cleaf) {
+            double EC[20], aC[3];
 #pragma unroll
-                for (int r = 0; r < 10; r++) M3P[r] = 0.0;
-            }
-            // (ii) this cell as the source of P's expansion (R = X_P - X_C)
-            {
-                double EP[20], aP[3];
+            for (int r = 0; r < 20; r++) EC[r] = locbar[r * N + cell];
 #pragma unroll
-                for (int r = 0; r < 20; r++) EP[r] = locbar[r * N + pc];
+            for (int r = 0; r < 3; r++) aC[r] = locbar[(20 + r) * N + cell];
+#pragma unroll 1
+            for (int q = it.z; q < it.w; q++) {
+                const int e = __ldg(p.entries + base + q);
+                const int dx = entry_dx(e), dy = entry_dy(e), dz = entry_dz(e);
+                const int sx = i + dx, sy = j + dy, sz = k + dz;
+                const int slot = ((sx >> 3) + 1) + 3 * ((sy >> 3) + 1) + 9 * ((sz >> 3) + 1);
+                const int nb = s_nb[w][slot];
+                if (nb < 0) continue;
+                const bool pleaf = s_lf[w][slot] != 0;
+                if (!pleaf && entry_near(e)) continue;
+                const long long pc = (long long)nb * kCells + (sx & 7) + 8 * (sy & 7) + 64 * (sz & 7);
+                const double mP = t.mom64[pc];
+                const double Rn[3] = {h * (dC[0] - (double)dx - t.mom64[N + pc]),
+                                      h * (dC[1] - (double)dy - t.mom64[2 * N + pc]),
+                                      h * (dC[2] - (double)dz - t.mom64[3 * N + pc])};
+                double M2P[6], M3P[10];
 #pragma unroll
-                for (int r = 0; r < 3; r++) aP[r] = locbar[(20 + r) * N + pc];
-                if (pleaf) {
+                for (int r = 0; r < 6; r++) M2P[r] = pleaf ? 0.0 : h2 * t.mom64[(4 + r) * N + pc];
 #pragma unroll
-                    for (int r = 4; r < 20; r++) EP[r] = 0.0;
-                }
-                PairAdjOut o;
-                adj_zero(o);
-                m2l_pair_reverse(R, G, am, mC, M2C, M3C, !cleaf, mP, M3P, !pleaf, EP[0], EP + 1,
-                                 EP + 4, EP + 10, aP, true, false, !cleaf, o);
-                acc.mB += o.mB;
-#pragma unroll
-                for (int r = 0; r < 6; r++) acc.M2B[r] += o.M2B[r];
-#pragma unroll
-                for (int r = 0; r < 10; r++) acc.M3B[r] += o.M3B[r];
-#pragma unroll
-                for (int s = 0; s < 3; s++) Xs[s] -= o.R[s];
-            }
-            // (i) this cell as the target of P (R = X_C - X_P): position and ratio
-            if (!cleaf) {
-                const double Rn[3] = {-R[0], -R[1], -R[2]};
-                PairAdjOut o;
-                adj_zero(o);
-                m2l_pair_reverse(Rn, G, am, mP, M2P, M3P, !pleaf, mC, M3C, true, EC[0], EC + 1,
-                                 EC + 4, EC + 10, aC, false, true, true, o);
-                acc.mA += o.mA;
-#pragma unroll
-                for (int r = 0; r < 10; r++) acc.M3A[r] += o.M3A[r];
-#pragma unroll
-                for (int s = 0; s < 3; s++) Xs[s] += o.R[s];
+                for (int r = 0; r < 10; r++) M3P[r] = pleaf ? 0.0 : h3 * t.mom64[(10 + r) * N + pc];
+                m2l_pair_reverse<false, true>(Rn, G, am, mP, M2P, M3P, !pleaf, mC, M3C, true, EC[0], EC + 1,
+                                              EC + 4, EC + 10, aC, true, 1.0, acc);
             }
         }
         const double hi = 1.0 / h;
         atomicAdd(mombar + cell, acc.mB + acc.mA - G * (lat0 * hi - lat1 * hi * hi));
         if (!cleaf) {
 #pragma unroll
-            for (int s = 0; s < 3; s++) atomicAdd(mombar + (1 + s) * N + cell, Xs[s]);
+            for (int s = 0; s < 3; s++) atomicAdd(mombar + (1 + s) * N + cell, acc.R[s]);
 #pragma unroll
             for (int r = 0; r < 6; r++) atomicAdd(mombar + (4 + r) * N + cell, acc.M2B[r]);
 #pragma unroll
