@@ -250,11 +250,14 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
             for (int r = 0; r < 20; r++) EP[r] = (pleaf && r >= 4) ? 0.0 : locbar[r * N + pc];
 #pragma unroll
             for (int r = 0; r < 3; r++) aP[r] = locbar[(20 + r) * N + pc];
+            // the R-gradient of this pair moves this cell's centre of mass; an
+            // interior partner adds it in its own pass 2, a leaf partner has none
             m2l_pair_reverse<true, false>(R, G, am, mC, M2C, M3C, !cleaf, mP, M3P, !pleaf, EP[0], EP + 1,
-                                          EP + 4, EP + 10, aP, !cleaf, -1.0, acc);
+                                          EP + 4, EP + 10, aP, !cleaf && pleaf, -1.0, acc.R, acc);
         }
         // Pass 2 (interior cells): this cell as the target of its partners
-        // (R = X_C - X_P): its centre of mass and the correction's mass ratio.
+        // (R = X_C - X_P): the correction's mass ratio, and the pair's
+        // R-gradient for both centres of mass.
         if (!cleaf) {
             double EC[20], aC[3];
 #pragma unroll
@@ -281,8 +284,17 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
                 for (int r = 0; r < 6; r++) M2P[r] = pleaf ? 0.0 : h2 * t.mom64[(4 + r) * N + pc];
 #pragma unroll
                 for (int r = 0; r < 10; r++) M3P[r] = pleaf ? 0.0 : h3 * t.mom64[(10 + r) * N + pc];
+                double gR[3] = {0.0, 0.0, 0.0};
                 m2l_pair_reverse<false, true>(Rn, G, am, mP, M2P, M3P, !pleaf, mC, M3C, true, EC[0], EC + 1,
-                                              EC + 4, EC + 10, aC, true, 1.0, acc);
+                                              EC + 4, EC + 10, aC, true, 1.0, gR, acc);
+                // dJ/dR moves both centres of mass: + this cell's, - an interior
+                // partner's (a leaf's centre is fixed)
+#pragma unroll
+                for (int s = 0; s < 3; s++) acc.R[s] += gR[s];
+                if (!pleaf) {
+#pragma unroll
+                    for (int s = 0; s < 3; s++) atomicAdd(mombar + (1 + s) * N + pc, -gR[s]);
+                }
             }
         }
         const double hi = 1.0 / h;

@@ -135,7 +135,7 @@ inline double rsqrt_adj(double a) { return 1.0 / sqrt(a); }
 // Reverse of one pair, added into out.  SRC: source-moment adjoints (mB
 // always; M2B, M3B when the source is an interior cell).  TGT: the
 // target-side mass-ratio adjoints (interior targets only).  want_R: dJ/dR,
-// added to out.R times sR (+1 for the target's centre of mass, -1 for the
+// added to gR times sR (+1 for the target's centre of mass, -1 for the
 // source's).
 template <bool SRC, bool TGT>
 __host__ __device__ __forceinline__ void m2l_pair_reverse(
@@ -143,7 +143,7 @@ __host__ __device__ __forceinline__ void m2l_pair_reverse(
     double mB, const double* M2B, const double* M3B, bool multiB,   // source moments
     double mA, const double* M3A, bool multiA,                      // target moments (ratio)
     double E0, const double* E1, const double* E2, const double* E3, const double* ac,
-    bool want_R, double sR, PairAdjOut& out) {
+    bool want_R, double sR, double* gR, PairAdjOut& out) {
     RMono m;
     r_mono(Rv[0], Rv[1], Rv[2], m);
     const double x = m.x, y = m.y, z = m.z;
@@ -235,7 +235,7 @@ __host__ __device__ __forceinline__ void m2l_pair_reverse(
                 g[p] += cr * R[p] + cmr * MR[p] + cq2 * m3.q2[p] + ct * m3.t[p] + ce1 * E1[p] + f2 * ME1[p];
         }
 #pragma unroll
-        for (int p = 0; p < 3; p++) out.R[p] += -sR * G * g[p];
+        for (int p = 0; p < 3; p++) gR[p] += -sR * G * g[p];
         if (am && (multiB || useA)) {
             // a . (D4 : Q), Q = M3_B - ratio M3_A
             double Q[10];
@@ -252,7 +252,7 @@ __host__ __device__ __forceinline__ void m2l_pair_reverse(
             const double ca = f4 * q.q3 + 3.0 * f3 * q.Rt;
 #pragma unroll
             for (int p = 0; p < 3; p++)
-                out.R[p] += -sR * k6 * (cv * R[p] + ca * a[p] + 3.0 * f4 * aR * q.q2[p] + 6.0 * f3 * u[p] +
+                gR[p] += -sR * k6 * (cv * R[p] + ca * a[p] + 3.0 * f4 * aR * q.q2[p] + 6.0 * f3 * u[p] +
                                         3.0 * f3 * aR * q.t[p]);
         }
     }
