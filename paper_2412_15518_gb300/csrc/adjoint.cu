@@ -48,28 +48,15 @@ __global__ void __launch_bounds__(256) k_adj_seed(DevTree t, const int* __restri
 }
 
 // packed index tables
-__constant__ int c_i2[6] = {0, 0, 0, 1, 1, 2};
-__constant__ int c_j2[6] = {0, 1, 2, 1, 2, 2};
-__constant__ int c_i3[10] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 2};
-__constant__ int c_j3[10] = {0, 0, 0, 1, 1, 2, 1, 1, 2, 2};
-__constant__ int c_k3[10] = {0, 1, 2, 1, 2, 2, 1, 2, 2, 2};
-
-__device__ __forceinline__ int pk2(int i, int j) {
-    if (i > j) { int s = i; i = j; j = s; }
-    return i == 0 ? j : (i == 1 ? 2 + j : 5);
-}
-__device__ __forceinline__ int pk3(int i, int j, int k) {
-    // sort i <= j <= k
-    if (i > j) { int s = i; i = j; j = s; }
-    if (j > k) { int s = j; j = k; k = s; }
-    if (i > j) { int s = i; i = j; j = s; }
-    const int tab[3][3][3] = {{{0, 1, 2}, {1, 3, 4}, {2, 4, 5}},
-                              {{1, 3, 4}, {3, 6, 7}, {4, 7, 8}},
-                              {{2, 4, 5}, {4, 7, 8}, {5, 8, 9}}};
-    return tab[i][j][k];
-}
-
-// L2L reverse at parent level: one thread per parent cell.
+// L2L reverse at parent level: one thread per parent cell.  The forward
+// shift by d = X_child - X_parent is
+//   C0 = L0 + L1.d + d.L2.d / 2 + L3:ddd / 6,  C1 = L1 + L2 d + L3:dd / 2,
+//   C2 = L2 + L3 d,  C3 = L3,
+// so with the child's adjoints C the parent's adjoints E gather
+//   E0 += C0,  E1 += C0 d + C1,  E2 += C0 dd / 2 + sym(C1 d) + C2,
+//   E3 += C0 ddd / 6 + sym(C1 dd) / 6 + sym(C2 d) / 3 + C3,
+// and d gets dbar = C0 (L1 + L2 d + L3:dd / 2) + L2 C1 + L3:sym(C1 d) + L3:C2,
+// added to the child's centre of mass and subtracted from the parent's.
 __global__ void __launch_bounds__(128) k_l2l_reverse(DevTree t, int first, double* locbar,
                                                      double* mombar) {
     const int node = first + blockIdx.x;
@@ -87,77 +74,66 @@ __global__ void __launch_bounds__(128) k_l2l_reverse(DevTree t, int first, doubl
         const double* L2 = P + 4;
         const double* L3 = P + 10;
         const double pd[3] = {t.mom64[N + pcell], t.mom64[2 * N + pcell], t.mom64[3 * N + pcell]};
-        double E[20], A[3];
+        double E[20], A[3] = {0.0, 0.0, 0.0}, Xp[3] = {0.0, 0.0, 0.0};
 #pragma unroll
         for (int r = 0; r < 20; r++) E[r] = 0.0;
-        A[0] = A[1] = A[2] = 0.0;
-        double Xp[3] = {0.0, 0.0, 0.0};
         const int cn = child0 + (i >> 2) + 2 * (j >> 2) + 4 * (k >> 2);
 #pragma unroll 1
         for (int q = 0; q < 8; q++) {
             const int a = q & 1, b = (q >> 1) & 1, e = q >> 2;
             const long long cc = (long long)cn * kCells + (2 * (i & 3) + a) + 8 * (2 * (j & 3) + b) +
                                  64 * (2 * (k & 3) + e);
-            const double off[3] = {(double)a, (double)b, (double)e};
-            double d[3];
-#pragma unroll
-            for (int s = 0; s < 3; s++)
-                d[s] = hc * ((off[s] - 0.5) + t.mom64[(1 + s) * N + cc] - 2.0 * pd[s]);
+            const double d[3] = {hc * ((a - 0.5) + t.mom64[N + cc] - 2.0 * pd[0]),
+                                 hc * ((b - 0.5) + t.mom64[2 * N + cc] - 2.0 * pd[1]),
+                                 hc * ((e - 0.5) + t.mom64[3 * N + cc] - 2.0 * pd[2])};
             double C[20];
 #pragma unroll
             for (int r = 0; r < 20; r++) C[r] = locbar[r * N + cc];
             const double C0 = C[0];
             const double* C1 = C + 1;
             const double* C2 = C + 4;
-            const double* C3 = C + 10;
-            // E0 += C0; E1 += C0 d + C1
+            RMono md;
+            r_mono(d[0], d[1], d[2], md);
+            // E0, E1
             E[0] += C0;
 #pragma unroll
             for (int s = 0; s < 3; s++) E[1 + s] += C0 * d[s] + C1[s];
-            // E2 += C0 dd / 2 + sym(C1 d) + C2
-#pragma unroll
-            for (int n = 0; n < 6; n++) {
-                const int u = c_i2[n], v = c_j2[n];
-                E[4 + n] += 0.5 * C0 * d[u] * d[v] + 0.5 * (C1[u] * d[v] + C1[v] * d[u]) + C2[n];
-            }
-            // E3 += C0 ddd / 6 + sym(C1 dd) / 2 + sym(C2 d) + C3
-#pragma unroll
-            for (int n = 0; n < 10; n++) {
-                const int u = c_i3[n], v = c_j3[n], w = c_k3[n];
-                E[10 + n] += (1.0 / 6.0) * C0 * d[u] * d[v] * d[w] +
-                             (1.0 / 6.0) * (C1[u] * d[v] * d[w] + C1[v] * d[u] * d[w] + C1[w] * d[u] * d[v]) +
-                             (1.0 / 3.0) * (C2[pk2(u, v)] * d[w] + C2[pk2(u, w)] * d[v] + C2[pk2(v, w)] * d[u]) +
-                             C3[n];
-            }
+            // E2 += C0 dd / 2 + sym(C1 d) + C2  (sym(C1 d)_uv = (C1_u d_v + C1_v d_u) / 2)
+            const double h0 = 0.5 * C0;
+            E[4] += h0 * md.xx + C1[0] * d[0] + C2[0];
+            E[5] += h0 * md.xy + 0.5 * (C1[0] * d[1] + C1[1] * d[0]) + C2[1];
+            E[6] += h0 * md.xz + 0.5 * (C1[0] * d[2] + C1[2] * d[0]) + C2[2];
+            E[7] += h0 * md.yy + C1[1] * d[1] + C2[3];
+            E[8] += h0 * md.yz + 0.5 * (C1[1] * d[2] + C1[2] * d[1]) + C2[4];
+            E[9] += h0 * md.zz + C1[2] * d[2] + C2[5];
+            // E3 += C0 ddd / 6 + (C1 dd)_sym / 6 + (C2 d)_sym / 3 + C3
+            add_rank3(E + 10, md, C1, C0 / 6.0, 1.0 / 6.0, 0.0, 0.0);
+            const double t3 = 1.0 / 3.0;
+            E[10] += t3 * (3.0 * C2[0] * d[0]) + C[10];
+            E[11] += t3 * (C2[0] * d[1] + 2.0 * C2[1] * d[0]) + C[11];
+            E[12] += t3 * (C2[0] * d[2] + 2.0 * C2[2] * d[0]) + C[12];
+            E[13] += t3 * (2.0 * C2[1] * d[1] + C2[3] * d[0]) + C[13];
+            E[14] += t3 * (C2[1] * d[2] + C2[2] * d[1] + C2[4] * d[0]) + C[14];
+            E[15] += t3 * (2.0 * C2[2] * d[2] + C2[5] * d[0]) + C[15];
+            E[16] += t3 * (3.0 * C2[3] * d[1]) + C[16];
+            E[17] += t3 * (C2[3] * d[2] + 2.0 * C2[4] * d[1]) + C[17];
+            E[18] += t3 * (2.0 * C2[4] * d[2] + C2[5] * d[1]) + C[18];
+            E[19] += t3 * (3.0 * C2[5] * d[2]) + C[19];
 #pragma unroll
             for (int s = 0; s < 3; s++) A[s] += locbar[(20 + s) * N + cc];
-            // delta-bar = C0 (L1 + L2 d + L3:dd / 2) + C1 . (L2 + L3 d) + C2 : L3
-            double db[3];
-#pragma unroll
-            for (int p = 0; p < 3; p++) {
-                double l2d = 0.0, l3dd = 0.0;
-#pragma unroll
-                for (int s = 0; s < 3; s++) {
-                    l2d += L2[pk2(p, s)] * d[s];
-#pragma unroll
-                    for (int u = 0; u < 3; u++) l3dd += L3[pk3(p, s, u)] * d[s] * d[u];
-                }
-                double v = C0 * (P[1 + p] + l2d + 0.5 * l3dd);
-#pragma unroll
-                for (int s = 0; s < 3; s++) {
-                    double l3d = 0.0;
-#pragma unroll
-                    for (int u = 0; u < 3; u++) l3d += L3[pk3(s, p, u)] * d[u];
-                    v += C1[s] * (L2[pk2(s, p)] + l3d);
-#pragma unroll
-                    for (int u = 0; u < 3; u++) v += C2[pk2(s, u)] * L3[pk3(s, u, p)];
-                }
-                db[p] = v;
-            }
+            // dbar = C0 (L1 + L2 d + L3:dd / 2) + L2 C1 + L3:sym(C1 d) + L3:C2
+            double L2d[3], L3dd[3], L2C1[3], L3C1d[3], L3C2[3];
+            sym2_vec(L2, d, L2d);
+            sym3_contract(L3, md.xx, md.yy, md.zz, md.xy2, md.xz2, md.yz2, L3dd);
+            sym2_vec(L2, C1, L2C1);
+            sym3_contract(L3, C1[0] * d[0], C1[1] * d[1], C1[2] * d[2], C1[0] * d[1] + C1[1] * d[0],
+                          C1[0] * d[2] + C1[2] * d[0], C1[1] * d[2] + C1[2] * d[1], L3C1d);
+            sym3_contract(L3, C2[0], C2[3], C2[5], 2.0 * C2[1], 2.0 * C2[2], 2.0 * C2[4], L3C2);
 #pragma unroll
             for (int s = 0; s < 3; s++) {
-                mombar[(1 + s) * N + cc] += db[s];
-                Xp[s] -= db[s];
+                const double db = C0 * (P[1 + s] + L2d[s] + 0.5 * L3dd[s]) + L2C1[s] + L3C1d[s] + L3C2[s];
+                mombar[(1 + s) * N + cc] += db;
+                Xp[s] -= db;
             }
         }
 #pragma unroll
@@ -311,7 +287,16 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
     }
 }
 
-// M2M reverse at parent level: one thread per parent cell, writes its children.
+// M2M reverse at parent level: one thread per parent cell, writes its
+// children.  Forward (parent units, child offsets d = X_k - X_P):
+//   M = sum m_k,  X_P = sum m_k X_k / M,  M2 = sum M2_k + m_k d d,
+//   M3 = sum M3_k + 3 sym(M2_k d) + m_k d d d,
+// so with the parent's adjoints (Bm, BX, B2, B3) each child gathers
+//   M3bar_k += B3,  M2bar_k += B2 + 3 B3 d,  mbar_k += B2:dd + B3:ddd,
+//   dbar = 2 m_k B2 d + 3 B3:M2_k + 3 m_k B3:dd,
+// and then the centre of mass: Xbar_k += Xtot m_k / M, mbar_k += Xtot.d / M
+// + Bm with Xtot = BX - sum dbar (the geometric centre, a constant, when
+// M = 0).  Child offsets are recomputed in the second pass, not stored.
 __global__ void __launch_bounds__(128) k_m2m_reverse(DevTree t, int first, double* mombar) {
     const int node = first + blockIdx.x;
     const int child0 = t.node_child[node];
@@ -324,87 +309,67 @@ __global__ void __launch_bounds__(128) k_m2m_reverse(DevTree t, int first, doubl
         const long long pcell = (long long)node * kCells + c;
         const double M = t.mom64[pcell];
         const double XP[3] = {t.mom64[N + pcell], t.mom64[2 * N + pcell], t.mom64[3 * N + pcell]};
-        double Bm = mombar[pcell];
-        double BX[3], B2[6], B3[10];
-#pragma unroll
-        for (int s = 0; s < 3; s++) BX[s] = mombar[(1 + s) * N + pcell];
+        const double Bm = mombar[pcell];
+        double B2[6], B3[10];
 #pragma unroll
         for (int r = 0; r < 6; r++) B2[r] = mombar[(4 + r) * N + pcell];
 #pragma unroll
         for (int r = 0; r < 10; r++) B3[r] = mombar[(10 + r) * N + pcell];
         const int cn = child0 + (i >> 2) + 2 * (j >> 2) + 4 * (k >> 2);
-        double Xtot[3] = {BX[0], BX[1], BX[2]};
-        double dk[8][3];
-        long long cix[8];
+        double Xtot[3] = {mombar[N + pcell], mombar[2 * N + pcell], mombar[3 * N + pcell]};
+        auto child = [&](int q, long long& cc, double* d) {
+            const int a = q & 1, b = (q >> 1) & 1, e = q >> 2;
+            cc = (long long)cn * kCells + (2 * (i & 3) + a) + 8 * (2 * (j & 3) + b) + 64 * (2 * (k & 3) + e);
+            d[0] = hp * (0.5 * ((a - 0.5) + t.mom64[N + cc]) - XP[0]);
+            d[1] = hp * (0.5 * ((b - 0.5) + t.mom64[2 * N + cc]) - XP[1]);
+            d[2] = hp * (0.5 * ((e - 0.5) + t.mom64[3 * N + cc]) - XP[2]);
+        };
         // first pass: moment adjoints and delta-bar
 #pragma unroll 1
         for (int q = 0; q < 8; q++) {
-            const int a = q & 1, b = (q >> 1) & 1, e = q >> 2;
-            const long long cc = (long long)cn * kCells + (2 * (i & 3) + a) + 8 * (2 * (j & 3) + b) +
-                                 64 * (2 * (k & 3) + e);
-            cix[q] = cc;
-            const double off[3] = {(double)a, (double)b, (double)e};
-            const double m = t.mom64[cc];
+            long long cc;
             double d[3];
-#pragma unroll
-            for (int s = 0; s < 3; s++) {
-                d[s] = hp * (0.5 * ((off[s] - 0.5) + t.mom64[(1 + s) * N + cc]) - XP[s]);
-                dk[q][s] = d[s];
-            }
+            child(q, cc, d);
+            const double m = t.mom64[cc];
             double M2k[6];
 #pragma unroll
             for (int r = 0; r < 6; r++) M2k[r] = hc * hc * t.mom64[(4 + r) * N + cc];
-            // M3bar_k += B3 ; M2bar_k += B2 + 3 B3 . d
-            double add2[6];
-#pragma unroll
-            for (int n = 0; n < 6; n++) {
-                const int u = c_i2[n], v = c_j2[n];
-                double s3 = 0.0;
-#pragma unroll
-                for (int l = 0; l < 3; l++) s3 += B3[pk3(u, v, l)] * d[l];
-                add2[n] = B2[n] + 3.0 * s3;
-            }
+            // M2bar_k += B2 + 3 B3 d
+            double B3d[6];
+            sym3_vec(B3, d, B3d);
             // mbar_k += B2 : dd + B3 : ddd
-            double B2d[3];
+            double B2d[3], B3dd[3], B3M2[3];
             sym2_vec(B2, d, B2d);
-            double B3dd[3];
             sym3_rr(B3, d, B3dd);
+            sym3_contract(B3, M2k[0], M2k[3], M2k[5], 2.0 * M2k[1], 2.0 * M2k[2], 2.0 * M2k[4], B3M2);
             const double dd = B2d[0] * d[0] + B2d[1] * d[1] + B2d[2] * d[2];
             const double ddd = B3dd[0] * d[0] + B3dd[1] * d[1] + B3dd[2] * d[2];
-            // dbar = 2 m B2 d + 3 B3 : M2_k + 3 m B3 : dd
-            double db[3];
-#pragma unroll
-            for (int p = 0; p < 3; p++) {
-                double s = 0.0;
-#pragma unroll
-                for (int n = 0; n < 6; n++) {
-                    const int u = c_i2[n], v = c_j2[n];
-                    const double mult = (u == v) ? 1.0 : 2.0;
-                    s += mult * B3[pk3(p, u, v)] * M2k[n];
-                }
-                db[p] = 2.0 * m * B2d[p] + 3.0 * s + 3.0 * m * B3dd[p];
-                Xtot[p] -= db[p];
-            }
             mombar[cc] += dd + ddd;
 #pragma unroll
-            for (int s = 0; s < 3; s++) mombar[(1 + s) * N + cc] += db[s];
+            for (int p = 0; p < 3; p++) {
+                // dbar = 2 m B2 d + 3 B3 : M2_k + 3 m B3 : dd
+                const double db = 2.0 * m * B2d[p] + 3.0 * B3M2[p] + 3.0 * m * B3dd[p];
+                Xtot[p] -= db;
+                mombar[(1 + p) * N + cc] += db;
+            }
 #pragma unroll
-            for (int n = 0; n < 6; n++) mombar[(4 + n) * N + cc] += add2[n];
+            for (int n = 0; n < 6; n++) mombar[(4 + n) * N + cc] += B2[n] + 3.0 * B3d[n];
 #pragma unroll
             for (int n = 0; n < 10; n++) mombar[(10 + n) * N + cc] += B3[n];
         }
         // second pass: the centre of mass X_P = sum m_k X_k / M and M = sum m_k
-        // (the geometric centre, a constant, when M = 0)
         const double iM = M != 0.0 ? 1.0 / M : 0.0;
 #pragma unroll 1
         for (int q = 0; q < 8; q++) {
-            const long long cc = cix[q];
+            long long cc;
+            double d[3];
+            child(q, cc, d);
             const double m = t.mom64[cc];
             double s = 0.0;
 #pragma unroll
             for (int p = 0; p < 3; p++) {
                 mombar[(1 + p) * N + cc] += Xtot[p] * m * iM;
-                s += Xtot[p] * dk[q][p] * iM;
+                s += Xtot[p] * d[p] * iM;
             }
             mombar[cc] += s + Bm;
         }

@@ -69,6 +69,16 @@ __host__ __device__ __forceinline__ void sym3_rr(const double* c, const double* 
     sym3_contract(c, x * x, y * y, z * z, 2 * x * y, 2 * x * z, 2 * y * z, q);
 }
 
+// (T d)_n = T_uvl d_l for a packed symmetric rank-3 T: a packed rank-2 result.
+__host__ __device__ __forceinline__ void sym3_vec(const double* c, const double* d, double* o) {
+    o[0] = c[0] * d[0] + c[1] * d[1] + c[2] * d[2];
+    o[1] = c[1] * d[0] + c[3] * d[1] + c[4] * d[2];
+    o[2] = c[2] * d[0] + c[4] * d[1] + c[5] * d[2];
+    o[3] = c[3] * d[0] + c[6] * d[1] + c[7] * d[2];
+    o[4] = c[4] * d[0] + c[7] * d[1] + c[8] * d[2];
+    o[5] = c[5] * d[0] + c[8] * d[1] + c[9] * d[2];
+}
+
 __host__ __device__ __forceinline__ void sym3_trace(const double* c, double* t) {
     t[0] = c[0] + c[3] + c[5];
     t[1] = c[1] + c[6] + c[8];
