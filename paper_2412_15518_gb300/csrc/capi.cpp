@@ -299,7 +299,7 @@ void enqueue_leaf_moments(ot_tree* t, const double* rho, cudaStream_t s) {
 void enqueue_m2m(ot_tree* t, cudaStream_t s) {
     DevTree d = dev_tree(t);
     for (int L = t->h.n_levels - 2; L >= 0; L--)
-        launch_m2m(d, L, t->h.level_first[L], t->h.level_first[L + 1] - t->h.level_first[L], s);
+        launch_m2m(d, t->h.m2m_kinds(L), t->h.level_first[L], t->h.level_first[L + 1] - t->h.level_first[L], s);
 }
 void enqueue_moments(ot_tree* t, const double* rho, cudaStream_t s) {
     enqueue_leaf_moments(t, rho, s);
@@ -353,7 +353,7 @@ void enqueue_downward(ot_tree* t, const double* rho, double* phi, double* g,
                       const ot_solve_opts& o, cudaStream_t s) {
     DevTree d = dev_tree(t);
     for (int L = 0; L < t->h.n_levels; L++)
-        launch_l2l(d, L, t->h.level_first[L], t->h.level_first[L + 1] - t->h.level_first[L], rho,
+        launch_l2l(d, t->h.l2l_kinds(L), t->h.level_first[L], t->h.level_first[L + 1] - t->h.level_first[L], rho,
                    phi, g, o.G, o.self_term ? 1 : 0, s);
 }
 

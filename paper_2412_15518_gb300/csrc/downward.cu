@@ -236,12 +236,11 @@ __global__ void __launch_bounds__(256) k_l2l_leafkids(DevTree t, int first,
 
 }  // namespace
 
-void launch_l2l(const DevTree& t, int level, int first, int count, const double* rho,
+void launch_l2l(const DevTree& t, int kinds, int first, int count, const double* rho,
                 double* phi, double* g, double G, int self_term, cudaStream_t s) {
-    (void)level;
     if (count <= 0) return;
-    k_l2l<<<count * 8, 64, 0, s>>>(t, first, rho, phi, g, G, self_term);
-    k_l2l_leafkids<<<count * 2, 256, 0, s>>>(t, first, rho, phi, g, G, self_term);
+    if (kinds & 1) k_l2l<<<count * 8, 64, 0, s>>>(t, first, rho, phi, g, G, self_term);
+    if (kinds & 2) k_l2l_leafkids<<<count * 2, 256, 0, s>>>(t, first, rho, phi, g, G, self_term);
 }
 
 }  // namespace otfmm

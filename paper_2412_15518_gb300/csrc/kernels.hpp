@@ -8,18 +8,21 @@
 namespace otfmm {
 
 // Upward pass: leaf masses, then exact M2M level by level (Lmax-1 .. 0).
+// kinds: bit 0 the kernel for cells with interior children, bit 1 the one
+// for cells with leaf children (HostTree::m2m_kinds).
 void launch_leaf_moments(const DevTree& t, const int* leaf_node, const double* rho,
                          cudaStream_t s);
-void launch_m2m(const DevTree& t, int level, int first, int count, cudaStream_t s);
+void launch_m2m(const DevTree& t, int kinds, int first, int count, cudaStream_t s);
 
 // All cell-to-cell interactions of every level: persistent launch over the
 // work items (precision 0 = FP64, 1 = FP32 bulk).
 void launch_interact(const DevTree& t, const DevPlan& p, int precision, double G, int am,
                      int ctas, int warps_per_cta, cudaStream_t s);
 
-// Downward pass for one level: L2L from the parent (L >= 1), then phi and g
-// at the level's leaf cells.
-void launch_l2l(const DevTree& t, int level, int first, int count, const double* rho,
+// Downward pass for one level: L2L from the parent into the level's interior
+// cells (kinds bit 0), then phi and g at the leaf cells of its children
+// (bit 1) (HostTree::l2l_kinds).
+void launch_l2l(const DevTree& t, int kinds, int first, int count, const double* rho,
                 double* phi, double* g, double G, int self_term, cudaStream_t s);
 
 }  // namespace otfmm

@@ -245,11 +245,10 @@ void launch_leaf_moments(const DevTree& t, const int* leaf_node, const double* r
     k_leaf_moments<<<t.n_leaf, 256, 0, s>>>(t, leaf_node, rho);
 }
 
-void launch_m2m(const DevTree& t, int level, int first, int count, cudaStream_t s) {
-    (void)level;
+void launch_m2m(const DevTree& t, int kinds, int first, int count, cudaStream_t s) {
     if (count <= 0) return;
-    k_m2m<<<count * 16, 256, 0, s>>>(t, first);
-    k_m2m_leafkids<<<count * 2, 256, 0, s>>>(t, first);
+    if (kinds & 1) k_m2m<<<count * 16, 256, 0, s>>>(t, first);
+    if (kinds & 2) k_m2m_leafkids<<<count * 2, 256, 0, s>>>(t, first);
 }
 
 }  // namespace otfmm

@@ -257,7 +257,7 @@ extern "C" int ot_solve_gravity_static(const ot_tree_desc* desc, const double* r
     }
     launch_leaf_moments(d, (const int*)(base + l.leaf_node), rho, s);
     for (int L = h.n_levels - 2; L >= 0; L--)
-        launch_m2m(d, L, h.level_first[L], h.level_first[L + 1] - h.level_first[L], s);
+        launch_m2m(d, h.m2m_kinds(L), h.level_first[L], h.level_first[L + 1] - h.level_first[L], s);
     DevLattice dl = {};
     dl.hoff_far = (const int*)(base + l.hoff_far);
     dl.hoff_near = (const int*)(base + l.hoff_near);
@@ -271,7 +271,7 @@ extern "C" int ot_solve_gravity_static(const ot_tree_desc* desc, const double* r
     launch_lattice(d, dp, dl, o.precision, o.G, 0, s);
     launch_interact(d, dp, o.precision, o.G, o.am_correction ? 1 : 0, 4 * sms, 4, s);
     for (int L = 0; L < h.n_levels; L++)
-        launch_l2l(d, L, h.level_first[L], h.level_first[L + 1] - h.level_first[L], rho, phi, g,
+        launch_l2l(d, h.l2l_kinds(L), h.level_first[L], h.level_first[L + 1] - h.level_first[L], rho, phi, g,
                    o.G, o.self_term ? 1 : 0, s);
     if (cudaGetLastError() != cudaSuccess) return OT_ERR_CUDA;
     return OT_OK;

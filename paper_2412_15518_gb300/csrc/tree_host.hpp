@@ -21,6 +21,27 @@ struct HostTree {
     std::vector<int> nbr;          // [n_nodes][27], slot = (ox+1) + 3 (oy+1) + 9 (oz+1)
     std::vector<int> leaf_node;    // [n_leaf] node index of each caller leaf
     int n_nodes() const { return (int)node_level.size(); }
+    // leaf and interior nodes of level L (0 outside the tree)
+    int leaf_nodes_at(int L) const {
+        if (L < 0 || L >= n_levels) return 0;
+        int n = 0;
+        for (int v = level_first[L]; v < level_first[L + 1]; v++) n += node_leaf[v] >= 0;
+        return n;
+    }
+    int interior_nodes_at(int L) const {
+        if (L < 0 || L >= n_levels) return 0;
+        return level_first[L + 1] - level_first[L] - leaf_nodes_at(L);
+    }
+    // Which of the two upward (M2M) kernels level L needs: bit 0 cells with
+    // interior children, bit 1 cells with leaf children.
+    int m2m_kinds(int L) const {
+        return (interior_nodes_at(L + 1) > 0 ? 1 : 0) | (leaf_nodes_at(L + 1) > 0 ? 2 : 0);
+    }
+    // Which of the two downward (L2L) kernels level L needs: bit 0 the
+    // level's own interior nodes (and a root leaf), bit 1 its leaf children.
+    int l2l_kinds(int L) const {
+        return (L == 0 || interior_nodes_at(L) > 0 ? 1 : 0) | (leaf_nodes_at(L + 1) > 0 ? 2 : 0);
+    }
 };
 
 // Builds the tree; returns OT_OK, OT_ERR_INVALID_ARG, OT_ERR_INVALID_TREE or
