@@ -33,12 +33,12 @@ namespace otfmm {
 
 template <bool FULL, bool MULTI, bool AM> static double count_pair() {
     g_flops = 0;
-    CountT b2[6], b3[10], bt[4], a3[10], ta[3];
+    CountT b2[6], b3[10], bt[4];
     Acc<CountT> A;
     CountT x, y, z, m;
     // R' = d + (dX_A - dX_B): 2 flops per component
     g_flops += 6;
-    m2l_pair<CountT, FULL, MULTI, AM>(x, y, z, m, b2, b3, bt, a3, ta, A);
+    m2l_pair<CountT, FULL, MULTI, AM>(x, y, z, m, b2, b3, bt, A);
     return (double)g_flops;
 }
 

@@ -208,8 +208,6 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
     const long long cell = (long long)node * kCells + i + 8 * j + 64 * k;
     T ma, dax, day, daz;
     load_head(t, cell, ma, dax, day, daz);
-    T a3[10], ta[4];
-    if (FULL && AM) load_octupole_per_mass(t, cell, a3, ta);
     Acc<T> A;
     acc_zero(A);
     double n0 = 0.0, n1 = 0.0, n2 = 0.0, n3 = 0.0;  // FP64 near leaf pairs (bulk form)
@@ -241,11 +239,17 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
             for (int r = 0; r < 10; r++) atomicAdd(loc + (10 + r) * N + cell, scaled(A.L3[r], s4));
         }
         if (AM) {
-            // a_c = -(G/6) h^-2 (S - P)
+            // a_c = -(G/6) h^-2 (S - P), P from A4 and the target's octupole
+            // per unit mass (loaded here, not held across the pair loop)
             const T sa = sl[4];
+            T P[3] = {T(0.0), T(0.0), T(0.0)};
+            if (FULL) {
+                T a3[10], ta[3];
+                load_octupole_per_mass(t, cell, a3, ta);
+                correction_target(A, a3, ta, P);
+            }
 #pragma unroll
-            for (int a = 0; a < 3; a++)
-                atomicAdd(loc + (20 + a) * N + cell, scaled(FULL ? A.S[a] - A.P[a] : A.S[a], sa));
+            for (int a = 0; a < 3; a++) atomicAdd(loc + (20 + a) * N + cell, scaled(A.S[a] - P[a], sa));
         }
     };
     if (FULL && item_list(it) == kRootList) {
@@ -267,7 +271,7 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
             const T x = (fi + dax) - (small_int(sx, T(0)) + bx);
             const T y = (fj + day) - (small_int(sy, T(0)) + by);
             const T z = (fk + daz) - (small_int(sz, T(0)) + bz);
-            m2l_pair<T, FULL, true, AM>(x, y, z, m, b2, b3, bt, a3, ta, A);
+            m2l_pair<T, FULL, true, AM>(x, y, z, m, b2, b3, bt, A);
         }
     } else if (std::is_same<T, float>::value && L > 0) {
         // FP32 form, levels >= 1: the next source's loads are issued before
@@ -295,7 +299,7 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
                     const float y = (day - h.z) - d.y;
                     const float z = (daz - h.w) - d.z;
                     if (kind == 1) {
-                        m2l_pair<float, FULL, false, AM>(x, y, z, h.x, nullptr, nullptr, nullptr, a3, ta, A);
+                        m2l_pair<float, FULL, false, AM>(x, y, z, h.x, nullptr, nullptr, nullptr, A);
                     } else {
                         const float4 v1 = ws->rec[st][1][lane], v2 = ws->rec[st][2][lane],
                                      v3 = ws->rec[st][3][lane], v4 = ws->rec[st][4][lane];
@@ -303,7 +307,7 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
                         const float b3[10] = {v2.z, v2.w, v3.x, v3.y, v3.z, v3.w, v4.x, v4.y, v4.z, v4.w};
                         const float bt[4] = {b3[0] + b3[3] + b3[5], b3[1] + b3[6] + b3[8],
                                              b3[2] + b3[7] + b3[9], b2[0] + b2[3] + b2[5]};
-                        m2l_pair<float, FULL, true, AM>(x, y, z, h.x, b2, b3, bt, a3, ta, A);
+                        m2l_pair<float, FULL, true, AM>(x, y, z, h.x, b2, b3, bt, A);
                     }
                 }
                 kind = kind_next;
@@ -363,11 +367,11 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
         const T y = (day - by) - oy;
         const T z = (daz - bz) - oz;
         if (sleaf) {
-            m2l_pair<T, FULL, false, AM>(x, y, z, m, nullptr, nullptr, nullptr, a3, ta, A);
+            m2l_pair<T, FULL, false, AM>(x, y, z, m, nullptr, nullptr, nullptr, A);
         } else {
             T b2[6], b3[10], bt[4];
             load_tail(t, sc, b2, b3, bt);
-            m2l_pair<T, FULL, true, AM>(x, y, z, m, b2, b3, bt, a3, ta, A);
+            m2l_pair<T, FULL, true, AM>(x, y, z, m, b2, b3, bt, A);
         }
     }
     }

@@ -9,8 +9,11 @@
 //   L^(n)_A += -G sum_{m <= 3-n} (-1)^m / m!  M^(m)_B ._m D^(n+m)(R)
 //   a_c,A   += -(G/6) D^(4)(R) ._3 [M3_B - (m_B / m_A) M3_A]
 //            = -(G/6) [S - P],  S = sum_B D4 ._3 M3_B,
-//                               P = sum_B m_B D4 ._3 (M3_A / m_A)
-// (the caller divides the target octupole by m_A once per target, in FP64)
+//                               P = (sum_B m_B D4) ._3 (M3_A / m_A)
+// The target octupole per unit mass is fixed for a target, so P is formed
+// once per target (correction_target) from the sum A4 = sum_B m_B f4 R^4 of
+// the pairs' pure quartic parts: D4 is traceless, so its lower parts follow
+// from A4's traces (sum m f3 R R = -tr A4 / 7, sum m f2 = tr tr A4 / 35).
 // With f_k = (-1)^k (2k-1)!! / r^(2k+1), every contraction of a symmetric
 // tensor with D^(n) reduces to a few scalars: for S = M2 (Mx = M2 R,
 // xMx = R.M2.R, tr = trace) and T = M3 (q2 = T:RR, q3 = R.q2, t_i = T_ijj,
@@ -29,8 +32,9 @@ namespace otfmm {
 
 template <class T> struct Acc {
     T L0, L1[3], L2[6], L3[10];
-    T S[3];  // correction sum of the source octupoles
-    T P[3];  // correction sum of the target octupole per unit mass
+    T S[3];   // correction sum of the source octupoles
+    T A4[15]; // sum m_B f4 R^4 of interior targets (xxxx xxxy xxxz xxyy xxyz xxzz xyyy
+              // xyyz xyzz xzzz yyyy yyyz yyzz yzzz zzzz)
 };
 // The Kronecker parts of L2 and L3 are not accumulated: D2 and D3 are
 // traceless, so per pair sum m f1 = -trace(m f2 R R) / 3 and
@@ -43,8 +47,9 @@ template <class T> __host__ __device__ __forceinline__ void acc_zero(Acc<T>& A) 
     for (int i = 0; i < 3; i++) {
         A.L1[i] = T(0.0);
         A.S[i] = T(0.0);
-        A.P[i] = T(0.0);
     }
+#pragma unroll
+    for (int i = 0; i < 15; i++) A.A4[i] = T(0.0);
 #pragma unroll
     for (int i = 0; i < 6; i++) A.L2[i] = T(0.0);
 #pragma unroll
@@ -100,15 +105,45 @@ __host__ __device__ __forceinline__ void contract_rr(const T* c, T xx, T yy, T z
     qz = fma_(c[2], xx, fma_(c[7], yy, fma_(c[9], zz, fma_(c[4], xy2, fma_(c[5], xz2, c[8] * yz2)))));
 }
 
+// The target part of the correction, P_i = sum_jkl (sum m D4)_ijkl a_jkl,
+// from A4 with a = M3' / m_A (packed) and t its trace vector:
+//   P = A4 : a + 3 Q : a + 3 Q t + 3 c0 t,  Q = -tr A4 / 7,  c0 = tr tr A4 / 35.
+template <class T>
+__host__ __device__ __forceinline__ void correction_target(const Acc<T>& A, const T* a, const T* t,
+                                                           T* P) {
+    const T* q = A.A4;
+    const T s7 = T(-1.0 / 7.0);
+    const T Qxx = s7 * (q[0] + q[3] + q[5]), Qxy = s7 * (q[1] + q[6] + q[8]);
+    const T Qxz = s7 * (q[2] + q[7] + q[9]), Qyy = s7 * (q[3] + q[10] + q[12]);
+    const T Qyz = s7 * (q[4] + q[11] + q[13]), Qzz = s7 * (q[5] + q[12] + q[14]);
+    const T c0 = T(1.0 / 35.0) * (q[0] + q[10] + q[14] + T(2.0) * (q[3] + q[5] + q[12]));
+    // a weighted by the multiplicity of its packed index in a full contraction
+    const T w[10] = {a[0], T(3.0) * a[1], T(3.0) * a[2], T(3.0) * a[3], T(6.0) * a[4],
+                     T(3.0) * a[5], a[6], T(3.0) * a[7], T(3.0) * a[8], a[9]};
+    const T Ax = q[0] * w[0] + q[1] * w[1] + q[2] * w[2] + q[3] * w[3] + q[4] * w[4] + q[5] * w[5] +
+                 q[6] * w[6] + q[7] * w[7] + q[8] * w[8] + q[9] * w[9];
+    const T Ay = q[1] * w[0] + q[3] * w[1] + q[4] * w[2] + q[6] * w[3] + q[7] * w[4] + q[8] * w[5] +
+                 q[10] * w[6] + q[11] * w[7] + q[12] * w[8] + q[13] * w[9];
+    const T Az = q[2] * w[0] + q[4] * w[1] + q[5] * w[2] + q[7] * w[3] + q[8] * w[4] + q[9] * w[5] +
+                 q[11] * w[6] + q[12] * w[7] + q[13] * w[8] + q[14] * w[9];
+    T Qax, Qay, Qaz;
+    contract_rr(a, Qxx, Qyy, Qzz, Qxy + Qxy, Qxz + Qxz, Qyz + Qyz, Qax, Qay, Qaz);
+    const T Qtx = Qxx * t[0] + Qxy * t[1] + Qxz * t[2];
+    const T Qty = Qxy * t[0] + Qyy * t[1] + Qyz * t[2];
+    const T Qtz = Qxz * t[0] + Qyz * t[1] + Qzz * t[2];
+    P[0] = Ax + T(3.0) * (Qax + Qtx + c0 * t[0]);
+    P[1] = Ay + T(3.0) * (Qay + Qty + c0 * t[1]);
+    P[2] = Az + T(3.0) * (Qaz + Qtz + c0 * t[2]);
+}
+
 // TGT_FULL: the target is an interior cell (needs L2, L3 and the target part
 // of the correction).  SRC_MULTI: the source is an interior cell (has M2, M3).
 // AM: the correction is on.  (x, y, z) = R', m = source mass, b2/b3 = source
 // M2'/M3', bt = the source's M3 trace vector (t_i = M3_ijj) and trace of M2
-// (bt[3]), a3/ta = target M3' / m_A and its trace vector.
+// (bt[3]).
 template <class T, bool TGT_FULL, bool SRC_MULTI, bool AM>
 __host__ __device__ __forceinline__ void m2l_pair(T x, T y, T z, T m, const T* b2, const T* b3,
-                                                  const T* bt, const T* a3, const T* ta,
-                                                  Acc<T>& A) {
+                                                  const T* bt, Acc<T>& A) {
     const T r2 = fma_(x, x, fma_(y, y, z * z));
     const T f0 = rsqrt_(r2);
     const T ri2 = f0 * f0;
@@ -121,7 +156,7 @@ __host__ __device__ __forceinline__ void m2l_pair(T x, T y, T z, T m, const T* b
     const T xx = x * x, yy = y * y, zz = z * z;
     const T xy = x * y, xz = x * z, yz = y * z;
     T xy2 = T(0.0), xz2 = T(0.0), yz2 = T(0.0), u = T(0.0), w = T(0.0);
-    if (SRC_MULTI || (TGT_FULL && AM)) {
+    if (SRC_MULTI) {
         xy2 = xy + xy;
         xz2 = xz + xz;
         yz2 = yz + yz;
@@ -182,15 +217,24 @@ __host__ __device__ __forceinline__ void m2l_pair(T x, T y, T z, T m, const T* b
         A.L3[8] = fma_(ty3, zz, A.L3[8]);
         A.L3[9] = fma_(tz3, zz, A.L3[9]);
         if (AM) {
-            // P += m_B D4 : (M3_A / m_A) = m_B (R k' + u q2_A + w t_A)
-            T qx, qy, qz;
-            contract_rr(a3, xx, yy, zz, xy2, xz2, yz2, qx, qy, qz);
-            const T q3 = fma_(x, qx, fma_(y, qy, z * qz));
-            const T Rt = fma_(x, ta[0], fma_(y, ta[1], z * ta[2]));
-            const T mk = m * fma_(u, Rt, f4 * q3), mu = m * u, mw = m * w;
-            A.P[0] = fma_(mk, x, fma_(mu, qx, fma_(mw, ta[0], A.P[0])));
-            A.P[1] = fma_(mk, y, fma_(mu, qy, fma_(mw, ta[1], A.P[1])));
-            A.P[2] = fma_(mk, z, fma_(mu, qz, fma_(mw, ta[2], A.P[2])));
+            // A4 += m f4 R^4 (the target octupole is contracted once per target)
+            const T s4 = m * f4;
+            const T txx = s4 * xx, txy = s4 * xy, txz = s4 * xz, tyy = s4 * yy, tyz = s4 * yz, tzz = s4 * zz;
+            A.A4[0] = fma_(txx, xx, A.A4[0]);
+            A.A4[1] = fma_(txx, xy, A.A4[1]);
+            A.A4[2] = fma_(txx, xz, A.A4[2]);
+            A.A4[3] = fma_(txx, yy, A.A4[3]);
+            A.A4[4] = fma_(txx, yz, A.A4[4]);
+            A.A4[5] = fma_(txx, zz, A.A4[5]);
+            A.A4[6] = fma_(txy, yy, A.A4[6]);
+            A.A4[7] = fma_(txy, yz, A.A4[7]);
+            A.A4[8] = fma_(txy, zz, A.A4[8]);
+            A.A4[9] = fma_(txz, zz, A.A4[9]);
+            A.A4[10] = fma_(tyy, yy, A.A4[10]);
+            A.A4[11] = fma_(tyy, yz, A.A4[11]);
+            A.A4[12] = fma_(tyy, zz, A.A4[12]);
+            A.A4[13] = fma_(tyz, zz, A.A4[13]);
+            A.A4[14] = fma_(tzz, zz, A.A4[14]);
         }
     }
 }
