@@ -48,15 +48,33 @@ __global__ void __launch_bounds__(256) k_leaf_moments(DevTree t, const int* __re
     }
 }
 
-// (i, j, k) of the packed components of symmetric rank-2 and rank-3 tensors
-__constant__ int c_i2[6] = {0, 0, 0, 1, 1, 2};
-__constant__ int c_j2[6] = {0, 1, 2, 1, 2, 2};
-__constant__ int c_t3[10][3] = {{0, 0, 0}, {0, 0, 1}, {0, 0, 2}, {0, 1, 1}, {0, 1, 2},
-                                {0, 2, 2}, {1, 1, 1}, {1, 1, 2}, {1, 2, 2}, {2, 2, 2}};
-
-__device__ __forceinline__ int p2(int i, int j) {
-    // packed index of (i, j) in xx xy xz yy yz zz
-    return i <= j ? (i == 0 ? j : (i == 1 ? 2 + j : 5)) : (j == 0 ? i : (j == 1 ? 2 + i : 5));
+// Packed symmetric tensors (rank 2: xx xy xz yy yz zz; rank 3: xxx xxy xxz
+// xyy xyz xzz yyy yyz yzz zzz), written out component by component so that
+// nothing is indexed at run time.
+// o = s u v (rank 2, u v symmetric in use: u = s' v)
+__device__ __forceinline__ void outer2(double s, const double* v, double* o) {
+    o[0] = s * v[0] * v[0]; o[1] = s * v[0] * v[1]; o[2] = s * v[0] * v[2];
+    o[3] = s * v[1] * v[1]; o[4] = s * v[1] * v[2]; o[5] = s * v[2] * v[2];
+}
+// o = s v v v (rank 3)
+__device__ __forceinline__ void outer3(double s, const double* v, double* o) {
+    const double xx = s * v[0] * v[0], yy = s * v[1] * v[1], zz = s * v[2] * v[2];
+    o[0] = xx * v[0]; o[1] = xx * v[1]; o[2] = xx * v[2]; o[3] = yy * v[0];
+    o[4] = s * v[0] * v[1] * v[2]; o[5] = zz * v[0]; o[6] = yy * v[1]; o[7] = yy * v[2];
+    o[8] = zz * v[1]; o[9] = zz * v[2];
+}
+// o_ijk = P_ij v_k + P_ik v_j + P_jk v_i for a packed symmetric rank-2 P
+__device__ __forceinline__ void sym3_of(const double* P, const double* v, double* o) {
+    o[0] = 3.0 * P[0] * v[0];
+    o[1] = P[0] * v[1] + 2.0 * P[1] * v[0];
+    o[2] = P[0] * v[2] + 2.0 * P[2] * v[0];
+    o[3] = 2.0 * P[1] * v[1] + P[3] * v[0];
+    o[4] = P[1] * v[2] + P[2] * v[1] + P[4] * v[0];
+    o[5] = 2.0 * P[2] * v[2] + P[5] * v[0];
+    o[6] = 3.0 * P[3] * v[1];
+    o[7] = P[3] * v[2] + 2.0 * P[4] * v[1];
+    o[8] = 2.0 * P[4] * v[2] + P[5] * v[1];
+    o[9] = 3.0 * P[5] * v[2];
 }
 
 // sum over the 8 lanes of a parent cell (lanes 8g .. 8g+7 of a warp)
@@ -98,18 +116,17 @@ __global__ void __launch_bounds__(256) k_m2m(DevTree t, int first) {
 #pragma unroll
     for (int s = 0; s < 3; s++) X[s] *= iM;
     const double d[3] = {pos[0] - X[0], pos[1] - X[1], pos[2] - X[2]};
-    double c2[6], S[16];
+    // the child's shifted moments: M2 + m d d, M3 + sym(M2 d) + m d d d
+    double c2[6], S[16], t3[10];
 #pragma unroll
     for (int r = 0; r < 6; r++) c2[r] = 0.25 * t.mom64[(4 + r) * N + cc];  // child units -> parent
-    const double md[3] = {m * d[0], m * d[1], m * d[2]};
+    outer2(m, d, S);
 #pragma unroll
-    for (int r = 0; r < 6; r++) S[r] = c2[r] + md[c_i2[r]] * d[c_j2[r]];
+    for (int r = 0; r < 6; r++) S[r] += c2[r];
+    outer3(m, d, S + 6);
+    sym3_of(c2, d, t3);
 #pragma unroll
-    for (int r = 0; r < 10; r++) {
-        const int ii = c_t3[r][0], jj = c_t3[r][1], kk = c_t3[r][2];
-        S[6 + r] = md[ii] * d[jj] * d[kk] + 0.125 * t.mom64[(10 + r) * N + cc] +
-                   c2[p2(ii, jj)] * d[kk] + c2[p2(ii, kk)] * d[jj] + c2[p2(jj, kk)] * d[ii];
-    }
+    for (int r = 0; r < 10; r++) S[6 + r] += 0.125 * t.mom64[(10 + r) * N + cc] + t3[r];
 #pragma unroll
     for (int r = 0; r < 16; r++) S[r] = sum8(S[r]);
     const long long cell = (long long)node * kCells + c;
@@ -197,15 +214,16 @@ __global__ void __launch_bounds__(256) k_m2m_leafkids(DevTree t, int first) {
     const double P3[10] = {s64 * Sx, s64 * Sy, s64 * Sz, s64 * Sx, s64 * Sxyz,
                            s64 * Sx, s64 * Sy, s64 * Sz, s64 * Sy, s64 * Sz};
     double S2[6], S3[10];
-    const double MX[3] = {M * X[0], M * X[1], M * X[2]};
+    // parallel-axis shift to the centre of mass: M2 = P2 - M X X,
+    // M3 = P3 - sym(P2 X) + 2 M X X X
+    double xx2[6], xxx3[10], px3[10];
+    outer2(M, X, xx2);
+    outer3(2.0 * M, X, xxx3);
+    sym3_of(P2, X, px3);
 #pragma unroll
-    for (int r = 0; r < 6; r++) S2[r] = P2[r] - MX[c_i2[r]] * X[c_j2[r]];
+    for (int r = 0; r < 6; r++) S2[r] = P2[r] - xx2[r];
 #pragma unroll
-    for (int r = 0; r < 10; r++) {
-        const int ii = c_t3[r][0], jj = c_t3[r][1], kk = c_t3[r][2];
-        S3[r] = P3[r] - (X[ii] * P2[p2(jj, kk)] + X[jj] * P2[p2(ii, kk)] + X[kk] * P2[p2(ii, jj)]) +
-                2.0 * MX[ii] * X[jj] * X[kk];
-    }
+    for (int r = 0; r < 10; r++) S3[r] = P3[r] - px3[r] + xxx3[r];
     const long long cell = (long long)node * kCells + c;
     double v[kRec];
     v[0] = M;
