@@ -500,7 +500,7 @@ int ot_build_tree(const ot_tree_desc* desc, int device, ot_tree** out) {
         return fail(OT_ERR_CUDA);
     }
     t->have_plan = false;
-    if (configure_lattice() != 0) return fail(OT_ERR_CUDA);
+    if (configure_lattice() != 0 || configure_interact() != 0) return fail(OT_ERR_CUDA);
     if ((e = ensure_plan(t, 0.5))) return fail(e);
     *out = t;
     return OT_OK;

@@ -18,6 +18,9 @@ void launch_m2m(const DevTree& t, int kinds, int first, int count, cudaStream_t 
 // work items (precision 0 = FP64, 1 = FP32 bulk).
 void launch_interact(const DevTree& t, const DevPlan& p, int precision, double G, int am,
                      int ctas, int warps_per_cta, cudaStream_t s);
+// Sets the general kernels' shared-memory carveout (once per device, outside
+// any stream capture); 0 on success.
+int configure_interact();
 
 // Downward pass for one level: L2L from the parent into the level's interior
 // cells (kinds bit 0), then phi and g at the leaf cells of its children

@@ -114,7 +114,7 @@ int scratch_address(int device, unsigned char** out) {
             cudaGetLastError();
             return OT_ERR_CUDA;
         }
-        if (configure_lattice() != 0) return OT_ERR_CUDA;
+        if (configure_lattice() != 0 || configure_interact() != 0) return OT_ERR_CUDA;
         g_scratch_addr[device] = (unsigned char*)p;
     }
     *out = g_scratch_addr[device];
