@@ -415,19 +415,18 @@ def run_ours(args):
                                      "includes": "forward solve + reverse sweep",
                                      "ratio_to_forward": sum(bms) / sum(solve_ms)}
         extra["cpu_baseline"] = cpu_baseline(leaves, rho_np)
-    # leaf moments, 2 M2M kernels per interior level, lattice, interactions,
-    # 2 L2L kernels per level
     # library kernels of one solve: leaf moments; per parent level the M2M
     # kernel for cells with interior children and/or the one for cells with
     # leaf children; the general interaction kernel; the lattice kernels (1 in
     # the FP64 form, near + far in the FP32-bulk form; none without leaf nodes
-    # below the root); per level the L2L kernel for its interior cells and/or
-    # the one evaluating its leaf children
+    # below the root); per level the L2L kernel for its interior cells below
+    # the root (or a leaf root) and/or the one evaluating its leaf children
     nl = info["n_levels"]
     leaf_at = lambda L: info["n_leaf_nodes"][L] if 0 <= L < nl else 0
     inner_at = lambda L: info["n_nodes"][L] - info["n_leaf_nodes"][L] if 0 <= L < nl else 0
     m2m = sum((inner_at(L + 1) > 0) + (leaf_at(L + 1) > 0) for L in range(nl - 1))
-    l2l = sum((L == 0 or inner_at(L) > 0) + (leaf_at(L + 1) > 0) for L in range(nl))
+    l2l = sum((leaf_at(0) > 0 if L == 0 else inner_at(L) > 0) + (leaf_at(L + 1) > 0)
+              for L in range(nl))
     lattice = sum(info["n_leaf_nodes"][1:nl]) > 0
     n_lat = (2 if prec == fmm.OT_PRECISION_FP32_BULK else 1) if lattice else 0
     launches = (1 + m2m + 1 + n_lat + l2l) * args.steps

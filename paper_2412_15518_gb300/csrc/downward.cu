@@ -5,8 +5,8 @@
 // delta = X_cell - X_parent, and inherits the parent's angular-momentum
 // correction acceleration (Sec. 4.3.1).  At a leaf cell (X = cell centre) the
 // result is evaluated: phi = L0 (+ the optional uniform-cube self term) and
-// g = -L1 + a_c.  One thread per cell, 8 blocks of 64 threads per node (so the
-// coarse levels spread over many SMs), levels top-down, FP64 throughout.
+// g = -L1 + a_c.  One thread per cell, one warp per block (so the coarse
+// levels spread over many SMs), levels top-down, FP64 throughout.
 #include "kernels.hpp"
 
 namespace otfmm {
@@ -19,11 +19,12 @@ __host__ __device__ inline double cube_self_constant() {
     return 3.0 * (log(2.0 + sqrt(3.0)) - 3.14159265358979323846 / 6.0);
 }
 
-// 64 threads per block, 8 blocks per node (one z-layer of 64 cells each).
-__global__ void __launch_bounds__(64) k_l2l(DevTree t, int first, const double* __restrict__ rho,
+// 32 threads per block, 16 blocks per node.  The root is launched only when
+// it is a leaf (an interior root has no parent expansion to add).
+__global__ void __launch_bounds__(32) k_l2l(DevTree t, int first, const double* __restrict__ rho,
                                             double* __restrict__ phi, double* __restrict__ g,
                                             double G, int self_term) {
-    const int node = first + (blockIdx.x >> 3);
+    const int node = first + (blockIdx.x >> 4);
     const int L = t.node_level[node];
     const int parent = t.node_parent[node];
     const int leaf = t.node_leaf[node];
@@ -32,7 +33,7 @@ __global__ void __launch_bounds__(64) k_l2l(DevTree t, int first, const double* 
     const int* xyz = t.node_xyz + 3 * node;
     if (leaf >= 0 && parent >= 0) return;  // leaf cells of level >= 1: k_l2l_leafkids
     {
-        const int c = ((blockIdx.x & 7) << 6) + threadIdx.x;
+        const int c = ((blockIdx.x & 15) << 5) + threadIdx.x;
         const int ci[3] = {c & 7, (c >> 3) & 7, c >> 6};
         const long long cell = (long long)node * kCells + c;
         double E[kLoc];
@@ -138,17 +139,18 @@ __device__ __forceinline__ void corners8(double* c) {
 //   phi(s) = A0 + eps A1.s + eps^2 s.A2.s / 2 + eps^3 A3:sss / 6
 //   grad(s) = A1 + eps A2 s + eps^2 A3:ss / 2
 // evaluated as 8-point sign transforms.  Each child adds its own-level
-// terms (L0, L1, a_c) and the parent's correction acceleration.
-__global__ void __launch_bounds__(256) k_l2l_leafkids(DevTree t, int first,
+// terms (L0, L1, a_c) and the parent's correction acceleration (folded into
+// the constant coefficient of the gradient).  8 blocks of 64 threads per node.
+__global__ void __launch_bounds__(64) k_l2l_leafkids(DevTree t, int first,
                                                       const double* __restrict__ rho,
                                                       double* __restrict__ phi,
                                                       double* __restrict__ g, double G,
                                                       int self_term) {
-    const int node = first + (blockIdx.x >> 1);
+    const int node = first + (blockIdx.x >> 3);
     const int child0 = t.node_child[node];
     if (child0 < 0) return;
     const long long N = t.n_cells;
-    const int c = ((blockIdx.x & 1) << 8) + threadIdx.x;
+    const int c = ((blockIdx.x & 7) << 6) + threadIdx.x;
     const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
     const int cn = child0 + (i >> 2) + 2 * (j >> 2) + 4 * (k >> 2);
     const int leaf = t.node_leaf[cn];
@@ -207,7 +209,8 @@ __global__ void __launch_bounds__(256) k_l2l_leafkids(DevTree t, int first,
         const int pb = p == 0 ? 1 : (p == 1 ? 3 : 4);  // packed (p, y)
         const int pc = p == 0 ? 2 : (p == 1 ? 4 : 5);  // packed (p, z)
         double* v = cg[p];
-        v[0] = A[1 + p] + 0.5 * e2 * (A3[pk3(p, 0, 0)] + A3[pk3(p, 1, 1)] + A3[pk3(p, 2, 2)]);
+        v[0] = A[1 + p] + 0.5 * e2 * (A3[pk3(p, 0, 0)] + A3[pk3(p, 1, 1)] + A3[pk3(p, 2, 2)]) -
+               P[20 + p];
         v[1] = e1 * A2[pa];
         v[2] = e1 * A2[pb];
         v[4] = e1 * A2[pc];
@@ -230,7 +233,7 @@ __global__ void __launch_bounds__(256) k_l2l_leafkids(DevTree t, int first,
 #pragma unroll
         for (int p = 0; p < 3; p++)
             g[((long long)leaf * 3 + p) * kCells + cl] =
-                -(t.loc[(1 + p) * N + cc] + cg[p][q]) + t.loc[(20 + p) * N + cc] + P[20 + p];
+                (t.loc[(20 + p) * N + cc] - t.loc[(1 + p) * N + cc]) - cg[p][q];
     }
 }
 
@@ -239,8 +242,8 @@ __global__ void __launch_bounds__(256) k_l2l_leafkids(DevTree t, int first,
 void launch_l2l(const DevTree& t, int kinds, int first, int count, const double* rho,
                 double* phi, double* g, double G, int self_term, cudaStream_t s) {
     if (count <= 0) return;
-    if (kinds & 1) k_l2l<<<count * 8, 64, 0, s>>>(t, first, rho, phi, g, G, self_term);
-    if (kinds & 2) k_l2l_leafkids<<<count * 2, 256, 0, s>>>(t, first, rho, phi, g, G, self_term);
+    if (kinds & 1) k_l2l<<<count * 16, 32, 0, s>>>(t, first, rho, phi, g, G, self_term);
+    if (kinds & 2) k_l2l_leafkids<<<count * 8, 64, 0, s>>>(t, first, rho, phi, g, G, self_term);
 }
 
 }  // namespace otfmm

@@ -9,11 +9,11 @@
 // cells, which the interaction kernels then accumulate into.
 //
 // M2M of cells with interior children uses 8 threads per parent cell, one
-// per child: the children's masses
-// and mass-weighted positions are summed by warp shuffles, every lane forms
-// its child's contribution about the common centre of mass, and a second
-// shuffle reduction sums them.  So the coarse levels (1 node at level 0,
-// 8 at level 1) still spread over many SMs of the FP64 pipe.  Cells whose
+// per child: the children's masses and mass-weighted positions are summed by
+// warp shuffles, every lane forms its child's contribution about the common
+// centre of mass, and a reduce-scatter leaves each lane with the sums of the
+// record entries it writes.  One warp per block, so the coarse levels (1 node
+// at level 0, 8 at level 1) still spread over many SMs of the FP64 pipe.  Cells whose
 // children are leaves (the most numerous) take a cheaper path: their children
 // sit at fixed offsets, so the moments are signed sums of 8 masses.
 #include "kernels.hpp"
@@ -85,15 +85,25 @@ __device__ __forceinline__ double sum8(double v) {
     return v;
 }
 
-// 256 threads = 32 parent cells x 8 children; 16 blocks per node.  Cells
-// whose children are leaf cells are left to k_m2m_leafkids.  The 4 cells of a
-// warp share one child node, so that test is uniform per warp.
-__global__ void __launch_bounds__(256) k_m2m(DevTree t, int first) {
-    const int node = first + (blockIdx.x >> 4);
+// Butterfly step of a reduce-scatter over lanes q and q ^ mask: a lane keeps
+// the component of each pair (lo, hi) on its own side of the mask bit, adds
+// its partner's copy of it, and hands over the other one.
+__device__ __forceinline__ double keep_add(bool upper, double lo, double hi, int mask) {
+    const double keep = upper ? hi : lo;
+    const double give = upper ? lo : hi;
+    return keep + __shfl_xor_sync(0xffffffffu, give, mask);
+}
+
+// One warp per block = 4 parent cells x 8 children; 128 blocks per node, so
+// that the single node of level 0 already spreads over 128 SMs.  Cells whose
+// children are leaf cells are left to k_m2m_leafkids; the 4 cells of a warp
+// share one child node, so that test is uniform per warp.
+__global__ void __launch_bounds__(32) k_m2m(DevTree t, int first) {
+    const int node = first + (blockIdx.x >> 7);
     const int child0 = t.node_child[node];
     if (child0 < 0) return;  // leaf node: moments come from rho
     const long long N = t.n_cells;
-    const int c = ((blockIdx.x & 15) << 5) + (threadIdx.x >> 3);  // parent cell in the node
+    const int c = ((blockIdx.x & 127) << 2) + (threadIdx.x >> 3);  // parent cell in the node
     const int q = threadIdx.x & 7;                                  // child octant
     const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
     const int a = q & 1, b = (q >> 1) & 1, e = q >> 2;
@@ -127,42 +137,56 @@ __global__ void __launch_bounds__(256) k_m2m(DevTree t, int first) {
     sym3_of(c2, d, t3);
 #pragma unroll
     for (int r = 0; r < 10; r++) S[6 + r] += 0.125 * t.mom64[(10 + r) * N + cc] + t3[r];
+    // the traces are linear in the moments: M3 trace vector t_i = M3_ijj
+    // (packed xxx+xyy+xzz, xxy+yyy+yzz, xxz+yyz+zzz) and trace(M2)
+    const double T[4] = {S[6] + S[9] + S[11], S[7] + S[12] + S[14], S[8] + S[13] + S[15],
+                         S[0] + S[3] + S[5]};
+    // reduce-scatter over the 8 lanes: lane q ends with the sums of S[q] and
+    // S[q + 8] (record entries 4 + q and 12 + q) and of T[q >> 1]
+    const bool u4 = q & 4, u2 = q & 2, u1 = q & 1;
+    double R8[8], R4[4], R2[2];
 #pragma unroll
-    for (int r = 0; r < 16; r++) S[r] = sum8(S[r]);
+    for (int h = 0; h < 8; h++) {
+        const int lo = (h & 3) | ((h & 4) << 1);  // components with bit 2 clear
+        R8[h] = keep_add(u4, S[lo], S[lo | 4], 4);
+    }
+#pragma unroll
+    for (int h = 0; h < 4; h++) {
+        const int lo = (h & 1) | ((h & 2) << 1);
+        R4[h] = keep_add(u2, R8[lo], R8[lo | 2], 2);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; h++) R2[h] = keep_add(u1, R4[2 * h], R4[2 * h + 1], 1);
+    const double U0 = keep_add(u4, T[0], T[2], 4);
+    const double U1 = keep_add(u4, T[1], T[3], 4);
+    double V = keep_add(u2, U0, U1, 2);
+    V += __shfl_xor_sync(0xffffffffu, V, 1);
+    // each lane writes the record entries it owns: 20 moments (+ the two
+    // traces) and 23 zeroed expansions
     const long long cell = (long long)node * kCells + c;
-    // lane q writes the components it owns: 20 moments (+ the record's two
-    // traces), 23 zeroed expansions
-    double vals[kRec];
-    vals[0] = M;
-    vals[1] = X[0];
-    vals[2] = X[1];
-    vals[3] = X[2];
-#pragma unroll
-    for (int r = 0; r < 16; r++) vals[4 + r] = S[r];
-    // M3 trace vector t_i = M3_ijj and trace(M2)
-    vals[20] = S[6 + 0] + S[6 + 3] + S[6 + 5];
-    vals[21] = S[6 + 1] + S[6 + 6] + S[6 + 8];
-    vals[22] = S[6 + 2] + S[6 + 7] + S[6 + 9];
-    vals[23] = S[0] + S[3] + S[5];
-#pragma unroll
-    for (int r = 0; r < kRec; r++) {
-        if ((r & 7) == q) {
-            if (r < kMom) {
-                t.mom64[r * N + cell] = vals[r];
-                t.mom32[cell * kMom + r] = (float)vals[r];
-            }
-            t.rec64[cell * kRec + r] = vals[r];
-        }
+    double* rec = t.rec64 + cell * kRec;
+    float* m32 = t.mom32 + cell * kMom;
+    rec[4 + q] = R2[0];
+    rec[12 + q] = R2[1];
+    t.mom64[(4 + q) * N + cell] = R2[0];
+    t.mom64[(12 + q) * N + cell] = R2[1];
+    m32[4 + q] = (float)R2[0];
+    m32[12 + q] = (float)R2[1];
+    if (q < 4) {
+        const double v = q == 0 ? M : (q == 1 ? X[0] : (q == 2 ? X[1] : X[2]));
+        rec[q] = v;
+        t.mom64[q * N + cell] = v;
+        m32[q] = (float)v;
     }
-    // FP32 octupole per unit mass (M3 / m and its trace vector) for the
-    // correction's target term, the division done here in FP64
-#pragma unroll
-    for (int r = 0; r < kOct; r++) {
-        if ((r & 7) == q) {
-            const double v = r < 13 ? vals[10 + r] : 0.0;
-            t.oct32[cell * kOct + r] = (float)(v * iM);
-        }
-    }
+    if (!u1) rec[20 + (q >> 1)] = V;
+    // FP32 octupole per unit mass (M3 / m, entries 10..19, and its trace
+    // vector, 20..22) for the correction's target term, the division done
+    // here in FP64; entries 13..15 are zero
+    float* o32 = t.oct32 + cell * kOct;
+    o32[2 + q] = (float)(R2[1] * iM);
+    if (q >= 6) o32[q - 6] = (float)(R2[0] * iM);
+    if (!u1) o32[10 + (q >> 1)] = q < 6 ? (float)(V * iM) : 0.f;
+    if (q == 1 || q == 3) o32[14 + (q >> 1)] = 0.f;
 #pragma unroll
     for (int r = q; r < kLoc; r += 8) t.loc[r * N + cell] = 0.0;
 }
@@ -187,13 +211,13 @@ __device__ __forceinline__ void walsh8(double* w) {
 // signed sums of the masses (a Walsh transform); the parallel-axis shift to
 // the centre of mass X gives
 //   M2 = P2 - M X X,   M3 = P3 - 3 sym(X P2) + 2 M X X X.
-// One thread per parent cell, 2 blocks of 256 per node.
-__global__ void __launch_bounds__(256) k_m2m_leafkids(DevTree t, int first) {
-    const int node = first + (blockIdx.x >> 1);
+// One thread per parent cell, 8 blocks of 64 per node.
+__global__ void __launch_bounds__(64) k_m2m_leafkids(DevTree t, int first) {
+    const int node = first + (blockIdx.x >> 3);
     const int child0 = t.node_child[node];
     if (child0 < 0) return;
     const long long N = t.n_cells;
-    const int c = ((blockIdx.x & 1) << 8) + threadIdx.x;
+    const int c = ((blockIdx.x & 7) << 6) + threadIdx.x;
     const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
     const int cn = child0 + (i >> 2) + 2 * (j >> 2) + 4 * (k >> 2);
     if (t.node_child[cn] >= 0) return;  // interior children: k_m2m
@@ -265,8 +289,8 @@ void launch_leaf_moments(const DevTree& t, const int* leaf_node, const double* r
 
 void launch_m2m(const DevTree& t, int kinds, int first, int count, cudaStream_t s) {
     if (count <= 0) return;
-    if (kinds & 1) k_m2m<<<count * 16, 256, 0, s>>>(t, first);
-    if (kinds & 2) k_m2m_leafkids<<<count * 2, 256, 0, s>>>(t, first);
+    if (kinds & 1) k_m2m<<<count * 128, 32, 0, s>>>(t, first);
+    if (kinds & 2) k_m2m_leafkids<<<count * 8, 64, 0, s>>>(t, first);
 }
 
 }  // namespace otfmm

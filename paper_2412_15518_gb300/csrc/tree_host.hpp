@@ -38,9 +38,11 @@ struct HostTree {
         return (interior_nodes_at(L + 1) > 0 ? 1 : 0) | (leaf_nodes_at(L + 1) > 0 ? 2 : 0);
     }
     // Which of the two downward (L2L) kernels level L needs: bit 0 the
-    // level's own interior nodes (and a root leaf), bit 1 its leaf children.
+    // level's own interior nodes below the root (an interior root has no
+    // parent expansion to add) or a root leaf, bit 1 its leaf children.
     int l2l_kinds(int L) const {
-        return (L == 0 || interior_nodes_at(L) > 0 ? 1 : 0) | (leaf_nodes_at(L + 1) > 0 ? 2 : 0);
+        const bool own = L == 0 ? leaf_nodes_at(0) > 0 : interior_nodes_at(L) > 0;
+        return (own ? 1 : 0) | (leaf_nodes_at(L + 1) > 0 ? 2 : 0);
     }
 };
 
