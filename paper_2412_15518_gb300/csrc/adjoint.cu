@@ -47,102 +47,142 @@ __global__ void __launch_bounds__(256) k_adj_seed(DevTree t, const int* __restri
     }
 }
 
-// packed index tables
-// L2L reverse at parent level: one thread per parent cell.  The forward
-// shift by d = X_child - X_parent is
+// Butterfly step of a reduce-scatter over lanes q and q ^ mask: a lane keeps
+// the component of each pair (lo, hi) on its own side of the mask bit, adds
+// its partner's copy of it, and hands over the other one.
+__device__ __forceinline__ double keep_add(bool upper, double lo, double hi, int mask) {
+    const double keep = upper ? hi : lo;
+    const double give = upper ? lo : hi;
+    return keep + __shfl_xor_sync(0xffffffffu, give, mask);
+}
+
+// Sum over the 8 lanes of a parent cell of 32 values: lane q ends with the
+// sums of components q, q + 8, q + 16 and q + 24 (out[0..3]).
+__device__ __forceinline__ void reduce_scatter8(const double* V, int q, double* out) {
+    const bool u4 = q & 4, u2 = q & 2, u1 = q & 1;
+    double R16[16], R8[8];
+#pragma unroll
+    for (int h = 0; h < 16; h++) {
+        const int lo = (h & 3) | ((h & 12) << 1);  // components with bit 2 clear
+        R16[h] = keep_add(u4, V[lo], V[lo | 4], 4);
+    }
+#pragma unroll
+    for (int g = 0; g < 8; g++) {
+        const int lo = (g & 1) | ((g & 6) << 1);
+        R8[g] = keep_add(u2, R16[lo], R16[lo | 2], 2);
+    }
+#pragma unroll
+    for (int f = 0; f < 4; f++) out[f] = keep_add(u1, R8[2 * f], R8[2 * f + 1], 1);
+}
+
+__device__ __forceinline__ double sum8(double v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    return v;
+}
+
+// L2L reverse at parent level: 8 lanes per parent cell, one per child (one
+// warp = 4 parent cells, 128 blocks per node, so even the single level-0 node
+// spreads over 128 SMs).  The forward shift by d = X_child - X_parent is
 //   C0 = L0 + L1.d + d.L2.d / 2 + L3:ddd / 6,  C1 = L1 + L2 d + L3:dd / 2,
 //   C2 = L2 + L3 d,  C3 = L3,
 // so with the child's adjoints C the parent's adjoints E gather
 //   E0 += C0,  E1 += C0 d + C1,  E2 += C0 dd / 2 + sym(C1 d) + C2,
 //   E3 += C0 ddd / 6 + sym(C1 dd) / 6 + sym(C2 d) / 3 + C3,
 // and d gets dbar = C0 (L1 + L2 d + L3:dd / 2) + L2 C1 + L3:sym(C1 d) + L3:C2,
-// added to the child's centre of mass and subtracted from the parent's.
-__global__ void __launch_bounds__(128) k_l2l_reverse(DevTree t, int first, double* locbar,
-                                                     double* mombar) {
-    const int node = first + blockIdx.x;
+// added to the child's centre of mass and subtracted from the parent's.  The
+// parent's sums over its children are a reduce-scatter over the 8 lanes.
+__global__ void __launch_bounds__(32) k_l2l_reverse(DevTree t, int first, double* locbar,
+                                                    double* mombar) {
+    const int node = first + (blockIdx.x >> 7);
     const int child0 = t.node_child[node];
     if (child0 < 0) return;
     const long long N = t.n_cells;
     const int L = t.node_level[node];
     const double hc = t.size / (double)(16 << L);  // child cell side
-    for (int c = threadIdx.x; c < kCells; c += blockDim.x) {
-        const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
-        const long long pcell = (long long)node * kCells + c;
-        double P[20];
+    const int c = ((blockIdx.x & 127) << 2) + (threadIdx.x >> 3);  // parent cell in the node
+    const int q = threadIdx.x & 7;                                  // child octant
+    const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
+    const long long pcell = (long long)node * kCells + c;
+    double P[20];
 #pragma unroll
-        for (int r = 0; r < 20; r++) P[r] = t.loc[r * N + pcell];
-        const double* L2 = P + 4;
-        const double* L3 = P + 10;
-        const double pd[3] = {t.mom64[N + pcell], t.mom64[2 * N + pcell], t.mom64[3 * N + pcell]};
-        double E[20], A[3] = {0.0, 0.0, 0.0}, Xp[3] = {0.0, 0.0, 0.0};
+    for (int r = 0; r < 20; r++) P[r] = t.loc[r * N + pcell];
+    const double* L2 = P + 4;
+    const double* L3 = P + 10;
+    const double pd[3] = {t.mom64[N + pcell], t.mom64[2 * N + pcell], t.mom64[3 * N + pcell]};
+    const int cn = child0 + (i >> 2) + 2 * (j >> 2) + 4 * (k >> 2);
+    const int a = q & 1, b = (q >> 1) & 1, e = q >> 2;
+    const long long cc = (long long)cn * kCells + (2 * (i & 3) + a) + 8 * (2 * (j & 3) + b) +
+                         64 * (2 * (k & 3) + e);
+    const double d[3] = {hc * ((a - 0.5) + t.mom64[N + cc] - 2.0 * pd[0]),
+                         hc * ((b - 0.5) + t.mom64[2 * N + cc] - 2.0 * pd[1]),
+                         hc * ((e - 0.5) + t.mom64[3 * N + cc] - 2.0 * pd[2])};
+    double C[20];
 #pragma unroll
-        for (int r = 0; r < 20; r++) E[r] = 0.0;
-        const int cn = child0 + (i >> 2) + 2 * (j >> 2) + 4 * (k >> 2);
-#pragma unroll 1
-        for (int q = 0; q < 8; q++) {
-            const int a = q & 1, b = (q >> 1) & 1, e = q >> 2;
-            const long long cc = (long long)cn * kCells + (2 * (i & 3) + a) + 8 * (2 * (j & 3) + b) +
-                                 64 * (2 * (k & 3) + e);
-            const double d[3] = {hc * ((a - 0.5) + t.mom64[N + cc] - 2.0 * pd[0]),
-                                 hc * ((b - 0.5) + t.mom64[2 * N + cc] - 2.0 * pd[1]),
-                                 hc * ((e - 0.5) + t.mom64[3 * N + cc] - 2.0 * pd[2])};
-            double C[20];
+    for (int r = 0; r < 20; r++) C[r] = locbar[r * N + cc];
+    const double C0 = C[0];
+    const double* C1 = C + 1;
+    const double* C2 = C + 4;
+    RMono md;
+    r_mono(d[0], d[1], d[2], md);
+    // this child's part of the parent's sums: V[0..19] = E, V[20..22] = a,
+    // V[23..25] = the parent's centre-of-mass adjoint; V[26..31] unused
+    double V[32];
 #pragma unroll
-            for (int r = 0; r < 20; r++) C[r] = locbar[r * N + cc];
-            const double C0 = C[0];
-            const double* C1 = C + 1;
-            const double* C2 = C + 4;
-            RMono md;
-            r_mono(d[0], d[1], d[2], md);
-            // E0, E1
-            E[0] += C0;
+    for (int r = 0; r < 32; r++) V[r] = 0.0;
+    double* E = V;
+    // E0, E1
+    E[0] = C0;
 #pragma unroll
-            for (int s = 0; s < 3; s++) E[1 + s] += C0 * d[s] + C1[s];
-            // E2 += C0 dd / 2 + sym(C1 d) + C2  (sym(C1 d)_uv = (C1_u d_v + C1_v d_u) / 2)
-            const double h0 = 0.5 * C0;
-            E[4] += h0 * md.xx + C1[0] * d[0] + C2[0];
-            E[5] += h0 * md.xy + 0.5 * (C1[0] * d[1] + C1[1] * d[0]) + C2[1];
-            E[6] += h0 * md.xz + 0.5 * (C1[0] * d[2] + C1[2] * d[0]) + C2[2];
-            E[7] += h0 * md.yy + C1[1] * d[1] + C2[3];
-            E[8] += h0 * md.yz + 0.5 * (C1[1] * d[2] + C1[2] * d[1]) + C2[4];
-            E[9] += h0 * md.zz + C1[2] * d[2] + C2[5];
-            // E3 += C0 ddd / 6 + (C1 dd)_sym / 6 + (C2 d)_sym / 3 + C3
-            add_rank3(E + 10, md, C1, C0 / 6.0, 1.0 / 6.0, 0.0, 0.0);
-            const double t3 = 1.0 / 3.0;
-            E[10] += t3 * (3.0 * C2[0] * d[0]) + C[10];
-            E[11] += t3 * (C2[0] * d[1] + 2.0 * C2[1] * d[0]) + C[11];
-            E[12] += t3 * (C2[0] * d[2] + 2.0 * C2[2] * d[0]) + C[12];
-            E[13] += t3 * (2.0 * C2[1] * d[1] + C2[3] * d[0]) + C[13];
-            E[14] += t3 * (C2[1] * d[2] + C2[2] * d[1] + C2[4] * d[0]) + C[14];
-            E[15] += t3 * (2.0 * C2[2] * d[2] + C2[5] * d[0]) + C[15];
-            E[16] += t3 * (3.0 * C2[3] * d[1]) + C[16];
-            E[17] += t3 * (C2[3] * d[2] + 2.0 * C2[4] * d[1]) + C[17];
-            E[18] += t3 * (2.0 * C2[4] * d[2] + C2[5] * d[1]) + C[18];
-            E[19] += t3 * (3.0 * C2[5] * d[2]) + C[19];
+    for (int s = 0; s < 3; s++) E[1 + s] = C0 * d[s] + C1[s];
+    // E2 = C0 dd / 2 + sym(C1 d) + C2  (sym(C1 d)_uv = (C1_u d_v + C1_v d_u) / 2)
+    const double h0 = 0.5 * C0;
+    E[4] = h0 * md.xx + C1[0] * d[0] + C2[0];
+    E[5] = h0 * md.xy + 0.5 * (C1[0] * d[1] + C1[1] * d[0]) + C2[1];
+    E[6] = h0 * md.xz + 0.5 * (C1[0] * d[2] + C1[2] * d[0]) + C2[2];
+    E[7] = h0 * md.yy + C1[1] * d[1] + C2[3];
+    E[8] = h0 * md.yz + 0.5 * (C1[1] * d[2] + C1[2] * d[1]) + C2[4];
+    E[9] = h0 * md.zz + C1[2] * d[2] + C2[5];
+    // E3 = C0 ddd / 6 + (C1 dd)_sym / 6 + (C2 d)_sym / 3 + C3
+    add_rank3(E + 10, md, C1, C0 / 6.0, 1.0 / 6.0, 0.0, 0.0);
+    const double t3 = 1.0 / 3.0;
+    E[10] += t3 * (3.0 * C2[0] * d[0]) + C[10];
+    E[11] += t3 * (C2[0] * d[1] + 2.0 * C2[1] * d[0]) + C[11];
+    E[12] += t3 * (C2[0] * d[2] + 2.0 * C2[2] * d[0]) + C[12];
+    E[13] += t3 * (2.0 * C2[1] * d[1] + C2[3] * d[0]) + C[13];
+    E[14] += t3 * (C2[1] * d[2] + C2[2] * d[1] + C2[4] * d[0]) + C[14];
+    E[15] += t3 * (2.0 * C2[2] * d[2] + C2[5] * d[0]) + C[15];
+    E[16] += t3 * (3.0 * C2[3] * d[1]) + C[16];
+    E[17] += t3 * (C2[3] * d[2] + 2.0 * C2[4] * d[1]) + C[17];
+    E[18] += t3 * (2.0 * C2[4] * d[2] + C2[5] * d[1]) + C[18];
+    E[19] += t3 * (3.0 * C2[5] * d[2]) + C[19];
 #pragma unroll
-            for (int s = 0; s < 3; s++) A[s] += locbar[(20 + s) * N + cc];
-            // dbar = C0 (L1 + L2 d + L3:dd / 2) + L2 C1 + L3:sym(C1 d) + L3:C2
-            double L2d[3], L3dd[3], L2C1[3], L3C1d[3], L3C2[3];
-            sym2_vec(L2, d, L2d);
-            sym3_contract(L3, md.xx, md.yy, md.zz, md.xy2, md.xz2, md.yz2, L3dd);
-            sym2_vec(L2, C1, L2C1);
-            sym3_contract(L3, C1[0] * d[0], C1[1] * d[1], C1[2] * d[2], C1[0] * d[1] + C1[1] * d[0],
-                          C1[0] * d[2] + C1[2] * d[0], C1[1] * d[2] + C1[2] * d[1], L3C1d);
-            sym3_contract(L3, C2[0], C2[3], C2[5], 2.0 * C2[1], 2.0 * C2[2], 2.0 * C2[4], L3C2);
+    for (int s = 0; s < 3; s++) V[20 + s] = locbar[(20 + s) * N + cc];
+    // dbar = C0 (L1 + L2 d + L3:dd / 2) + L2 C1 + L3:sym(C1 d) + L3:C2, added
+    // to the child's centre of mass and subtracted from the parent's
+    double L2d[3], L3dd[3], L2C1[3], L3C1d[3], L3C2[3];
+    sym2_vec(L2, d, L2d);
+    sym3_contract(L3, md.xx, md.yy, md.zz, md.xy2, md.xz2, md.yz2, L3dd);
+    sym2_vec(L2, C1, L2C1);
+    sym3_contract(L3, C1[0] * d[0], C1[1] * d[1], C1[2] * d[2], C1[0] * d[1] + C1[1] * d[0],
+                  C1[0] * d[2] + C1[2] * d[0], C1[1] * d[2] + C1[2] * d[1], L3C1d);
+    sym3_contract(L3, C2[0], C2[3], C2[5], 2.0 * C2[1], 2.0 * C2[2], 2.0 * C2[4], L3C2);
 #pragma unroll
-            for (int s = 0; s < 3; s++) {
-                const double db = C0 * (P[1 + s] + L2d[s] + 0.5 * L3dd[s]) + L2C1[s] + L3C1d[s] + L3C2[s];
-                mombar[(1 + s) * N + cc] += db;
-                Xp[s] -= db;
-            }
-        }
+    for (int s = 0; s < 3; s++) {
+        const double db = C0 * (P[1 + s] + L2d[s] + 0.5 * L3dd[s]) + L2C1[s] + L3C1d[s] + L3C2[s];
+        mombar[(1 + s) * N + cc] += db;  // this lane's child only
+        V[23 + s] = -db;
+    }
+    // the parent's sums: component r = q + 8 f of the 32; r < 23 is
+    // locbar[r], 23..25 the parent's centre-of-mass adjoint
+    double S[4];
+    reduce_scatter8(V, q, S);
 #pragma unroll
-        for (int r = 0; r < 20; r++) locbar[r * N + pcell] = E[r];
-#pragma unroll
-        for (int s = 0; s < 3; s++) {
-            locbar[(20 + s) * N + pcell] = A[s];
-            mombar[(1 + s) * N + pcell] += Xp[s];
-        }
+    for (int f = 0; f < 4; f++) {
+        const int r = q + 8 * f;
+        if (r < 23) locbar[r * N + pcell] = S[f];
+        else if (r < 26) mombar[(r - 22) * N + pcell] += S[f];
     }
 }
 
@@ -287,8 +327,8 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
     }
 }
 
-// M2M reverse at parent level: one thread per parent cell, writes its
-// children.  Forward (parent units, child offsets d = X_k - X_P):
+// M2M reverse at parent level: 8 lanes per parent cell, one per child (one
+// warp = 4 parent cells, 128 blocks per node); each lane writes its child.  Forward (parent units, child offsets d = X_k - X_P):
 //   M = sum m_k,  X_P = sum m_k X_k / M,  M2 = sum M2_k + m_k d d,
 //   M3 = sum M3_k + 3 sym(M2_k d) + m_k d d d,
 // so with the parent's adjoints (Bm, BX, B2, B3) each child gathers
@@ -296,84 +336,66 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
 //   dbar = 2 m_k B2 d + 3 B3:M2_k + 3 m_k B3:dd,
 // and then the centre of mass: Xbar_k += Xtot m_k / M, mbar_k += Xtot.d / M
 // + Bm with Xtot = BX - sum dbar (the geometric centre, a constant, when
-// M = 0).  Child offsets are recomputed in the second pass, not stored.
-__global__ void __launch_bounds__(128) k_m2m_reverse(DevTree t, int first, double* mombar) {
-    const int node = first + blockIdx.x;
+// M = 0), Xtot summed over the 8 lanes.
+__global__ void __launch_bounds__(32) k_m2m_reverse(DevTree t, int first, double* mombar) {
+    const int node = first + (blockIdx.x >> 7);
     const int child0 = t.node_child[node];
     if (child0 < 0) return;
     const long long N = t.n_cells;
     const int L = t.node_level[node];
     const double hp = t.size / (double)(8 << L), hc = 0.5 * hp;
-    for (int c = threadIdx.x; c < kCells; c += blockDim.x) {
-        const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
-        const long long pcell = (long long)node * kCells + c;
-        const double M = t.mom64[pcell];
-        const double XP[3] = {t.mom64[N + pcell], t.mom64[2 * N + pcell], t.mom64[3 * N + pcell]};
-        const double Bm = mombar[pcell];
-        double B2[6], B3[10];
+    const int c = ((blockIdx.x & 127) << 2) + (threadIdx.x >> 3);  // parent cell in the node
+    const int q = threadIdx.x & 7;                                  // child octant
+    const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
+    const long long pcell = (long long)node * kCells + c;
+    const double M = t.mom64[pcell];
+    const double XP[3] = {t.mom64[N + pcell], t.mom64[2 * N + pcell], t.mom64[3 * N + pcell]};
+    const double Bm = mombar[pcell];
+    double B2[6], B3[10];
 #pragma unroll
-        for (int r = 0; r < 6; r++) B2[r] = mombar[(4 + r) * N + pcell];
+    for (int r = 0; r < 6; r++) B2[r] = mombar[(4 + r) * N + pcell];
 #pragma unroll
-        for (int r = 0; r < 10; r++) B3[r] = mombar[(10 + r) * N + pcell];
-        const int cn = child0 + (i >> 2) + 2 * (j >> 2) + 4 * (k >> 2);
-        double Xtot[3] = {mombar[N + pcell], mombar[2 * N + pcell], mombar[3 * N + pcell]};
-        auto child = [&](int q, long long& cc, double* d) {
-            const int a = q & 1, b = (q >> 1) & 1, e = q >> 2;
-            cc = (long long)cn * kCells + (2 * (i & 3) + a) + 8 * (2 * (j & 3) + b) + 64 * (2 * (k & 3) + e);
-            d[0] = hp * (0.5 * ((a - 0.5) + t.mom64[N + cc]) - XP[0]);
-            d[1] = hp * (0.5 * ((b - 0.5) + t.mom64[2 * N + cc]) - XP[1]);
-            d[2] = hp * (0.5 * ((e - 0.5) + t.mom64[3 * N + cc]) - XP[2]);
-        };
-        // first pass: moment adjoints and delta-bar
-#pragma unroll 1
-        for (int q = 0; q < 8; q++) {
-            long long cc;
-            double d[3];
-            child(q, cc, d);
-            const double m = t.mom64[cc];
-            double M2k[6];
+    for (int r = 0; r < 10; r++) B3[r] = mombar[(10 + r) * N + pcell];
+    const int cn = child0 + (i >> 2) + 2 * (j >> 2) + 4 * (k >> 2);
+    const int a = q & 1, b = (q >> 1) & 1, e = q >> 2;
+    const long long cc = (long long)cn * kCells + (2 * (i & 3) + a) + 8 * (2 * (j & 3) + b) +
+                         64 * (2 * (k & 3) + e);
+    const double d[3] = {hp * (0.5 * ((a - 0.5) + t.mom64[N + cc]) - XP[0]),
+                         hp * (0.5 * ((b - 0.5) + t.mom64[2 * N + cc]) - XP[1]),
+                         hp * (0.5 * ((e - 0.5) + t.mom64[3 * N + cc]) - XP[2])};
+    const double m = t.mom64[cc];
+    double M2k[6];
 #pragma unroll
-            for (int r = 0; r < 6; r++) M2k[r] = hc * hc * t.mom64[(4 + r) * N + cc];
-            // M2bar_k += B2 + 3 B3 d
-            double B3d[6];
-            sym3_vec(B3, d, B3d);
-            // mbar_k += B2 : dd + B3 : ddd
-            double B2d[3], B3dd[3], B3M2[3];
-            sym2_vec(B2, d, B2d);
-            sym3_rr(B3, d, B3dd);
-            sym3_contract(B3, M2k[0], M2k[3], M2k[5], 2.0 * M2k[1], 2.0 * M2k[2], 2.0 * M2k[4], B3M2);
-            const double dd = B2d[0] * d[0] + B2d[1] * d[1] + B2d[2] * d[2];
-            const double ddd = B3dd[0] * d[0] + B3dd[1] * d[1] + B3dd[2] * d[2];
-            mombar[cc] += dd + ddd;
+    for (int r = 0; r < 6; r++) M2k[r] = hc * hc * t.mom64[(4 + r) * N + cc];
+    // M2bar_k += B2 + 3 B3 d
+    double B3d[6];
+    sym3_vec(B3, d, B3d);
+    // mbar_k += B2 : dd + B3 : ddd
+    double B2d[3], B3dd[3], B3M2[3];
+    sym2_vec(B2, d, B2d);
+    sym3_rr(B3, d, B3dd);
+    sym3_contract(B3, M2k[0], M2k[3], M2k[5], 2.0 * M2k[1], 2.0 * M2k[2], 2.0 * M2k[4], B3M2);
+    const double dd = B2d[0] * d[0] + B2d[1] * d[1] + B2d[2] * d[2];
+    const double ddd = B3dd[0] * d[0] + B3dd[1] * d[1] + B3dd[2] * d[2];
+    // dbar = 2 m B2 d + 3 B3 : M2_k + 3 m B3 : dd, and Xtot = BX - sum dbar
+    double db[3], Xtot[3];
 #pragma unroll
-            for (int p = 0; p < 3; p++) {
-                // dbar = 2 m B2 d + 3 B3 : M2_k + 3 m B3 : dd
-                const double db = 2.0 * m * B2d[p] + 3.0 * B3M2[p] + 3.0 * m * B3dd[p];
-                Xtot[p] -= db;
-                mombar[(1 + p) * N + cc] += db;
-            }
+    for (int p = 0; p < 3; p++) db[p] = 2.0 * m * B2d[p] + 3.0 * B3M2[p] + 3.0 * m * B3dd[p];
 #pragma unroll
-            for (int n = 0; n < 6; n++) mombar[(4 + n) * N + cc] += B2[n] + 3.0 * B3d[n];
+    for (int p = 0; p < 3; p++) Xtot[p] = mombar[(1 + p) * N + pcell] - sum8(db[p]);  // every lane
+    // the centre of mass X_P = sum m_k X_k / M and M = sum m_k
+    const double iM = M != 0.0 ? 1.0 / M : 0.0;
+    double s = 0.0;
 #pragma unroll
-            for (int n = 0; n < 10; n++) mombar[(10 + n) * N + cc] += B3[n];
-        }
-        // second pass: the centre of mass X_P = sum m_k X_k / M and M = sum m_k
-        const double iM = M != 0.0 ? 1.0 / M : 0.0;
-#pragma unroll 1
-        for (int q = 0; q < 8; q++) {
-            long long cc;
-            double d[3];
-            child(q, cc, d);
-            const double m = t.mom64[cc];
-            double s = 0.0;
-#pragma unroll
-            for (int p = 0; p < 3; p++) {
-                mombar[(1 + p) * N + cc] += Xtot[p] * m * iM;
-                s += Xtot[p] * d[p] * iM;
-            }
-            mombar[cc] += s + Bm;
-        }
+    for (int p = 0; p < 3; p++) {
+        mombar[(1 + p) * N + cc] += db[p] + Xtot[p] * m * iM;
+        s += Xtot[p] * d[p] * iM;
     }
+    mombar[cc] += (dd + ddd) + (s + Bm);
+#pragma unroll
+    for (int n = 0; n < 6; n++) mombar[(4 + n) * N + cc] += B2[n] + 3.0 * B3d[n];
+#pragma unroll
+    for (int n = 0; n < 10; n++) mombar[(10 + n) * N + cc] += B3[n];
 }
 
 __global__ void __launch_bounds__(256) k_rho_bar(DevTree t, const int* __restrict__ leaf_node,
@@ -401,7 +423,7 @@ void launch_adj_seed(const DevTree& t, const int* leaf_node, const double* w1, c
 
 void launch_l2l_reverse(const DevTree& t, int first, int count, double* locbar, double* mombar,
                         cudaStream_t s) {
-    if (count > 0) k_l2l_reverse<<<count, 128, 0, s>>>(t, first, locbar, mombar);
+    if (count > 0) k_l2l_reverse<<<count * 128, 32, 0, s>>>(t, first, locbar, mombar);
 }
 
 void launch_m2l_reverse(const DevTree& t, const DevPlan& p, const double* locbar, double* mombar,
@@ -410,7 +432,7 @@ void launch_m2l_reverse(const DevTree& t, const DevPlan& p, const double* locbar
 }
 
 void launch_m2m_reverse(const DevTree& t, int first, int count, double* mombar, cudaStream_t s) {
-    if (count > 0) k_m2m_reverse<<<count, 128, 0, s>>>(t, first, mombar);
+    if (count > 0) k_m2m_reverse<<<count * 128, 32, 0, s>>>(t, first, mombar);
 }
 
 void launch_rho_bar(const DevTree& t, const int* leaf_node, const double* mombar, const double* w1,
