@@ -354,7 +354,7 @@ void enqueue_downward(ot_tree* t, const double* rho, double* phi, double* g,
     DevTree d = dev_tree(t);
     for (int L = 0; L < t->h.n_levels; L++)
         launch_l2l(d, t->h.l2l_kinds(L), t->h.level_first[L], t->h.level_first[L + 1] - t->h.level_first[L], rho,
-                   phi, g, o.G, o.self_term ? 1 : 0, s);
+                   phi, g, o.G, o.self_term ? 1 : 0, o.precision, s);
 }
 
 // Enqueues the whole solve on the capture stream; the four timing events

@@ -24,8 +24,9 @@ int configure_interact();
 
 // Downward pass for one level: L2L from the parent into the level's interior
 // cells (kinds bit 0), then phi and g at the leaf cells of its children
-// (bit 1) (HostTree::l2l_kinds).
+// (bit 1) (HostTree::l2l_kinds).  precision 1 (FP32-bulk form): the shift
+// arithmetic in FP32, every sum in FP64.
 void launch_l2l(const DevTree& t, int kinds, int first, int count, const double* rho,
-                double* phi, double* g, double G, int self_term, cudaStream_t s);
+                double* phi, double* g, double G, int self_term, int precision, cudaStream_t s);
 
 }  // namespace otfmm

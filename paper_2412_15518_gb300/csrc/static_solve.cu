@@ -272,7 +272,7 @@ extern "C" int ot_solve_gravity_static(const ot_tree_desc* desc, const double* r
     launch_interact(d, dp, o.precision, o.G, o.am_correction ? 1 : 0, 4 * sms, 4, s);
     for (int L = 0; L < h.n_levels; L++)
         launch_l2l(d, h.l2l_kinds(L), h.level_first[L], h.level_first[L + 1] - h.level_first[L], rho, phi, g,
-                   o.G, o.self_term ? 1 : 0, s);
+                   o.G, o.self_term ? 1 : 0, o.precision, s);
     if (cudaGetLastError() != cudaSuccess) return OT_ERR_CUDA;
     return OT_OK;
 }
