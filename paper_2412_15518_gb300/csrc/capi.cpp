@@ -296,14 +296,15 @@ int check_dev_ptr(const ot_tree* t, const void* p) {
 void enqueue_leaf_moments(ot_tree* t, const double* rho, cudaStream_t s) {
     launch_leaf_moments(dev_tree(t), t->d_leaf_node, rho, s);
 }
-void enqueue_m2m(ot_tree* t, cudaStream_t s) {
+void enqueue_m2m(ot_tree* t, int precision, cudaStream_t s) {
     DevTree d = dev_tree(t);
     for (int L = t->h.n_levels - 2; L >= 0; L--)
-        launch_m2m(d, t->h.m2m_kinds(L), t->h.level_first[L], t->h.level_first[L + 1] - t->h.level_first[L], s);
+        launch_m2m(d, t->h.m2m_kinds(L), t->h.level_first[L], t->h.level_first[L + 1] - t->h.level_first[L],
+                   precision, s);
 }
-void enqueue_moments(ot_tree* t, const double* rho, cudaStream_t s) {
+void enqueue_moments(ot_tree* t, const double* rho, int precision, cudaStream_t s) {
     enqueue_leaf_moments(t, rho, s);
-    enqueue_m2m(t, s);
+    enqueue_m2m(t, precision, s);
 }
 
 // The interaction kernels only add into the expansions with atomics, so they
@@ -370,7 +371,7 @@ int enqueue_solve(ot_tree* t, const double* rho, double* phi, double* g, const o
     // branches, before the general kernel
     TRYC(cudaEventRecordWithFlags(t->ev[1], s, cudaEventRecordExternal));
     TRY(fork_lattice(t, o, s));
-    enqueue_m2m(t, s);
+    enqueue_m2m(t, o.precision, s);
     launch_general(t, o, s);
     TRY(join_lattice(t, o, s));
     TRYC(cudaEventRecordWithFlags(t->ev[2], s, cudaEventRecordExternal));
@@ -539,7 +540,7 @@ int ot_compute_moments(ot_tree* t, const double* rho, void* stream) {
     DeviceGuard guard(t->device);
     TRY(check_dev_ptr(t, rho));
     cudaStream_t s = (cudaStream_t)stream;
-    enqueue_moments(t, rho, s);
+    enqueue_moments(t, rho, OT_PRECISION_FP64, s);
     TRYC(cudaGetLastError());
     t->last_stream = s;
     return OT_OK;
@@ -602,7 +603,7 @@ int ot_gravity_backward(ot_tree* t, const double* rho, const double* w1, const d
     cudaStream_t s = (cudaStream_t)stream;
     t->last_stream = s;
     // forward pass: moments and complete expansions stay in the workspace
-    enqueue_moments(t, rho, s);
+    enqueue_moments(t, rho, o.precision, s);
     TRY(enqueue_interact(t, o, s));
     enqueue_downward(t, rho, t->d_phi_out, t->d_g_out, o, s);
     TRYC(cudaGetLastError());
@@ -664,7 +665,7 @@ int ot_autotune(ot_tree* t, const double* rho, double* phi, double* g, const ot_
         const int c = chunks[ci];
         t->chunk = c;
         if ((err = ensure_plan(t, o.theta))) break;
-        enqueue_moments(t, rho, s);
+        enqueue_moments(t, rho, o.precision, s);
         for (int p : cps) {
             for (int li = 0; li < n_lcps && err == OT_OK; li++) {
                 t->ctas_per_sm = p;

@@ -9,10 +9,11 @@ namespace otfmm {
 
 // Upward pass: leaf masses, then exact M2M level by level (Lmax-1 .. 0).
 // kinds: bit 0 the kernel for cells with interior children, bit 1 the one
-// for cells with leaf children (HostTree::m2m_kinds).
+// for cells with leaf children (HostTree::m2m_kinds).  precision 1 (FP32-bulk
+// form): the shift products in FP32, every sum in FP64.
 void launch_leaf_moments(const DevTree& t, const int* leaf_node, const double* rho,
                          cudaStream_t s);
-void launch_m2m(const DevTree& t, int kinds, int first, int count, cudaStream_t s);
+void launch_m2m(const DevTree& t, int kinds, int first, int count, int precision, cudaStream_t s);
 
 // All cell-to-cell interactions of every level: persistent launch over the
 // work items (precision 0 = FP64, 1 = FP32 bulk).

@@ -52,29 +52,29 @@ __global__ void __launch_bounds__(256) k_leaf_moments(DevTree t, const int* __re
 // xyy xyz xzz yyy yyz yzz zzz), written out component by component so that
 // nothing is indexed at run time.
 // o = s u v (rank 2, u v symmetric in use: u = s' v)
-__device__ __forceinline__ void outer2(double s, const double* v, double* o) {
+template <class T> __device__ __forceinline__ void outer2(T s, const T* v, T* o) {
     o[0] = s * v[0] * v[0]; o[1] = s * v[0] * v[1]; o[2] = s * v[0] * v[2];
     o[3] = s * v[1] * v[1]; o[4] = s * v[1] * v[2]; o[5] = s * v[2] * v[2];
 }
 // o = s v v v (rank 3)
-__device__ __forceinline__ void outer3(double s, const double* v, double* o) {
-    const double xx = s * v[0] * v[0], yy = s * v[1] * v[1], zz = s * v[2] * v[2];
+template <class T> __device__ __forceinline__ void outer3(T s, const T* v, T* o) {
+    const T xx = s * v[0] * v[0], yy = s * v[1] * v[1], zz = s * v[2] * v[2];
     o[0] = xx * v[0]; o[1] = xx * v[1]; o[2] = xx * v[2]; o[3] = yy * v[0];
     o[4] = s * v[0] * v[1] * v[2]; o[5] = zz * v[0]; o[6] = yy * v[1]; o[7] = yy * v[2];
     o[8] = zz * v[1]; o[9] = zz * v[2];
 }
 // o_ijk = P_ij v_k + P_ik v_j + P_jk v_i for a packed symmetric rank-2 P
-__device__ __forceinline__ void sym3_of(const double* P, const double* v, double* o) {
-    o[0] = 3.0 * P[0] * v[0];
-    o[1] = P[0] * v[1] + 2.0 * P[1] * v[0];
-    o[2] = P[0] * v[2] + 2.0 * P[2] * v[0];
-    o[3] = 2.0 * P[1] * v[1] + P[3] * v[0];
+template <class T> __device__ __forceinline__ void sym3_of(const T* P, const T* v, T* o) {
+    o[0] = T(3) * P[0] * v[0];
+    o[1] = P[0] * v[1] + T(2) * P[1] * v[0];
+    o[2] = P[0] * v[2] + T(2) * P[2] * v[0];
+    o[3] = T(2) * P[1] * v[1] + P[3] * v[0];
     o[4] = P[1] * v[2] + P[2] * v[1] + P[4] * v[0];
-    o[5] = 2.0 * P[2] * v[2] + P[5] * v[0];
-    o[6] = 3.0 * P[3] * v[1];
-    o[7] = P[3] * v[2] + 2.0 * P[4] * v[1];
-    o[8] = 2.0 * P[4] * v[2] + P[5] * v[1];
-    o[9] = 3.0 * P[5] * v[2];
+    o[5] = T(2) * P[2] * v[2] + P[5] * v[0];
+    o[6] = T(3) * P[3] * v[1];
+    o[7] = P[3] * v[2] + T(2) * P[4] * v[1];
+    o[8] = T(2) * P[4] * v[2] + P[5] * v[1];
+    o[9] = T(3) * P[5] * v[2];
 }
 
 // sum over the 8 lanes of a parent cell (lanes 8g .. 8g+7 of a warp)
@@ -97,7 +97,11 @@ __device__ __forceinline__ double keep_add(bool upper, double lo, double hi, int
 // One warp per block = 4 parent cells x 8 children; 128 blocks per node, so
 // that the single node of level 0 already spreads over 128 SMs.  Cells whose
 // children are leaf cells are left to k_m2m_leafkids; the 4 cells of a warp
-// share one child node, so that test is uniform per warp.
+// share one child node, so that test is uniform per warp.  BULK (FP32-bulk
+// form): the products of the shift (m d d, sym(M2 d), m d d d) in FP32, each
+// widened exactly and added to the FP64 sums; masses, centres of mass and
+// every sum stay FP64.
+template <bool BULK>
 __global__ void __launch_bounds__(32) k_m2m(DevTree t, int first) {
     const int node = first + (blockIdx.x >> 7);
     const int child0 = t.node_child[node];
@@ -125,18 +129,36 @@ __global__ void __launch_bounds__(32) k_m2m(DevTree t, int first) {
     const double iM = M != 0.0 ? 1.0 / M : 0.0;               // zero mass: moments about the centre
 #pragma unroll
     for (int s = 0; s < 3; s++) X[s] *= iM;
-    const double d[3] = {pos[0] - X[0], pos[1] - X[1], pos[2] - X[2]};
     // the child's shifted moments: M2 + m d d, M3 + sym(M2 d) + m d d d
-    double c2[6], S[16], t3[10];
+    double S[16];
+    if (BULK) {
+        const float* mc = t.mom32 + cc * kMom;
+        const float dfv[3] = {0.5f * (((float)a - 0.5f) + mc[1]) - (float)X[0],
+                              0.5f * (((float)b - 0.5f) + mc[2]) - (float)X[1],
+                              0.5f * (((float)e - 0.5f) + mc[3]) - (float)X[2]};
+        float c2[6], p2[6], p3[10], t3[10];
 #pragma unroll
-    for (int r = 0; r < 6; r++) c2[r] = 0.25 * t.mom64[(4 + r) * N + cc];  // child units -> parent
-    outer2(m, d, S);
+        for (int r = 0; r < 6; r++) c2[r] = 0.25f * mc[4 + r];  // child units -> parent
+        outer2(mc[0], dfv, p2);
+        outer3(mc[0], dfv, p3);
+        sym3_of(c2, dfv, t3);
 #pragma unroll
-    for (int r = 0; r < 6; r++) S[r] += c2[r];
-    outer3(m, d, S + 6);
-    sym3_of(c2, d, t3);
+        for (int r = 0; r < 6; r++) S[r] = fma(0.25, t.mom64[(4 + r) * N + cc], widen(p2[r]));
 #pragma unroll
-    for (int r = 0; r < 10; r++) S[6 + r] += 0.125 * t.mom64[(10 + r) * N + cc] + t3[r];
+        for (int r = 0; r < 10; r++) S[6 + r] = fma(0.125, t.mom64[(10 + r) * N + cc], widen(p3[r] + t3[r]));
+    } else {
+        const double d[3] = {pos[0] - X[0], pos[1] - X[1], pos[2] - X[2]};
+        double c2[6], t3[10];
+#pragma unroll
+        for (int r = 0; r < 6; r++) c2[r] = 0.25 * t.mom64[(4 + r) * N + cc];  // child units -> parent
+        outer2(m, d, S);
+#pragma unroll
+        for (int r = 0; r < 6; r++) S[r] += c2[r];
+        outer3(m, d, S + 6);
+        sym3_of(c2, d, t3);
+#pragma unroll
+        for (int r = 0; r < 10; r++) S[6 + r] += 0.125 * t.mom64[(10 + r) * N + cc] + t3[r];
+    }
     // the traces are linear in the moments: M3 trace vector t_i = M3_ijj
     // (packed xxx+xyy+xzz, xxy+yyy+yzz, xxz+yyz+zzz) and trace(M2)
     const double T[4] = {S[6] + S[9] + S[11], S[7] + S[12] + S[14], S[8] + S[13] + S[15],
@@ -211,7 +233,9 @@ __device__ __forceinline__ void walsh8(double* w) {
 // signed sums of the masses (a Walsh transform); the parallel-axis shift to
 // the centre of mass X gives
 //   M2 = P2 - M X X,   M3 = P3 - 3 sym(X P2) + 2 M X X X.
-// One thread per parent cell, 8 blocks of 64 per node.
+// One thread per parent cell, 8 blocks of 64 per node.  BULK: the
+// parallel-axis products in FP32, widened exactly into the FP64 sums.
+template <bool BULK>
 __global__ void __launch_bounds__(64) k_m2m_leafkids(DevTree t, int first) {
     const int node = first + (blockIdx.x >> 3);
     const int child0 = t.node_child[node];
@@ -240,14 +264,29 @@ __global__ void __launch_bounds__(64) k_m2m_leafkids(DevTree t, int first) {
     double S2[6], S3[10];
     // parallel-axis shift to the centre of mass: M2 = P2 - M X X,
     // M3 = P3 - sym(P2 X) + 2 M X X X
-    double xx2[6], xxx3[10], px3[10];
-    outer2(M, X, xx2);
-    outer3(2.0 * M, X, xxx3);
-    sym3_of(P2, X, px3);
+    if (BULK) {
+        const float Mf = (float)M;
+        const float Xf[3] = {(float)X[0], (float)X[1], (float)X[2]};
+        const float P2f[6] = {0.0625f * Mf, 0.0625f * (float)Sxy, 0.0625f * (float)Sxz,
+                              0.0625f * Mf, 0.0625f * (float)Syz, 0.0625f * Mf};
+        float xx2[6], xxx3[10], px3[10];
+        outer2(Mf, Xf, xx2);
+        outer3(2.0f * Mf, Xf, xxx3);
+        sym3_of(P2f, Xf, px3);
 #pragma unroll
-    for (int r = 0; r < 6; r++) S2[r] = P2[r] - xx2[r];
+        for (int r = 0; r < 6; r++) S2[r] = P2[r] - widen(xx2[r]);
 #pragma unroll
-    for (int r = 0; r < 10; r++) S3[r] = P3[r] - px3[r] + xxx3[r];
+        for (int r = 0; r < 10; r++) S3[r] = P3[r] + widen(xxx3[r] - px3[r]);
+    } else {
+        double xx2[6], xxx3[10], px3[10];
+        outer2(M, X, xx2);
+        outer3(2.0 * M, X, xxx3);
+        sym3_of(P2, X, px3);
+#pragma unroll
+        for (int r = 0; r < 6; r++) S2[r] = P2[r] - xx2[r];
+#pragma unroll
+        for (int r = 0; r < 10; r++) S3[r] = P3[r] - px3[r] + xxx3[r];
+    }
     const long long cell = (long long)node * kCells + c;
     double v[kRec];
     v[0] = M;
@@ -287,10 +326,17 @@ void launch_leaf_moments(const DevTree& t, const int* leaf_node, const double* r
     k_leaf_moments<<<t.n_leaf, 256, 0, s>>>(t, leaf_node, rho);
 }
 
-void launch_m2m(const DevTree& t, int kinds, int first, int count, cudaStream_t s) {
+void launch_m2m(const DevTree& t, int kinds, int first, int count, int precision, cudaStream_t s) {
     if (count <= 0) return;
-    if (kinds & 1) k_m2m<<<count * 128, 32, 0, s>>>(t, first);
-    if (kinds & 2) k_m2m_leafkids<<<count * 8, 64, 0, s>>>(t, first);
+    const bool bulk = precision == 1;
+    if (kinds & 1) {
+        if (bulk) k_m2m<true><<<count * 128, 32, 0, s>>>(t, first);
+        else k_m2m<false><<<count * 128, 32, 0, s>>>(t, first);
+    }
+    if (kinds & 2) {
+        if (bulk) k_m2m_leafkids<true><<<count * 8, 64, 0, s>>>(t, first);
+        else k_m2m_leafkids<false><<<count * 8, 64, 0, s>>>(t, first);
+    }
 }
 
 }  // namespace otfmm

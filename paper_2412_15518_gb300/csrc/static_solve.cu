@@ -257,7 +257,7 @@ extern "C" int ot_solve_gravity_static(const ot_tree_desc* desc, const double* r
     }
     launch_leaf_moments(d, (const int*)(base + l.leaf_node), rho, s);
     for (int L = h.n_levels - 2; L >= 0; L--)
-        launch_m2m(d, h.m2m_kinds(L), h.level_first[L], h.level_first[L + 1] - h.level_first[L], s);
+        launch_m2m(d, h.m2m_kinds(L), h.level_first[L], h.level_first[L + 1] - h.level_first[L], o.precision, s);
     DevLattice dl = {};
     dl.hoff_far = (const int*)(base + l.hoff_far);
     dl.hoff_near = (const int*)(base + l.hoff_near);
