@@ -187,13 +187,12 @@ __host__ __device__ inline int entry_near(int e) { return (e >> 15) & 1; }
 // halo_sub(w).  kHaloPy = 12 and halo_pz = 16 (mod 32) make the 32 lanes of a
 // warp (4 x 4 x 2 targets) hit 32 distinct banks.
 constexpr int kHaloPy = 12;
-__host__ __device__ inline int halo_hh(int w) { return w + 4; }
-__host__ __device__ inline int halo_pz(int w) {
-    const int need = kHaloPy * (w + 4);
-    return need + (((16 - need) % 32) + 32) % 32;
+__host__ __device__ constexpr int halo_hh(int w) { return w + 4; }
+__host__ __device__ constexpr int halo_pz(int w) {
+    return kHaloPy * (w + 4) + (((16 - kHaloPy * (w + 4)) % 32) + 32) % 32;
 }
-__host__ __device__ inline int halo_sub(int w) { return halo_pz(w) * halo_hh(w); }
-__host__ __device__ inline int halo_index(int x, int y, int z, int w) {
+__host__ __device__ constexpr int halo_sub(int w) { return halo_pz(w) * halo_hh(w); }
+__host__ __device__ constexpr int halo_index(int x, int y, int z, int w) {
     return ((x & 1) + 2 * (y & 1) + 4 * (z & 1)) * halo_sub(w) + ((x + w) >> 1) +
            kHaloPy * ((y + w) >> 1) + halo_pz(w) * ((z + w) >> 1);
 }

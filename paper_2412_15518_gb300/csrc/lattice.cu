@@ -71,6 +71,73 @@ __device__ __forceinline__ void fill_halo(const DevTree& t, int node, int w, T* 
 // kernel and of the FP32-pipe kernels share the SMs.
 enum LatticeMode { kAll = 0, kNear = 1, kFar = 2 };
 
+// Exact near pairs for the near set 0 < |d|^2 <= 4 (theta = 0.5): its 32
+// offsets are 16 pairs (d, -d), unrolled with the parity class as a template
+// parameter, so every halo offset is an immediate, the coefficients
+// D0 = 1/|d| and D1 = d/|d|^3 are constants and the zero components of D1
+// cost nothing: 78 FP64 operations per target instead of 96, and no table
+// loads.  Representative d of pair n, packed (dx+2) + 5 (dy+2) + 25 (dz+2).
+__host__ __device__ constexpr int near2_code(int n) {
+    return n == 0 ? 3 + 5 * 2 + 25 * 2 :          // (1, 0, 0)
+           n == 1 ? 2 + 5 * 3 + 25 * 2 :          // (0, 1, 0)
+           n == 2 ? 2 + 5 * 2 + 25 * 3 :          // (0, 0, 1)
+           n == 3 ? 3 + 5 * 3 + 25 * 2 :          // (1, 1, 0)
+           n == 4 ? 3 + 5 * 1 + 25 * 2 :          // (1, -1, 0)
+           n == 5 ? 3 + 5 * 2 + 25 * 3 :          // (1, 0, 1)
+           n == 6 ? 3 + 5 * 2 + 25 * 1 :          // (1, 0, -1)
+           n == 7 ? 2 + 5 * 3 + 25 * 3 :          // (0, 1, 1)
+           n == 8 ? 2 + 5 * 3 + 25 * 1 :          // (0, 1, -1)
+           n == 9 ? 3 + 5 * 3 + 25 * 3 :          // (1, 1, 1)
+           n == 10 ? 3 + 5 * 3 + 25 * 1 :         // (1, 1, -1)
+           n == 11 ? 3 + 5 * 1 + 25 * 3 :         // (1, -1, 1)
+           n == 12 ? 3 + 5 * 1 + 25 * 1 :         // (1, -1, -1)
+           n == 13 ? 4 + 5 * 2 + 25 * 2 :         // (2, 0, 0)
+           n == 14 ? 2 + 5 * 4 + 25 * 2 :         // (0, 2, 0)
+                     2 + 5 * 2 + 25 * 4;          // (0, 0, 2)
+}
+// 1/|d| and 1/|d|^3 for |d|^2 = 1, 2, 3, 4
+__host__ __device__ constexpr double near2_inv_r(int r2) {
+    return r2 == 1 ? 1.0 : r2 == 2 ? 0.70710678118654752440 : r2 == 3 ? 0.57735026918962576451 : 0.5;
+}
+__host__ __device__ constexpr double near2_inv_r3(int r2) {
+    return r2 == 1 ? 1.0 : r2 == 2 ? 0.35355339059327376220 : r2 == 3 ? 0.19245008972987525484 : 0.125;
+}
+
+template <int PAR, int N>
+__device__ __forceinline__ void near2_pairs(const double* hd, int t1, double (&dv)[4], double (&ev)[4]) {
+    constexpr int code = near2_code(N);
+    constexpr int dx = code % 5 - 2, dy = (code / 5) % 5 - 2, dz = code / 25 - 2;
+    constexpr int r2 = dx * dx + dy * dy + dz * dz;
+    constexpr int px = PAR & 1, py = (PAR >> 1) & 1, pz = PAR >> 2;
+    constexpr int op = halo_index(px + dx, py + dy, pz + dz, 2);
+    constexpr int om = halo_index(px - dx, py - dy, pz - dz, 2);
+    constexpr int t2 = 2 * halo_pz(2);  // the second target, 4 cells up in z
+    constexpr double c0 = near2_inv_r(r2);
+    constexpr double cx = dx * near2_inv_r3(r2), cy = dy * near2_inv_r3(r2), cz = dz * near2_inv_r3(r2);
+    const double p1 = hd[t1 + op], q1 = hd[t1 + om], p2 = hd[t1 + op + t2], q2 = hd[t1 + om + t2];
+    const double s1 = p1 + q1, r1 = p1 - q1, s2 = p2 + q2, r2v = p2 - q2;
+    dv[0] = fma(s1, c0, dv[0]);
+    ev[0] = fma(s2, c0, ev[0]);
+    if (dx != 0) {
+        dv[1] = fma(r1, cx, dv[1]);
+        ev[1] = fma(r2v, cx, ev[1]);
+    }
+    if (dy != 0) {
+        dv[2] = fma(r1, cy, dv[2]);
+        ev[2] = fma(r2v, cy, ev[2]);
+    }
+    if (dz != 0) {
+        dv[3] = fma(r1, cz, dv[3]);
+        ev[3] = fma(r2v, cz, ev[3]);
+    }
+    if constexpr (N + 1 < 16) near2_pairs<PAR, N + 1>(hd, t1, dv, ev);
+}
+
+template <int PAR>
+__device__ __forceinline__ void near2_all(const double* hd, int t1, double (&dv)[4], double (&ev)[4]) {
+    near2_pairs<PAR, 0>(hd, t1, dv, ev);
+}
+
 // One node of the lattice pairs, by a CTA of 8 warps (one per parity class).
 template <int MODE>
 __device__ __forceinline__ void lattice_node(const DevTree& t, const DevPlan& p, const DevLattice& lp,
@@ -91,7 +158,22 @@ __device__ __forceinline__ void lattice_node(const DevTree& t, const DevPlan& p,
     const int t2 = 2 * halo_pz(w);                     // second target: 4 cells up in z
     double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;    // FP64 sums, target 1
     double e0 = 0.0, e1 = 0.0, e2 = 0.0, e3 = 0.0;    // FP64 sums, target 2
-    if (MODE != kFar) {
+    if (MODE == kNear && lp.n_near == 32 && w == 2) {
+        const double* hd = reinterpret_cast<const double*>(smem);
+        double dv[4] = {0.0, 0.0, 0.0, 0.0}, ev[4] = {0.0, 0.0, 0.0, 0.0};
+        switch (par) {  // warp-uniform
+            case 0: near2_all<0>(hd, t1, dv, ev); break;
+            case 1: near2_all<1>(hd, t1, dv, ev); break;
+            case 2: near2_all<2>(hd, t1, dv, ev); break;
+            case 3: near2_all<3>(hd, t1, dv, ev); break;
+            case 4: near2_all<4>(hd, t1, dv, ev); break;
+            case 5: near2_all<5>(hd, t1, dv, ev); break;
+            case 6: near2_all<6>(hd, t1, dv, ev); break;
+            default: near2_all<7>(hd, t1, dv, ev); break;
+        }
+        d0 = dv[0]; d1 = dv[1]; d2 = dv[2]; d3 = dv[3];
+        e0 = ev[0]; e1 = ev[1]; e2 = ev[2]; e3 = ev[3];
+    } else if (MODE != kFar) {
         // Near entries come in (d, -d) pairs: entry q and entry n_near - 1 - q
         // (the near set is centrally symmetric and sorted).  With D0 even and
         // D1 odd, a pair costs 6 FP64 operations per target instead of 8:
