@@ -661,24 +661,27 @@ int ot_autotune(ot_tree* t, const double* rho, double* phi, double* g, const ot_
     float best = 1e30f;
     int bc = t->chunk, bp = t->ctas_per_sm, bl = t->lattice_ctas_per_sm;
     int err = OT_OK;
+    // every candidate is timed as the solve runs it: the whole solve graph
+    // (the lattice branches start beside the M2M chain, so the best CTA
+    // counts depend on that schedule), captured afresh for each candidate
     for (int ci = 0; ci < n_chunks; ci++) {
         const int c = chunks[ci];
         t->chunk = c;
         if ((err = ensure_plan(t, o.theta))) break;
-        enqueue_moments(t, rho, o.precision, s);
         for (int p : cps) {
             for (int li = 0; li < n_lcps && err == OT_OK; li++) {
                 t->ctas_per_sm = p;
                 t->lattice_ctas_per_sm = lcps[li];
+                destroy_graphs(t);
                 float ms_sum = 0.0f;
                 for (int rep = 0; rep < 4 && err == OT_OK; rep++) {
                     cudaEventRecord(e0, s);
-                    err = enqueue_interact(t, o, s);
+                    err = solve_graph(t, rho, phi, g, o, s);
                     cudaEventRecord(e1, s);
                     cudaEventSynchronize(e1);
                     float ms = 0.0f;
                     cudaEventElapsedTime(&ms, e0, e1);
-                    if (rep > 0) ms_sum += ms;  // first run warms the plan
+                    if (rep > 0) ms_sum += ms;  // the first run captures the graph
                 }
                 if (err == OT_OK && ms_sum < best) {
                     best = ms_sum;
