@@ -653,11 +653,17 @@ int ot_autotune(ot_tree* t, const double* rho, double* phi, double* g, const ot_
     const int chunks_bulk[] = {32, 64};
     const int* chunks = bulk ? chunks_bulk : chunks_fp64;
     const int n_chunks = bulk ? 2 : 4;
-    const int cps[] = {1, 2, 4, 8};
-    const int lcps_bulk[] = {1, 2, 4, 0};
+    // general CTAs per SM (at most 3 or 4 are resident, by registers; more
+    // stay queued and start as others finish) and, for the bulk form, the
+    // lattice kernels' persistent CTAs per SM (0: one per node)
+    const int cps_fp64[] = {1, 2, 4, 8};
+    const int cps_bulk[] = {1, 2, 3, 4, 6, 8};
+    const int* cps = bulk ? cps_bulk : cps_fp64;
+    const int n_cps = bulk ? 6 : 4;
+    const int lcps_bulk[] = {1, 2, 3, 4, 0};
     const int lcps_fp64[] = {0};
     const int* lcps = bulk ? lcps_bulk : lcps_fp64;
-    const int n_lcps = bulk ? 4 : 1;
+    const int n_lcps = bulk ? 5 : 1;
     float best = 1e30f;
     int bc = t->chunk, bp = t->ctas_per_sm, bl = t->lattice_ctas_per_sm;
     int err = OT_OK;
@@ -668,7 +674,8 @@ int ot_autotune(ot_tree* t, const double* rho, double* phi, double* g, const ot_
         const int c = chunks[ci];
         t->chunk = c;
         if ((err = ensure_plan(t, o.theta))) break;
-        for (int p : cps) {
+        for (int pi = 0; pi < n_cps; pi++) {
+            const int p = cps[pi];
             for (int li = 0; li < n_lcps && err == OT_OK; li++) {
                 t->ctas_per_sm = p;
                 t->lattice_ctas_per_sm = lcps[li];
