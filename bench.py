@@ -48,8 +48,8 @@ L2_FLUSH_BYTES = 256 << 20
 # the interaction kernels summarised in profiles/ (k_interact + the lattice
 # kernels of the form, per launch).  Valid for these kernels as captured; a
 # workload or form without a capture reports null.
-TRAFFIC_BYTES = {("binary_l3", "fp64"): 15.289e6 + 10.638e6,
-                 ("binary_l3", "fp32_bulk"): 13.474e6 + 10.567e6 + 9.563e6}
+TRAFFIC_BYTES = {("binary_l3", "fp64"): 15.327e6 + 10.637e6,
+                 ("binary_l3", "fp32_bulk"): 13.473e6 + 10.664e6 + 9.564e6}
 
 WORKLOAD_TEXT = {
     "sphere_l1": "uniform level-1 octree, 8 leaves of 8^3 (4,096 cells), one polytrope",
