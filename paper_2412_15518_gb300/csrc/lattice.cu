@@ -71,38 +71,11 @@ __device__ __forceinline__ void fill_halo(const DevTree& t, int node, int w, T* 
 // kernel and of the FP32-pipe kernels share the SMs.
 enum LatticeMode { kAll = 0, kNear = 1, kFar = 2 };
 
-// Exact near pairs for the near set 0 < |d|^2 <= 4 (theta = 0.5): its 32
-// offsets are 16 pairs (d, -d), unrolled with the parity class as a template
-// parameter, so every halo offset is an immediate, the coefficients
-// D0 = 1/|d| and D1 = d/|d|^3 are constants and the zero components of D1
-// cost nothing: 78 FP64 operations per target instead of 96, and no table
-// loads.  Representative d of pair n, packed (dx+2) + 5 (dy+2) + 25 (dz+2).
-__host__ __device__ constexpr int near2_code(int n) {
-    return n == 0 ? 3 + 5 * 2 + 25 * 2 :          // (1, 0, 0)
-           n == 1 ? 2 + 5 * 3 + 25 * 2 :          // (0, 1, 0)
-           n == 2 ? 2 + 5 * 2 + 25 * 3 :          // (0, 0, 1)
-           n == 3 ? 3 + 5 * 3 + 25 * 2 :          // (1, 1, 0)
-           n == 4 ? 3 + 5 * 1 + 25 * 2 :          // (1, -1, 0)
-           n == 5 ? 3 + 5 * 2 + 25 * 3 :          // (1, 0, 1)
-           n == 6 ? 3 + 5 * 2 + 25 * 1 :          // (1, 0, -1)
-           n == 7 ? 2 + 5 * 3 + 25 * 3 :          // (0, 1, 1)
-           n == 8 ? 2 + 5 * 3 + 25 * 1 :          // (0, 1, -1)
-           n == 9 ? 3 + 5 * 3 + 25 * 3 :          // (1, 1, 1)
-           n == 10 ? 3 + 5 * 3 + 25 * 1 :         // (1, 1, -1)
-           n == 11 ? 3 + 5 * 1 + 25 * 3 :         // (1, -1, 1)
-           n == 12 ? 3 + 5 * 1 + 25 * 1 :         // (1, -1, -1)
-           n == 13 ? 4 + 5 * 2 + 25 * 2 :         // (2, 0, 0)
-           n == 14 ? 2 + 5 * 4 + 25 * 2 :         // (0, 2, 0)
-                     2 + 5 * 2 + 25 * 4;          // (0, 0, 2)
-}
-// 1/|d| and 1/|d|^3 for |d|^2 = 1, 2, 3, 4
-__host__ __device__ constexpr double near2_inv_r(int r2) {
-    return r2 == 1 ? 1.0 : r2 == 2 ? 0.70710678118654752440 : r2 == 3 ? 0.57735026918962576451 : 0.5;
-}
-__host__ __device__ constexpr double near2_inv_r3(int r2) {
-    return r2 == 1 ? 1.0 : r2 == 2 ? 0.35355339059327376220 : r2 == 3 ? 0.19245008972987525484 : 0.125;
-}
-
+// Exact near pairs for the near set 0 < |d|^2 <= 4 (theta = 0.5), unrolled
+// with the parity class as a template parameter (near2_code and its
+// coefficients are in lattice.hpp): every halo offset is an immediate, the
+// coefficients are constants and the zero components of D1 cost nothing --
+// 78 FP64 operations per target instead of 96, and no table loads.
 template <int PAR, int N>
 __device__ __forceinline__ void near2_pairs(const double* hd, int t1, double (&dv)[4], double (&ev)[4]) {
     constexpr int code = near2_code(N);

@@ -10,6 +10,36 @@
 
 namespace otfmm {
 
+// The near set 0 < |d|^2 <= 4 (theta = 0.5) as 16 pairs (d, -d): the
+// representative d of pair n, packed (dx+2) + 5 (dy+2) + 25 (dz+2), and by
+// |d|^2 the factors 1/|d| (D0) and 1/|d|^3 (D1 = d / |d|^3).
+// The lattice kernel unrolls its exact near pairs over these at compile time.
+__host__ __device__ constexpr int near2_code(int n) {
+    return n == 0 ? 3 + 5 * 2 + 25 * 2 :          // (1, 0, 0)
+           n == 1 ? 2 + 5 * 3 + 25 * 2 :          // (0, 1, 0)
+           n == 2 ? 2 + 5 * 2 + 25 * 3 :          // (0, 0, 1)
+           n == 3 ? 3 + 5 * 3 + 25 * 2 :          // (1, 1, 0)
+           n == 4 ? 3 + 5 * 1 + 25 * 2 :          // (1, -1, 0)
+           n == 5 ? 3 + 5 * 2 + 25 * 3 :          // (1, 0, 1)
+           n == 6 ? 3 + 5 * 2 + 25 * 1 :          // (1, 0, -1)
+           n == 7 ? 2 + 5 * 3 + 25 * 3 :          // (0, 1, 1)
+           n == 8 ? 2 + 5 * 3 + 25 * 1 :          // (0, 1, -1)
+           n == 9 ? 3 + 5 * 3 + 25 * 3 :          // (1, 1, 1)
+           n == 10 ? 3 + 5 * 3 + 25 * 1 :         // (1, 1, -1)
+           n == 11 ? 3 + 5 * 1 + 25 * 3 :         // (1, -1, 1)
+           n == 12 ? 3 + 5 * 1 + 25 * 1 :         // (1, -1, -1)
+           n == 13 ? 4 + 5 * 2 + 25 * 2 :         // (2, 0, 0)
+           n == 14 ? 2 + 5 * 4 + 25 * 2 :         // (0, 2, 0)
+                     2 + 5 * 2 + 25 * 4;          // (0, 0, 2)
+}
+// 1/|d| and 1/|d|^3 for |d|^2 = 1, 2, 3, 4
+__host__ __device__ constexpr double near2_inv_r(int r2) {
+    return r2 == 1 ? 1.0 : r2 == 2 ? 0.70710678118654752440 : r2 == 3 ? 0.57735026918962576451 : 0.5;
+}
+__host__ __device__ constexpr double near2_inv_r3(int r2) {
+    return r2 == 1 ? 1.0 : r2 == 2 ? 0.35355339059327376220 : r2 == 3 ? 0.19245008972987525484 : 0.125;
+}
+
 // Dynamic shared memory of one CTA of a kernel mode (0: FP64 all pairs,
 // 1: FP64 near pairs, 2: FP32 far pairs), halo widths and staged far-table
 // entries (mode 2).

@@ -81,6 +81,17 @@ def test_fp64_other_theta(fmm, theta):
     assert rel(g, g_o) < TOL64
 
 
+@pytest.mark.parametrize("theta", [0.4, 1.0 / 3.0, 0.75])
+def test_fp32_bulk_other_theta(fmm, theta):
+    # near sets other than theta = 0.5's run the lattice kernel's generic near
+    # loop; theta = 1/3 also takes the widest far halo
+    lv, rho = CASES["amr_l3_seams"]()
+    phi, g = gpu_solve(fmm, lv, rho, theta=theta, precision=fmm.OT_PRECISION_FP32_BULK)
+    phi_o, g_o = O.solve(lv, rho, theta=theta)
+    assert rel(phi, phi_o) < TOL32
+    assert rel(g, g_o) < TOL32
+
+
 def test_fp64_self_term_and_G(fmm):
     lv, rho = CASES["sphere_l1_shuffled"]()
     phi, g = gpu_solve(fmm, lv, rho, self_term=True, G=6.674e-8)
