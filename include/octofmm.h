@@ -62,8 +62,14 @@ extern "C" {
 
 #define OT_PRECISION_FP64 0      /* every step in FP64                           */
 #define OT_PRECISION_FP32_BULK 1 /* cell-to-cell multipole interactions in FP32,
-                                    FP64 accumulation; FP64 near field, moments,
-                                    expansions and correction assembly          */
+                                    FP64 accumulation; FP64 near field (the
+                                    monopole pairs), masses, centres of mass,
+                                    every moment and expansion sum and the
+                                    correction's mass ratio; the products of the
+                                    M2M and L2L shifts (the terms in the offsets)
+                                    in FP32, each widened exactly into an FP64
+                                    sum.  Error vs FP64 <= 1e-6 (relative to the
+                                    field's maximum)                           */
 
 typedef struct ot_tree ot_tree; /* opaque, library-owned */
 
