@@ -168,9 +168,11 @@ int ot_solve_gravity_host(ot_tree* tree, const double* rho_host, double* phi_hos
 int ot_gravity_backward(ot_tree* tree, const double* rho, const double* w1, const double* w2,
                         double* drho, const ot_solve_opts* opts, void* stream);
 
-/* Times the candidate work-item shapes of the persistent launch for this
- * plan on `stream` (synchronises it) and keeps the fastest.  rho/phi/g as in
- * ot_solve_gravity (their contents are overwritten by the timing runs). */
+/* Chooses the persistent launch's stencil-chunk length and the CTAs per SM
+ * of the general kernel (and, FP32-bulk form, of the lattice kernels) for
+ * this plan: every candidate is timed as the whole solve graph it would run,
+ * on `stream` (synchronised), and the fastest is kept.  rho/phi/g as in
+ * ot_solve_gravity (phi and g hold the solve's result afterwards). */
 int ot_autotune(ot_tree* tree, const double* rho, double* phi, double* g,
                 const ot_solve_opts* opts, void* stream);
 
