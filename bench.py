@@ -238,8 +238,20 @@ def cpu_baseline(leaves, rho, budget_s: float = 20.0):
         dt = time.perf_counter() - t0
         sample = f"oracle solve of {k:,} seeded leaf cells and their ancestors' expansions"
     n = c["m2l"] + c["p2p"] + c["seam"]
-    return {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
-            "seconds": dt, "interactions": n}
+    out = {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+           "seconds": dt, "interactions": n}
+    # the same oracle on one core, on a smaller seeded sample (about 5 s)
+    if cores > 1:
+        oracle.set_threads(1)
+        k1 = int(min(n_cells, max(64, 5.0 * (rate / cores) / max(per_cell, 1.0))))
+        s1 = np.sort(np.random.default_rng(1).choice(n_cells, size=k1, replace=False))
+        t0 = time.perf_counter()
+        _, _, c1 = oracle.solve_sample(leaves, rho, s1, return_counts=True)
+        dt1 = time.perf_counter() - t0
+        oracle.set_threads(0)
+        out["value_1core"] = (c1["m2l"] + c1["p2p"] + c1["seam"]) / dt1
+        out["sample_1core"] = f"oracle solve of {k1:,} seeded leaf cells on 1 core"
+    return out
 
 
 def run_reference(args):
