@@ -6,10 +6,11 @@
 //   L2L^T      per interior cell, gathered over its 8 children, bottom-up:
 //              E_parent = sum shift^T(E_child, delta), a_parent = sum a_child,
 //              delta-bar to the children's and the parent's centre of mass
-//   M2L^T      every cell gathers over its stencil both of its roles: as the
-//              source of each partner's expansion (adjoints of its moments and
-//              of its centre of mass) and as the target (its centre of mass and
-//              the correction's mass ratio); leaf-leaf pairs use the lattice
+//   M2L^T      every directed pair reversed once: a pair with an interior
+//              target in that target's pass (its centre of mass and the
+//              correction's mass ratio gathered, the source's moment and
+//              centre-of-mass adjoints sent by atomics), a pair with a leaf
+//              target in the source's pass; leaf-leaf pairs use the lattice
 //              table transposed; one persistent launch over all levels
 //   M2M^T      per interior cell, top-down: adjoints of the 8 children's
 //              moments and centres of mass
@@ -234,9 +235,12 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
         adj_zero(acc);
         double lat0 = 0.0, lat1 = 0.0;   // lattice pairs: dJ/dm of this leaf cell (h, h^2 parts)
         const int base = p.list_first[item_list(it)];
-        // Two passes over the partners, each holding only what its role needs.
-        // Pass 1: this cell as the source of its partners' expansions
-        // (R = X_P - X_C), and the transposed lattice pairs of a leaf cell.
+        // Two passes over the partners, each holding only what its role needs;
+        // every directed pair is reversed once.  Pass 1: this cell as the
+        // source of a leaf partner's expansion (R = X_P - X_C), and the
+        // transposed lattice pairs of a leaf cell.  A pair with an interior
+        // target is reversed whole in that target's pass 2, which sends the
+        // source-side adjoints here with atomics.
 #pragma unroll 1
         for (int q = it.z; q < it.w; q++) {
             const int e = __ldg(p.entries + base + q);
@@ -254,7 +258,7 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
                 lat1 = fma(locbar[N + pc], t0.y, fma(locbar[2 * N + pc], t1.x, fma(locbar[3 * N + pc], t1.y, lat1)));
                 continue;
             }
-            if (!cleaf && !pleaf && entry_near(e)) continue;
+            if (!pleaf) continue;  // an interior target: its own pass 2
             const double mP = t.mom64[pc];
             const double R[3] = {h * ((double)dx + t.mom64[N + pc] - dC[0]),
                                  h * ((double)dy + t.mom64[2 * N + pc] - dC[1]),
@@ -266,14 +270,32 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
             for (int r = 0; r < 20; r++) EP[r] = (pleaf && r >= 4) ? 0.0 : locbar[r * N + pc];
 #pragma unroll
             for (int r = 0; r < 3; r++) aP[r] = locbar[(20 + r) * N + pc];
-            // the R-gradient of this pair moves this cell's centre of mass; an
-            // interior partner adds it in its own pass 2, a leaf partner has none
-            m2l_pair_reverse<true, false>(R, G, am, mC, M2C, M3C, !cleaf, mP, M3P, !pleaf, EP[0], EP + 1,
-                                          EP + 4, EP + 10, aP, !cleaf && pleaf, -1.0, acc.R, acc);
+            // the R-gradient of this pair moves this cell's centre of mass (a
+            // leaf partner's centre is fixed)
+            m2l_pair_reverse<true, false>(R, G, am, mC, M2C, M3C, !cleaf, mP, M3P, false, EP[0], EP + 1,
+                                          EP + 4, EP + 10, aP, !cleaf, -1.0, acc.R, acc);
+        }
+        // this cell's source-side adjoints so far; acc's source fields then
+        // carry one pair's partner adjoints at a time in pass 2
+        const double hi = 1.0 / h;
+        atomicAdd(mombar + cell, acc.mB - G * (lat0 * hi - lat1 * hi * hi));
+        acc.mB = 0.0;
+        if (!cleaf) {
+#pragma unroll
+            for (int r = 0; r < 6; r++) {
+                atomicAdd(mombar + (4 + r) * N + cell, acc.M2B[r]);
+                acc.M2B[r] = 0.0;
+            }
+#pragma unroll
+            for (int r = 0; r < 10; r++) {
+                atomicAdd(mombar + (10 + r) * N + cell, acc.M3B[r]);
+                acc.M3B[r] = 0.0;
+            }
         }
         // Pass 2 (interior cells): this cell as the target of its partners
-        // (R = X_C - X_P): the correction's mass ratio, and the pair's
-        // R-gradient for both centres of mass.
+        // (R = X_C - X_P), each pair reversed whole: the correction's mass
+        // ratio and the pair's R-gradient for this cell, the partner's
+        // source-side adjoints and its part of the R-gradient by atomics.
         if (!cleaf) {
             double EC[20], aC[3];
 #pragma unroll
@@ -301,8 +323,23 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
 #pragma unroll
                 for (int r = 0; r < 10; r++) M3P[r] = pleaf ? 0.0 : h3 * t.mom64[(10 + r) * N + pc];
                 double gR[3] = {0.0, 0.0, 0.0};
-                m2l_pair_reverse<false, true>(Rn, G, am, mP, M2P, M3P, !pleaf, mC, M3C, true, EC[0], EC + 1,
-                                              EC + 4, EC + 10, aC, true, 1.0, gR, acc);
+                m2l_pair_reverse<true, true>(Rn, G, am, mP, M2P, M3P, !pleaf, mC, M3C, true, EC[0], EC + 1,
+                                             EC + 4, EC + 10, aC, true, 1.0, gR, acc);
+                // the partner's source-side adjoints of this pair
+                atomicAdd(mombar + pc, acc.mB);
+                acc.mB = 0.0;
+                if (!pleaf) {
+#pragma unroll
+                    for (int r = 0; r < 6; r++) {
+                        atomicAdd(mombar + (4 + r) * N + pc, acc.M2B[r]);
+                        acc.M2B[r] = 0.0;
+                    }
+#pragma unroll
+                    for (int r = 0; r < 10; r++) {
+                        atomicAdd(mombar + (10 + r) * N + pc, acc.M3B[r]);
+                        acc.M3B[r] = 0.0;
+                    }
+                }
                 // dJ/dR moves both centres of mass: + this cell's, - an interior
                 // partner's (a leaf's centre is fixed)
 #pragma unroll
@@ -313,15 +350,14 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
                 }
             }
         }
-        const double hi = 1.0 / h;
-        atomicAdd(mombar + cell, acc.mB + acc.mA - G * (lat0 * hi - lat1 * hi * hi));
+        // this cell's target-side adjoints (the correction's mass ratio) and
+        // centre-of-mass adjoint
         if (!cleaf) {
+            atomicAdd(mombar + cell, acc.mA);
 #pragma unroll
             for (int s = 0; s < 3; s++) atomicAdd(mombar + (1 + s) * N + cell, acc.R[s]);
 #pragma unroll
-            for (int r = 0; r < 6; r++) atomicAdd(mombar + (4 + r) * N + cell, acc.M2B[r]);
-#pragma unroll
-            for (int r = 0; r < 10; r++) atomicAdd(mombar + (10 + r) * N + cell, acc.M3B[r] + acc.M3A[r]);
+            for (int r = 0; r < 10; r++) atomicAdd(mombar + (10 + r) * N + cell, acc.M3A[r]);
         }
         __syncwarp();
     }
