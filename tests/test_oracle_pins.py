@@ -15,7 +15,9 @@ mathematics that holds independently of the reading:
 * conservation of momentum and angular momentum (Sec. 4.3.1);
 * degree-1 homogeneity, the uniform-sphere closed form, the cube self
   potential closed form;
-* the dual-number derivative against central differences.
+* the dual-number derivative against central differences;
+* the sampled solve against the full solve at its cells;
+* the pair reverse against central differences of the pair.
 """
 import itertools
 
@@ -571,3 +573,54 @@ def test_zero_mass_gradient(which, request):
     _, _, dphi, dg = O.solve_jvp(lv, rho0, v)
     jvp = (w1 * dphi).sum() + (w2 * dg).sum()
     assert abs((gr0 * v).sum() - jvp) < 1e-12 * abs(jvp)
+
+
+# --------------------------------------------------------------------------
+# the sampled solve and the pair reverse
+
+
+def test_sampled_solve_equals_the_full_solve_at_its_cells(small_amr):
+    # the sampled solve (used at full sizes, where the full oracle is too slow)
+    # evaluates the same algorithm for the sampled leaf cells only
+    lv, rho = small_amr
+    phi, g = O.solve(lv, rho)
+    rng = np.random.default_rng(7)
+    sample = np.sort(rng.choice(lv.shape[0] * 512, size=200, replace=False))
+    phi_s, g_s = O.solve_sample(lv, rho, sample)
+    assert rel(phi_s, phi.reshape(-1)[sample]) < 1e-13
+    g_full = np.moveaxis(g, 1, 2).reshape(-1, 3)[sample]
+    assert rel(g_s, g_full) < 1e-13
+
+
+def _sym_moment_direction(rng):
+    # a direction in moment space (m, X[3], M2[9], M3[27]) with symmetric M2, M3
+    v = np.zeros(40)
+    v[0] = rng.standard_normal()
+    v[1:4] = rng.standard_normal(3)
+    a = rng.standard_normal((3, 3))
+    v[4:13] = ((a + a.T) / 2).reshape(-1)
+    b = rng.standard_normal((3, 3, 3))
+    s = sum(np.transpose(b, p) for p in itertools.permutations(range(3))) / 6.0
+    v[13:40] = s.reshape(-1)
+    return v
+
+
+@pytest.mark.parametrize("am", [True, False])
+def test_pair_reverse_is_the_gradient_of_the_pair(am):
+    # J = Ebar . m2l(A, B); the pair reverse must give dJ/dA and dJ/dB, checked
+    # by central differences along random symmetric directions
+    rng = np.random.default_rng(11)
+    pa = rng.uniform(-0.05, 0.05, (6, 3)) + np.array([0.1, 0.2, 0.3])
+    pb = rng.uniform(-0.05, 0.05, (6, 3)) + np.array([0.9, 0.6, 0.45])
+    A = O.p2m_m2m(pa, rng.uniform(0.5, 1.5, 6))
+    B = O.p2m_m2m(pb, rng.uniform(0.5, 1.5, 6))
+    E = rng.standard_normal(43)
+    J = lambda a, b: float(E @ O.m2l(a, b, am_correction=am))
+    ga, gb = O.m2l_reverse(A, B, E, am_correction=am)
+    for _ in range(4):
+        va, vb = _sym_moment_direction(rng), _sym_moment_direction(rng)
+        eps = 1e-5
+        da = (J(A + eps * va, B) - J(A - eps * va, B)) / (2 * eps)
+        db = (J(A, B + eps * vb) - J(A, B - eps * vb)) / (2 * eps)
+        assert abs(ga @ va - da) <= 1e-7 * (abs(da) + np.abs(ga).max())
+        assert abs(gb @ vb - db) <= 1e-7 * (abs(db) + np.abs(gb).max())
