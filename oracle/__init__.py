@@ -7,6 +7,13 @@ fixed order).  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may import it.  It imports nothing from the
 GPU package and shares no code with it.
 
+Every function here is pinned by ``tests/test_oracle_pins.py`` (and the
+tree checks by ``tests/test_abi_host.py``) against facts that do not come
+from the oracle: direct summation, closed forms, finite differences of the
+D tensors, of the pair and of the whole solve, moments taken directly from
+point masses, an independent pair enumeration, and momentum and angular
+momentum conservation.  None is parity-unpinned.
+
 Every function takes plain numpy arrays:
 
 * ``leaves``: int32 ``[n_leaf, 4]`` = (level, ix, iy, iz) of each leaf node;
