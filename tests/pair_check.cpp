@@ -1,0 +1,83 @@
+// Evaluates the GPU library's own pair formulas on the host -- the forward
+// cell-to-cell interaction (pair_formula.cuh: m2l_pair, the Kronecker parts
+// from the traces, the correction's target term) and its reverse
+// (adjoint_pair.cuh: m2l_pair_reverse) -- for pairs read from stdin, in FP64
+// and physical units (cell side 1), so that a test can compare them with
+// the oracle's unpacked formulation.
+//
+// Input, one pair per line: am G  XA[3] XB[3]  mA M3A[10]  mB M2B[6] M3B[10]
+//   E0 E1[3] E2[6] E3[10] a[3]       (symmetric tensors packed: xx xy xz yy
+//   yz zz; xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz)
+// Output, one line per pair: the expansion at A due to B, L0 L1[3] L2[6]
+// L3[10] ac[3]; then the reverse given the adjoints (E, a): dJ/dmB,
+// dJ/dM2B[6], dJ/dM3B[10], dJ/dmA, dJ/dM3A[10], dJ/dR[3] (R = XA - XB).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+
+#include "../paper_2412_15518_gb300/csrc/pair_formula.cuh"
+#include "../paper_2412_15518_gb300/csrc/adjoint_pair.cuh"
+
+using namespace otfmm;
+
+static bool rd(double* v, int n) {
+    for (int i = 0; i < n; i++)
+        if (std::scanf("%lf", v + i) != 1) return false;
+    return true;
+}
+
+static void trace3(const double* c, double* t) {
+    t[0] = c[0] + c[3] + c[5];
+    t[1] = c[1] + c[6] + c[8];
+    t[2] = c[2] + c[7] + c[9];
+}
+
+int main() {
+    int am;
+    double G;
+    while (std::scanf("%d %lf", &am, &G) == 2) {
+        double XA[3], XB[3], mA, M3A[10], mB, M2B[6], M3B[10], E0, E1[3], E2[6], E3[10], a[3];
+        if (!(rd(XA, 3) && rd(XB, 3) && rd(&mA, 1) && rd(M3A, 10) && rd(&mB, 1) && rd(M2B, 6) &&
+              rd(M3B, 10) && rd(&E0, 1) && rd(E1, 3) && rd(E2, 6) && rd(E3, 10) && rd(a, 3)))
+            return 1;
+        const double R[3] = {XA[0] - XB[0], XA[1] - XB[1], XA[2] - XB[2]};
+        // forward, as the general kernel assembles it for an interior target
+        Acc<double> A;
+        acc_zero(A);
+        double bt[4];
+        trace3(M3B, bt);
+        bt[3] = M2B[0] + M2B[3] + M2B[5];
+        if (am)
+            m2l_pair<double, true, true, true>(R[0], R[1], R[2], mB, M2B, M3B, bt, A);
+        else
+            m2l_pair<double, true, true, false>(R[0], R[1], R[2], mB, M2B, M3B, bt, A);
+        finish_acc(A);
+        double P[3] = {0.0, 0.0, 0.0};
+        if (am && mA != 0.0) {
+            double a3[10], ta[3];
+            for (int r = 0; r < 10; r++) a3[r] = M3A[r] / mA;
+            trace3(a3, ta);
+            correction_target(A, a3, ta, P);
+        }
+        std::printf("%.17g", -G * A.L0);
+        for (double v : A.L1) std::printf(" %.17g", -G * v);
+        for (double v : A.L2) std::printf(" %.17g", -G * v);
+        for (double v : A.L3) std::printf(" %.17g", -G * v);
+        for (int i = 0; i < 3; i++) std::printf(" %.17g", am ? -(G / 6.0) * (A.S[i] - P[i]) : 0.0);
+        // reverse of the same pair, both roles and the R-gradient
+        PairAdjOut o;
+        adj_zero(o);
+        double gR[3] = {0.0, 0.0, 0.0};
+        m2l_pair_reverse<true, true>(R, G, am, mB, M2B, M3B, true, mA, M3A, true, E0, E1, E2, E3, a, true,
+                                     1.0, gR, o);
+        std::printf(" %.17g", o.mB);
+        for (double v : o.M2B) std::printf(" %.17g", v);
+        for (double v : o.M3B) std::printf(" %.17g", v);
+        std::printf(" %.17g", o.mA);
+        for (double v : o.M3A) std::printf(" %.17g", v);
+        for (double v : gR) std::printf(" %.17g", v);
+        std::printf("\n");
+    }
+    return 0;
+}
