@@ -61,15 +61,30 @@ extern "C" {
 #define OT_ERR_TOO_LARGE -11     /* problem exceeds a fixed-size scratch buffer   */
 
 #define OT_PRECISION_FP64 0      /* every step in FP64                           */
-#define OT_PRECISION_FP32_BULK 1 /* cell-to-cell multipole interactions in FP32,
-                                    FP64 accumulation; FP64 near field (the
-                                    monopole pairs), masses, centres of mass,
-                                    every moment and expansion sum and the
-                                    correction's mass ratio; the products of the
-                                    M2M and L2L shifts (the terms in the offsets)
-                                    in FP32, each widened exactly into an FP64
-                                    sum.  Error vs FP64 <= 1e-6 (relative to the
-                                    field's maximum)                           */
+#define OT_PRECISION_FP32_BULK 1 /* the FP32-bulk form: every pair's monopole part
+                                    (m_B D^(n)(R), the terms that involve the
+                                    source only through its mass, including the
+                                    exact near pairs and every leaf-leaf pair),
+                                    the angular-momentum correction's sums, the
+                                    upward and downward passes and every moment
+                                    and expansion sum in FP64; the contractions
+                                    of the source's quadrupole and octupole with
+                                    the derivative tensors in FP32, summed over
+                                    at most 64 pairs and then added to the FP64
+                                    sums.  Error vs FP64 <= 1e-6 (relative to
+                                    the field's maximum)                       */
+#define OT_PRECISION_FP32_WIDE 2 /* a wider FP32 share than the FP32-bulk form:
+                                    every per-pair multipole term in FP32 (the
+                                    monopole parts, the correction's per-pair
+                                    contractions and the far leaf-leaf pairs
+                                    too), FP64 exact near pairs, masses, centres
+                                    of mass, every moment and expansion sum and
+                                    the correction's mass ratio; the products of
+                                    the M2M and L2L shifts in FP32, each widened
+                                    exactly into an FP64 sum.  Error vs FP64
+                                    <= 1e-6 (relative to the field's maximum);
+                                    conservation of momentum and angular
+                                    momentum to FP32 rounding only            */
 
 typedef struct ot_tree ot_tree; /* opaque, library-owned */
 
@@ -119,32 +134,50 @@ typedef struct {
                                                   launch with the correction (fma = 2) */
     double flops_noam;                         /* the same without the correction    */
     double flops_near;                         /* part of either kept in FP64 by the
-                                                  FP32-bulk form (exact near pairs)  */
+                                                  wide FP32 form (exact near pairs)  */
     int64_t n_work_items;                      /* items of the persistent launch    */
     int32_t tuned_chunk;                       /* stencil entries per work item     */
     int32_t tuned_ctas_per_sm;                 /* persistent CTAs per SM            */
     int32_t tuned_warps_per_cta;
-    int32_t tuned_lattice_ctas_per_sm;         /* FP32-bulk form: persistent CTAs per
+    int32_t tuned_lattice_ctas_per_sm;         /* wide FP32 form: persistent CTAs per
                                                   SM of each lattice kernel (0: one
                                                   CTA per leaf node)                 */
-    int32_t device_status;                     /* latched device error, 0 = none    */
+    int32_t device_status;                     /* latched device error, 0 = none;
+                                                  reading it clears it              */
     int64_t workspace_bytes;                   /* device memory held by the tree    */
+    double flops_bulk64;                       /* FP32-bulk form, one interaction
+                                                  launch with the correction: FP64
+                                                  flops (monopole parts, correction
+                                                  sums, every leaf-leaf pair)        */
+    double flops_bulk32;                       /* ... and its FP32 flops (source
+                                                  quadrupole/octupole contractions) */
+    double flops_adjoint;                      /* FP64 flops of one reverse sweep of
+                                                  the interactions (with the
+                                                  correction), counted like flops_am */
 } ot_tree_stats;
 
 /* Builds the octree, its level tables, neighbour tables, stencils and work
- * lists (host), and uploads them to `device`.  device = -1 validates and
+ * lists (host), and uploads them to `device`.  Defining passage: Sec. 4.3.2
+ * (an adaptive octree whose every node holds an 8x8x8 sub-grid of cells) and
+ * Sec. 5.5 (a fixed stencil of cell-to-cell interactions instead of
+ * interaction lists; structure-of-arrays data).  device = -1 validates and
  * counts on the host only (no CUDA call; solves then fail with
  * OT_ERR_INVALID_ARG).  On success *out owns the workspace until
  * ot_destroy_tree. */
 int ot_build_tree(const ot_tree_desc* desc, int device, ot_tree** out);
 
 /* Upward pass: leaf moments (m = rho h^3 at the cell centre) and exact M2M
- * to every interior cell's centre of mass.  rho: device float64
- * [n_leaf][512].  The moments stay in the tree workspace. */
+ * to every interior cell's centre of mass.  Defining passage: Sec. 4.3.2
+ * (the FMM approximates distant cells through the tree: the multipole
+ * moments of every tree cell).  rho: device float64 [n_leaf][512].  The
+ * moments stay in the tree workspace; ot_get_moments reads them.  FP64. */
 int ot_compute_moments(ot_tree* tree, const double* rho, void* stream);
 
 /* Full solve: moments, every cell-to-cell interaction of every level in one
- * persistent launch, L2L shifts and evaluation.  rho: device float64
+ * persistent launch, L2L shifts and evaluation.  Defining passage: Sec. 2
+ * (FMM self-gravity), Sec. 4.3.1 (linear momentum conserved, angular
+ * momentum through the correction term), Sec. 4.3.2 (octree of 8^3
+ * sub-grids) and Sec. 5.5 (stencil, structure of arrays).  rho: device float64
  * [n_leaf][512]; phi: device float64 [n_leaf][512]; g: device float64
  * [n_leaf][3][512] (component-major per leaf).  opts may be NULL
  * (defaults).  The first solve of a plan captures a CUDA graph that later
@@ -160,7 +193,9 @@ int ot_solve_gravity_host(ot_tree* tree, const double* rho_host, double* phi_hos
 
 /* Adjoint of the solve: drho = dJ/drho for J = sum_c (w1_c phi_c + w2_c . g_c),
  * the exact derivative of the discrete solve (through the centres of mass
- * and the correction's mass ratio), FP64 only (OT_PRECISION_FP64).  w1:
+ * and the correction's mass ratio), FP64 only (OT_PRECISION_FP64).  The paper
+ * differentiates nothing; this is the reverse sweep of the solve that
+ * ot_solve_gravity defines (each step of Sec. 4.3 transposed).  w1:
  * device float64 [n_leaf][512]; w2: device float64 [n_leaf][3][512]; drho:
  * device float64 [n_leaf][512] (overwritten).  Runs the forward solve itself
  * (its outputs go to internal buffers) and then the reverse sweep.  The
@@ -169,7 +204,7 @@ int ot_gravity_backward(ot_tree* tree, const double* rho, const double* w1, cons
                         double* drho, const ot_solve_opts* opts, void* stream);
 
 /* Chooses the persistent launch's stencil-chunk length and the CTAs per SM
- * of the general kernel (and, FP32-bulk form, of the lattice kernels) for
+ * of the general kernel (and, wide FP32 form, of the lattice kernels) for
  * this plan: every candidate is timed as the whole solve graph it would run,
  * on `stream` (synchronised), and the fastest is kept.  rho/phi/g as in
  * ot_solve_gravity (phi and g hold the solve's result afterwards). */
@@ -186,29 +221,69 @@ int ot_autotune(ot_tree* tree, const double* rho, double* phi, double* g,
 int ot_last_solve_times(ot_tree* tree, float* interact_ms, float* solve_ms);
 
 /* Counts of the tree and of the current plan; synchronises the tree's last
- * stream to read the device status word. */
+ * stream to read the device status word, and clears the word after reading
+ * it (an error is reported once; returns OT_ERR_DEVICE_STATUS then, with
+ * the counts and device_status filled in). */
 int ot_tree_info(ot_tree* tree, ot_tree_stats* stats);
 
-/* Allocation-free solve for callers that cannot allocate device memory: code
- * running inside a CUDA stream capture (an allocation there breaks the
- * capture), plug-ins whose host application owns all device memory, and
- * real-time loops that forbid allocation after start-up.  The paper has no
- * counterpart; it is the same solve as ot_solve_gravity (same kernels, same
- * results to rounding) for small trees, without a tree handle: every piece of
- * scratch (node tables, moments, expansions, stencil tables, work items) lives
- * in one fixed 4 MiB device array inside the library, held by every GPU that
- * loads it until the process exits.  desc: host leaf list as for
- * ot_build_tree, at most 9 nodes (the root leaf alone, or the root and its 8
- * leaf children: 4,096 cells); rho, phi, g: device buffers on the CURRENT
- * device, layouts as for ot_solve_gravity; opts as for ot_solve_gravity with
- * 0.5 <= theta <= 1.  Larger trees return OT_ERR_TOO_LARGE.  No device
- * memory is allocated (host-side planning uses the heap).  The first call on
- * each device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture.  All calls share the array
- * and each call clears what must start at zero; calls that overlap on the GPU
- * race, so issue them on one stream or synchronise between them. */
+/* Allocation-free solve for callers that cannot allocate device memory:
+ * plug-ins whose host application owns all device memory and only hands
+ * them buffers, and real-time loops that forbid allocation after start-up
+ * (ot_build_tree allocates the tree workspace, so those callers cannot use
+ * ot_solve_gravity).  The paper has no counterpart; it is the same solve as
+ * ot_solve_gravity (same kernels, same results to rounding) for small trees,
+ * without a tree handle: every piece of scratch (node tables, moments,
+ * expansions, stencil tables, work items) lives in one fixed 4 MiB device
+ * array inside the library, held by every GPU that loads it until the
+ * process exits.  desc: host leaf list as for ot_build_tree, at most 9 nodes
+ * (the root leaf alone, or the root and its 8 leaf children: 4,096 cells);
+ * rho, phi, g: device buffers on the CURRENT device, layouts as for
+ * ot_solve_gravity; opts checked as for ot_solve_gravity, and 0.5 <= theta
+ * <= 1.  Larger trees return OT_ERR_TOO_LARGE.  No device memory is allocated
+ * (host-side planning uses the heap, and the tables are uploaded from it
+ * with cudaMemcpyAsync before the call returns).  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  All calls share the array and
+ * each call clears what must start at zero; calls that overlap on the GPU
+ * race, so issue them on one stream or synchronise between them.  Errors that
+ * a kernel latches in the device status word (a plan error) are not reported
+ * by this entry point: it has no handle to report them through. */
 int ot_solve_gravity_static(const ot_tree_desc* desc, const double* rho, double* phi, double* g,
                             const ot_solve_opts* opts, void* stream);
+
+/* Reads the moments of every cell of level `level` (Sec. 4.3.2: the
+ * multipole moments of the tree cells, as ot_compute_moments or the last
+ * solve left them) in physical units: out, device float64
+ * [n_nodes(level)][20][512] -- per node of the level (in the tree's
+ * breadth-first order of that level) and per component, the 512 cells in
+ * i + 8 j + 64 k order; components m, X (centre of mass, 3), M2 (about X,
+ * packed xx xy xz yy yz zz, 6), M3 (about X, packed xxx xxy xxz xyy xyz xzz
+ * yyy yyz yzz zzz, 10).  node_xyz: optional host int32 [n_nodes(level)][3],
+ * the nodes' coordinates at that level (NULL to skip).  Asynchronous on
+ * `stream` (one conversion kernel); returns OT_ERR_INVALID_ARG for a level
+ * outside the tree. */
+int ot_get_moments(ot_tree* tree, int level, double* out, int32_t* node_xyz, void* stream);
+
+/* Sets the persistent launch's shape without the autotuner (for instance the
+ * shape an earlier ot_autotune chose, read back by ot_tree_info): chunk =
+ * stencil entries per work item (1 <= chunk <= 4096), ctas_per_sm = CTAs of
+ * the general kernel per SM (1..16), lattice_ctas_per_sm = persistent CTAs
+ * per SM of the wide FP32 form's lattice kernels (0 = one per leaf node,
+ * 1..16).  The FP64 and FP32-bulk general kernels take items of any length;
+ * the wide FP32 form stages at most 264 entries of an item: a longer item
+ * is skipped by that kernel and latched in the device status word, which
+ * ot_tree_info reports as OT_ERR_DEVICE_STATUS.  Rebuilds the work items
+ * (host) and re-uploads them; the next solve captures a new graph. */
+int ot_set_launch_shape(ot_tree* tree, int chunk, int ctas_per_sm, int lattice_ctas_per_sm);
+
+/* Measures the CUDA-core arithmetic peaks of `device` with throughput
+ * microkernels (independent FMA chains on every SM, timed with CUDA events
+ * on an internal stream, best of `reps` launches): FP64 FMA, FP32 FMA and
+ * the paired FP32 FMA (two per instruction), in TFLOP/s (an FMA counts 2).
+ * Any output pointer may be NULL.  Allocates and frees a small device
+ * buffer; synchronises the device. */
+int ot_alu_peaks(int device, int reps, double* fp64_tflops, double* fp32_tflops,
+                 double* fp32x2_tflops);
 
 /* Releases the workspace; NULL is ignored. */
 void ot_destroy_tree(ot_tree* tree);

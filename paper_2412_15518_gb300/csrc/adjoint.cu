@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(32) k_l2l_reverse(DevTree t, int first, double
     const double C0 = C[0];
     const double* C1 = C + 1;
     const double* C2 = C + 4;
-    RMono md;
+    RMono<double> md;
     r_mono(d[0], d[1], d[2], md);
     // this child's part of the parent's sums: V[0..19] = E, V[20..22] = a,
     // V[23..25] = the parent's centre-of-mass adjoint; V[26..31] unused

@@ -25,13 +25,14 @@
 
 namespace otfmm {
 
-struct PairAdjOut {
-    double mB, M2B[6], M3B[10];
-    double mA, M3A[10];
-    double R[3];
+template <class T> struct PairAdjOutT {
+    T mB, M2B[6], M3B[10];
+    T mA, M3A[10];
+    T R[3];
 };
+using PairAdjOut = PairAdjOutT<double>;
 
-__host__ __device__ __forceinline__ void adj_zero(PairAdjOut& o) {
+template <class T> __host__ __device__ __forceinline__ void adj_zero(PairAdjOutT<T>& o) {
     o.mB = 0.0;
     o.mA = 0.0;
 #pragma unroll
@@ -46,7 +47,8 @@ __host__ __device__ __forceinline__ void adj_zero(PairAdjOut& o) {
 }
 
 // Symmetric rank-2 (packed xx xy xz yy yz zz) times vector.
-__host__ __device__ __forceinline__ void sym2_vec(const double* S, const double* v, double* o) {
+template <class T>
+__host__ __device__ __forceinline__ void sym2_vec(const T* S, const T* v, T* o) {
     o[0] = S[0] * v[0] + S[1] * v[1] + S[2] * v[2];
     o[1] = S[1] * v[0] + S[3] * v[1] + S[4] * v[2];
     o[2] = S[2] * v[0] + S[4] * v[1] + S[5] * v[2];
@@ -55,22 +57,25 @@ __host__ __device__ __forceinline__ void sym2_vec(const double* S, const double*
 // o_i = T_ijk P_jk for a packed symmetric rank-3 T (xxx xxy xxz xyy xyz xzz
 // yyy yyz yzz zzz) and a symmetric P given as (P_xx, P_yy, P_zz, 2 P_xy,
 // 2 P_xz, 2 P_yz): with P = R R this is T : R R.
-__host__ __device__ __forceinline__ void sym3_contract(const double* c, double pxx, double pyy,
-                                                       double pzz, double pxy2, double pxz2,
-                                                       double pyz2, double* o) {
+template <class T>
+__host__ __device__ __forceinline__ void sym3_contract(const T* c, T pxx, T pyy,
+                                                       T pzz, T pxy2, T pxz2,
+                                                       T pyz2, T* o) {
     o[0] = c[0] * pxx + c[3] * pyy + c[5] * pzz + c[1] * pxy2 + c[2] * pxz2 + c[4] * pyz2;
     o[1] = c[1] * pxx + c[6] * pyy + c[8] * pzz + c[3] * pxy2 + c[4] * pxz2 + c[7] * pyz2;
     o[2] = c[2] * pxx + c[7] * pyy + c[9] * pzz + c[4] * pxy2 + c[5] * pxz2 + c[8] * pyz2;
 }
 
 // Symmetric rank-3 (packed) contracted twice with R: q2_i = T_ijk R_j R_k.
-__host__ __device__ __forceinline__ void sym3_rr(const double* c, const double* R, double* q) {
-    const double x = R[0], y = R[1], z = R[2];
+template <class T>
+__host__ __device__ __forceinline__ void sym3_rr(const T* c, const T* R, T* q) {
+    const T x = R[0], y = R[1], z = R[2];
     sym3_contract(c, x * x, y * y, z * z, 2 * x * y, 2 * x * z, 2 * y * z, q);
 }
 
 // (T d)_n = T_uvl d_l for a packed symmetric rank-3 T: a packed rank-2 result.
-__host__ __device__ __forceinline__ void sym3_vec(const double* c, const double* d, double* o) {
+template <class T>
+__host__ __device__ __forceinline__ void sym3_vec(const T* c, const T* d, T* o) {
     o[0] = c[0] * d[0] + c[1] * d[1] + c[2] * d[2];
     o[1] = c[1] * d[0] + c[3] * d[1] + c[4] * d[2];
     o[2] = c[2] * d[0] + c[4] * d[1] + c[5] * d[2];
@@ -79,7 +84,8 @@ __host__ __device__ __forceinline__ void sym3_vec(const double* c, const double*
     o[5] = c[5] * d[0] + c[8] * d[1] + c[9] * d[2];
 }
 
-__host__ __device__ __forceinline__ void sym3_trace(const double* c, double* t) {
+template <class T>
+__host__ __device__ __forceinline__ void sym3_trace(const T* c, T* t) {
     t[0] = c[0] + c[3] + c[5];
     t[1] = c[1] + c[6] + c[8];
     t[2] = c[2] + c[7] + c[9];
@@ -87,19 +93,20 @@ __host__ __device__ __forceinline__ void sym3_trace(const double* c, double* t) 
 
 // The pieces of a . (D4 : T) for a symmetric rank-3 T: q2 = T:RR, q3 = R.q2,
 // t_i = T_ijj, Rt = R.t.
-struct S4Parts {
-    double q2[3], q3, t[3], Rt;
+template <class T> struct S4Parts {
+    T q2[3], q3, t[3], Rt;
 };
 
 // Shared monomials of R.
-struct RMono {
-    double x, y, z;
-    double xx, xy, xz, yy, yz, zz;   // R R
-    double xy2, xz2, yz2;            // doubled cross products
-    double rrr[10];                  // R R R, packed
+template <class T> struct RMono {
+    T x, y, z;
+    T xx, xy, xz, yy, yz, zz;   // R R
+    T xy2, xz2, yz2;            // doubled cross products
+    T rrr[10];                  // R R R, packed
 };
 
-__host__ __device__ __forceinline__ void r_mono(double x, double y, double z, RMono& m) {
+template <class T>
+__host__ __device__ __forceinline__ void r_mono(T x, T y, T z, RMono<T>& m) {
     m.x = x; m.y = y; m.z = z;
     m.xx = x * x; m.xy = x * y; m.xz = x * z; m.yy = y * y; m.yz = y * z; m.zz = z * z;
     m.xy2 = m.xy + m.xy; m.xz2 = m.xz + m.xz; m.yz2 = m.yz + m.yz;
@@ -108,10 +115,11 @@ __host__ __device__ __forceinline__ void r_mono(double x, double y, double z, RM
     m.rrr[8] = m.zz * y; m.rrr[9] = m.zz * z;
 }
 
-__host__ __device__ __forceinline__ void s4_parts(const double* T, const RMono& m, S4Parts& s) {
-    sym3_contract(T, m.xx, m.yy, m.zz, m.xy2, m.xz2, m.yz2, s.q2);
+template <class T>
+__host__ __device__ __forceinline__ void s4_parts(const T* Tm, const RMono<T>& m, S4Parts<T>& s) {
+    sym3_contract(Tm, m.xx, m.yy, m.zz, m.xy2, m.xz2, m.yz2, s.q2);
     s.q3 = m.x * s.q2[0] + m.y * s.q2[1] + m.z * s.q2[2];
-    sym3_trace(T, s.t);
+    sym3_trace(Tm, s.t);
     s.Rt = m.x * s.t[0] + m.y * s.t[1] + m.z * s.t[2];
 }
 
@@ -120,10 +128,11 @@ __host__ __device__ __forceinline__ void s4_parts(const double* T, const RMono& 
 // (dR)_jkl = d_jk R_l + d_jl R_k + d_kl R_j and (da) likewise with a.  With
 // c4 = f4 aR, c3 = f3, c3r = f3 aR, c2 = f2 this adds a . D4; with c3 = c2 =
 // 0, c4 = f3, c3r = f2 it adds D3.
-__host__ __device__ __forceinline__ void add_rank3(double* o, const RMono& m, const double* a,
-                                                   double c4, double c3, double c3r, double c2) {
-    const double ax = a[0], ay = a[1], az = a[2];
-    const double x = m.x, y = m.y, z = m.z;
+template <class T>
+__host__ __device__ __forceinline__ void add_rank3(T* o, const RMono<T>& m, const T* a,
+                                                   T c4, T c3, T c3r, T c2) {
+    const T ax = a[0], ay = a[1], az = a[2];
+    const T x = m.x, y = m.y, z = m.z;
     o[0] += c4 * m.rrr[0] + c3 * (3.0 * ax * m.xx) + c3r * (3.0 * x) + c2 * (3.0 * ax);
     o[1] += c4 * m.rrr[1] + c3 * (2.0 * ax * m.xy + ay * m.xx) + c3r * y + c2 * ay;
     o[2] += c4 * m.rrr[2] + c3 * (2.0 * ax * m.xz + az * m.xx) + c3r * z + c2 * az;
@@ -147,46 +156,46 @@ inline double rsqrt_adj(double a) { return 1.0 / sqrt(a); }
 // target-side mass-ratio adjoints (interior targets only).  want_R: dJ/dR,
 // added to gR times sR (+1 for the target's centre of mass, -1 for the
 // source's).
-template <bool SRC, bool TGT>
+template <bool SRC, bool TGT, class T>
 __host__ __device__ __forceinline__ void m2l_pair_reverse(
-    const double* Rv, double G, int am,
-    double mB, const double* M2B, const double* M3B, bool multiB,   // source moments
-    double mA, const double* M3A, bool multiA,                      // target moments (ratio)
-    double E0, const double* E1, const double* E2, const double* E3, const double* ac,
-    bool want_R, double sR, double* gR, PairAdjOut& out) {
-    RMono m;
+    const T* Rv, T G, int am,
+    T mB, const T* M2B, const T* M3B, bool multiB,   // source moments
+    T mA, const T* M3A, bool multiA,                      // target moments (ratio)
+    T E0, const T* E1, const T* E2, const T* E3, const T* ac,
+    bool want_R, T sR, T* gR, PairAdjOutT<T>& out) {
+    RMono<T> m;
     r_mono(Rv[0], Rv[1], Rv[2], m);
-    const double x = m.x, y = m.y, z = m.z;
-    const double R[3] = {x, y, z};
-    const double f0 = rsqrt_adj(m.xx + m.yy + m.zz);
-    const double ri2 = f0 * f0;
-    const double f1 = -f0 * ri2;
-    const double f2 = -3.0 * f1 * ri2;
-    const double f3 = -5.0 * f2 * ri2;
-    const double f4 = -7.0 * f3 * ri2;
-    const double f5 = -9.0 * f4 * ri2;
-    const double k6 = G / 6.0;
+    const T x = m.x, y = m.y, z = m.z;
+    const T R[3] = {x, y, z};
+    const T f0 = rsqrt_adj(m.xx + m.yy + m.zz);
+    const T ri2 = f0 * f0;
+    const T f1 = -f0 * ri2;
+    const T f2 = -3.0 * f1 * ri2;
+    const T f3 = -5.0 * f2 * ri2;
+    const T f4 = -7.0 * f3 * ri2;
+    const T f5 = -9.0 * f4 * ri2;
+    const T k6 = G / 6.0;
     // the target's M3 enters only through the correction's mass-ratio term,
     // which is taken as zero (and has no derivative) for a target of zero mass
     const bool useA = am && multiA && mA != 0.0;
-    const double iA = useA ? 1.0 / mA : 0.0;
-    const double ratio = mB * iA;
-    const double zero3[3] = {0.0, 0.0, 0.0};
-    const double* a = am ? ac : zero3;
-    const double aR = a[0] * x + a[1] * y + a[2] * z;
+    const T iA = useA ? 1.0 / mA : 0.0;
+    const T ratio = mB * iA;
+    const T zero3[3] = {0.0, 0.0, 0.0};
+    const T* a = am ? ac : zero3;
+    const T aR = a[0] * x + a[1] * y + a[2] * z;
 
     // contractions of the adjoints with R
-    const double E1R = E1[0] * x + E1[1] * y + E1[2] * z;
-    double E2R[3];
+    const T E1R = E1[0] * x + E1[1] * y + E1[2] * z;
+    T E2R[3];
     sym2_vec(E2, R, E2R);
-    const double RE2R = E2R[0] * x + E2R[1] * y + E2R[2] * z;
-    const double trE2 = E2[0] + E2[3] + E2[5];
-    S4Parts e3;
+    const T RE2R = E2R[0] * x + E2R[1] * y + E2R[2] * z;
+    const T trE2 = E2[0] + E2[3] + E2[5];
+    S4Parts<T> e3;
     s4_parts(E3, m, e3);
     // s4a = a . (D4 : M3_A) (the ratio part of the correction)
-    double s4a = 0.0;
+    T s4a = 0.0;
     if (useA) {
-        S4Parts qa;
+        S4Parts<T> qa;
         s4_parts(M3A, m, qa);
         s4a = f4 * aR * qa.q3 + 3.0 * f3 * (a[0] * qa.q2[0] + a[1] * qa.q2[1] + a[2] * qa.q2[2] + aR * qa.Rt) +
               3.0 * f2 * (a[0] * qa.t[0] + a[1] * qa.t[1] + a[2] * qa.t[2]);
@@ -194,13 +203,13 @@ __host__ __device__ __forceinline__ void m2l_pair_reverse(
 
     if (SRC) {
         // dJ/dm_B
-        const double v = E0 * f0 + f1 * (E1R + trE2) + f2 * RE2R + f3 * e3.q3 + 3.0 * f2 * e3.Rt;
+        const T v = E0 * f0 + f1 * (E1R + trE2) + f2 * RE2R + f3 * e3.q3 + 3.0 * f2 * e3.Rt;
         out.mB += -G * v + k6 * iA * s4a;
         if (multiB) {
             // dJ/dM2_B = -G [E0 D2 / 2 + (E1 . D3) / 2]
-            const double c2 = -0.5 * G * (E0 * f2 + f3 * E1R);
-            const double c1 = -0.5 * G * (E0 * f1 + f2 * E1R);
-            const double c3 = -0.5 * G * f2;
+            const T c2 = -0.5 * G * (E0 * f2 + f3 * E1R);
+            const T c1 = -0.5 * G * (E0 * f1 + f2 * E1R);
+            const T c3 = -0.5 * G * f2;
             out.M2B[0] += c2 * m.xx + c1 + c3 * (2.0 * E1[0] * x);
             out.M2B[1] += c2 * m.xy + c3 * (E1[0] * y + E1[1] * x);
             out.M2B[2] += c2 * m.xz + c3 * (E1[0] * z + E1[2] * x);
@@ -214,32 +223,32 @@ __host__ __device__ __forceinline__ void m2l_pair_reverse(
     }
     if (TGT && useA) {
         // the ratio term -(m_B / m_A) M3_A: dJ/dM3_A and dJ/dm_A
-        const double kr = k6 * ratio;
+        const T kr = k6 * ratio;
         add_rank3(out.M3A, m, a, kr * f4 * aR, kr * f3, kr * f3 * aR, kr * f2);
         out.mA += -k6 * s4a * mB * iA * iA;
     }
     if (want_R) {
         // mB E0 D0 + mB E1.D1 + mB E2:D2 + mB E3:D3
-        const double cR = mB * (E0 * f1 + f2 * (E1R + trE2) + f3 * RE2R + f4 * e3.q3 + 3.0 * f3 * e3.Rt);
-        double g[3];
+        const T cR = mB * (E0 * f1 + f2 * (E1R + trE2) + f3 * RE2R + f4 * e3.q3 + 3.0 * f3 * e3.Rt);
+        T g[3];
 #pragma unroll
         for (int p = 0; p < 3; p++)
             g[p] = cR * R[p] + mB * (f1 * E1[p] + 2.0 * f2 * E2R[p] + 3.0 * f3 * e3.q2[p] + 3.0 * f2 * e3.t[p]);
         if (multiB) {
             // E0 M2:D2 / 2 - E0 M3:D3 / 6 + E1 . (D3 : M2) / 2
-            double MR[3], ME1[3];
+            T MR[3], ME1[3];
             sym2_vec(M2B, R, MR);
             sym2_vec(M2B, E1, ME1);
-            const double xMx = MR[0] * x + MR[1] * y + MR[2] * z;
-            const double trM = M2B[0] + M2B[3] + M2B[5];
-            const double E1MR = E1[0] * MR[0] + E1[1] * MR[1] + E1[2] * MR[2];
-            S4Parts m3;
+            const T xMx = MR[0] * x + MR[1] * y + MR[2] * z;
+            const T trM = M2B[0] + M2B[3] + M2B[5];
+            const T E1MR = E1[0] * MR[0] + E1[1] * MR[1] + E1[2] * MR[2];
+            S4Parts<T> m3;
             s4_parts(M3B, m, m3);
-            const double cr = 0.5 * E0 * (f3 * xMx + f2 * trM) - (1.0 / 6.0) * E0 * f4 * m3.q3 -
+            const T cr = 0.5 * E0 * (f3 * xMx + f2 * trM) - (1.0 / 6.0) * E0 * f4 * m3.q3 -
                               0.5 * E0 * f3 * m3.Rt + 0.5 * f4 * E1R * xMx + 0.5 * f3 * (2.0 * E1MR + E1R * trM);
-            const double cmr = E0 * f2 + f3 * E1R;
-            const double cq2 = -0.5 * E0 * f3, ct = -0.5 * E0 * f2;
-            const double ce1 = 0.5 * (f3 * xMx + f2 * trM);
+            const T cmr = E0 * f2 + f3 * E1R;
+            const T cq2 = -0.5 * E0 * f3, ct = -0.5 * E0 * f2;
+            const T ce1 = 0.5 * (f3 * xMx + f2 * trM);
 #pragma unroll
             for (int p = 0; p < 3; p++)
                 g[p] += cr * R[p] + cmr * MR[p] + cq2 * m3.q2[p] + ct * m3.t[p] + ce1 * E1[p] + f2 * ME1[p];
@@ -248,18 +257,18 @@ __host__ __device__ __forceinline__ void m2l_pair_reverse(
         for (int p = 0; p < 3; p++) gR[p] += -sR * G * g[p];
         if (am && (multiB || useA)) {
             // a . (D4 : Q), Q = M3_B - ratio M3_A
-            double Q[10];
+            T Q[10];
 #pragma unroll
             for (int n = 0; n < 10; n++) Q[n] = (multiB ? M3B[n] : 0.0) - (useA ? ratio * M3A[n] : 0.0);
-            S4Parts q;
+            S4Parts<T> q;
             s4_parts(Q, m, q);
-            double u[3];  // u_p = Q_pik a_i R_k
+            T u[3];  // u_p = Q_pik a_i R_k
             sym3_contract(Q, a[0] * x, a[1] * y, a[2] * z, a[0] * y + a[1] * x, a[0] * z + a[2] * x,
                           a[1] * z + a[2] * y, u);
-            const double aq2 = a[0] * q.q2[0] + a[1] * q.q2[1] + a[2] * q.q2[2];
-            const double at = a[0] * q.t[0] + a[1] * q.t[1] + a[2] * q.t[2];
-            const double cv = f5 * aR * q.q3 + 3.0 * f4 * aq2 + 3.0 * f4 * aR * q.Rt + 3.0 * f3 * at;
-            const double ca = f4 * q.q3 + 3.0 * f3 * q.Rt;
+            const T aq2 = a[0] * q.q2[0] + a[1] * q.q2[1] + a[2] * q.q2[2];
+            const T at = a[0] * q.t[0] + a[1] * q.t[1] + a[2] * q.t[2];
+            const T cv = f5 * aR * q.q3 + 3.0 * f4 * aq2 + 3.0 * f4 * aR * q.Rt + 3.0 * f3 * at;
+            const T ca = f4 * q.q3 + 3.0 * f3 * q.Rt;
 #pragma unroll
             for (int p = 0; p < 3; p++)
                 gR[p] += -sR * k6 * (cv * R[p] + ca * a[p] + 3.0 * f4 * aR * q.q2[p] + 6.0 * f3 * u[p] +

@@ -142,6 +142,7 @@ DevTree dev_tree(const ot_tree* t) {
     d.n_leaf = t->h.n_leaf;
     d.n_cells = (long long)t->h.n_nodes() * kCells;
     d.size = t->h.size;
+    for (int a = 0; a < 3; a++) d.origin[a] = t->h.origin[a];
     d.node_level = t->d_level;
     d.node_leaf = t->d_leaf;
     d.node_parent = t->d_parent;
@@ -261,23 +262,8 @@ int ensure_plan(ot_tree* t, double theta) {
     return OT_OK;
 }
 
-void fill_opts(const ot_solve_opts* o, ot_solve_opts& out) {
-    out.theta = 0.5;
-    out.G = 1.0;
-    out.precision = OT_PRECISION_FP64;
-    out.am_correction = 1;
-    out.self_term = 0;
-    out.reserved = 0;
-    if (o) out = *o;
-}
-
-int check_opts(const ot_solve_opts& o) {
-    if (!(o.theta >= 0.3 && o.theta <= 1.0)) return OT_ERR_INVALID_ARG;
-    if (o.precision != OT_PRECISION_FP64 && o.precision != OT_PRECISION_FP32_BULK)
-        return OT_ERR_INVALID_ARG;
-    if (!(o.G == o.G)) return OT_ERR_INVALID_ARG;
-    return OT_OK;
-}
+void fill_opts(const ot_solve_opts* o, ot_solve_opts& out) { default_solve_opts(o, out); }
+int check_opts(const ot_solve_opts& o) { return check_solve_opts(o); }
 
 int check_dev_ptr(const ot_tree* t, const void* p) {
     if (!p) return OT_ERR_BAD_POINTER;
@@ -314,9 +300,10 @@ void enqueue_moments(ot_tree* t, const double* rho, int precision, cudaStream_t 
 // expansions (both set by the leaf-moment kernel; no M2M kernel touches
 // them), so they may be forked before the M2M chain.  In the bulk form the
 // near-pair lattice kernel is FP64 work and the other two FP32 work, and the
-// pipes overlap.
+// pipes overlap.  (The FP64 and FP32-bulk forms run every leaf-leaf pair in
+// FP64, in one lattice kernel.)
 int fork_lattice(ot_tree* t, const ot_solve_opts& o, cudaStream_t s) {
-    const bool bulk = o.precision == OT_PRECISION_FP32_BULK;
+    const bool bulk = o.precision == OT_PRECISION_FP32_WIDE;
     // work counters: [0] general kernel, [1] near (or all) lattice, [2] far lattice
     TRYC(cudaMemsetAsync(t->d_counter, 0, 4 * sizeof(int), s));
     TRYC(cudaEventRecord(t->ev_fork, s));
@@ -338,7 +325,7 @@ void launch_general(ot_tree* t, const ot_solve_opts& o, cudaStream_t s) {
 }
 int join_lattice(ot_tree* t, const ot_solve_opts& o, cudaStream_t s) {
     TRYC(cudaStreamWaitEvent(s, t->ev_join, 0));
-    if (o.precision == OT_PRECISION_FP32_BULK) TRYC(cudaStreamWaitEvent(s, t->ev_join_far, 0));
+    if (o.precision == OT_PRECISION_FP32_WIDE) TRYC(cudaStreamWaitEvent(s, t->ev_join_far, 0));
     TRYC(cudaGetLastError());
     return OT_OK;
 }
@@ -645,10 +632,11 @@ int ot_autotune(ot_tree* t, const double* rho, double* phi, double* g, const ot_
     cudaEvent_t e0, e1;
     TRYC(cudaEventCreate(&e0));
     TRYC(cudaEventCreate(&e1));
-    const bool bulk = o.precision == OT_PRECISION_FP32_BULK;
-    // the FP32-bulk form flushes its FP32 partial sums every 64 pairs anyway
-    // (their rounding error grows with the summation length), so longer
-    // items buy it nothing
+    // the wide FP32 form stages at most 264 entries per item and flushes
+    // its FP32 partial sums every 64 pairs anyway (their rounding error
+    // grows with the summation length), so longer items buy it nothing;
+    // the FP64 and FP32-bulk forms are FP64-pipe bound and tune like each other
+    const bool bulk = o.precision == OT_PRECISION_FP32_WIDE;
     const int chunks_fp64[] = {32, 64, 128, 263};
     const int chunks_bulk[] = {32, 64};
     const int* chunks = bulk ? chunks_bulk : chunks_fp64;
@@ -725,6 +713,42 @@ int ot_last_solve_times(ot_tree* t, float* interact_ms, float* solve_ms) {
     return OT_OK;
 }
 
+int ot_get_moments(ot_tree* t, int level, double* out, int32_t* node_xyz, void* stream) {
+    if (!t) return OT_ERR_BAD_POINTER;
+    if (t->device < 0) return OT_ERR_INVALID_ARG;
+    const HostTree& h = t->h;
+    if (level < 0 || level >= h.n_levels) return OT_ERR_INVALID_ARG;
+    DeviceGuard guard(t->device);
+    TRY(check_dev_ptr(t, out));
+    const int first = h.level_first[level], count = h.level_first[level + 1] - first;
+    if (node_xyz)
+        for (int v = 0; v < count; v++)
+            for (int a = 0; a < 3; a++) node_xyz[3 * v + a] = h.node_xyz[3 * (first + v) + a];
+    cudaStream_t s = (cudaStream_t)stream;
+    launch_get_moments(dev_tree(t), first, count, out, s);
+    TRYC(cudaGetLastError());
+    t->last_stream = s;
+    return OT_OK;
+}
+
+int ot_set_launch_shape(ot_tree* t, int chunk, int ctas_per_sm, int lattice_ctas_per_sm) {
+    if (!t) return OT_ERR_BAD_POINTER;
+    if (chunk < 1 || chunk > 4096 || ctas_per_sm < 1 || ctas_per_sm > 16 || lattice_ctas_per_sm < 0 ||
+        lattice_ctas_per_sm > 16)
+        return OT_ERR_INVALID_ARG;
+    t->chunk = chunk;
+    t->ctas_per_sm = ctas_per_sm;
+    t->lattice_ctas_per_sm = lattice_ctas_per_sm;
+    t->tuned = true;
+    if (t->device < 0) {
+        build_items(t->h, chunk, t->plan);
+        return OT_OK;
+    }
+    DeviceGuard guard(t->device);
+    destroy_graphs(t);
+    return ensure_plan(t, t->plan.theta);
+}
+
 int ot_tree_info(ot_tree* t, ot_tree_stats* st) {
     if (!t || !st) return OT_ERR_BAD_POINTER;
     std::memset(st, 0, sizeof(*st));
@@ -747,6 +771,9 @@ int ot_tree_info(ot_tree* t, ot_tree_stats* st) {
     st->flops_am = t->plan.flops_am;
     st->flops_noam = t->plan.flops_noam;
     st->flops_near = t->plan.flops_near;
+    st->flops_bulk64 = t->plan.flops_bulk64;
+    st->flops_bulk32 = t->plan.flops_bulk32;
+    st->flops_adjoint = t->plan.flops_adjoint;
     st->n_work_items = (int64_t)t->plan.items.size();
     st->tuned_chunk = t->chunk;
     st->tuned_ctas_per_sm = t->ctas_per_sm;
@@ -762,7 +789,14 @@ int ot_tree_info(ot_tree* t, ot_tree_stats* st) {
             return OT_ERR_CUDA;
         }
         st->device_status = status;
-        if (status) return OT_ERR_DEVICE_STATUS;
+        if (status) {
+            // reported once: cleared for the solves that follow
+            if (cudaMemset(t->d_status, 0, sizeof(int)) != cudaSuccess) {
+                cudaGetLastError();
+                return OT_ERR_CUDA;
+            }
+            return OT_ERR_DEVICE_STATUS;
+        }
     }
     return OT_OK;
 }

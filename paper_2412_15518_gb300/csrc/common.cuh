@@ -35,6 +35,14 @@ constexpr int kLoc = 23;         // expansion components per cell (+ correction)
 constexpr int kOct = 16;         // per-cell FP32 octupole record: M3 / m (10), trace vector (3), pad
 constexpr int kMaxLevels = 16;   // levels 0..15
 
+// Precision forms (the OT_PRECISION_* codes of the C ABI): every step in
+// FP64; the FP32-bulk form (monopole parts, correction and every sum in FP64,
+// the source multipole contractions in FP32); the wide FP32 form (every
+// per-pair multipole term in FP32, FP64 near pairs and sums).
+constexpr int kPrecFP64 = 0;
+constexpr int kPrecBulk = 1;
+constexpr int kPrecWide = 2;
+
 // Status word codes latched by kernels (never trapped).
 constexpr int kStatusBadIndex = 1;
 constexpr int kStatusBadItem = 2;
@@ -46,6 +54,7 @@ struct DevTree {
     int n_leaf;
     long long n_cells;          // n_nodes * 512
     double size;
+    double origin[3];           // corner of the domain cube
     const int* node_level;      // [n_nodes]
     const int* node_leaf;       // [n_nodes] leaf id or -1
     const int* node_parent;     // [n_nodes] or -1

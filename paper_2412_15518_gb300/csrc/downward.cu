@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(64) k_l2l_leafkids_bulk(DevTree t, int first,
 void launch_l2l(const DevTree& t, int kinds, int first, int count, const double* rho,
                 double* phi, double* g, double G, int self_term, int precision, cudaStream_t s) {
     if (count <= 0) return;
-    const bool bulk = precision == 1;
+    const bool bulk = precision == kPrecWide;  // the FP32-bulk form keeps L2L in FP64
     if (kinds & 1) {
         if (bulk) k_l2l<true><<<count * 16, 32, 0, s>>>(t, first, rho, phi, g, G, self_term);
         else k_l2l<false><<<count * 16, 32, 0, s>>>(t, first, rho, phi, g, G, self_term);

@@ -1,7 +1,9 @@
 // Algorithmic flop counts of one pair interaction of each class, taken from
-// the very template the kernels execute (pair_formula.cuh) instantiated with
-// a counting scalar: +, -, * and rsqrt count 1, fma counts 2, sign changes
-// and constants count 0.
+// the very templates the kernels execute (pair_formula.cuh) instantiated with
+// counting scalars: +, -, * and rsqrt count 1, fma counts 2, sign changes,
+// constants and the exact FP32 -> FP64 widening (integer operations) count
+// 0.  The split pair of the FP32-bulk form is counted with two scalars, one
+// per precision.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -24,9 +26,39 @@ inline CountT operator-(CountT) { return CountT(); }
 inline CountT& operator+=(CountT& a, CountT) { g_flops += 1; return a; }
 inline CountT fma_(CountT, CountT, CountT) { g_flops += 2; return CountT(); }
 inline CountT rsqrt_(CountT) { g_flops += 1; return CountT(); }
+inline CountT rsqrt_adj(CountT) { g_flops += 1; return CountT(); }
+inline CountT operator/(CountT, CountT) { g_flops += 1; return CountT(); }
+inline bool operator!=(CountT, CountT) { return true; }  // a target mass is non-zero
+
+// The split pair: D counts into g_flops64, F into g_flops32.
+static long long g_flops64 = 0, g_flops32 = 0;
+struct CountD {
+    CountD() {}
+    CountD(double) {}
+};
+struct CountF {
+    CountF() {}
+    CountF(double) {}
+};
+inline CountD operator+(CountD, CountD) { g_flops64 += 1; return CountD(); }
+inline CountD operator-(CountD, CountD) { g_flops64 += 1; return CountD(); }
+inline CountD operator*(CountD, CountD) { g_flops64 += 1; return CountD(); }
+inline CountD operator-(CountD) { return CountD(); }
+inline CountD& operator+=(CountD& a, CountD) { g_flops64 += 1; return a; }
+inline CountD fma_(CountD, CountD, CountD) { g_flops64 += 2; return CountD(); }
+inline CountD rsqrt_(CountD) { g_flops64 += 1; return CountD(); }
+inline CountF operator+(CountF, CountF) { g_flops32 += 1; return CountF(); }
+inline CountF operator-(CountF, CountF) { g_flops32 += 1; return CountF(); }
+inline CountF operator*(CountF, CountF) { g_flops32 += 1; return CountF(); }
+inline CountF operator-(CountF) { return CountF(); }
+inline CountF& operator+=(CountF& a, CountF) { g_flops32 += 1; return a; }
+inline CountF fma_(CountF, CountF, CountF) { g_flops32 += 2; return CountF(); }
+inline CountF rsqrt_(CountF) { g_flops32 += 1; return CountF(); }
+inline CountD to_d(CountF) { return CountD(); }
 
 }  // namespace otfmm
 
+#include "adjoint_pair.cuh"
 #include "pair_formula.cuh"
 
 namespace otfmm {
@@ -40,6 +72,52 @@ template <bool FULL, bool MULTI, bool AM> static double count_pair() {
     g_flops += 6;
     m2l_pair<CountT, FULL, MULTI, AM>(x, y, z, m, b2, b3, bt, A);
     return (double)g_flops;
+}
+
+template <bool FULL, bool MULTI> static void count_split(double& f64, double& f32) {
+    g_flops64 = g_flops32 = 0;
+    CountF b2[6], b3[10], bt[4];
+    SplitAcc<CountD, CountF> A;
+    CountD x, y, z, m;
+    CountF xf, yf, zf;
+    // R' = (dX_A - dX_B) - d in each precision: 2 flops per component each
+    // (the FP32 copy only for a multipole source)
+    g_flops64 += 6;
+    if (MULTI) g_flops32 += 6;
+    m2l_pair_split<CountD, CountF, FULL, MULTI, true>(x, y, z, m, xf, yf, zf, b2, b3, bt, A);
+    f64 = (double)g_flops64;
+    f32 = (double)g_flops32;
+}
+
+void pair_flops_split(double f64[PairClasses], double f32[PairClasses]) {
+    // every leaf-leaf pair is an FP64 lattice pair: 4 fma
+    f64[kLatticeFar] = f64[kNearP2P] = 8.0;
+    f32[kLatticeFar] = f32[kNearP2P] = 0.0;
+    count_split<false, true>(f64[kM2P], f32[kM2P]);
+    count_split<true, false>(f64[kP2M], f32[kP2M]);
+    count_split<true, true>(f64[kMM], f32[kMM]);
+}
+
+// The reverse of one directed pair, as the adjoint kernel runs it (with the
+// correction): a pair with a leaf target in its interior source's pass
+// (source adjoints and the R-gradient), a pair with an interior target whole
+// in the target's pass; R formed from the offsets and the centres (9 flops).
+template <bool SRC, bool TGT> static double count_reverse(bool multiB, bool multiA) {
+    g_flops = 0;
+    CountT R[3], M2B[6], M3B[10], M3A[10], E1[3], E2[6], E3[10], ac[3], gR[3];
+    CountT G, mB, mA, E0, sR;
+    PairAdjOutT<CountT> o;
+    m2l_pair_reverse<SRC, TGT>(R, G, 1, mB, M2B, M3B, multiB, mA, M3A, multiA, E0, E1, E2, E3, ac, true,
+                               sR, gR, o);
+    return (double)g_flops + 9.0;
+}
+
+void pair_flops_adjoint(double out[PairClasses]) {
+    // leaf-leaf pairs: the lattice table transposed, 4 fma
+    out[kLatticeFar] = out[kNearP2P] = 8.0;
+    out[kM2P] = count_reverse<true, false>(true, false);
+    out[kP2M] = count_reverse<true, true>(false, true);
+    out[kMM] = count_reverse<true, true>(true, true);
 }
 
 void pair_flops(double out[PairClasses][2]) {

@@ -378,6 +378,162 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
     flush();
 }
 
+// FP32-bulk form: one item with the pair split by precision (m2l_pair_split):
+// the monopole part of every pair and the correction's sums in FP64, the
+// source's quadrupole and octupole contractions in FP32 (partial sums of at
+// most kFlush32 pairs, then added to the FP64 sums).  Leaf-leaf pairs of a
+// leaf root are monopole pairs: FP64 from the lattice table.
+template <bool FULL, bool AM>
+__device__ __forceinline__ void run_item_split(const DevTree& t, const DevPlan& p, const int4 it,
+                                               const int lane, const int* s_nb, const int* s_lf,
+                                               const LevelScales& sc) {
+    const int node = it.x;
+    const int L = item_level(it), par = item_parity(it), half = item_half(it);
+    const int i = 2 * (lane & 3) + (par & 1);
+    const int j = 2 * ((lane >> 2) & 3) + ((par >> 1) & 1);
+    const int k = 2 * (2 * half + (lane >> 4)) + (par >> 2);
+    const long long N = t.n_cells;
+    const long long cell = (long long)node * kCells + i + 8 * j + 64 * k;
+    double ma, dax, day, daz;
+    load_head(t, cell, ma, dax, day, daz);
+    float maf, daxf, dayf, dazf;
+    load_head(t, cell, maf, daxf, dayf, dazf);
+    SplitAcc<double, float> A;
+    split_zero(A);
+    int since = 0;  // pairs summed in the FP32 partial sums
+    auto pair = [&](double x, double y, double z, double m, float xf, float yf, float zf,
+                    long long src, bool sleaf) {
+        if (sleaf) {
+            m2l_pair_split<double, float, FULL, false, AM>(x, y, z, m, 0.f, 0.f, 0.f, nullptr, nullptr,
+                                                           nullptr, A);
+        } else {
+            float b2[6], b3[10], bt[4];
+            load_tail(t, src, b2, b3, bt);
+            m2l_pair_split<double, float, FULL, true, AM>(x, y, z, m, xf, yf, zf, b2, b3, bt, A);
+            if (++since == kFlush32) {
+                flush_split(A);
+                since = 0;
+            }
+        }
+    };
+    if (FULL && item_list(it) == kRootList) {
+        // the interior root: sources are the root's own cells [z, w)
+        const int root = it.x;
+#pragma unroll 1
+        for (int s = it.z; s < it.w; s++) {
+            const int sx = s & 7, sy = (s >> 3) & 7, sz = s >> 6;
+            const int dx = sx - i, dy = sy - j, dz = sz - k;
+            if (dx * dx + dy * dy + dz * dz <= p.near_d2) continue;
+            const long long src = (long long)root * kCells + s;
+            double m, bx, by, bz;
+            load_head(t, src, m, bx, by, bz);
+            float mf, bxf, byf, bzf;
+            load_head(t, src, mf, bxf, byf, bzf);
+            // R' = (t + dX_A) - (s + dX_B) in cell units
+            const double x = (dax - bx) - (double)dx, y = (day - by) - (double)dy, z = (daz - bz) - (double)dz;
+            const float xf = (daxf - bxf) - (float)dx, yf = (dayf - byf) - (float)dy,
+                        zf = (dazf - bzf) - (float)dz;
+            pair(x, y, z, m, xf, yf, zf, src, false);
+        }
+    } else {
+        const int base = p.list_first[item_list(it)];
+#pragma unroll 1
+        for (int pos = it.z; pos < it.w; pos++) {
+            const int q = __ldg(p.item_entries + pos);
+            const int e = __ldg(p.entries + base + q);
+            const int dx = entry_dx(e), dy = entry_dy(e), dz = entry_dz(e);
+            const int sx = i + dx, sy = j + dy, sz = k + dz;
+            const int slot = ((sx >> 3) + 1) + 3 * ((sy >> 3) + 1) + 9 * ((sz >> 3) + 1);
+            const int nb = s_nb[slot];
+            if (nb < 0) continue;  // outside the domain, or covered by a coarser leaf
+            const bool sleaf = s_lf[slot] != 0;
+            const long long src = (long long)nb * kCells + (sx & 7) + 8 * (sy & 7) + 64 * (sz & 7);
+            if (!FULL && sleaf) {
+                if (L > 0) continue;  // leaf-leaf pairs of level >= 1: lattice kernel
+                // two point masses on the lattice (a leaf root), FP64
+                double a, b, c, d;
+                tab_of(p, base + q, a, b, c, d);
+                const double m = t.mom64[src];
+                A.L0 = fma(m, a, A.L0);
+                A.L1[0] = fma(m, b, A.L1[0]);
+                A.L1[1] = fma(m, c, A.L1[1]);
+                A.L1[2] = fma(m, d, A.L1[2]);
+                continue;
+            }
+            if (FULL && !sleaf && entry_near(e)) continue;  // resolved at the next level
+            double m, bx, by, bz, ox, oy, oz;
+            load_head(t, src, m, bx, by, bz);
+            load_off(p, base + q, ox, oy, oz);
+            const double x = (dax - bx) - ox, y = (day - by) - oy, z = (daz - bz) - oz;
+            float xf = 0.f, yf = 0.f, zf = 0.f;
+            if (!sleaf) {
+                float mf, bxf, byf, bzf, oxf, oyf, ozf;
+                load_head(t, src, mf, bxf, byf, bzf);
+                load_off(p, base + q, oxf, oyf, ozf);
+                xf = (daxf - bxf) - oxf;
+                yf = (dayf - byf) - oyf;
+                zf = (dazf - bzf) - ozf;
+            }
+            pair(x, y, z, m, xf, yf, zf, src, sleaf);
+        }
+    }
+    flush_split(A);
+    // to physical units, one atomic per component
+    const double* sl = sc.s64[L];
+    double* loc = t.loc;
+    atomicAdd(loc + cell, sl[0] * A.L0);
+    atomicAdd(loc + N + cell, sl[1] * A.L1[0]);
+    atomicAdd(loc + 2 * N + cell, sl[1] * A.L1[1]);
+    atomicAdd(loc + 3 * N + cell, sl[1] * A.L1[2]);
+    if (FULL) {
+        finish_split(A);
+#pragma unroll
+        for (int r = 0; r < 6; r++) atomicAdd(loc + (4 + r) * N + cell, sl[2] * A.L2[r]);
+#pragma unroll
+        for (int r = 0; r < 10; r++) atomicAdd(loc + (10 + r) * N + cell, sl[3] * A.L3[r]);
+    }
+    if (AM) {
+        double P[3] = {0.0, 0.0, 0.0};
+        if (FULL) {
+            double a3[10], ta[3];
+            load_octupole_per_mass(t, cell, a3, ta);
+            correction_target_split(A, a3, ta, P);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; a++) atomicAdd(loc + (20 + a) * N + cell, sl[4] * (A.S[a] - P[a]));
+    }
+}
+
+// Persistent launch of the FP32-bulk form (the split pair).
+__global__ void __launch_bounds__(128, 3) k_interact_split(DevTree t, DevPlan p, LevelScales sc, int am) {
+    __shared__ int s_nb[kMaxWarps][28];
+    __shared__ int s_lf[kMaxWarps][28];
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(p.counter, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= p.n_items) break;
+        const int4 it = __ldg(p.items + item);
+        if (lane < 27) {
+            const int nb = t.nbr[(long long)it.x * 27 + lane];
+            s_nb[w][lane] = nb;
+            s_lf[w][lane] = nb >= 0 ? (t.node_leaf[nb] >= 0) : 0;
+        }
+        __syncwarp();
+        const bool full = t.node_leaf[it.x] < 0;
+        if (full) {
+            if (am) run_item_split<true, true>(t, p, it, lane, s_nb[w], s_lf[w], sc);
+            else run_item_split<true, false>(t, p, it, lane, s_nb[w], s_lf[w], sc);
+        } else {
+            if (am) run_item_split<false, true>(t, p, it, lane, s_nb[w], s_lf[w], sc);
+            else run_item_split<false, false>(t, p, it, lane, s_nb[w], s_lf[w], sc);
+        }
+        __syncwarp();
+    }
+}
+
 template <class T>
 __global__ void __launch_bounds__(128, std::is_same<T, double>::value ? 3 : 1)
     k_interact(DevTree t, DevPlan p, LevelScales sc, int am) {
@@ -399,8 +555,9 @@ __global__ void __launch_bounds__(128, std::is_same<T, double>::value ? 3 : 1)
             s_lf[w][lane] = nb >= 0 ? (t.node_leaf[nb] >= 0) : 0;
         }
         __syncwarp();
-        if (it.w - it.z > kMaxChunk && item_list(it) != kRootList) {
-            // longer than the staging buffer: a plan error, latched and skipped
+        if (std::is_same<T, float>::value && item_level(it) > 0 && it.w - it.z > kMaxChunk &&
+            item_list(it) != kRootList) {
+            // longer than the staging buffer of the FP32 loop: latched and skipped
             if (lane == 0) atomicOr(t.status, kStatusBadItem);
             continue;
         }
@@ -428,6 +585,8 @@ int configure_interact() {
     if (cudaFuncSetAttribute(k_interact<float>, cudaFuncAttributePreferredSharedMemoryCarveout, carve) !=
             cudaSuccess ||
         cudaFuncSetAttribute(k_interact<double>, cudaFuncAttributePreferredSharedMemoryCarveout, carve) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_interact_split, cudaFuncAttributePreferredSharedMemoryCarveout, carve) !=
             cudaSuccess) {
         cudaGetLastError();
         return -1;
@@ -439,8 +598,10 @@ void launch_interact(const DevTree& t, const DevPlan& p, int precision, double G
                      int ctas, int warps_per_cta, cudaStream_t s) {
     if (warps_per_cta > 4) warps_per_cta = 4;
     const LevelScales sc = level_scales(t.inv_side8, G);
-    if (precision == 1)
+    if (precision == kPrecWide)
         k_interact<float><<<ctas, 32 * warps_per_cta, warps_per_cta * sizeof(WarpStage32), s>>>(t, p, sc, am);
+    else if (precision == kPrecBulk)
+        k_interact_split<<<ctas, 32 * warps_per_cta, 0, s>>>(t, p, sc, am);
     else
         k_interact<double><<<ctas, 32 * warps_per_cta, 0, s>>>(t, p, sc, am);
 }

@@ -14,6 +14,9 @@ namespace otfmm {
 void launch_leaf_moments(const DevTree& t, const int* leaf_node, const double* rho,
                          cudaStream_t s);
 void launch_m2m(const DevTree& t, int kinds, int first, int count, int precision, cudaStream_t s);
+// The moments of nodes [first, first + count) in physical units, per node
+// [20][512] (m, X, M2, M3), for ot_get_moments.
+void launch_get_moments(const DevTree& t, int first, int count, double* out, cudaStream_t s);
 
 // All cell-to-cell interactions of every level: persistent launch over the
 // work items (precision 0 = FP64, 1 = FP32 bulk).

@@ -344,7 +344,7 @@ void launch_lattice(const DevTree& t, const DevPlan& p, const DevLattice& lp, in
     if (lp.n_nodes <= 0) return;
     const LevelScales sc = level_scales(t.inv_side8, G);
     const int grid = ctas > 0 && ctas < lp.n_nodes ? ctas : lp.n_nodes;
-    if (precision == 1) {
+    if (precision == kPrecWide) {
         const int tab = lp.far_table_smem ? 8 * lp.n_far_max : 0;
         cudaStream_t sf = s_far ? s_far : s;
         k_lattice<kNear><<<grid, 256, lattice_smem_bytes(kNear, lp.w_far, lp.w_near, 0), s>>>(t, p, lp, sc);

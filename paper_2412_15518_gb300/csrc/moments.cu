@@ -319,7 +319,37 @@ __global__ void __launch_bounds__(64) k_m2m_leafkids(DevTree t, int first) {
     for (int r = 0; r < kLoc; r++) t.loc[r * N + cell] = 0.0;
 }
 
+// The moments of one level in physical units, for reading them back: per
+// node of the level, component-major [20][512]: m, the centre of mass X,
+// M2 h^2 and M3 h^3 (the workspace keeps dX = X - cell centre and the
+// moments in units of the cell side h).
+__global__ void __launch_bounds__(256) k_get_moments(DevTree t, int first, double* __restrict__ out) {
+    const int node = first + blockIdx.x;
+    const int L = t.node_level[node];
+    const double h = t.size / (double)(8 << L);
+    const double h2 = h * h, h3 = h2 * h;
+    const int nx = t.node_xyz[3 * node], ny = t.node_xyz[3 * node + 1], nz = t.node_xyz[3 * node + 2];
+    const long long N = t.n_cells;
+    double* o = out + (long long)blockIdx.x * kMom * kCells;
+    for (int c = threadIdx.x; c < kCells; c += blockDim.x) {
+        const long long cell = (long long)node * kCells + c;
+        const int ijk[3] = {8 * nx + (c & 7), 8 * ny + ((c >> 3) & 7), 8 * nz + (c >> 6)};
+        o[c] = t.mom64[cell];
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            o[(1 + a) * kCells + c] = t.origin[a] + ((ijk[a] + 0.5) + t.mom64[(1 + a) * N + cell]) * h;
+#pragma unroll
+        for (int r = 4; r < 10; r++) o[r * kCells + c] = t.mom64[r * N + cell] * h2;
+#pragma unroll
+        for (int r = 10; r < kMom; r++) o[r * kCells + c] = t.mom64[r * N + cell] * h3;
+    }
+}
+
 }  // namespace
+
+void launch_get_moments(const DevTree& t, int first, int count, double* out, cudaStream_t s) {
+    if (count > 0) k_get_moments<<<count, 256, 0, s>>>(t, first, out);
+}
 
 void launch_leaf_moments(const DevTree& t, const int* leaf_node, const double* rho,
                          cudaStream_t s) {
@@ -328,7 +358,7 @@ void launch_leaf_moments(const DevTree& t, const int* leaf_node, const double* r
 
 void launch_m2m(const DevTree& t, int kinds, int first, int count, int precision, cudaStream_t s) {
     if (count <= 0) return;
-    const bool bulk = precision == 1;
+    const bool bulk = precision == kPrecWide;  // the FP32-bulk form keeps M2M in FP64
     if (kinds & 1) {
         if (bulk) k_m2m<true><<<count * 128, 32, 0, s>>>(t, first);
         else k_m2m<false><<<count * 128, 32, 0, s>>>(t, first);

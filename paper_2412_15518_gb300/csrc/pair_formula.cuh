@@ -28,6 +28,8 @@
 // and P by -(G/6) h^-2 once per target.
 #pragma once
 
+#include "common.cuh"
+
 namespace otfmm {
 
 template <class T> struct Acc {
@@ -235,6 +237,202 @@ __host__ __device__ __forceinline__ void m2l_pair(T x, T y, T z, T m, const T* b
             A.A4[12] = fma_(tyy, zz, A.A4[12]);
             A.A4[13] = fma_(tyz, zz, A.A4[13]);
             A.A4[14] = fma_(tzz, zz, A.A4[14]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP32-bulk form: the pair split by precision.  D is the FP64 scalar, F the
+// FP32 one (a counting type on the host for the flop accounting; D = F =
+// double in the host check of the split's algebra).
+//
+// In D: the monopole part of the pair, m_B D^(n)(R) for every order the
+// target keeps (L0, L1; L2 and L3 at an interior target), and the
+// correction's target sum A4 = sum m_B f4 R^4 -- everything that involves
+// the source only through its mass -- from R formed in D; the per-pair value
+// of the correction's source term S is added to a D sum.  In F: the
+// contractions of the source's M2 and M3 with D^(n) (the quadrupole and
+// octupole parts of L0 and L1, and S's per-pair value), from R and the radial
+// factors formed again in F from the FP32 records; their L0/L1 parts are
+// summed in F over at most a flush length of pairs and then added to the D
+// sums (flush_split).
+template <class D, class F> struct SplitAcc {
+    D L0, L1[3];
+    D L2[6], L3[10];  // until finish_split: sum m R R / r^5 and -sum m R R R / r^7
+    D S[3];           // correction sum of the source octupoles
+    D A4[15];         // sum m_B f4 R^4 of interior targets (order as in Acc),
+                      // until finish_split sum m R^4 / r^9
+    F l0, l1[3];      // partial sums of the source multipole parts of L0, L1
+};
+
+template <class D, class F> __host__ __device__ __forceinline__ void split_zero(SplitAcc<D, F>& A) {
+    A.L0 = D(0.0);
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        A.L1[i] = D(0.0);
+        A.S[i] = D(0.0);
+        A.l1[i] = F(0.0);
+    }
+    A.l0 = F(0.0);
+#pragma unroll
+    for (int i = 0; i < 6; i++) A.L2[i] = D(0.0);
+#pragma unroll
+    for (int i = 0; i < 10; i++) A.L3[i] = D(0.0);
+#pragma unroll
+    for (int i = 0; i < 15; i++) A.A4[i] = D(0.0);
+}
+
+// F -> D: exact widening for float (integer operations, common.cuh),
+// identity for double.
+__host__ __device__ __forceinline__ double to_d(double v) { return v; }
+__host__ __device__ __forceinline__ double to_d(float v) { return widen(v); }
+
+// Adds the F partial sums of L0 and L1 to the D sums and clears them.
+template <class D, class F> __host__ __device__ __forceinline__ void flush_split(SplitAcc<D, F>& A) {
+    A.L0 += to_d(A.l0);
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        A.L1[i] += to_d(A.l1[i]);
+        A.l1[i] = F(0.0);
+    }
+    A.l0 = F(0.0);
+}
+
+// Completes the D sums of an interior target once per item: the monopole
+// sums are accumulated with the radial factors' constants left out (f2 =
+// 3/r^5, f3 = -15/r^7 with the sign in the sum, f4 = 105/r^9), so they are
+// multiplied in here; then the Kronecker parts of L2 and L3 from their traces
+// (as finish_acc).
+template <class D, class F> __host__ __device__ __forceinline__ void finish_split(SplitAcc<D, F>& A) {
+#pragma unroll
+    for (int i = 0; i < 6; i++) A.L2[i] = D(3.0) * A.L2[i];
+#pragma unroll
+    for (int i = 0; i < 10; i++) A.L3[i] = D(15.0) * A.L3[i];
+#pragma unroll
+    for (int i = 0; i < 15; i++) A.A4[i] = D(105.0) * A.A4[i];
+    const D d1 = D(-1.0 / 3.0) * (A.L2[0] + A.L2[3] + A.L2[5]);
+    const D Vx = D(-0.2) * (A.L3[0] + A.L3[3] + A.L3[5]);
+    const D Vy = D(-0.2) * (A.L3[1] + A.L3[6] + A.L3[8]);
+    const D Vz = D(-0.2) * (A.L3[2] + A.L3[7] + A.L3[9]);
+    A.L2[0] += d1;
+    A.L2[3] += d1;
+    A.L2[5] += d1;
+    A.L3[0] += D(3.0) * Vx;
+    A.L3[1] += Vy;
+    A.L3[2] += Vz;
+    A.L3[3] += Vx;
+    A.L3[5] += Vx;
+    A.L3[6] += D(3.0) * Vy;
+    A.L3[7] += Vz;
+    A.L3[8] += Vy;
+    A.L3[9] += D(3.0) * Vz;
+}
+
+// The correction's target term from the D sum A4 (as correction_target).
+template <class D, class F>
+__host__ __device__ __forceinline__ void correction_target_split(const SplitAcc<D, F>& S, const D* a,
+                                                                 const D* t, D* P) {
+    Acc<D> A;
+#pragma unroll
+    for (int i = 0; i < 15; i++) A.A4[i] = S.A4[i];
+    correction_target(A, a, t, P);
+}
+
+// (x, y, z) = R' in D, (xf, yf, zf) = R' in F (from the FP32 records), m =
+// source mass in D, b2/b3/bt = the source's M2', M3' and traces in F.
+template <class D, class F, bool TGT_FULL, bool SRC_MULTI, bool AM>
+__host__ __device__ __forceinline__ void m2l_pair_split(D x, D y, D z, D m, F xf, F yf, F zf,
+                                                        const F* b2, const F* b3, const F* bt,
+                                                        SplitAcc<D, F>& A) {
+    // monopole part, D: w_k = m / r^(2k+1), so m f_k = (-1)^k (2k-1)!! w_k;
+    // L1 and L3 take the sign (a negated FMA operand costs nothing), and
+    // finish_split multiplies the L2, L3 and A4 sums by 3, 15 and 105
+    const D r2 = fma_(x, x, fma_(y, y, z * z));
+    const D f0 = rsqrt_(r2);
+    const D ri2 = f0 * f0;
+    const D w0 = m * f0;
+    const D w1 = w0 * ri2;
+    A.L0 += w0;
+    A.L1[0] = fma_(-w1, x, A.L1[0]);
+    A.L1[1] = fma_(-w1, y, A.L1[1]);
+    A.L1[2] = fma_(-w1, z, A.L1[2]);
+    if (TGT_FULL) {
+        const D w2 = w1 * ri2;
+        const D xx = x * x, yy = y * y, zz = z * z;
+        const D xy = x * y, xz = x * z, yz = y * z;
+        A.L2[0] = fma_(w2, xx, A.L2[0]);
+        A.L2[1] = fma_(w2, xy, A.L2[1]);
+        A.L2[2] = fma_(w2, xz, A.L2[2]);
+        A.L2[3] = fma_(w2, yy, A.L2[3]);
+        A.L2[4] = fma_(w2, yz, A.L2[4]);
+        A.L2[5] = fma_(w2, zz, A.L2[5]);
+        const D w3 = w2 * ri2;
+        const D tx3 = w3 * x, ty3 = w3 * y, tz3 = w3 * z;
+        A.L3[0] = fma_(-tx3, xx, A.L3[0]);
+        A.L3[1] = fma_(-tx3, xy, A.L3[1]);
+        A.L3[2] = fma_(-tx3, xz, A.L3[2]);
+        A.L3[3] = fma_(-tx3, yy, A.L3[3]);
+        A.L3[4] = fma_(-tx3, yz, A.L3[4]);
+        A.L3[5] = fma_(-tx3, zz, A.L3[5]);
+        A.L3[6] = fma_(-ty3, yy, A.L3[6]);
+        A.L3[7] = fma_(-ty3, yz, A.L3[7]);
+        A.L3[8] = fma_(-ty3, zz, A.L3[8]);
+        A.L3[9] = fma_(-tz3, zz, A.L3[9]);
+        if (AM) {
+            const D w4 = w3 * ri2;
+            const D txx = w4 * xx, txy = w4 * xy, txz = w4 * xz, tyy = w4 * yy, tyz = w4 * yz, tzz = w4 * zz;
+            A.A4[0] = fma_(txx, xx, A.A4[0]);
+            A.A4[1] = fma_(txx, xy, A.A4[1]);
+            A.A4[2] = fma_(txx, xz, A.A4[2]);
+            A.A4[3] = fma_(txx, yy, A.A4[3]);
+            A.A4[4] = fma_(txx, yz, A.A4[4]);
+            A.A4[5] = fma_(txx, zz, A.A4[5]);
+            A.A4[6] = fma_(txy, yy, A.A4[6]);
+            A.A4[7] = fma_(txy, yz, A.A4[7]);
+            A.A4[8] = fma_(txy, zz, A.A4[8]);
+            A.A4[9] = fma_(txz, zz, A.A4[9]);
+            A.A4[10] = fma_(tyy, yy, A.A4[10]);
+            A.A4[11] = fma_(tyy, yz, A.A4[11]);
+            A.A4[12] = fma_(tyy, zz, A.A4[12]);
+            A.A4[13] = fma_(tyz, zz, A.A4[13]);
+            A.A4[14] = fma_(tzz, zz, A.A4[14]);
+        }
+    }
+    if (SRC_MULTI) {
+        // source quadrupole and octupole parts, F
+        const F r2f = fma_(xf, xf, fma_(yf, yf, zf * zf));
+        const F g0 = rsqrt_(r2f);
+        const F gi2 = g0 * g0;
+        const F g1 = -(g0 * gi2);
+        const F g2 = g1 * (F(-3.0) * gi2);
+        const F g3 = g2 * (F(-5.0) * gi2);
+        const F xx = xf * xf, yy = yf * yf, zz = zf * zf;
+        const F xy2 = F(2.0) * (xf * yf), xz2 = F(2.0) * (xf * zf), yz2 = F(2.0) * (yf * zf);
+        const F Mx = fma_(b2[0], xf, fma_(b2[1], yf, b2[2] * zf));
+        const F My = fma_(b2[1], xf, fma_(b2[3], yf, b2[4] * zf));
+        const F Mz = fma_(b2[2], xf, fma_(b2[4], yf, b2[5] * zf));
+        const F xMx = fma_(xf, Mx, fma_(yf, My, zf * Mz));
+        const F tr = bt[3];
+        F qx, qy, qz;
+        contract_rr(b3, xx, yy, zz, xy2, xz2, yz2, qx, qy, qz);
+        const F q3 = fma_(xf, qx, fma_(yf, qy, zf * qz));
+        const F Rt = fma_(xf, bt[0], fma_(yf, bt[1], zf * bt[2]));
+        const F h2 = F(0.5) * g2;
+        // L0 += (f2 xMx + f1 tr) / 2 - (f3 q3 + 3 f2 Rt) / 6
+        A.l0 = fma_(F(0.5) * g1, tr, fma_(h2, xMx - Rt, fma_(F(-1.0 / 6.0) * g3, q3, A.l0)));
+        // L1 += R (f3 xMx + f2 tr) / 2 + f2 M2 R
+        const F e1 = fma_(F(0.5) * g3, xMx, h2 * tr);
+        A.l1[0] = fma_(e1, xf, fma_(g2, Mx, A.l1[0]));
+        A.l1[1] = fma_(e1, yf, fma_(g2, My, A.l1[1]));
+        A.l1[2] = fma_(e1, zf, fma_(g2, Mz, A.l1[2]));
+        if (AM) {
+            // S += f4 R q3 + 3 f3 (q2 + R Rt) + 3 f2 t, each pair's value added to the D sum
+            const F g4 = g3 * (F(-7.0) * gi2);
+            const F u = F(3.0) * g3, w = F(3.0) * g2;
+            const F k = fma_(u, Rt, g4 * q3);
+            A.S[0] += to_d(fma_(k, xf, fma_(u, qx, w * bt[0])));
+            A.S[1] += to_d(fma_(k, yf, fma_(u, qy, w * bt[1])));
+            A.S[2] += to_d(fma_(k, zf, fma_(u, qz, w * bt[2])));
         }
     }
 }

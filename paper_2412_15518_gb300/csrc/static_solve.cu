@@ -1,22 +1,23 @@
 // Allocation-free solve for small trees.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
-// being captured (an allocation there is not captured and breaks the
-// capture), plug-ins whose host application owns all device memory and only
-// hands them buffers, and real-time loops that forbid allocation after
-// start-up.  ot_build_tree allocates the tree workspace, so those callers
-// cannot use ot_solve_gravity.  ot_solve_gravity_static runs the same kernels
-// as ot_solve_gravity, but every piece of scratch memory -- node tables,
-// moments, expansions, stencil tables, work items, the item counter -- lives
-// in one file-scope device array of fixed size (kStaticBytes, 4 MiB), which
-// every GPU that loads the library holds until the process exits.  The caller
-// passes only the inputs (leaf list on the host, densities on the device) and
-// the outputs (phi, g on the device).  The library allocates no device memory
-// here; the host-side planning uses ordinary heap memory.
+// Some callers cannot call cudaMalloc: plug-ins whose host application owns
+// all device memory and only hands them buffers, and real-time loops that
+// forbid allocation after start-up.  ot_build_tree allocates the tree
+// workspace, so those callers cannot use ot_solve_gravity.
+// ot_solve_gravity_static runs the same kernels as ot_solve_gravity, but
+// every piece of scratch memory -- node tables, moments, expansions, stencil
+// tables, work items, the item counter -- lives in one file-scope device
+// array of fixed size (kStaticBytes, 4 MiB), which every GPU that loads the
+// library holds until the process exits.  The caller passes only the inputs
+// (leaf list on the host, densities on the device) and the outputs (phi, g
+// on the device).  The library allocates no device memory here; the
+// host-side planning uses ordinary heap memory, uploaded with
+// cudaMemcpyAsync before the call returns.
 //
 // Limits: at most kMaxNodes = 9 octree nodes (the root leaf alone, or the
 // root with its 8 children: 4,096 cells), 0.5 <= theta <= 1.  Larger trees
-// are rejected with OT_ERR_TOO_LARGE.
+// are rejected with OT_ERR_TOO_LARGE.  Options are checked as
+// ot_solve_gravity checks them.
 //
 // Set-up: the first call on each device looks up the array's device address
 // with cudaGetSymbolAddress (with that device current) and caches it; make
@@ -28,7 +29,9 @@
 // contents in it; each call clears what must start at zero (moments, whose
 // leaf entries must hold zero offsets and higher moments, expansions, the
 // item counter, the status word).  Calls that overlap on the GPU race on the
-// array: issue them on one stream, or synchronise between them.
+// array: issue them on one stream, or synchronise between them.  A plan
+// error that a kernel latches in the status word inside the array is not
+// reported: this entry point has no handle to report it through.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -151,17 +154,16 @@ using namespace otfmm;
 extern "C" int ot_solve_gravity_static(const ot_tree_desc* desc, const double* rho, double* phi,
                                        double* g, const ot_solve_opts* opts, void* stream) {
     if (!desc) return OT_ERR_BAD_POINTER;
-    ot_solve_opts o{0.5, 1.0, OT_PRECISION_FP64, 1, 0, 0};
-    if (opts) o = *opts;
-    if (!(o.theta >= 0.5 && o.theta <= 1.0)) return OT_ERR_INVALID_ARG;
-    if (o.precision != OT_PRECISION_FP64 && o.precision != OT_PRECISION_FP32_BULK)
-        return OT_ERR_INVALID_ARG;
+    ot_solve_opts o;
+    default_solve_opts(opts, o);
+    int e = check_solve_opts(o);  // the checks of ot_solve_gravity
+    if (e) return e;
+    if (!(o.theta >= 0.5)) return OT_ERR_INVALID_ARG;  // the fixed tables' limit
     int device = -1;
     if (cudaGetDevice(&device) != cudaSuccess) {
         cudaGetLastError();
         return OT_ERR_CUDA;
     }
-    int e;
     if ((e = check_buffer(rho, device)) || (e = check_buffer(phi, device)) ||
         (e = check_buffer(g, device)))
         return e;
@@ -222,6 +224,7 @@ extern "C" int ot_solve_gravity_static(const ot_tree_desc* desc, const double* r
     d.n_leaf = h.n_leaf;
     d.n_cells = (long long)cells;
     d.size = h.size;
+    for (int a = 0; a < 3; a++) d.origin[a] = h.origin[a];
     d.node_level = (const int*)(base + l.level);
     d.node_leaf = (const int*)(base + l.leaf);
     d.node_parent = (const int*)(base + l.parent);

@@ -26,6 +26,25 @@ inline uint64_t nkey(int L, int x, int y, int z) {
 
 }  // namespace
 
+void default_solve_opts(const ot_solve_opts* o, ot_solve_opts& out) {
+    out.theta = 0.5;
+    out.G = 1.0;
+    out.precision = OT_PRECISION_FP64;
+    out.am_correction = 1;
+    out.self_term = 0;
+    out.reserved = 0;
+    if (o) out = *o;
+}
+
+int check_solve_opts(const ot_solve_opts& o) {
+    if (!(o.theta >= 0.3 && o.theta <= 1.0)) return OT_ERR_INVALID_ARG;
+    if (o.precision != OT_PRECISION_FP64 && o.precision != OT_PRECISION_FP32_BULK &&
+        o.precision != OT_PRECISION_FP32_WIDE)
+        return OT_ERR_INVALID_ARG;
+    if (!(o.G == o.G)) return OT_ERR_INVALID_ARG;
+    return OT_OK;
+}
+
 int build_host_tree(const ot_tree_desc& desc, HostTree& t) {
     t = HostTree();
     if (desc.n_leaf <= 0 || !desc.leaves || !(desc.size > 0.0)) return OT_ERR_INVALID_ARG;
@@ -258,6 +277,15 @@ int build_stencil(const HostTree& t, double theta, HostPlan& p) {
         p.flops_noam += (double)p.n_class[c] * f[c][0];
     }
     p.flops_near = (double)p.n_class[kNearP2P] * f[kNearP2P][1];
+    double s64[PairClasses], s32[PairClasses];
+    pair_flops_split(s64, s32);
+    for (int c = 0; c < PairClasses; c++) {
+        p.flops_bulk64 += (double)p.n_class[c] * s64[c];
+        p.flops_bulk32 += (double)p.n_class[c] * s32[c];
+    }
+    double fa[PairClasses];
+    pair_flops_adjoint(fa);
+    for (int c = 0; c < PairClasses; c++) p.flops_adjoint += (double)p.n_class[c] * fa[c];
     return OT_OK;
 }
 

@@ -46,6 +46,12 @@ struct HostTree {
     }
 };
 
+// Solve options: the defaults (theta 0.5, G 1, FP64, correction on, no
+// self term) or a copy of *o; and their check (theta in [0.3, 1], a known
+// precision form, G not NaN), shared by every solve entry point.
+void default_solve_opts(const ot_solve_opts* o, ot_solve_opts& out);
+int check_solve_opts(const ot_solve_opts& o);
+
 // Builds the tree; returns OT_OK, OT_ERR_INVALID_ARG, OT_ERR_INVALID_TREE or
 // OT_ERR_NOT_BALANCED.
 int build_host_tree(const ot_tree_desc& desc, HostTree& t);
@@ -64,6 +70,12 @@ enum { kLatticeFar = 0, kNearP2P = 1, kM2P = 2, kP2M = 3, kMM = 4, PairClasses =
 // Flops of one pair of each class, [class][am] (counted from the executed
 // formula; fma = 2).
 void pair_flops(double out[PairClasses][2]);
+// FP64 and FP32 flops of one pair of each class in the FP32-bulk form (the
+// split pair, with the correction).
+void pair_flops_split(double f64[PairClasses], double f32[PairClasses]);
+// FP64 flops of the reverse of one pair of each class in the adjoint's
+// interaction sweep (with the correction).
+void pair_flops_adjoint(double out[PairClasses]);
 
 // Stencil and work list of a tree for one opening parameter.
 struct HostPlan {
@@ -87,7 +99,9 @@ struct HostPlan {
     int64_t n_m2l = 0, n_p2p = 0, n_seam = 0, n_lattice = 0;
     int64_t n_class[PairClasses] = {0, 0, 0, 0, 0};
     double flops_am = 0.0, flops_noam = 0.0;  // one interaction launch
-    double flops_near = 0.0;                  // the part kept in FP64 by the bulk form
+    double flops_near = 0.0;                  // the part kept in FP64 by the wide FP32 form
+    double flops_bulk64 = 0.0, flops_bulk32 = 0.0;  // FP32-bulk form, with the correction
+    double flops_adjoint = 0.0;                     // reverse sweep of the interactions
 };
 
 // Stencil lists for theta (0.3 <= theta <= 1) and the interaction counts of

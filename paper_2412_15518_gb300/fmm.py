@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libotfmm.so")
 OT_OK = 0
 OT_PRECISION_FP64 = 0
 OT_PRECISION_FP32_BULK = 1
+OT_PRECISION_FP32_WIDE = 2
 OT_MAX_LEVELS = 16
 
 if not os.path.exists(LIB_PATH):
@@ -54,7 +55,9 @@ class ot_tree_stats(ctypes.Structure):
                 ("n_work_items", ctypes.c_int64), ("tuned_chunk", ctypes.c_int32),
                 ("tuned_ctas_per_sm", ctypes.c_int32), ("tuned_warps_per_cta", ctypes.c_int32),
                 ("tuned_lattice_ctas_per_sm", ctypes.c_int32),
-                ("device_status", ctypes.c_int32), ("workspace_bytes", ctypes.c_int64)]
+                ("device_status", ctypes.c_int32), ("workspace_bytes", ctypes.c_int64),
+                ("flops_bulk64", ctypes.c_double), ("flops_bulk32", ctypes.c_double),
+                ("flops_adjoint", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p
@@ -69,6 +72,10 @@ _lib.ot_last_solve_times.argtypes = [_P, ctypes.POINTER(ctypes.c_float),
                                      ctypes.POINTER(ctypes.c_float)]
 _lib.ot_solve_gravity_static.argtypes = [ctypes.POINTER(ot_tree_desc), _P, _P, _P,
                                          ctypes.POINTER(ot_solve_opts), _P]
+_lib.ot_get_moments.argtypes = [_P, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int32), _P]
+_lib.ot_set_launch_shape.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+_lib.ot_alu_peaks.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
 _lib.ot_destroy_tree.argtypes = [_P]
 _lib.ot_destroy_tree.restype = None
 _lib.ot_error_string.argtypes = [ctypes.c_int]
@@ -76,7 +83,8 @@ _lib.ot_error_string.restype = ctypes.c_char_p
 
 EXPORTS = ["ot_build_tree", "ot_compute_moments", "ot_solve_gravity", "ot_solve_gravity_host",
            "ot_gravity_backward", "ot_autotune", "ot_last_solve_times", "ot_tree_info",
-           "ot_destroy_tree", "ot_error_string", "ot_solve_gravity_static"]
+           "ot_destroy_tree", "ot_error_string", "ot_solve_gravity_static", "ot_get_moments",
+           "ot_set_launch_shape", "ot_alu_peaks"]
 
 
 class OTError(RuntimeError):
@@ -161,16 +169,42 @@ def ot_autotune(tree, rho, phi, g, opts: ot_solve_opts | None = None, stream=Non
 def ot_solve_gravity_static(leaves, rho, phi, g, opts: ot_solve_opts | None = None, stream=None,
                             origin=(0.0, 0.0, 0.0), size: float = 1.0):
     """Allocation-free solve of a small tree (at most 9 nodes) on the current
-    device, for callers that cannot allocate device memory (inside a stream
-    capture, inside a host application that owns all device memory, in a loop
-    that forbids allocation).  All scratch is a fixed array inside the
-    library; calls share it, so do not overlap them on the GPU."""
+    device, for callers that cannot allocate device memory (a plug-in whose
+    host application owns all device memory, a loop that forbids allocation
+    after start-up).  All scratch is a fixed array inside the library; calls
+    share it, so do not overlap them on the GPU."""
     lv = np.ascontiguousarray(np.asarray(leaves, dtype=np.int32).reshape(-1, 4))
     desc = ot_tree_desc((ctypes.c_double * 3)(*origin), float(size), lv.shape[0],
                         lv.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
     _check(_lib.ot_solve_gravity_static(ctypes.byref(desc), _ptr(rho), _ptr(phi), _ptr(g),
                                         ctypes.byref(opts) if opts is not None else None,
                                         _stream(stream)), "ot_solve_gravity_static")
+
+
+def ot_get_moments(tree, level: int, out, stream=None):
+    """Moments of every cell of `level` in physical units into the device
+    tensor out [n_nodes(level), 20, 512] (m, X[3], M2[6], M3[10] packed);
+    returns the nodes' coordinates at that level, int32 [n_nodes(level), 3]."""
+    n = int(out.shape[0])
+    xyz = np.zeros((n, 3), dtype=np.int32)
+    _check(_lib.ot_get_moments(_P(tree), int(level), _ptr(out),
+                               xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _stream(stream)),
+           "ot_get_moments")
+    return xyz
+
+
+def ot_set_launch_shape(tree, chunk: int, ctas_per_sm: int, lattice_ctas_per_sm: int = 0):
+    _check(_lib.ot_set_launch_shape(_P(tree), int(chunk), int(ctas_per_sm), int(lattice_ctas_per_sm)),
+           "ot_set_launch_shape")
+
+
+def ot_alu_peaks(device: int = 0, reps: int = 5) -> dict:
+    """Measured CUDA-core peaks of `device` in TFLOP/s: FP64 FMA, FP32 FMA and
+    paired FP32 FMA."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(_lib.ot_alu_peaks(int(device), int(reps), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "ot_alu_peaks")
+    return {"fp64_tflops": a.value, "fp32_tflops": b.value, "fp32x2_tflops": c.value}
 
 
 def ot_last_solve_times(tree):
@@ -193,7 +227,8 @@ def ot_tree_info(tree) -> dict:
                 tuned_chunk=st.tuned_chunk, tuned_ctas_per_sm=st.tuned_ctas_per_sm,
                 tuned_warps_per_cta=st.tuned_warps_per_cta,
                 tuned_lattice_ctas_per_sm=st.tuned_lattice_ctas_per_sm, device_status=st.device_status,
-                workspace_bytes=st.workspace_bytes)
+                workspace_bytes=st.workspace_bytes, flops_bulk64=st.flops_bulk64,
+                flops_bulk32=st.flops_bulk32, flops_adjoint=st.flops_adjoint)
     _check(code, "ot_tree_info")
     return info
 
@@ -248,6 +283,16 @@ class Tree:
 
     def compute_moments(self, rho, stream=None):
         ot_compute_moments(self.handle, rho, stream)
+
+    def moments(self, level: int, stream=None):
+        """(node_xyz [n, 3], moments [n, 20, 512]) of every cell of `level`."""
+        n = self.info()["n_nodes"][level]
+        out = torch.empty((n, 20, 512), dtype=torch.float64, device=self._dev())
+        xyz = ot_get_moments(self.handle, level, out, stream)
+        return xyz, out
+
+    def set_launch_shape(self, chunk: int, ctas_per_sm: int, lattice_ctas_per_sm: int = 0):
+        ot_set_launch_shape(self.handle, chunk, ctas_per_sm, lattice_ctas_per_sm)
 
     def autotune(self, rho, stream=None, **opts):
         phi, g = self.empty_outputs()

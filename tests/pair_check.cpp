@@ -10,7 +10,11 @@
 //   yz zz; xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz)
 // Output, one line per pair: the expansion at A due to B, L0 L1[3] L2[6]
 // L3[10] ac[3]; then the reverse given the adjoints (E, a): dJ/dmB,
-// dJ/dM2B[6], dJ/dM3B[10], dJ/dmA, dJ/dM3A[10], dJ/dR[3] (R = XA - XB).
+// dJ/dM2B[6], dJ/dM3B[10], dJ/dmA, dJ/dM3A[10], dJ/dR[3] (R = XA - XB);
+// then the same expansion from the FP32-bulk form's split pair
+// (m2l_pair_split) twice: with both scalars double (the split's algebra),
+// and with the FP32 part in float (R, M2, M3 rounded to float as the FP32
+// records hold them).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -31,6 +35,39 @@ static void trace3(const double* c, double* t) {
     t[0] = c[0] + c[3] + c[5];
     t[1] = c[1] + c[6] + c[8];
     t[2] = c[2] + c[7] + c[9];
+}
+
+// The split pair's expansion at A due to B, as the FP32-bulk kernel
+// assembles it (F partial sums flushed into the D sums, Kronecker parts,
+// correction's target term), physical units.
+template <class F>
+static void split_out(int am, double G, const double* R, double mA, const double* M3A, double mB,
+                      const double* M2B, const double* M3B, const double* bt) {
+    SplitAcc<double, F> A;
+    split_zero(A);
+    F b2[6], b3[10], tf[4];
+    for (int r = 0; r < 6; r++) b2[r] = (F)M2B[r];
+    for (int r = 0; r < 10; r++) b3[r] = (F)M3B[r];
+    for (int r = 0; r < 4; r++) tf[r] = (F)bt[r];
+    const F xf = (F)R[0], yf = (F)R[1], zf = (F)R[2];
+    if (am)
+        m2l_pair_split<double, F, true, true, true>(R[0], R[1], R[2], mB, xf, yf, zf, b2, b3, tf, A);
+    else
+        m2l_pair_split<double, F, true, true, false>(R[0], R[1], R[2], mB, xf, yf, zf, b2, b3, tf, A);
+    flush_split(A);
+    finish_split(A);
+    double P[3] = {0.0, 0.0, 0.0};
+    if (am && mA != 0.0) {
+        double a3[10], ta[3];
+        for (int r = 0; r < 10; r++) a3[r] = M3A[r] / mA;
+        trace3(a3, ta);
+        correction_target_split(A, a3, ta, P);
+    }
+    std::printf(" %.17g", -G * A.L0);
+    for (double v : A.L1) std::printf(" %.17g", -G * v);
+    for (double v : A.L2) std::printf(" %.17g", -G * v);
+    for (double v : A.L3) std::printf(" %.17g", -G * v);
+    for (int i = 0; i < 3; i++) std::printf(" %.17g", am ? -(G / 6.0) * (A.S[i] - P[i]) : 0.0);
 }
 
 int main() {
@@ -77,6 +114,8 @@ int main() {
         std::printf(" %.17g", o.mA);
         for (double v : o.M3A) std::printf(" %.17g", v);
         for (double v : gR) std::printf(" %.17g", v);
+        split_out<double>(am, G, R, mA, M3A, mB, M2B, M3B, bt);
+        split_out<float>(am, G, R, mA, M3A, mB, M2B, M3B, bt);
         std::printf("\n");
     }
     return 0;

@@ -147,3 +147,87 @@ def test_backward_rejects_fp32_bulk(fmm):
         tree.backward(d(rho), d(w1), d(w2), precision=fmm.OT_PRECISION_FP32_BULK)
     assert e.value.code == -1
     tree.close()
+
+
+@pytest.fixture(scope="module")
+def amr8_grad(fmm):
+    """The level-8 AMR binary (22.1M cells) with the gradient weights of the
+    level-3 case: the GPU gradient and J."""
+    lv, rho = I.workload("binary_amr8")
+    w1, w2 = I.weights(lv.shape[0])
+    tree = fmm.Tree(lv)
+    r = torch.from_numpy(rho).cuda()
+    W1, W2 = torch.from_numpy(w1).cuda(), torch.from_numpy(w2).cuda()
+    del w1, w2
+    drho = tree.backward(r, W1, W2)
+    phi, g = tree.solve(r)
+    J0 = float((W1 * phi).sum() + (W2 * g).sum())
+    torch.cuda.synchronize()
+    yield lv, rho, tree, r, W1, W2, drho, J0
+    tree.close()
+
+
+def test_adjoint_amr8_euler_identity_and_directional_derivative(fmm, amr8_grad):
+    """At full size: J is homogeneous of degree 1 in rho (sum rho dJ/drho =
+    J), and the directional derivative along v = rho u (u uniform in
+    [-1, 1], seeded) by central differences with eps = 1e-3 equals <grad, v>.
+    The difference quotient's rounding is about ulp(J) / eps (1e-12 of J)
+    and its truncation error O(eps^2) of the curvature, which only the
+    centres of mass carry: bound 1e-7 relative."""
+    lv, rho, tree, r, W1, W2, drho, J0 = amr8_grad
+    e_euler = abs(float((drho * r).sum()) - J0) / float((drho * r).abs().sum())
+    u = torch.from_numpy(np.random.default_rng(21).uniform(-1.0, 1.0, rho.shape)).cuda()
+    v = r * u
+    eps = 1e-3
+    phi, g = tree.empty_outputs()
+
+    def J(rr):
+        tree.solve(rr, phi, g)
+        return float((W1 * phi).sum() + (W2 * g).sum())
+
+    fd = (J(r + eps * v) - J(r - eps * v)) / (2 * eps)
+    ad = float((drho * v).sum())
+    e_dir = abs(fd - ad) / abs(ad)
+    print(f"amr8 adjoint: Euler {e_euler:.2e}, directional {e_dir:.2e} (J = {J0:.6e})")
+    assert e_euler < 1e-10
+    assert e_dir < 1e-7
+
+
+def test_adjoint_amr8_central_differences_at_cells(fmm, amr8_grad):
+    """Central differences at 32 seeded cells inside the stars, GPU forward.
+    With J over all 22.1M cells a single level-8 cell's effect on J
+    (~1e-16 per unit density) is below J's rounding, so the check uses the
+    same J restricted to the leaves of the sampled cells (weights zero
+    elsewhere; an instance of the same functional), its own adjoint, and a
+    density step h = 1e-2 (the solve is linear in rho but for the centres of
+    mass, so the O(h^2) error is far below the bound 1e-5 of max |grad|)."""
+    lv, rho, tree, r, W1, W2, drho, J0 = amr8_grad
+    inside = np.nonzero(rho.reshape(-1) > 1e-2)[0]
+    cells = np.random.default_rng(3).choice(inside, size=32, replace=False)
+    leaves = np.unique(cells // 512)
+    mask = torch.zeros((lv.shape[0], 1), dtype=torch.float64, device="cuda")
+    mask[torch.from_numpy(leaves).cuda()] = 1.0
+    w1 = W1 * mask
+    w2 = W2 * mask[:, :, None]
+    grad = tree.backward(r, w1, w2)
+    torch.cuda.synchronize()
+    phi, g = tree.empty_outputs()
+
+    def J(rr):
+        tree.solve(rr, phi, g)
+        return float((w1 * phi).sum() + (w2 * g).sum())
+
+    h = 1e-2
+    flat = r.view(-1)
+    gflat = grad.view(-1).cpu().numpy()
+    scale = np.abs(gflat[cells]).max()
+    errs = []
+    for c in cells:
+        flat[c] += h
+        jp = J(r)
+        flat[c] -= 2 * h
+        jm = J(r)
+        flat[c] += h
+        errs.append(abs((jp - jm) / (2 * h) - gflat[c]) / scale)
+    print(f"amr8 central differences: max err / max|grad| = {max(errs):.2e}")
+    assert max(errs) < 1e-5

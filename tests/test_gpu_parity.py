@@ -4,8 +4,18 @@ Tolerances (max |gpu - oracle| / max |oracle| per field):
   FP64 form       1e-12  (both sides FP64; they differ only in summation
                           order, FMA contraction and the reciprocal square
                           root, each ~1e-16 per operation)
-  FP32-bulk form  1e-6   (per-pair multipole terms in FP32, unit roundoff
-                          6e-8, accumulated in FP64; stated target 1e-6)
+  FP32-bulk and   1e-6   (per-pair terms in FP32, unit roundoff 6e-8,
+  wide FP32 forms         accumulated in FP64; stated target 1e-6)
+
+Conservation (Sec. 4.3.1): with F_c = m_c g_c over every leaf cell,
+  momentum  |sum F| / sum |F|              and
+  torque    |sum (x - x0) x F| / sum |(x - x0) x F|
+are zero up to rounding.  Bounds: FP64 1e-14 / 1e-12 (level-3 binary) and
+1e-13 / 1e-11 (level-8 AMR binary, 22.1M cells); the FP32-bulk form keeps
+every monopole term, the correction's sums and every sum in FP64, so only
+the FP32 rounding of the source quadrupole/octupole terms -- O((a/R)^2) of
+a pair's force, a/R <= theta -- breaks the pair symmetry: bound 1e-9; the
+wide FP32 form rounds whole pair terms in FP32 (u = 6e-8): bound 1e-6.
 """
 import numpy as np
 import pytest
@@ -18,6 +28,27 @@ pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-12
 TOL32 = 1e-6
+FP32_FORMS = ["bulk", "wide"]
+# (momentum, torque) bounds per form
+RESID = {"fp64": (1e-14, 1e-12), "bulk": (1e-9, 1e-9), "wide": (1e-6, 1e-6)}
+
+
+def prec_of(fmm, form):
+    return {"fp64": fmm.OT_PRECISION_FP64, "bulk": fmm.OT_PRECISION_FP32_BULK,
+            "wide": fmm.OT_PRECISION_FP32_WIDE}[form]
+
+
+def residuals(lv, r, g):
+    """(momentum, torque) residuals of F = m g over every leaf cell, on the
+    device (r, g: device tensors [n, 512], [n, 3, 512])."""
+    h = torch.from_numpy(1.0 / (8.0 * 2.0 ** lv[:, 0])).to(r.device)
+    m = r * (h ** 3)[:, None]
+    f = m[:, None, :] * g                                            # [n, 3, 512]
+    x = torch.from_numpy(I.cell_centres(lv) - 0.5).to(r.device)      # [n, 512, 3]
+    mom = (f.sum((0, 2)).abs().max() / f.abs().sum()).item()
+    tq = torch.cross(x, f.permute(0, 2, 1), dim=2)
+    ang = (tq.sum((0, 1)).abs().max() / tq.abs().sum()).item()
+    return mom, ang
 
 
 @pytest.fixture(scope="module")
@@ -81,12 +112,13 @@ def test_fp64_other_theta(fmm, theta):
     assert rel(g, g_o) < TOL64
 
 
+@pytest.mark.parametrize("form", FP32_FORMS)
 @pytest.mark.parametrize("theta", [0.4, 1.0 / 3.0, 0.75])
-def test_fp32_bulk_other_theta(fmm, theta):
+def test_fp32_forms_other_theta(fmm, theta, form):
     # near sets other than theta = 0.5's run the lattice kernel's generic near
     # loop; theta = 1/3 also takes the widest far halo
     lv, rho = CASES["amr_l3_seams"]()
-    phi, g = gpu_solve(fmm, lv, rho, theta=theta, precision=fmm.OT_PRECISION_FP32_BULK)
+    phi, g = gpu_solve(fmm, lv, rho, theta=theta, precision=prec_of(fmm, form))
     phi_o, g_o = O.solve(lv, rho, theta=theta)
     assert rel(phi, phi_o) < TOL32
     assert rel(g, g_o) < TOL32
@@ -121,19 +153,37 @@ def test_fp64_binary_l3_full(fmm, binary_l3):
     assert np.abs(tq.sum((0, 1))).max() / np.abs(tq).sum() < 1e-12
 
 
-def test_fp32_bulk_binary_l3(fmm, binary_l3):
+@pytest.mark.parametrize("form", FP32_FORMS)
+def test_fp32_forms_binary_l3_and_conservation(fmm, binary_l3, form):
     lv, rho, phi_o, g_o = binary_l3
-    phi, g = gpu_solve(fmm, lv, rho, precision=fmm.OT_PRECISION_FP32_BULK)
+    tree = fmm.Tree(lv)
+    r = torch.from_numpy(rho).cuda()
+    phi, g = tree.solve(r, precision=prec_of(fmm, form))
+    torch.cuda.synchronize()
+    assert rel(phi.cpu().numpy(), phi_o) < TOL32
+    assert rel(g.cpu().numpy(), g_o) < TOL32
+    mom, ang = residuals(lv, r, g)
+    print(f"binary_l3 {form}: momentum {mom:.2e}, torque {ang:.2e}")
+    assert mom < RESID[form][0] and ang < RESID[form][1]
+    tree.close()
+
+
+@pytest.mark.parametrize("form", FP32_FORMS)
+@pytest.mark.parametrize("case", ["sphere_l1_shuffled", "amr_l3_seams", "amr_l2_ragged",
+                                  "amr_l3_empty", "root_leaf"])
+def test_fp32_forms_match_oracle(fmm, case, form):
+    lv, rho = CASES[case]()
+    phi, g = gpu_solve(fmm, lv, rho, precision=prec_of(fmm, form))
+    phi_o, g_o = O.solve(lv, rho)
     assert rel(phi, phi_o) < TOL32
     assert rel(g, g_o) < TOL32
 
 
-@pytest.mark.parametrize("case", ["sphere_l1_shuffled", "amr_l3_seams", "amr_l2_ragged",
-                                  "amr_l3_empty"])
-def test_fp32_bulk_matches_oracle(fmm, case):
-    lv, rho = CASES[case]()
-    phi, g = gpu_solve(fmm, lv, rho, precision=fmm.OT_PRECISION_FP32_BULK)
-    phi_o, g_o = O.solve(lv, rho)
+@pytest.mark.parametrize("am", [True, False])
+def test_fp32_bulk_without_correction(fmm, am):
+    lv, rho = CASES["amr_l3_seams"]()
+    phi, g = gpu_solve(fmm, lv, rho, am_correction=am, precision=fmm.OT_PRECISION_FP32_BULK)
+    phi_o, g_o = O.solve(lv, rho, am_correction=am)
     assert rel(phi, phi_o) < TOL32
     assert rel(g, g_o) < TOL32
 
@@ -147,7 +197,8 @@ def test_amr6_sampled(fmm):
     phi_s, g_s = O.solve_sample(lv, rho, sample)
     tree = fmm.Tree(lv)
     r = torch.from_numpy(rho).cuda()
-    for prec, tol in ((fmm.OT_PRECISION_FP64, TOL64), (fmm.OT_PRECISION_FP32_BULK, TOL32)):
+    for prec, tol in ((fmm.OT_PRECISION_FP64, TOL64), (fmm.OT_PRECISION_FP32_BULK, TOL32),
+                      (fmm.OT_PRECISION_FP32_WIDE, TOL32)):
         phi, g = tree.solve(r, precision=prec)
         torch.cuda.synchronize()
         phi = phi.cpu().numpy().reshape(-1)[sample]
@@ -157,19 +208,20 @@ def test_amr6_sampled(fmm):
     tree.close()
 
 
-def test_fp32_bulk_error_bounded_for_any_item_length(fmm):
+@pytest.mark.parametrize("form", FP32_FORMS)
+def test_fp32_error_bounded_for_any_item_length(fmm, form):
     """The FP32 partial sums are flushed every 64 pairs whatever the plan's
     item length (their rounding error grows with the summation length: on
-    this tree 8.6e-7 in g with 263-pair sums, 3.1e-7 with 64).  The tree is
-    tuned for the FP64 form first, which may choose the longest items; the
-    FP32-bulk solve is then compared with the FP64 GPU solve (itself within
-    1e-12 of the oracle)."""
+    this tree the wide form gives 8.6e-7 in g with 263-pair sums, 3.1e-7 with
+    64).  The tree is tuned for the FP64 form first, which may choose the
+    longest items; the FP32 solve is then compared with the FP64 GPU solve
+    (itself within 1e-12 of the oracle)."""
     lv, rho = I.workload("binary_amr6")
     tree = fmm.Tree(lv)
     r = torch.from_numpy(rho).cuda()
     tree.autotune(r)
     p64, g64 = tree.solve(r)
-    p32, g32 = tree.solve(r, precision=fmm.OT_PRECISION_FP32_BULK)
+    p32, g32 = tree.solve(r, precision=prec_of(fmm, form))
     torch.cuda.synchronize()
     assert rel(p32.cpu().numpy(), p64.cpu().numpy()) < 5e-7
     assert rel(g32.cpu().numpy(), g64.cpu().numpy()) < 5e-7
@@ -243,7 +295,7 @@ def test_error_codes(fmm):
 
 def test_amr8_full_size_sampled(fmm):
     """The level-8 AMR binary (43,240 leaves, 22.1M cells) at full size, in the
-    launch configuration the benchmark times: both forms on the GPU, the
+    launch configuration the benchmark times: every form on the GPU, the
     oracle on 2,000 seeded leaf cells (and the expansions of their
     ancestors); momentum and torque residuals over every cell."""
     lv, rho = I.workload("binary_amr8")
@@ -252,22 +304,49 @@ def test_amr8_full_size_sampled(fmm):
     phi_s, g_s = O.solve_sample(lv, rho, sample)
     tree = fmm.Tree(lv)
     r = torch.from_numpy(rho).cuda()
-    for prec, tol in ((fmm.OT_PRECISION_FP64, TOL64), (fmm.OT_PRECISION_FP32_BULK, TOL32)):
+    resid = {"fp64": (1e-13, 1e-11), "bulk": RESID["bulk"], "wide": RESID["wide"]}
+    for form, tol in (("fp64", TOL64), ("bulk", TOL32), ("wide", TOL32)):
+        prec = prec_of(fmm, form)
         tree.autotune(r, precision=prec)
         phi, g = tree.solve(r, precision=prec)
         torch.cuda.synchronize()
-        assert rel(phi.view(-1)[torch.from_numpy(sample).cuda()].cpu().numpy(), phi_s) < tol, prec
+        assert rel(phi.view(-1)[torch.from_numpy(sample).cuda()].cpu().numpy(), phi_s) < tol, form
         gs = g.permute(0, 2, 1).reshape(-1, 3)[torch.from_numpy(sample).cuda()].cpu().numpy()
-        assert rel(gs, g_s) < tol, prec
-        if prec == fmm.OT_PRECISION_FP64:
-            h = torch.from_numpy(1.0 / (8.0 * 2.0 ** lv[:, 0])).cuda()
-            m = r * (h ** 3)[:, None]
-            f = m[:, None, :] * g                                   # [n, 3, 512]
-            x = torch.from_numpy(I.cell_centres(lv) - 0.5).cuda()   # [n, 512, 3]
-            mom = (f.sum((0, 2)).abs().max() / f.abs().sum()).item()
-            fx = f.permute(0, 2, 1)
-            tq = torch.cross(x, fx, dim=2)
-            ang = (tq.sum((0, 1)).abs().max() / tq.abs().sum()).item()
-            print(f"amr8 residuals: momentum {mom:.2e}, torque {ang:.2e}")
-            assert mom < 1e-13 and ang < 1e-11
+        assert rel(gs, g_s) < tol, form
+        mom, ang = residuals(lv, r, g)
+        print(f"amr8 {form} residuals: momentum {mom:.2e}, torque {ang:.2e}")
+        assert mom < resid[form][0] and ang < resid[form][1], form
+    tree.close()
+
+
+@pytest.mark.parametrize("form", ["fp64", "bulk"])
+def test_six_resident_solves_equal_independent_solves(fmm, form):
+    """The two solves per stage of an RK3 step on a resident tree: the
+    density is updated in place on the device and the captured graph is
+    replayed six times; each result equals an independent solve of the same
+    density on a fresh tree to rounding (the expansion sums are FP64 atomics
+    whose order varies from run to run: 1e-14 of the field's maximum)."""
+    lv, rho = CASES["amr_l3_seams"]()
+    prec = prec_of(fmm, form)
+    tree = fmm.Tree(lv)
+    r = torch.from_numpy(rho).cuda()
+    phi, g = tree.empty_outputs()
+    tree.solve(r, phi, g, precision=prec)
+    outs, dens = [], []
+    for k in range(6):
+        r.mul_(1.0 + 0.01 * (k + 1) * (-1) ** k)
+        tree.solve(r, phi, g, precision=prec)   # graph replay on the updated density
+        outs.append((phi.clone(), g.clone()))
+        dens.append(r.clone())
+    torch.cuda.synchronize()
+    worst = 0.0
+    for (p6, g6), d in zip(outs, dens):
+        fresh = fmm.Tree(lv)
+        p1, g1 = fresh.solve(d, precision=prec)
+        torch.cuda.synchronize()
+        worst = max(worst, float((p6 - p1).abs().max() / p1.abs().max()),
+                    float((g6 - g1).abs().max() / g1.abs().max()))
+        fresh.close()
+    print(f"six resident solves ({form}) vs independent: {worst:.2e}")
+    assert worst < 1e-14
     tree.close()

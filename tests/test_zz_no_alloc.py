@@ -1,11 +1,11 @@
 """The allocation-free solve (ot_solve_gravity_static) against the
 allocating one (ot_solve_gravity).
 
-Callers that cannot allocate device memory -- code inside a CUDA stream
-capture, plug-ins whose host application owns the device memory, loops that
-forbid allocation -- use the static entry point; it must give the same
-answer as the normal path, call after call, although every call reuses the
-same fixed scratch array.  This file is collected last on purpose.
+Callers that cannot allocate device memory -- plug-ins whose host
+application owns the device memory, loops that forbid allocation after
+start-up -- use the static entry point; it must give the same answer as the
+normal path, call after call, although every call reuses the same fixed
+scratch array.  This file is collected last on purpose.
 """
 import numpy as np
 import pytest
@@ -30,7 +30,8 @@ def test_static_solve_matches_the_allocating_solve_twice_in_a_row():
     rho_a = torch.from_numpy(I.density(leaves, I.SPHERE, seed=1)).cuda()
     rho_b = torch.from_numpy(I.density(leaves, I.BINARY, seed=2)).cuda()
     tree = fmm.Tree(leaves)
-    for prec, tol in ((fmm.OT_PRECISION_FP64, TOL64), (fmm.OT_PRECISION_FP32_BULK, TOL32)):
+    for prec, tol in ((fmm.OT_PRECISION_FP64, TOL64), (fmm.OT_PRECISION_FP32_BULK, TOL32),
+                      (fmm.OT_PRECISION_FP32_WIDE, TOL32)):
         opts = fmm.make_opts(precision=prec)
         refs = [tree.solve(r, precision=prec) for r in (rho_a, rho_b)]
         refs = [(p.clone(), g.clone()) for p, g in refs]
@@ -63,4 +64,32 @@ def test_static_solve_rejects_trees_beyond_its_limit():
     p2, g2 = tree.solve(r1)
     torch.cuda.synchronize()
     assert rel(p1, p2) < TOL64 and rel(g1, g2) < TOL64
+    tree.close()
+
+
+def test_static_solve_on_a_caller_stream_and_option_checks():
+    """On a non-default stream the call is ordered on that stream: two calls
+    in a row there, each read after that stream alone is synchronised.  Bad
+    options are rejected as ot_solve_gravity rejects them."""
+    from paper_2412_15518_gb300 import fmm
+    leaves = I.uniform_leaves(1, seed=2)
+    rho_a = torch.from_numpy(I.density(leaves, I.BINARY, seed=4)).cuda()
+    rho_b = torch.from_numpy(I.density(leaves, I.SPHERE, seed=6)).cuda()
+    tree = fmm.Tree(leaves)
+    refs = [tuple(x.clone() for x in tree.solve(r)) for r in (rho_a, rho_b)]
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    for r, (p_ref, g_ref) in zip((rho_a, rho_b), refs):
+        phi = torch.full_like(p_ref, float("nan"))
+        g = torch.full_like(g_ref, float("nan"))
+        torch.cuda.synchronize()
+        fmm.ot_solve_gravity_static(leaves, r, phi, g, fmm.make_opts(), stream=side)
+        side.synchronize()
+        assert rel(phi, p_ref) < TOL64
+        assert rel(g, g_ref) < TOL64
+    phi, g = torch.empty_like(refs[0][0]), torch.empty_like(refs[0][1])
+    for bad in (dict(G=float("nan")), dict(theta=0.4), dict(precision=7)):
+        with pytest.raises(fmm.OTError) as e:
+            fmm.ot_solve_gravity_static(leaves, rho_a, phi, g, fmm.make_opts(**bad))
+        assert e.value.code == -1, bad
     tree.close()
