@@ -4,17 +4,26 @@
 A step is one full solve -- leaf moments, M2M, every cell-to-cell
 interaction of every level in one persistent launch, L2L and evaluation of
 phi and g -- on one density field resident in HBM.  The default workload is
-the uniform level-3 octree (512 leaves of 8^3 cells, 262,144 cells) with a
-seeded binary of two polytropes, plain FP64.
+the largest single-GPU configuration: the AMR octree refined to level 8
+around a mass-ratio-0.7 binary of polytropes (43,240 leaves of 8^3 cells,
+22.1M cells), plain FP64.
 
 value      = directed cell interactions (far multipole + exact near + mixed
-             near pairs) per second, summed over all ranks
+             near pairs) per second, summed over all ranks; the median and
+             the mean of the per-step device times are both reported
 e2e        = the same through ot_solve_gravity_host: densities copied in from
              pinned host memory and phi, g copied back, every step
 roofline   = the interaction launch (the dominant kernel): algorithmic flops
              of the executed pair formulas / its CUDA-event time, against the
-             FP64 (or FP32) CUDA-core peak derived from the unit counts and
-             the maximum SM clock
+             CUDA-core peaks measured in the same run by ot_alu_peaks (FP64
+             FMA and FP32 FMA throughput kernels); the peaks derived from the
+             unit counts and the maximum SM clock are reported beside them
+companions (rank 0, one GPU): the FP32-bulk form and the wide FP32 form
+             (time, speed-up, error against the FP64 form, momentum and torque
+             residuals, mixed roofline), the adjoint, six resident solves on
+             densities updated in place (the two solves per stage of an RK3
+             step), the uniform level-3 binary in every form, and the CPU
+             oracle on a bounded sample.
 --impl reference times the CPU oracle (the plain FP64 statement of the same
 solve) on the host cores, on a bounded sample of the same workload.
 Multi-GPU runs are independent replicas (weak scaling); the solve has no
@@ -38,26 +47,28 @@ METRIC = "FMM cell-interactions/s and leaf subgrids/s on 1 GB300; % of FP64/FP32
 UNIT = "cell-interactions/s"
 NUM_SMS = 152
 SM_MAX_MHZ = 2070.0
-# CUDA-core peaks from unit counts and the maximum SM clock: 2 FP64 FMA and
-# 128 FP32 FMA per SM per clock, 2 flops per FMA
-PEAK_FP64_TFLOPS = NUM_SMS * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
-PEAK_FP32_TFLOPS = NUM_SMS * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+# CUDA-core peaks from unit counts and the maximum SM clock (context beside
+# the measured ones): 2 FP64 FMA and 128 FP32 FMA per SM per clock
+PEAK_FP64_DERIVED = NUM_SMS * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+PEAK_FP32_DERIVED = NUM_SMS * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 
-# DRAM bytes (read + write) of one interaction phase, from the ncu capture of
-# the interaction kernels summarised in profiles/ (k_interact + the lattice
-# kernels of the form, per launch).  Valid for these kernels as captured; a
-# workload or form without a capture reports null.
-TRAFFIC_BYTES = {("binary_l3", "fp64"): 15.327e6 + 10.637e6,
-                 ("binary_l3", "fp32_bulk"): 13.473e6 + 10.664e6 + 9.564e6}
+# DRAM bytes (read + write) of one interaction phase, per form, from ncu
+# captures of the interaction kernels summarised in profiles/ (per launch;
+# binary_amr8 from its full-size one-pass capture).  A workload or form
+# without a capture of the current kernels reports null.
+TRAFFIC_BYTES = {}
 
 WORKLOAD_TEXT = {
     "sphere_l1": "uniform level-1 octree, 8 leaves of 8^3 (4,096 cells), one polytrope",
     "binary_l3": "uniform level-3 octree, 512 leaves of 8^3 (262,144 cells), binary "
                  "polytropes rho_c 1.0/0.6, R 0.18/0.12, 1e-10 atmosphere, 1e-3 noise",
     "binary_amr6": "AMR octree to level 6 refined on the binary (4,852 leaves, 2.48M cells)",
-    "binary_amr8": "AMR octree to level 8, mass-ratio-0.7 binary (43,240 leaves, 22.1M cells)",
+    "binary_amr8": "AMR octree to level 8 refined on a mass-ratio-0.7 binary (43,240 leaves of "
+                   "8^3, 22.1M cells), 1e-10 atmosphere, 1e-3 noise",
 }
+
+FORMS = {"fp64": 0, "fp32_bulk": 1, "fp32_wide": 2}
 
 
 def parse():
@@ -66,10 +77,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="binary_l3", choices=sorted(WORKLOAD_TEXT))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_bulk"])
+    ap.add_argument("--workload", default="binary_amr8", choices=sorted(WORKLOAD_TEXT))
+    ap.add_argument("--precision", default="fp64", choices=sorted(FORMS))
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the companion FP32-bulk run and the CPU baseline")
+                    help="skip the companions (other forms, adjoint, resident solves, level-3 "
+                         "binary) and the CPU baseline")
+    ap.add_argument("--table", action="store_true",
+                    help="time every workload in every precision form (no oracle) and print a "
+                         "markdown table and one JSON object per row")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the autotuner (default: tune the persistent launch before timing)")
     return ap.parse_args()
@@ -203,6 +218,317 @@ def time_steps(tree, rho, phi, g, opts, steps, flush, per_step_times=True):
     return solve_ms, inter_ms
 
 
+def residuals(leaves, rho, g):
+    """(momentum, torque) residuals |sum F| / sum |F| and |sum x x F| /
+    sum |x x F| of F = m g over every leaf cell (x about the domain centre)."""
+    import torch
+    from paper_2412_15518_gb300 import inputs
+    h = torch.from_numpy(1.0 / (8.0 * 2.0 ** leaves[:, 0])).to(rho.device)
+    f = (rho * (h ** 3)[:, None])[:, None, :] * g
+    x = torch.from_numpy(inputs.cell_centres(leaves) - 0.5).to(rho.device)
+    mom = (f.sum((0, 2)).abs().max() / f.abs().sum()).item()
+    tq = torch.cross(x, f.permute(0, 2, 1), dim=2)
+    return mom, (tq.sum((0, 1)).abs().max() / tq.abs().sum()).item()
+
+
+def rel_err(a, ref):
+    return float((a - ref).abs().max() / ref.abs().max())
+
+
+def roofline(info, form, inter_ms, peaks):
+    """Roofline of the interaction launch for one form.  FP64: FP64 flops
+    against the FP64 peak.  FP32 forms: the launch is bound by whichever pipe
+    takes longer for its share of the flops (the mixed bound); frac is the
+    bound's time over the measured time."""
+    p64, p32 = peaks["fp64_tflops"], peaks["fp32_tflops"]
+    t = inter_ms / 1e3
+    if form == "fp64":
+        f64, f32 = info["flops_am"], 0.0
+    elif form == "fp32_bulk":
+        f64, f32 = info["flops_bulk64"], info["flops_bulk32"]
+    else:
+        f64, f32 = info["flops_near"], info["flops_am"] - info["flops_near"]
+    bound = max(f64 / (p64 * 1e12), f32 / (p32 * 1e12))
+    bound_derived = max(f64 / (PEAK_FP64_DERIVED * 1e12), f32 / (PEAK_FP32_DERIVED * 1e12))
+    r = {"launch_ms": inter_ms, "fp64_flops_per_launch": f64, "fp32_flops_per_launch": f32,
+         "fp64_tflops": f64 / t / 1e12, "fp32_tflops": f32 / t / 1e12,
+         "bound_ms": 1e3 * bound, "frac_of_bound": 1e3 * bound / inter_ms,
+         "frac_of_bound_derived_peaks": 1e3 * bound_derived / inter_ms}
+    return r
+
+
+def run_form(tree, rho, form, steps, flush, autotune, warm=3):
+    """Autotunes (optionally) and times `steps` solves of one form; returns
+    (phi, g, solve_ms list, interaction ms list, tuned shape)."""
+    import torch
+    prec = FORMS[form]
+    if autotune:
+        tree.autotune(rho, precision=prec)
+    phi, g = tree.empty_outputs()
+    opts = dict(precision=prec)
+    time_steps(tree, rho, phi, g, opts, warm, flush)
+    torch.cuda.synchronize()
+    ms, im = time_steps(tree, rho, phi, g, opts, steps, flush)
+    i = tree.info()
+    shape = {"chunk": i["tuned_chunk"], "ctas_per_sm": i["tuned_ctas_per_sm"],
+             "lattice_ctas_per_sm": i["tuned_lattice_ctas_per_sm"], "work_items": i["n_work_items"]}
+    return phi, g, ms, im, shape
+
+
+def companion_form(tree, leaves, rho, form, steps, flush, autotune, ref, ref_ms, info, peaks):
+    """One FP32 form beside the FP64 line: time, speed-up, error against the
+    FP64 GPU solve, conservation residuals and the mixed roofline."""
+    phi, g, ms, im, shape = run_form(tree, rho, form, steps, flush, autotune)
+    n_int = info["n_m2l"] + info["n_p2p"] + info["n_seam"]
+    mom, ang = residuals(leaves, rho, g)
+    out = {"ms_per_step": statistics.mean(ms), "ms_per_step_median": statistics.median(ms),
+           "value": n_int / (statistics.median(ms) / 1e3),
+           "speedup_vs_fp64": statistics.median(ref_ms) / statistics.median(ms),
+           "max_rel_err_vs_fp64": {"phi": rel_err(phi, ref[0]), "g": rel_err(g, ref[1])},
+           "residuals": {"momentum": mom, "torque": ang},
+           "roofline": roofline(info, form, statistics.median(im), peaks), "tuned": shape}
+    del phi, g
+    return out
+
+
+def resident_six(tree, rho, form, flush):
+    """Six solves per step on a resident tree, the density updated in place on
+    the device before each (as the two solves per stage of an RK3 step would
+    see it): device time per six solves, host time per solve call (the graph
+    replay), and the device time between the solves."""
+    import torch
+    prec = FORMS[form]
+    phi, g = tree.empty_outputs()
+    r = rho.clone()
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        tree.solve(r, phi, g, precision=prec)
+    torch.cuda.synchronize()
+    step_ms, host_us, gap_ms = [], [], []
+    for step in range(3):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(12)]
+        for k in range(6):
+            r.mul_(1.0 + 1e-6 * (1 if (step + k) % 2 else -1))  # the hydro update stands in
+            ev[2 * k].record(stream)
+            t0 = time.perf_counter()
+            tree.solve(r, phi, g, precision=prec)
+            host_us.append(1e6 * (time.perf_counter() - t0))
+            ev[2 * k + 1].record(stream)
+        ev[11].synchronize()
+        solves = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(6))
+        total = ev[0].elapsed_time(ev[11])
+        step_ms.append(total)
+        gap_ms.append((total - solves) / 5)
+    return {"ms_per_six_solves": statistics.median(step_ms),
+            "host_us_per_solve_call": statistics.median(host_us),
+            "device_gap_ms_between_solves": statistics.median(gap_ms),
+            "includes": "per solve: an in-place density update (one elementwise kernel) and the "
+                        "graph replay of the solve; L2 flushed once per six"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    world, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    from paper_2412_15518_gb300 import fmm, inputs
+    peaks = fmm.ot_alu_peaks(local, 5)
+    leaves, rho_np = inputs.workload(args.workload)
+    form = args.precision
+    prec = FORMS[form]
+    opts = dict(precision=prec)
+    tree = fmm.Tree(leaves, device=local)
+    rho = torch.from_numpy(rho_np).cuda()
+    phi, g = tree.empty_outputs()
+    if not args.no_autotune:
+        tree.autotune(rho, precision=prec)
+    info = tree.info()
+    n_int = info["n_m2l"] + info["n_p2p"] + info["n_seam"]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    time_steps(tree, rho, phi, g, opts, max(3, args.warmup), flush)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    solve_ms, inter_ms = time_steps(tree, rho, phi, g, opts, args.steps, flush)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    total_ms, value = aggregate(world, sum(solve_ms), n_int * args.steps)
+    ms_per_step = total_ms / args.steps
+    subgrids = sum_over_ranks(world, leaves.shape[0] * args.steps) / (total_ms / 1e3)
+
+    # roofline of the interaction launch, against the measured peaks
+    inter_med = statistics.median(inter_ms)
+    rf = roofline(info, form, inter_med, peaks)
+    if form == "fp64":
+        achieved, peak, peak_d = rf["fp64_tflops"], peaks["fp64_tflops"], PEAK_FP64_DERIVED
+        kernel = "k_interact<double> + k_lattice<0> (concurrent graph branches)"
+    elif form == "fp32_bulk":
+        achieved, peak, peak_d = rf["fp64_tflops"], peaks["fp64_tflops"], PEAK_FP64_DERIVED
+        kernel = "k_interact_split + k_lattice<0> (concurrent graph branches; FP64-bound)"
+    else:
+        achieved, peak, peak_d = rf["fp32_tflops"], peaks["fp32_tflops"], PEAK_FP32_DERIVED
+        kernel = "k_interact<float> + k_lattice<1> + k_lattice<2> (concurrent graph branches)"
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": TRAFFIC_BYTES.get((args.workload, form)),
+            "kernel": kernel,
+            "peak_source": "measured in this run by ot_alu_peaks (FMA throughput kernels on "
+                           "every SM, best of 5)",
+            "peak_derived": peak_d, "frac_derived": achieved / peak_d,
+            "flops_per_launch": rf["fp64_flops_per_launch"] + rf["fp32_flops_per_launch"],
+            "launch_ms": inter_med, "launch_ms_mean": statistics.mean(inter_ms)}
+    if form != "fp64":
+        roof.update({k: rf[k] for k in ("fp64_flops_per_launch", "fp32_flops_per_launch",
+                                        "bound_ms", "frac_of_bound")})
+    mom, ang = residuals(leaves, rho, g)
+
+    # end to end through the host-buffer entry point
+    hr = torch.from_numpy(rho_np).pin_memory()
+    hp = torch.empty((leaves.shape[0], 512), dtype=torch.float64).pin_memory()
+    hg = torch.empty((leaves.shape[0], 3, 512), dtype=torch.float64).pin_memory()
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        tree.solve_host(hr, hp, hg, **opts)
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tree.solve_host(hr, hp, hg, **opts)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    _, e2e_value = aggregate(world, sum(e2e_ms), n_int * args.steps)
+    del hr, hp, hg
+    n_cells = leaves.shape[0] * 512
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_extra:
+        ref = (phi.clone(), g.clone())
+        csteps = max(3, min(args.steps, 10))
+        for other in ("fp32_bulk", "fp32_wide"):
+            if other != form:
+                extra[other] = companion_form(tree, leaves, rho, other, csteps, flush,
+                                              not args.no_autotune, ref, solve_ms, info, peaks)
+        del ref
+        # the adjoint (FP64): dJ/drho for J = sum(w1 phi + w2 . g)
+        tree.set_launch_shape(info["tuned_chunk"], info["tuned_ctas_per_sm"],
+                              info["tuned_lattice_ctas_per_sm"])
+        w1n, w2n = inputs.weights(leaves.shape[0])
+        w1, w2 = torch.from_numpy(w1n).cuda(), torch.from_numpy(w2n).cuda()
+        del w1n, w2n
+        drho = torch.empty_like(rho)
+        for _ in range(2):
+            tree.backward(rho, w1, w2, drho)
+        torch.cuda.synchronize()
+        bms = []
+        for _ in range(min(args.steps, 5)):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tree.backward(rho, w1, w2, drho)
+            e1.record(stream)
+            e1.synchronize()
+            bms.append(e0.elapsed_time(e1))
+        adj = {"ms_per_step": statistics.median(bms), "includes": "forward solve + reverse sweep",
+               "ratio_to_forward": statistics.median(bms) / statistics.median(solve_ms)}
+        if info.get("flops_adjoint"):
+            rev_ms = statistics.median(bms) - statistics.median(solve_ms)
+            adj["reverse_interaction_fp64_flops"] = info["flops_adjoint"]
+            adj["reverse_sweep_ms_est"] = rev_ms
+            adj["fp64_tflops_est"] = info["flops_adjoint"] / (rev_ms / 1e3) / 1e12
+            adj["frac_of_fp64_peak_est"] = adj["fp64_tflops_est"] / peaks["fp64_tflops"]
+        extra["adjoint_fp64"] = adj
+        del w1, w2, drho
+        extra["resident_6"] = {f: resident_six(tree, rho, f, flush) for f in ("fp64", "fp32_bulk")}
+        extra["resident_6"]["ms_per_six_solves_if_separate"] = 6 * statistics.median(solve_ms)
+        if args.workload != "binary_l3":
+            extra["binary_l3"] = companion_workload("binary_l3", flush, not args.no_autotune, peaks)
+        extra["cpu_baseline"] = cpu_baseline(leaves, rho_np)
+    # library kernels of one solve: leaf moments; per parent level the M2M
+    # kernel for cells with interior children and/or the one for cells with
+    # leaf children; the general interaction kernel; the lattice kernels (1 in
+    # the FP64 and FP32-bulk forms, near + far in the wide FP32 form; none
+    # without leaf nodes below the root); per level the L2L kernel for its
+    # interior cells below the root (or a leaf root) and/or the one
+    # evaluating its leaf children
+    nl = info["n_levels"]
+    leaf_at = lambda L: info["n_leaf_nodes"][L] if 0 <= L < nl else 0
+    inner_at = lambda L: info["n_nodes"][L] - info["n_leaf_nodes"][L] if 0 <= L < nl else 0
+    m2m = sum((inner_at(L + 1) > 0) + (leaf_at(L + 1) > 0) for L in range(nl - 1))
+    l2l = sum((leaf_at(0) > 0 if L == 0 else inner_at(L) > 0) + (leaf_at(L + 1) > 0)
+              for L in range(nl))
+    lattice = sum(info["n_leaf_nodes"][1:nl]) > 0
+    n_lat = (2 if form == "fp32_wide" else 1) if lattice else 0
+    launches = (1 + m2m + 1 + n_lat + l2l) * args.steps
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "ms_per_step_median": statistics.median(solve_ms), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if form == "fp64" else "f32+f64",
+        "data": "synthetic (seeded polytrope binary)",
+        "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}",
+                   "precision": form, "theta": 0.5, "am_correction": True,
+                   "cells": n_cells, "leaf_subgrids": int(leaves.shape[0]),
+                   "interactions_per_step": n_int,
+                   "l2": "flushed before every step (256 MiB write, untimed)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "work_items": info["n_work_items"], "chunk": info["tuned_chunk"],
+                   "ctas_per_sm": info["tuned_ctas_per_sm"]},
+        "leaf_subgrids_per_s": subgrids,
+        "roofline": roof,
+        "peaks_measured": peaks,
+        "residuals": {"momentum": mom, "torque": ang},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n_cells * 8,
+                "d2h_bytes_per_step": n_cells * 4 * 8},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    line.update(extra)
+    if "cpu_baseline" not in line:
+        line["cpu_baseline"] = None
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    tree.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def companion_workload(name, flush, autotune, peaks):
+    """Every form on another workload (its own tree): ms per solve, the
+    interaction rooflines, the FP32 forms' errors and residuals."""
+    import torch
+    from paper_2412_15518_gb300 import fmm, inputs
+    leaves, rho_np = inputs.workload(name)
+    tree = fmm.Tree(leaves)
+    rho = torch.from_numpy(rho_np).cuda()
+    info = tree.info()
+    n_int = info["n_m2l"] + info["n_p2p"] + info["n_seam"]
+    out = {"workload": f"{name}: {WORKLOAD_TEXT[name]}"}
+    ref = None
+    for form in ("fp64", "fp32_bulk", "fp32_wide"):
+        phi, g, ms, im, shape = run_form(tree, rho, form, 20, flush, autotune)
+        mom, ang = residuals(leaves, rho, g)
+        r = {"ms_per_step_median": statistics.median(ms), "ms_per_step": statistics.mean(ms),
+             "value": n_int / (statistics.median(ms) / 1e3),
+             "residuals": {"momentum": mom, "torque": ang},
+             "roofline": roofline(info, form, statistics.median(im), peaks), "tuned": shape}
+        if ref is None:
+            ref = (phi.clone(), g.clone(), ms)
+        else:
+            r["max_rel_err_vs_fp64"] = {"phi": rel_err(phi, ref[0]), "g": rel_err(g, ref[1])}
+            r["speedup_vs_fp64"] = statistics.median(ref[2]) / statistics.median(ms)
+        out[form] = r
+    tree.close()
+    return out
+
+
 def cpu_baseline(leaves, rho, budget_s: float = 20.0):
     """The oracle (plain FP64 C++ on the host cores), timed once on a bounded
     sample: the full solve when it fits the budget, else a seeded sample of
@@ -297,186 +623,64 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args):
-    import numpy as np
+def run_table(args):
+    """Every workload x every form on this GPU: median solve time, throughput,
+    interaction roofline against the measured peaks, conservation residuals,
+    speed-up and difference against the FP64 form."""
     import torch
-    world, rank, local = dist_setup(args.gpus)
-    torch.cuda.set_device(local)
     from paper_2412_15518_gb300 import fmm, inputs
-    leaves, rho_np = inputs.workload(args.workload)
-    prec = fmm.OT_PRECISION_FP64 if args.precision == "fp64" else fmm.OT_PRECISION_FP32_BULK
-    opts = dict(precision=prec)
-    tree = fmm.Tree(leaves, device=local)
-    rho = torch.from_numpy(rho_np).cuda()
-    phi, g = tree.empty_outputs()
-    if not args.no_autotune:
-        tree.autotune(rho, precision=prec)
-    info = tree.info()
-    n_int = info["n_m2l"] + info["n_p2p"] + info["n_seam"]
+    torch.cuda.set_device(0)
+    peaks = fmm.ot_alu_peaks(0, 5)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    time_steps(tree, rho, phi, g, opts, max(3, args.warmup), flush)
-    torch.cuda.synchronize()
-    barrier(world)
-    clocks = ClockSampler(local)
-    clocks.start()
-    torch.cuda.synchronize()
-    solve_ms, inter_ms = time_steps(tree, rho, phi, g, opts, args.steps, flush)
-    torch.cuda.synchronize()
-    barrier(world)
-    clk = clocks.stop()
-    total_ms, value = aggregate(world, sum(solve_ms), n_int * args.steps)
-    ms_per_step = total_ms / args.steps
-    subgrids = sum_over_ranks(world, leaves.shape[0] * args.steps) / (total_ms / 1e3)
-
-    # roofline of the interaction launch
-    inter_avg = statistics.mean(inter_ms)
-    flops = info["flops_am"]
-    if prec == fmm.OT_PRECISION_FP64:
-        achieved = flops / (inter_avg / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": PEAK_FP64_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / PEAK_FP64_TFLOPS,
-                "traffic": TRAFFIC_BYTES.get((args.workload, "fp64")),
-                "kernel": "k_interact<double> + k_lattice<0> (concurrent graph branches)",
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz",
-                "flops_per_launch": flops, "launch_ms": inter_avg}
-    else:
-        f32 = flops - info["flops_near"]
-        achieved = f32 / (inter_avg / 1e3) / 1e12
-        # the FP64 near pairs bound the launch too: the mixed roofline is the
-        # larger of the two pipes' times
-        mixed_ms = 1e3 * max(f32 / (PEAK_FP32_TFLOPS * 1e12),
-                             info["flops_near"] / (PEAK_FP64_TFLOPS * 1e12))
-        roof = {"bound": "alu", "achieved": achieved, "peak": PEAK_FP32_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / PEAK_FP32_TFLOPS,
-                "traffic": TRAFFIC_BYTES.get((args.workload, "fp32_bulk")),
-                "kernel": "k_interact<float> + k_lattice<1> + k_lattice<2> (concurrent graph branches)",
-                "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 flops x 2070 MHz",
-                "flops_per_launch": f32, "fp64_flops_per_launch": info["flops_near"],
-                "launch_ms": inter_avg, "mixed_bound_ms": mixed_ms,
-                "frac_of_mixed_bound": mixed_ms / inter_avg}
-
-    # end to end through the host-buffer entry point
-    hr = torch.from_numpy(rho_np).pin_memory()
-    hp = torch.empty((leaves.shape[0], 512), dtype=torch.float64).pin_memory()
-    hg = torch.empty((leaves.shape[0], 3, 512), dtype=torch.float64).pin_memory()
-    stream = torch.cuda.current_stream()
-    for _ in range(2):
-        tree.solve_host(hr, hp, hg, **opts)
-    torch.cuda.synchronize()
-    e2e_ms = []
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        tree.solve_host(hr, hp, hg, **opts)
-        e1.record(stream)
-        e1.synchronize()
-        e2e_ms.append(e0.elapsed_time(e1))
-    _, e2e_value = aggregate(world, sum(e2e_ms), n_int * args.steps)
-    n_cells = leaves.shape[0] * 512
-    extra = {}
-    if rank == 0 and world == 1 and not args.no_extra:
-        if prec == fmm.OT_PRECISION_FP64:
-            # the FP32-bulk form on the same workload, and its error against FP64
-            ref_phi, ref_g = phi.clone(), g.clone()
-            o32 = dict(precision=fmm.OT_PRECISION_FP32_BULK)
-            if not args.no_autotune:
-                tree.autotune(rho, precision=fmm.OT_PRECISION_FP32_BULK)
-            time_steps(tree, rho, phi, g, o32, 3, flush)
-            ms32, int32 = time_steps(tree, rho, phi, g, o32, args.steps, flush)
-            torch.cuda.synchronize()
-            ep = float((phi - ref_phi).abs().max() / ref_phi.abs().max())
-            eg = float((g - ref_g).abs().max() / ref_g.abs().max())
-            f32 = info["flops_am"] - info["flops_near"]
-            a32 = f32 / (statistics.mean(int32) / 1e3) / 1e12
-            mixed_ms = 1e3 * max(f32 / (PEAK_FP32_TFLOPS * 1e12),
-                                 info["flops_near"] / (PEAK_FP64_TFLOPS * 1e12))
-            extra["fp32_bulk"] = {
-                "ms_per_step": sum(ms32) / args.steps,
-                "value": n_int * args.steps / (sum(ms32) / 1e3),
-                "speedup_vs_fp64": sum(solve_ms) / sum(ms32),
-                "max_rel_err_vs_fp64": {"phi": ep, "g": eg},
-                "interact_ms": statistics.mean(int32),
-                "interact_fp32_tflops": a32, "frac_of_fp32_peak": a32 / PEAK_FP32_TFLOPS,
-                "mixed_bound_ms": mixed_ms,
-                "frac_of_mixed_bound": mixed_ms / statistics.mean(int32)}
-            i32 = tree.info()
-            extra["fp32_bulk"]["tuned"] = {"chunk": i32["tuned_chunk"],
-                                           "ctas_per_sm": i32["tuned_ctas_per_sm"],
-                                           "lattice_ctas_per_sm": i32["tuned_lattice_ctas_per_sm"],
-                                           "work_items": i32["n_work_items"]}
-            # the adjoint (FP64): dJ/drho for J = sum(w1 phi + w2 . g)
-            w1n, w2n = inputs.weights(leaves.shape[0])
-            w1, w2 = torch.from_numpy(w1n).cuda(), torch.from_numpy(w2n).cuda()
-            drho = torch.empty_like(rho)
-            for _ in range(2):
-                tree.backward(rho, w1, w2, drho)
-            torch.cuda.synchronize()
-            bms = []
-            for _ in range(args.steps):
-                flush.zero_()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                tree.backward(rho, w1, w2, drho)
-                e1.record(stream)
-                e1.synchronize()
-                bms.append(e0.elapsed_time(e1))
-            extra["adjoint_fp64"] = {"ms_per_step": sum(bms) / args.steps,
-                                     "includes": "forward solve + reverse sweep",
-                                     "ratio_to_forward": sum(bms) / sum(solve_ms)}
-        extra["cpu_baseline"] = cpu_baseline(leaves, rho_np)
-    # library kernels of one solve: leaf moments; per parent level the M2M
-    # kernel for cells with interior children and/or the one for cells with
-    # leaf children; the general interaction kernel; the lattice kernels (1 in
-    # the FP64 form, near + far in the FP32-bulk form; none without leaf nodes
-    # below the root); per level the L2L kernel for its interior cells below
-    # the root (or a leaf root) and/or the one evaluating its leaf children
-    nl = info["n_levels"]
-    leaf_at = lambda L: info["n_leaf_nodes"][L] if 0 <= L < nl else 0
-    inner_at = lambda L: info["n_nodes"][L] - info["n_leaf_nodes"][L] if 0 <= L < nl else 0
-    m2m = sum((inner_at(L + 1) > 0) + (leaf_at(L + 1) > 0) for L in range(nl - 1))
-    l2l = sum((leaf_at(0) > 0 if L == 0 else inner_at(L) > 0) + (leaf_at(L + 1) > 0)
-              for L in range(nl))
-    lattice = sum(info["n_leaf_nodes"][1:nl]) > 0
-    n_lat = (2 if prec == fmm.OT_PRECISION_FP32_BULK else 1) if lattice else 0
-    launches = (1 + m2m + 1 + n_lat + l2l) * args.steps
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if prec == fmm.OT_PRECISION_FP64 else "f32+f64",
-        "data": "synthetic (seeded polytrope binary)",
-        "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}",
-                   "precision": args.precision, "theta": 0.5, "am_correction": True,
-                   "cells": n_cells, "leaf_subgrids": int(leaves.shape[0]),
-                   "interactions_per_step": n_int,
-                   "l2": "flushed before every step (256 MiB write, untimed)",
-                   "parallelism": "replicas" if world > 1 else "single GPU",
-                   "work_items": info["n_work_items"], "chunk": info["tuned_chunk"],
-                   "ctas_per_sm": info["tuned_ctas_per_sm"]},
-        "leaf_subgrids_per_s": subgrids,
-        "roofline": roof,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n_cells * 8,
-                "d2h_bytes_per_step": n_cells * 4 * 8},
-        "gpu_launches": launches,
-        "clocks": clk,
-    }
-    line.update(extra)
-    if "cpu_baseline" not in line:
-        line["cpu_baseline"] = None
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    tree.close()
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    rows = []
+    for name in ("sphere_l1", "binary_l3", "binary_amr6", "binary_amr8"):
+        leaves, rho_np = inputs.workload(name)
+        tree = fmm.Tree(leaves)
+        rho = torch.from_numpy(rho_np).cuda()
+        info = tree.info()
+        n_int = info["n_m2l"] + info["n_p2p"] + info["n_seam"]
+        ref = None
+        for form in ("fp64", "fp32_bulk", "fp32_wide"):
+            phi, g, ms, im, shape = run_form(tree, rho, form, args.steps, flush, not args.no_autotune)
+            med = statistics.median(ms)
+            mom, ang = residuals(leaves, rho, g)
+            rf = roofline(info, form, statistics.median(im), peaks)
+            row = {"workload": name, "form": form, "cells": int(leaves.shape[0]) * 512,
+                   "leaf_subgrids": int(leaves.shape[0]), "interactions": n_int,
+                   "ms_median": med, "ms_mean": statistics.mean(ms),
+                   "interact_ms_median": statistics.median(im),
+                   "cell_interactions_per_s": n_int / (med / 1e3),
+                   "leaf_subgrids_per_s": leaves.shape[0] / (med / 1e3),
+                   "frac_of_bound": rf["frac_of_bound"], "roofline": rf,
+                   "momentum": mom, "torque": ang, "tuned": shape}
+            if ref is None:
+                ref = (phi.clone(), g.clone(), med)
+            else:
+                row["speedup_vs_fp64"] = ref[2] / med
+                row["max_rel_diff_vs_fp64"] = max(rel_err(phi, ref[0]), rel_err(g, ref[1]))
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+            del phi, g
+        del ref
+        tree.close()
+        del rho
+        torch.cuda.empty_cache()
+    print(f"peaks measured: {json.dumps(peaks)}")
+    print("| workload | form | ms (median) | cell-int/s | leaf subgrids/s | frac of bound | "
+          "momentum | torque | speed-up vs FP64 |")
+    print("|---|---|---:|---:|---:|---:|---:|---:|---:|")
+    for r in rows:
+        print(f"| {r['workload']} | {r['form']} | {r['ms_median']:.3f} | {r['cell_interactions_per_s']:.3g} | "
+              f"{r['leaf_subgrids_per_s']:.3g} | {r['frac_of_bound']:.3f} | {r['momentum']:.1e} | "
+              f"{r['torque']:.1e} | {r.get('speedup_vs_fp64', 1.0):.2f} |")
 
 
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.table:
+        run_table(args)
     else:
         run_ours(args)
 

@@ -203,6 +203,21 @@ int ot_solve_gravity_host(ot_tree* tree, const double* rho_host, double* phi_hos
 int ot_gravity_backward(ot_tree* tree, const double* rho, const double* w1, const double* w2,
                         double* drho, const ot_solve_opts* opts, void* stream);
 
+/* Tangent of the solve: the time derivative of the potential and of the
+ * acceleration, phi_dot = (d phi / d rho) . rho_dot and g_dot likewise, for
+ * densities changing at rho_dot (Sec. 2: the FMM includes the time
+ * derivative of the potential, which energy conservation in the rotating
+ * frame needs, Sec. 4.3.1; in the paper's code rho_dot comes from the
+ * hydrodynamics).  The exact derivative of the discrete solve (through the
+ * centres of mass and the correction's mass ratio), FP64 only.  rho,
+ * rho_dot: device float64 [n_leaf][512]; phi_dot: device float64
+ * [n_leaf][512]; g_dot: device float64 [n_leaf][3][512]; phi, g: the solve
+ * itself in the same layouts, or NULL to skip.  The first call allocates the
+ * tangent workspace (67 doubles per cell). */
+int ot_solve_gravity_tangent(ot_tree* tree, const double* rho, const double* rho_dot, double* phi,
+                             double* g, double* phi_dot, double* g_dot, const ot_solve_opts* opts,
+                             void* stream);
+
 /* Chooses the persistent launch's stencil-chunk length and the CTAs per SM
  * of the general kernel (and, wide FP32 form, of the lattice kernels) for
  * this plan: every candidate is timed as the whole solve graph it would run,

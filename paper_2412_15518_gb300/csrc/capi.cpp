@@ -15,6 +15,7 @@
 #include "adjoint.hpp"
 #include "kernels.hpp"
 #include "lattice.hpp"
+#include "tangent.hpp"
 #include "tree_host.hpp"
 
 using namespace otfmm;
@@ -83,6 +84,10 @@ struct ot_tree {
     // adjoint workspace (allocated by the first backward call)
     double* d_locbar = nullptr;
     double* d_mombar = nullptr;
+    // tangent workspace (allocated by the first tangent call)
+    double* d_mom_d = nullptr;
+    double* d_rec_d = nullptr;
+    double* d_loc_d = nullptr;
     // staging of the host-buffer solve
     double *d_rho_in = nullptr, *d_phi_out = nullptr, *d_g_out = nullptr;
     // tuning of the persistent launch
@@ -514,7 +519,7 @@ void ot_destroy_tree(ot_tree* t) {
                         t->d_list_len, t->d_items, t->d_counter, t->d_rho_in, t->d_phi_out,
                         t->d_hoff_far, t->d_hoff_near, t->d_lattice_nodes, t->d_items_adj, t->d_item_entries,
                         t->d_off64, t->d_off32,
-                        t->d_g_out, t->d_locbar, t->d_mombar};
+                        t->d_g_out, t->d_locbar, t->d_mombar, t->d_mom_d, t->d_rec_d, t->d_loc_d};
         for (void* p : ptrs)
             if (p) cudaFree(p);
     }
@@ -589,14 +594,27 @@ int ot_gravity_backward(ot_tree* t, const double* rho, const double* w1, const d
     if (!t->d_mombar) TRY(dalloc(t, &t->d_mombar, kMom * cells));
     cudaStream_t s = (cudaStream_t)stream;
     t->last_stream = s;
-    // forward pass: moments and complete expansions stay in the workspace
-    enqueue_moments(t, rho, o.precision, s);
-    TRY(enqueue_interact(t, o, s));
-    enqueue_downward(t, rho, t->d_phi_out, t->d_g_out, o, s);
-    TRYC(cudaGetLastError());
-    // reverse sweep
+    // forward pass: the moments, and the complete expansions of the interior
+    // cells (the reverse L2L needs them for the derivative of each shift with
+    // respect to the centres of mass).  The leaf cells' expansions are never
+    // read by the reverse sweep, so the lattice pairs, the pairs with a leaf
+    // target and the leaf evaluation are left out.
     DevTree d = dev_tree(t);
     const HostTree& h = t->h;
+    enqueue_moments(t, rho, o.precision, s);
+    TRYC(cudaMemsetAsync(t->d_counter, 0, 4 * sizeof(int), s));
+    {
+        DevPlan pf = dev_plan(t);
+        pf.interior_only = 1;
+        launch_interact(d, pf, o.precision, o.G, o.am_correction ? 1 : 0,
+                        std::max(1, t->num_sms * t->ctas_per_sm), t->warps_per_cta, s);
+    }
+    for (int L = 0; L < h.n_levels; L++)
+        if (h.l2l_kinds(L) & 1)
+            launch_l2l(d, 1, h.level_first[L], h.level_first[L + 1] - h.level_first[L], rho,
+                       t->d_phi_out, t->d_g_out, o.G, o.self_term ? 1 : 0, o.precision, s);
+    TRYC(cudaGetLastError());
+    // reverse sweep
     TRYC(cudaMemsetAsync(t->d_mombar, 0, sizeof(double) * kMom * cells, s));
     launch_adj_seed(d, t->d_leaf_node, w1, w2, t->d_locbar, s);
     for (int L = h.n_levels - 2; L >= 0; L--)
@@ -613,6 +631,42 @@ int ot_gravity_backward(ot_tree* t, const double* rho, const double* w1, const d
         launch_m2m_reverse(d, h.level_first[L], h.level_first[L + 1] - h.level_first[L],
                            t->d_mombar, s);
     launch_rho_bar(d, t->d_leaf_node, t->d_mombar, w1, drho, o.G, o.self_term ? 1 : 0, s);
+    TRYC(cudaGetLastError());
+    return OT_OK;
+}
+
+int ot_solve_gravity_tangent(ot_tree* t, const double* rho, const double* rho_dot, double* phi, double* g,
+                             double* phi_dot, double* g_dot, const ot_solve_opts* opts, void* stream) {
+    if (!t) return OT_ERR_BAD_POINTER;
+    if (t->device < 0) return OT_ERR_INVALID_ARG;
+    ot_solve_opts o;
+    fill_opts(opts, o);
+    TRY(check_opts(o));
+    if (o.precision != OT_PRECISION_FP64) return OT_ERR_INVALID_ARG;
+    DeviceGuard guard(t->device);
+    TRY(check_dev_ptr(t, rho));
+    TRY(check_dev_ptr(t, rho_dot));
+    TRY(check_dev_ptr(t, phi_dot));
+    TRY(check_dev_ptr(t, g_dot));
+    if (phi) TRY(check_dev_ptr(t, phi));
+    if (g) TRY(check_dev_ptr(t, g));
+    TRY(ensure_plan(t, o.theta));
+    const size_t cells = (size_t)t->h.n_nodes() * kCells;
+    if (!t->d_mom_d) {
+        TRY(dalloc(t, &t->d_mom_d, kMom * cells));
+        TRY(dalloc(t, &t->d_rec_d, kRec * cells));
+        TRY(dalloc(t, &t->d_loc_d, kLoc * cells));
+        // leaf cells' offsets and higher moments are constants: zero tangents
+        TRYC(cudaMemset(t->d_mom_d, 0, sizeof(double) * kMom * cells));
+        TRYC(cudaMemset(t->d_rec_d, 0, sizeof(double) * kRec * cells));
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    t->last_stream = s;
+    TRYC(cudaMemsetAsync(t->d_counter, 0, 4 * sizeof(int), s));
+    const TanArrays a = {t->d_mom_d, t->d_rec_d, t->d_loc_d};
+    launch_tangent(dev_tree(t), a, t->d_leaf_node, dev_plan(t), dev_lattice(t), t->h.level_first.data(),
+                   t->h.n_levels, rho, rho_dot, phi, g, phi_dot, g_dot, o.G, o.am_correction ? 1 : 0,
+                   o.self_term ? 1 : 0, std::max(1, t->num_sms * 4), s);
     TRYC(cudaGetLastError());
     return OT_OK;
 }

@@ -173,6 +173,8 @@ struct DevPlan {
     int n_items;
     int* counter;               // dynamic item counter of the persistent launch
     int near_d2;                // largest |d|^2 (cell units) of a near pair
+    int interior_only;          // 1: skip the items of leaf targets (the adjoint's
+                                // forward pass needs only interior expansions)
 };
 
 // List id of the items of an interior root: their range runs over the

@@ -562,6 +562,7 @@ __global__ void __launch_bounds__(128, std::is_same<T, double>::value ? 3 : 1)
             continue;
         }
         const bool full = t.node_leaf[it.x] < 0;
+        if (!full && p.interior_only) continue;
         if (full) {
             if (am) run_item<T, true, true>(t, p, it, lane, s_nb[w], s_lf[w], sc, ws);
             else run_item<T, true, false>(t, p, it, lane, s_nb[w], s_lf[w], sc, ws);

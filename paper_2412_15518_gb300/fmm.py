@@ -72,6 +72,7 @@ _lib.ot_last_solve_times.argtypes = [_P, ctypes.POINTER(ctypes.c_float),
                                      ctypes.POINTER(ctypes.c_float)]
 _lib.ot_solve_gravity_static.argtypes = [ctypes.POINTER(ot_tree_desc), _P, _P, _P,
                                          ctypes.POINTER(ot_solve_opts), _P]
+_lib.ot_solve_gravity_tangent.argtypes = [_P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(ot_solve_opts), _P]
 _lib.ot_get_moments.argtypes = [_P, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int32), _P]
 _lib.ot_set_launch_shape.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
 _lib.ot_alu_peaks.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -84,7 +85,7 @@ _lib.ot_error_string.restype = ctypes.c_char_p
 EXPORTS = ["ot_build_tree", "ot_compute_moments", "ot_solve_gravity", "ot_solve_gravity_host",
            "ot_gravity_backward", "ot_autotune", "ot_last_solve_times", "ot_tree_info",
            "ot_destroy_tree", "ot_error_string", "ot_solve_gravity_static", "ot_get_moments",
-           "ot_set_launch_shape", "ot_alu_peaks"]
+           "ot_set_launch_shape", "ot_alu_peaks", "ot_solve_gravity_tangent"]
 
 
 class OTError(RuntimeError):
@@ -158,6 +159,14 @@ def ot_gravity_backward(tree, rho, w1, w2, drho, opts: ot_solve_opts | None = No
     _check(_lib.ot_gravity_backward(_P(tree), _ptr(rho), _ptr(w1), _ptr(w2), _ptr(drho),
                                     ctypes.byref(opts) if opts is not None else None,
                                     _stream(stream)), "ot_gravity_backward")
+
+
+def ot_solve_gravity_tangent(tree, rho, rho_dot, phi, g, phi_dot, g_dot,
+                             opts: ot_solve_opts | None = None, stream=None):
+    _check(_lib.ot_solve_gravity_tangent(_P(tree), _ptr(rho), _ptr(rho_dot), _ptr(phi), _ptr(g),
+                                         _ptr(phi_dot), _ptr(g_dot),
+                                         ctypes.byref(opts) if opts is not None else None,
+                                         _stream(stream)), "ot_solve_gravity_tangent")
 
 
 def ot_autotune(tree, rho, phi, g, opts: ot_solve_opts | None = None, stream=None):
@@ -280,6 +289,15 @@ class Tree:
             drho = torch.empty_like(rho)
         ot_gravity_backward(self.handle, rho, w1, w2, drho, make_opts(**opts), stream)
         return drho
+
+    def tangent(self, rho, rho_dot, stream=None, with_values=False, **opts):
+        """(phi_dot, g_dot) -- or (phi, g, phi_dot, g_dot) with with_values --
+        the solve's derivative along rho_dot (the time derivative of the
+        potential and acceleration for densities changing at rho_dot)."""
+        pd, gd = self.empty_outputs()
+        phi, g = self.empty_outputs() if with_values else (None, None)
+        ot_solve_gravity_tangent(self.handle, rho, rho_dot, phi, g, pd, gd, make_opts(**opts), stream)
+        return (phi, g, pd, gd) if with_values else (pd, gd)
 
     def compute_moments(self, rho, stream=None):
         ot_compute_moments(self.handle, rho, stream)

@@ -38,6 +38,22 @@ def prec_of(fmm, form):
             "wide": fmm.OT_PRECISION_FP32_WIDE}[form]
 
 
+def error_metrics(phi, g, phi_o, g_o):
+    """Errors against the oracle per field: max-norm relative (the parity
+    bar), RMS relative, and the largest per-cell relative error with the
+    reference floored at 1e-6 of its maximum (g per cell as a vector)."""
+    out = {}
+    for name, a, b in (("phi", np.asarray(phi).reshape(-1, 1), np.asarray(phi_o).reshape(-1, 1)),
+                       ("g", np.moveaxis(np.asarray(g), -2, -1).reshape(-1, 3),
+                        np.moveaxis(np.asarray(g_o), -2, -1).reshape(-1, 3))):
+        d = np.linalg.norm(a - b, axis=1)
+        r = np.linalg.norm(b, axis=1)
+        out[name] = {"max": float(d.max() / r.max()),
+                     "rms": float(np.sqrt((d ** 2).mean() / (r ** 2).mean())),
+                     "cell": float((d / np.maximum(r, 1e-6 * r.max())).max())}
+    return out
+
+
 def residuals(lv, r, g):
     """(momentum, torque) residuals of F = m g over every leaf cell, on the
     device (r, g: device tensors [n, 512], [n, 3, 512])."""
@@ -205,6 +221,8 @@ def test_amr6_sampled(fmm):
         g = np.moveaxis(g.cpu().numpy(), 1, 2).reshape(-1, 3)[sample]
         assert rel(phi, phi_s) < tol, prec
         assert rel(g, g_s) < tol, prec
+        print(f"errors binary_amr6 (3,000 sampled cells) precision {prec}: "
+              f"{error_metrics(phi, np.swapaxes(g, -1, -2), phi_s, np.swapaxes(g_s, -1, -2))}")
     tree.close()
 
 
@@ -313,6 +331,9 @@ def test_amr8_full_size_sampled(fmm):
         assert rel(phi.view(-1)[torch.from_numpy(sample).cuda()].cpu().numpy(), phi_s) < tol, form
         gs = g.permute(0, 2, 1).reshape(-1, 3)[torch.from_numpy(sample).cuda()].cpu().numpy()
         assert rel(gs, g_s) < tol, form
+        ps = phi.view(-1)[torch.from_numpy(sample).cuda()].cpu().numpy()
+        print(f"errors binary_amr8 (2,000 sampled cells) {form}: "
+              f"{error_metrics(ps, np.swapaxes(gs, -1, -2), phi_s, np.swapaxes(g_s, -1, -2))}")
         mom, ang = residuals(lv, r, g)
         print(f"amr8 {form} residuals: momentum {mom:.2e}, torque {ang:.2e}")
         assert mom < resid[form][0] and ang < resid[form][1], form
@@ -349,4 +370,21 @@ def test_six_resident_solves_equal_independent_solves(fmm, form):
         fresh.close()
     print(f"six resident solves ({form}) vs independent: {worst:.2e}")
     assert worst < 1e-14
+    tree.close()
+
+
+@pytest.mark.parametrize("workload", ["sphere_l1", "binary_l3"])
+def test_error_metrics_every_form(fmm, workload):
+    """Every form against the full oracle solve: max-norm, RMS and floored
+    per-cell relative errors (printed; the max-norm bars asserted)."""
+    lv, rho = I.workload(workload)
+    phi_o, g_o = O.solve(lv, rho)
+    tree = fmm.Tree(lv)
+    r = torch.from_numpy(rho).cuda()
+    for form, tol in (("fp64", TOL64), ("bulk", TOL32), ("wide", TOL32)):
+        phi, g = tree.solve(r, precision=prec_of(fmm, form))
+        torch.cuda.synchronize()
+        m = error_metrics(phi.cpu().numpy(), g.cpu().numpy(), phi_o, g_o)
+        print(f"errors {workload} {form}: {m}")
+        assert m["phi"]["max"] < tol and m["g"]["max"] < tol
     tree.close()
