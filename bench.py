@@ -445,6 +445,32 @@ def run_ours(args):
             adj["frac_of_fp64_peak_est"] = adj["fp64_tflops_est"] / peaks["fp64_tflops"]
         extra["adjoint_fp64"] = adj
         del w1, w2, drho
+        # the tangent (time derivative of phi and g for densities changing at
+        # rho_dot = rho u, u uniform in [-1, 1]), FP64 dual numbers
+        rd = rho * torch.from_numpy(np.random.default_rng(7).uniform(-1.0, 1.0, rho_np.shape)).cuda()
+        pd, gd = tree.empty_outputs()
+        for _ in range(2):
+            fmm.ot_solve_gravity_tangent(tree.handle, rho, rd, None, None, pd, gd)
+        torch.cuda.synchronize()
+        tms = []
+        for _ in range(min(args.steps, 5)):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fmm.ot_solve_gravity_tangent(tree.handle, rho, rd, None, None, pd, gd)
+            e1.record(stream)
+            e1.synchronize()
+            tms.append(e0.elapsed_time(e1))
+        tmed = statistics.median(tms)
+        extra["tangent_fp64"] = {
+            "ms_per_step": tmed, "ratio_to_forward": tmed / statistics.median(solve_ms),
+            "includes": "values and tangents of every step (dual numbers)",
+            "interaction_fp64_flops": info["flops_tangent"],
+            "fp64_tflops_whole_solve": info["flops_tangent"] / (tmed / 1e3) / 1e12,
+            "frac_of_fp64_peak_whole_solve": info["flops_tangent"] / (tmed / 1e3) / 1e12 /
+                                             peaks["fp64_tflops"]}
+        del rd, pd, gd
         extra["resident_6"] = {f: resident_six(tree, rho, f, flush) for f in ("fp64", "fp32_bulk")}
         extra["resident_6"]["ms_per_six_solves_if_separate"] = 6 * statistics.median(solve_ms)
         if args.workload != "binary_l3":
@@ -566,6 +592,18 @@ def cpu_baseline(leaves, rho, budget_s: float = 20.0):
     n = c["m2l"] + c["p2p"] + c["seam"]
     out = {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
            "seconds": dt, "interactions": n}
+    # brute force beside it: direct O(N^2) summation on the 4,096-cell sphere
+    # (16.8M pairs) against the oracle's FMM solve of the same field
+    from paper_2412_15518_gb300 import inputs
+    lv1, r1 = inputs.workload("sphere_l1")
+    t0 = time.perf_counter()
+    oracle.direct(lv1, r1)
+    t_direct = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.solve(lv1, r1)
+    t_fmm = time.perf_counter() - t0
+    out["sphere_l1_direct_s"] = t_direct
+    out["sphere_l1_fmm_oracle_s"] = t_fmm
     # the same oracle on one core, on a smaller seeded sample (about 5 s)
     if cores > 1:
         oracle.set_threads(1)

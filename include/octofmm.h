@@ -154,6 +154,9 @@ typedef struct {
     double flops_adjoint;                      /* FP64 flops of one reverse sweep of
                                                   the interactions (with the
                                                   correction), counted like flops_am */
+    double flops_tangent;                      /* FP64 flops of the tangent solve's
+                                                  interactions (dual numbers: value
+                                                  and tangent, with the correction) */
 } ot_tree_stats;
 
 /* Builds the octree, its level tables, neighbour tables, stencils and work

@@ -828,6 +828,7 @@ int ot_tree_info(ot_tree* t, ot_tree_stats* st) {
     st->flops_bulk64 = t->plan.flops_bulk64;
     st->flops_bulk32 = t->plan.flops_bulk32;
     st->flops_adjoint = t->plan.flops_adjoint;
+    st->flops_tangent = t->plan.flops_tangent;
     st->n_work_items = (int64_t)t->plan.items.size();
     st->tuned_chunk = t->chunk;
     st->tuned_ctas_per_sm = t->ctas_per_sm;

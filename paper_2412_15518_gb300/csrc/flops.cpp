@@ -74,6 +74,40 @@ template <bool FULL, bool MULTI, bool AM> static double count_pair() {
     return (double)g_flops;
 }
 
+// The tangent's dual numbers: every dual operation counted as the FP64
+// operations it executes (add 2, multiply 3, fma 6, reciprocal square root
+// 5: the value's and the tangent's parts).
+static long long g_flops_dual = 0;
+struct CountDual {
+    CountDual() {}
+    CountDual(double) {}
+};
+inline CountDual operator+(CountDual, CountDual) { g_flops_dual += 2; return CountDual(); }
+inline CountDual operator-(CountDual, CountDual) { g_flops_dual += 2; return CountDual(); }
+inline CountDual operator*(CountDual, CountDual) { g_flops_dual += 3; return CountDual(); }
+inline CountDual operator-(CountDual) { return CountDual(); }
+inline CountDual& operator+=(CountDual& a, CountDual) { g_flops_dual += 2; return a; }
+inline CountDual fma_(CountDual, CountDual, CountDual) { g_flops_dual += 6; return CountDual(); }
+inline CountDual rsqrt_(CountDual) { g_flops_dual += 5; return CountDual(); }
+
+template <bool FULL, bool MULTI> static double count_tangent() {
+    g_flops_dual = 0;
+    CountDual b2[6], b3[10], bt[4];
+    Acc<CountDual> A;
+    CountDual x, y, z, m;
+    g_flops_dual += 12;  // R = (dX_A - dX_B) - d, dual
+    m2l_pair<CountDual, FULL, MULTI, true>(x, y, z, m, b2, b3, bt, A);
+    return (double)g_flops_dual;
+}
+
+void pair_flops_tangent(double out[PairClasses]) {
+    // leaf-leaf pairs: the lattice kernel on the masses and on their tangents
+    out[kLatticeFar] = out[kNearP2P] = 16.0;
+    out[kM2P] = count_tangent<false, true>();
+    out[kP2M] = count_tangent<true, false>();
+    out[kMM] = count_tangent<true, true>();
+}
+
 template <bool FULL, bool MULTI> static void count_split(double& f64, double& f32) {
     g_flops64 = g_flops32 = 0;
     CountF b2[6], b3[10], bt[4];

@@ -286,6 +286,9 @@ int build_stencil(const HostTree& t, double theta, HostPlan& p) {
     double fa[PairClasses];
     pair_flops_adjoint(fa);
     for (int c = 0; c < PairClasses; c++) p.flops_adjoint += (double)p.n_class[c] * fa[c];
+    double ft[PairClasses];
+    pair_flops_tangent(ft);
+    for (int c = 0; c < PairClasses; c++) p.flops_tangent += (double)p.n_class[c] * ft[c];
     return OT_OK;
 }
 

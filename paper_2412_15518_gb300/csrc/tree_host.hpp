@@ -76,6 +76,9 @@ void pair_flops_split(double f64[PairClasses], double f32[PairClasses]);
 // FP64 flops of the reverse of one pair of each class in the adjoint's
 // interaction sweep (with the correction).
 void pair_flops_adjoint(double out[PairClasses]);
+// FP64 flops of one pair of each class in the tangent solve (dual numbers:
+// value and tangent, with the correction).
+void pair_flops_tangent(double out[PairClasses]);
 
 // Stencil and work list of a tree for one opening parameter.
 struct HostPlan {
@@ -102,6 +105,7 @@ struct HostPlan {
     double flops_near = 0.0;                  // the part kept in FP64 by the wide FP32 form
     double flops_bulk64 = 0.0, flops_bulk32 = 0.0;  // FP32-bulk form, with the correction
     double flops_adjoint = 0.0;                     // reverse sweep of the interactions
+    double flops_tangent = 0.0;                     // tangent solve's interactions
 };
 
 // Stencil lists for theta (0.3 <= theta <= 1) and the interaction counts of

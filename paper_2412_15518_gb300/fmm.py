@@ -57,7 +57,7 @@ class ot_tree_stats(ctypes.Structure):
                 ("tuned_lattice_ctas_per_sm", ctypes.c_int32),
                 ("device_status", ctypes.c_int32), ("workspace_bytes", ctypes.c_int64),
                 ("flops_bulk64", ctypes.c_double), ("flops_bulk32", ctypes.c_double),
-                ("flops_adjoint", ctypes.c_double)]
+                ("flops_adjoint", ctypes.c_double), ("flops_tangent", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p
@@ -237,7 +237,8 @@ def ot_tree_info(tree) -> dict:
                 tuned_warps_per_cta=st.tuned_warps_per_cta,
                 tuned_lattice_ctas_per_sm=st.tuned_lattice_ctas_per_sm, device_status=st.device_status,
                 workspace_bytes=st.workspace_bytes, flops_bulk64=st.flops_bulk64,
-                flops_bulk32=st.flops_bulk32, flops_adjoint=st.flops_adjoint)
+                flops_bulk32=st.flops_bulk32, flops_adjoint=st.flops_adjoint,
+                flops_tangent=st.flops_tangent)
     _check(code, "ot_tree_info")
     return info
 
