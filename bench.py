@@ -57,7 +57,9 @@ L2_FLUSH_BYTES = 256 << 20
 # captures of the interaction kernels summarised in profiles/ (per launch;
 # binary_amr8 from its full-size one-pass capture).  A workload or form
 # without a capture of the current kernels reports null.
-TRAFFIC_BYTES = {}
+TRAFFIC_BYTES = {("binary_l3", "fp64"): 15.327e6 + 10.638e6,
+                 ("binary_l3", "fp32_bulk"): 18.347e6 + 10.638e6,
+                 ("binary_l3", "fp32_wide"): 13.474e6 + 10.664e6 + 9.563e6}
 
 WORKLOAD_TEXT = {
     "sphere_l1": "uniform level-1 octree, 8 leaves of 8^3 (4,096 cells), one polytrope",
