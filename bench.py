@@ -59,7 +59,9 @@ L2_FLUSH_BYTES = 256 << 20
 # without a capture of the current kernels reports null.
 TRAFFIC_BYTES = {("binary_l3", "fp64"): 15.327e6 + 10.638e6,
                  ("binary_l3", "fp32_bulk"): 18.347e6 + 10.638e6,
-                 ("binary_l3", "fp32_wide"): 13.474e6 + 10.664e6 + 9.563e6}
+                 ("binary_l3", "fp32_wide"): 13.474e6 + 10.664e6 + 9.563e6,
+                 ("binary_amr8", "fp64"): 5.19e9 + 1.51e9 + 0.914e9 + 0.654e9,
+                 ("binary_amr8", "fp32_bulk"): 6.06e9 + 1.50e9 + 0.911e9 + 0.653e9}
 
 WORKLOAD_TEXT = {
     "sphere_l1": "uniform level-1 octree, 8 leaves of 8^3 (4,096 cells), one polytrope",
