@@ -479,6 +479,7 @@ def run_ours(args):
         extra["resident_6"]["ms_per_six_solves_if_separate"] = 6 * statistics.median(solve_ms)
         if args.workload != "binary_l3":
             extra["binary_l3"] = companion_workload("binary_l3", flush, not args.no_autotune, peaks)
+        extra["ppm_reconstruction"] = ppm_companion(flush, peaks)
         extra["cpu_baseline"] = cpu_baseline(leaves, rho_np)
     # library kernels of one solve: leaf moments; per parent level the M2M
     # kernel for cells with interior children and/or the one for cells with
@@ -528,6 +529,68 @@ def run_ours(args):
     tree.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def hbm_peak():
+    """The measured copy bandwidth (GB/s) the driver writes beside the repo,
+    else the machine's fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def ppm_companion(flush, peaks, level=4, steps=20):
+    """The hydro solver's PPM reconstruction of the 26 directional values on
+    a uniform tree (8^level leaf sub-grids) with the five conserved fields:
+    median time and rooflines.  The kernel is FP64-bound on this GPU: per
+    cell, field and line 25 FP64 operations (one boundary value: 2 adds, 2
+    multiplies, 1 subtract, 4 min/max; the limiter: 10 adds and multiplies, 3
+    comparisons, 3 for one update) against the measured FP64 instruction rate
+    (the FMA peak / 2); the HBM share is the algorithmic bytes (each average
+    read once, its 26 values written once) over the measured copy rate."""
+    import numpy as np
+    import torch
+    from paper_2412_15518_gb300 import fmm, inputs
+    leaves = inputs.uniform_leaves(level)
+    u = torch.from_numpy(inputs.hydro_fields(leaves)).cuda()
+    tree = fmm.Tree(leaves)
+    out = torch.empty((u.shape[0], u.shape[1], 26, 512), dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        fmm.ot_ppm_reconstruct(tree.handle, u, out)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fmm.ot_ppm_reconstruct(tree.handle, u, out)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    med = statistics.median(ms)
+    cells = leaves.shape[0] * 512
+    nf = u.shape[1]
+    nbytes = cells * nf * 8 * (1 + 26)
+    ops = cells * nf * 13 * 25
+    hbm, src = hbm_peak()
+    gops = ops / (med / 1e3) / 1e12
+    peak_ops = peaks["fp64_tflops"] / 2.0
+    tree.close()
+    del u, out
+    return {"workload": f"uniform level-{level} octree ({leaves.shape[0]} leaf sub-grids, {cells} cells), "
+                        "5 conserved fields of the rotating binary",
+            "ms_per_launch": med, "cells_per_s": cells / (med / 1e3),
+            "roofline": {"bound": "alu", "achieved": gops, "peak": peak_ops, "unit": "T FP64 ops/s",
+                         "frac": gops / peak_ops,
+                         "peak_source": "measured FP64 FMA rate (ot_alu_peaks) / 2, one FP64 operation "
+                                        "per lane per issue slot",
+                         "fp64_ops_per_launch": ops, "fp64_ops_per_cell_field_line": 25},
+            "hbm": {"achieved_gbs": nbytes / (med / 1e3) / 1e9, "peak_gbs": hbm, "peak_source": src,
+                    "frac": nbytes / (med / 1e3) / 1e9 / hbm, "bytes_per_launch": nbytes}}
 
 
 def companion_workload(name, flush, autotune, peaks):

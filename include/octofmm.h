@@ -221,6 +221,22 @@ int ot_solve_gravity_tangent(ot_tree* tree, const double* rho, const double* rho
                              double* g, double* phi_dot, double* g_dot, const ot_solve_opts* opts,
                              void* stream);
 
+/* PPM reconstruction of the hydro solver's 26 directional cell values, the
+ * second workload on the same tree (Sec. 2: the finite-volume hydrodynamics
+ * computes the values at all 26 spatial directions of a grid cell with the
+ * piecewise parabolic method).  For each of the 13 lines through a cell (the
+ * 26 neighbour offsets up to sign), 1-D PPM (Colella & Woodward 1984) on the
+ * cell averages along the line: fourth-order boundary values held between the
+ * neighbouring averages, then the parabola constraints.  Cells outside the
+ * domain continue the averages by clamping each index into the grid.  The
+ * tree's leaves must all be at one level (OT_ERR_INVALID_ARG otherwise).
+ * u: device float64 [n_leaf][n_fields][512] cell averages (1 <= n_fields <=
+ * 64); out: device float64 [n_leaf][n_fields][26][512], direction index of
+ * offset o in {-1,0,1}^3 = (ox+1) + 3 (oy+1) + 9 (oz+1), minus 1 above 13.
+ * FP64, written so that the limiter's decisions match a plain FP64
+ * evaluation of the same formulas (no fused multiply-adds). */
+int ot_ppm_reconstruct(ot_tree* tree, const double* u, int n_fields, double* out, void* stream);
+
 /* Chooses the persistent launch's stencil-chunk length and the CTAs per SM
  * of the general kernel (and, wide FP32 form, of the lattice kernels) for
  * this plan: every candidate is timed as the whole solve graph it would run,

@@ -15,6 +15,7 @@
 #include "adjoint.hpp"
 #include "kernels.hpp"
 #include "lattice.hpp"
+#include "ppm.hpp"
 #include "tangent.hpp"
 #include "tree_host.hpp"
 
@@ -667,6 +668,22 @@ int ot_solve_gravity_tangent(ot_tree* t, const double* rho, const double* rho_do
     launch_tangent(dev_tree(t), a, t->d_leaf_node, dev_plan(t), dev_lattice(t), t->h.level_first.data(),
                    t->h.n_levels, rho, rho_dot, phi, g, phi_dot, g_dot, o.G, o.am_correction ? 1 : 0,
                    o.self_term ? 1 : 0, std::max(1, t->num_sms * 4), s);
+    TRYC(cudaGetLastError());
+    return OT_OK;
+}
+
+int ot_ppm_reconstruct(ot_tree* t, const double* u, int n_fields, double* out, void* stream) {
+    if (!t) return OT_ERR_BAD_POINTER;
+    if (t->device < 0 || n_fields < 1 || n_fields > 64) return OT_ERR_INVALID_ARG;
+    const HostTree& h = t->h;
+    const int L = h.n_levels - 1;
+    if (h.leaf_nodes_at(L) != h.n_leaf) return OT_ERR_INVALID_ARG;  // all leaves at one level
+    DeviceGuard guard(t->device);
+    TRY(check_dev_ptr(t, u));
+    TRY(check_dev_ptr(t, out));
+    cudaStream_t s = (cudaStream_t)stream;
+    t->last_stream = s;
+    launch_ppm(dev_tree(t), t->d_leaf_node, u, n_fields, 8 << L, out, s);
     TRYC(cudaGetLastError());
     return OT_OK;
 }

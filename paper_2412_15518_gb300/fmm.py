@@ -73,6 +73,7 @@ _lib.ot_last_solve_times.argtypes = [_P, ctypes.POINTER(ctypes.c_float),
 _lib.ot_solve_gravity_static.argtypes = [ctypes.POINTER(ot_tree_desc), _P, _P, _P,
                                          ctypes.POINTER(ot_solve_opts), _P]
 _lib.ot_solve_gravity_tangent.argtypes = [_P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(ot_solve_opts), _P]
+_lib.ot_ppm_reconstruct.argtypes = [_P, _P, ctypes.c_int, _P, _P]
 _lib.ot_get_moments.argtypes = [_P, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int32), _P]
 _lib.ot_set_launch_shape.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
 _lib.ot_alu_peaks.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -85,7 +86,8 @@ _lib.ot_error_string.restype = ctypes.c_char_p
 EXPORTS = ["ot_build_tree", "ot_compute_moments", "ot_solve_gravity", "ot_solve_gravity_host",
            "ot_gravity_backward", "ot_autotune", "ot_last_solve_times", "ot_tree_info",
            "ot_destroy_tree", "ot_error_string", "ot_solve_gravity_static", "ot_get_moments",
-           "ot_set_launch_shape", "ot_alu_peaks", "ot_solve_gravity_tangent"]
+           "ot_set_launch_shape", "ot_alu_peaks", "ot_solve_gravity_tangent",
+           "ot_ppm_reconstruct"]
 
 
 class OTError(RuntimeError):
@@ -167,6 +169,12 @@ def ot_solve_gravity_tangent(tree, rho, rho_dot, phi, g, phi_dot, g_dot,
                                          _ptr(phi_dot), _ptr(g_dot),
                                          ctypes.byref(opts) if opts is not None else None,
                                          _stream(stream)), "ot_solve_gravity_tangent")
+
+
+def ot_ppm_reconstruct(tree, u, out, stream=None):
+    """u: device [n_leaf, n_fields, 512] -> out: device [n_leaf, n_fields, 26, 512]."""
+    _check(_lib.ot_ppm_reconstruct(_P(tree), _ptr(u), int(u.shape[1]), _ptr(out), _stream(stream)),
+           "ot_ppm_reconstruct")
 
 
 def ot_autotune(tree, rho, phi, g, opts: ot_solve_opts | None = None, stream=None):
@@ -299,6 +307,13 @@ class Tree:
         phi, g = self.empty_outputs() if with_values else (None, None)
         ot_solve_gravity_tangent(self.handle, rho, rho_dot, phi, g, pd, gd, make_opts(**opts), stream)
         return (phi, g, pd, gd) if with_values else (pd, gd)
+
+    def ppm(self, u, stream=None):
+        """The 26 directional PPM values [n_leaf, n_fields, 26, 512] of the
+        cell averages u [n_leaf, n_fields, 512] (leaves all at one level)."""
+        out = torch.empty((u.shape[0], u.shape[1], 26, 512), dtype=torch.float64, device=u.device)
+        ot_ppm_reconstruct(self.handle, u, out, stream)
+        return out
 
     def compute_moments(self, rho, stream=None):
         ot_compute_moments(self.handle, rho, stream)

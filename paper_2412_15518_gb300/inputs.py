@@ -177,6 +177,24 @@ def amr_leaves(lmax: int, m_thr: float, stars, lmin: int = 1, do_balance: bool =
     return np.ascontiguousarray(out)
 
 
+def hydro_fields(leaves, stars=BINARY, seed: int = 0, omega: float = 2.0):
+    """Five conserved fields [n_leaf, 5, 512] for the hydro reconstruction:
+    density (the binary's polytropes in the atmosphere, with noise), momentum
+    of a rigid rotation about the z axis through the domain centre at angular
+    speed omega (the binary's orbit) with 1e-3 relative noise, and the total
+    energy of a polytropic gas, p = rho^(5/3) (gamma = 5/3), plus the kinetic
+    energy."""
+    rho = density(leaves, stars, seed)
+    x = cell_centres(leaves) - 0.5                                    # [n, 512, 3]
+    rng = np.random.Generator(np.random.PCG64(seed + 100))
+    vx = -omega * x[..., 1] * (1.0 + 1e-3 * rng.uniform(-1.0, 1.0, rho.shape))
+    vy = omega * x[..., 0] * (1.0 + 1e-3 * rng.uniform(-1.0, 1.0, rho.shape))
+    vz = 1e-3 * omega * rng.uniform(-1.0, 1.0, rho.shape) * np.abs(x[..., 2])
+    e_int = rho ** (5.0 / 3.0) / (5.0 / 3.0 - 1.0)
+    E = e_int + 0.5 * rho * (vx * vx + vy * vy + vz * vz)
+    return np.ascontiguousarray(np.stack([rho, rho * vx, rho * vy, rho * vz, E], axis=1))
+
+
 def weights(n_leaf: int, seed_w1: int = 1, seed_w2: int = 2):
     """Gaussian weights w1 [n_leaf, 512] and w2 [n_leaf, 3, 512] of the
     functional J = sum(w1 phi + w2 . g)."""
