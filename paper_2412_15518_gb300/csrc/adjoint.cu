@@ -353,6 +353,12 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
         // this cell's target-side adjoints (the correction's mass ratio) and
         // centre-of-mass adjoint
         if (!cleaf) {
+            if (am && mC != 0.0) {
+                double aC[3];
+#pragma unroll
+                for (int r = 0; r < 3; r++) aC[r] = locbar[(20 + r) * N + cell];
+                reverse_target_finish(acc, aC, (G / 6.0) / mC);
+            }
             atomicAdd(mombar + cell, acc.mA);
 #pragma unroll
             for (int s = 0; s < 3; s++) atomicAdd(mombar + (1 + s) * N + cell, acc.R[s]);

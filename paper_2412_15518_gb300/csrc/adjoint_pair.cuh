@@ -29,6 +29,7 @@ template <class T> struct PairAdjOutT {
     T mB, M2B[6], M3B[10];
     T mA, M3A[10];
     T R[3];
+    T A4[15];  // target side: sum over partners of m_B f4 R^4 (reverse_target_finish)
 };
 using PairAdjOut = PairAdjOutT<double>;
 
@@ -44,6 +45,8 @@ template <class T> __host__ __device__ __forceinline__ void adj_zero(PairAdjOutT
     }
 #pragma unroll
     for (int i = 0; i < 3; i++) o.R[i] = 0.0;
+#pragma unroll
+    for (int i = 0; i < 15; i++) o.A4[i] = 0.0;
 }
 
 // Symmetric rank-2 (packed xx xy xz yy yz zz) times vector.
@@ -194,8 +197,8 @@ __host__ __device__ __forceinline__ void m2l_pair_reverse(
     s4_parts(E3, m, e3);
     // s4a = a . (D4 : M3_A) (the ratio part of the correction)
     T s4a = 0.0;
+    S4Parts<T> qa;
     if (useA) {
-        S4Parts<T> qa;
         s4_parts(M3A, m, qa);
         s4a = f4 * aR * qa.q3 + 3.0 * f3 * (a[0] * qa.q2[0] + a[1] * qa.q2[1] + a[2] * qa.q2[2] + aR * qa.Rt) +
               3.0 * f2 * (a[0] * qa.t[0] + a[1] * qa.t[1] + a[2] * qa.t[2]);
@@ -222,11 +225,30 @@ __host__ __device__ __forceinline__ void m2l_pair_reverse(
         }
     }
     if (TGT && useA) {
-        // the ratio term -(m_B / m_A) M3_A: dJ/dM3_A and dJ/dm_A
-        const T kr = k6 * ratio;
-        add_rank3(out.M3A, m, a, kr * f4 * aR, kr * f3, kr * f3 * aR, kr * f2);
+        // the ratio term -(m_B / m_A) M3_A: dJ/dm_A here; dJ/dM3_A =
+        // (G/6) / m_A a . sum_B m_B D4(R_B) from the partners' quartic sum,
+        // contracted once per target (reverse_target_finish)
+        const T s4 = mB * f4;
+        const T txx = s4 * m.xx, txy = s4 * m.xy, txz = s4 * m.xz, tyy = s4 * m.yy, tyz = s4 * m.yz,
+                tzz = s4 * m.zz;
+        out.A4[0] += txx * m.xx;
+        out.A4[1] += txx * m.xy;
+        out.A4[2] += txx * m.xz;
+        out.A4[3] += txx * m.yy;
+        out.A4[4] += txx * m.yz;
+        out.A4[5] += txx * m.zz;
+        out.A4[6] += txy * m.yy;
+        out.A4[7] += txy * m.yz;
+        out.A4[8] += txy * m.zz;
+        out.A4[9] += txz * m.zz;
+        out.A4[10] += tyy * m.yy;
+        out.A4[11] += tyy * m.yz;
+        out.A4[12] += tyy * m.zz;
+        out.A4[13] += tyz * m.zz;
+        out.A4[14] += tzz * m.zz;
         out.mA += -k6 * s4a * mB * iA * iA;
     }
+    S4Parts<T> m3;  // the partner's octupole parts (interior partners)
     if (want_R) {
         // mB E0 D0 + mB E1.D1 + mB E2:D2 + mB E3:D3
         const T cR = mB * (E0 * f1 + f2 * (E1R + trE2) + f3 * RE2R + f4 * e3.q3 + 3.0 * f3 * e3.Rt);
@@ -242,7 +264,6 @@ __host__ __device__ __forceinline__ void m2l_pair_reverse(
             const T xMx = MR[0] * x + MR[1] * y + MR[2] * z;
             const T trM = M2B[0] + M2B[3] + M2B[5];
             const T E1MR = E1[0] * MR[0] + E1[1] * MR[1] + E1[2] * MR[2];
-            S4Parts<T> m3;
             s4_parts(M3B, m, m3);
             const T cr = 0.5 * E0 * (f3 * xMx + f2 * trM) - (1.0 / 6.0) * E0 * f4 * m3.q3 -
                               0.5 * E0 * f3 * m3.Rt + 0.5 * f4 * E1R * xMx + 0.5 * f3 * (2.0 * E1MR + E1R * trM);
@@ -260,8 +281,16 @@ __host__ __device__ __forceinline__ void m2l_pair_reverse(
             T Q[10];
 #pragma unroll
             for (int n = 0; n < 10; n++) Q[n] = (multiB ? M3B[n] : 0.0) - (useA ? ratio * M3A[n] : 0.0);
+            // the parts of Q are linear in Q: from the octupoles' own parts
             S4Parts<T> q;
-            s4_parts(Q, m, q);
+            const T rq = useA ? ratio : T(0.0);
+#pragma unroll
+            for (int p = 0; p < 3; p++) {
+                q.q2[p] = (multiB ? m3.q2[p] : T(0.0)) - (useA ? rq * qa.q2[p] : T(0.0));
+                q.t[p] = (multiB ? m3.t[p] : T(0.0)) - (useA ? rq * qa.t[p] : T(0.0));
+            }
+            q.q3 = (multiB ? m3.q3 : T(0.0)) - (useA ? rq * qa.q3 : T(0.0));
+            q.Rt = (multiB ? m3.Rt : T(0.0)) - (useA ? rq * qa.Rt : T(0.0));
             T u[3];  // u_p = Q_pik a_i R_k
             sym3_contract(Q, a[0] * x, a[1] * y, a[2] * z, a[0] * y + a[1] * x, a[0] * z + a[2] * x,
                           a[1] * z + a[2] * y, u);
@@ -274,6 +303,50 @@ __host__ __device__ __forceinline__ void m2l_pair_reverse(
                 gR[p] += -sR * k6 * (cv * R[p] + ca * a[p] + 3.0 * f4 * aR * q.q2[p] + 6.0 * f3 * u[p] +
                                         3.0 * f3 * aR * q.t[p]);
         }
+    }
+}
+
+
+// dJ/dM3_A of a target from the quartic sum A4 = sum_B m_B f4 R^4 that the
+// target's pairs accumulated: dJ/dM3_A = (G/6) / m_A a . sum_B m_B D4(R_B),
+// where sum m D4 = A4 + sym(delta Q) + c0 sym(delta delta) with Q = sum m f3
+// R R = -tr(A4) / 7 and c0 = sum m f2 = -tr(Q) / 5 (D4 is traceless); so per
+// packed jkl: (a.A4)_jkl + a_j Q_kl + a_k Q_jl + a_l Q_jk + delta_jk (Q a)_l
+// + delta_jl (Q a)_k + delta_kl (Q a)_j + c0 (a_j delta_kl + a_k delta_jl
+// + a_l delta_jk).  kr = (G/6) / m_A.
+template <class T>
+__host__ __device__ __forceinline__ void reverse_target_finish(PairAdjOutT<T>& o, const T* a, T kr) {
+    const T* q = o.A4;  // xxxx xxxy xxxz xxyy xxyz xxzz xyyy xyyz xyzz xzzz yyyy yyyz yyzz yzzz zzzz
+    const T s7 = T(-1.0 / 7.0);
+    const T Qxx = s7 * (q[0] + q[3] + q[5]), Qxy = s7 * (q[1] + q[6] + q[8]);
+    const T Qxz = s7 * (q[2] + q[7] + q[9]), Qyy = s7 * (q[3] + q[10] + q[12]);
+    const T Qyz = s7 * (q[4] + q[11] + q[13]), Qzz = s7 * (q[5] + q[12] + q[14]);
+    const T c0 = T(-0.2) * (Qxx + Qyy + Qzz);
+    const T Qa[3] = {Qxx * a[0] + Qxy * a[1] + Qxz * a[2], Qxy * a[0] + Qyy * a[1] + Qyz * a[2],
+                     Qxz * a[0] + Qyz * a[1] + Qzz * a[2]};
+    // (a . A4)_jkl for the packed rank-3 jkl: sum_i a_i A4_ijkl
+    const T aA[10] = {
+        a[0] * q[0] + a[1] * q[1] + a[2] * q[2],     // xxx
+        a[0] * q[1] + a[1] * q[3] + a[2] * q[4],     // xxy
+        a[0] * q[2] + a[1] * q[4] + a[2] * q[5],     // xxz
+        a[0] * q[3] + a[1] * q[6] + a[2] * q[7],     // xyy
+        a[0] * q[4] + a[1] * q[7] + a[2] * q[8],     // xyz
+        a[0] * q[5] + a[1] * q[8] + a[2] * q[9],     // xzz
+        a[0] * q[6] + a[1] * q[10] + a[2] * q[11],   // yyy
+        a[0] * q[7] + a[1] * q[11] + a[2] * q[12],   // yyz
+        a[0] * q[8] + a[1] * q[12] + a[2] * q[13],   // yzz
+        a[0] * q[9] + a[1] * q[13] + a[2] * q[14]};  // zzz
+    const T Q2[3][3] = {{Qxx, Qxy, Qxz}, {Qxy, Qyy, Qyz}, {Qxz, Qyz, Qzz}};
+    const int P3[10][3] = {{0, 0, 0}, {0, 0, 1}, {0, 0, 2}, {0, 1, 1}, {0, 1, 2},
+                           {0, 2, 2}, {1, 1, 1}, {1, 1, 2}, {1, 2, 2}, {2, 2, 2}};
+#pragma unroll
+    for (int n = 0; n < 10; n++) {
+        const int j = P3[n][0], k = P3[n][1], l = P3[n][2];
+        T v = aA[n] + a[j] * Q2[k][l] + a[k] * Q2[j][l] + a[l] * Q2[j][k];
+        if (j == k) v += Qa[l] + c0 * a[l];
+        if (j == l) v += Qa[k] + c0 * a[k];
+        if (k == l) v += Qa[j] + c0 * a[j];
+        o.M3A[n] += kr * v;
     }
 }
 

@@ -108,6 +108,7 @@ int main() {
         double gR[3] = {0.0, 0.0, 0.0};
         m2l_pair_reverse<true, true>(R, G, am, mB, M2B, M3B, true, mA, M3A, true, E0, E1, E2, E3, a, true,
                                      1.0, gR, o);
+        if (am && mA != 0.0) reverse_target_finish(o, a, (G / 6.0) / mA);
         std::printf(" %.17g", o.mB);
         for (double v : o.M2B) std::printf(" %.17g", v);
         for (double v : o.M3B) std::printf(" %.17g", v);
