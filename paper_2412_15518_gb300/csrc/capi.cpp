@@ -76,6 +76,10 @@ struct ot_tree {
     size_t item_entries_cap = 0;
     int4* d_items_adj = nullptr;
     size_t items_adj_cap = 0;
+    int4* d_items_grp = nullptr;
+    size_t items_grp_cap = 0;
+    uint16_t* d_grp_cells = nullptr;
+    size_t grp_cells_cap = 0;
     int* d_hoff_far = nullptr;
     int* d_hoff_near = nullptr;
     int* d_lattice_nodes = nullptr;
@@ -179,6 +183,9 @@ DevPlan dev_plan(const ot_tree* t) {
     p.items = t->d_items;
     p.item_entries = t->d_item_entries;
     p.n_items = (int)t->plan.items.size();
+    p.items_grp = t->d_items_grp;
+    p.n_items_grp = (int)t->plan.items_grp.size();
+    p.grp_cells = t->d_grp_cells;
     p.counter = t->d_counter;
     p.near_d2 = t->plan.near_d2;
     return p;
@@ -237,6 +244,16 @@ int ensure_plan(ot_tree* t, double theta) {
         t->item_entries_cap = std::max<size_t>(1, p.item_entries.size());
         TRY(dalloc(t, &t->d_item_entries, t->item_entries_cap));
     }
+    if (p.items_grp.size() > t->items_grp_cap || !t->d_items_grp) {
+        cudaFree(t->d_items_grp);
+        t->items_grp_cap = std::max<size_t>(1, p.items_grp.size());
+        TRY(dalloc(t, &t->d_items_grp, t->items_grp_cap));
+    }
+    if (p.grp_cells.size() > t->grp_cells_cap || !t->d_grp_cells) {
+        cudaFree(t->d_grp_cells);
+        t->grp_cells_cap = std::max<size_t>(1, p.grp_cells.size());
+        TRY(dalloc(t, &t->d_grp_cells, t->grp_cells_cap));
+    }
     if (p.items_adj.size() > t->items_adj_cap) {
         cudaFree(t->d_items_adj);
         t->items_adj_cap = p.items_adj.size();
@@ -244,6 +261,10 @@ int ensure_plan(ot_tree* t, double theta) {
     }
     TRY(upload(t->d_entries, p.entries));
     TRY(upload(t->d_item_entries, p.item_entries));
+    TRY(upload(t->d_grp_cells, p.grp_cells));
+    if (!p.items_grp.empty())
+        TRYC(cudaMemcpy(t->d_items_grp, p.items_grp.data(), p.items_grp.size() * sizeof(Item),
+                        cudaMemcpyHostToDevice));
     TRY(upload(t->d_hoff_far, p.hoff_far));
     TRY(upload(t->d_hoff_near, p.hoff_near));
     TRY(upload(t->d_lattice_nodes, p.lattice_nodes));
@@ -519,7 +540,7 @@ void ot_destroy_tree(ot_tree* t) {
                         t->d_status, t->d_entries, t->d_tab64, t->d_tab32, t->d_list_first,
                         t->d_list_len, t->d_items, t->d_counter, t->d_rho_in, t->d_phi_out,
                         t->d_hoff_far, t->d_hoff_near, t->d_lattice_nodes, t->d_items_adj, t->d_item_entries,
-                        t->d_off64, t->d_off32,
+                        t->d_off64, t->d_off32, t->d_items_grp, t->d_grp_cells,
                         t->d_g_out, t->d_locbar, t->d_mombar, t->d_mom_d, t->d_rec_d, t->d_loc_d};
         for (void* p : ptrs)
             if (p) cudaFree(p);

@@ -171,6 +171,9 @@ struct DevPlan {
     const int4* items;          // [n_items]
     const int* item_entries;    // forward items: list positions of their ranges
     int n_items;
+    const int4* items_grp;      // [n_items_grp] the FP64 and FP32-bulk forms' items
+    int n_items_grp;            //   (cells grouped by pair count, kGroupList)
+    const unsigned short* grp_cells;  // 32 node-local cell indices per group
     int* counter;               // dynamic item counter of the persistent launch
     int near_d2;                // largest |d|^2 (cell units) of a near pair
     int interior_only;          // 1: skip the items of leaf targets (the adjoint's
@@ -180,6 +183,10 @@ struct DevPlan {
 // List id of the items of an interior root: their range runs over the
 // root's own 512 cells as sources instead of over stencil entries.
 constexpr int kRootList = 9;
+// List id of grouped items: 32 cells of one node of level >= 1 chosen by
+// their number of pairs (grp_cells), each walking the list of its own parity
+// class over the item's range of list positions.
+constexpr int kGroupList = 10;
 
 __host__ __device__ inline int pack_entry(int dx, int dy, int dz, int near) {
     return (dx + 16) | ((dy + 16) << 5) | ((dz + 16) << 10) | (near << 15);
@@ -228,7 +235,9 @@ struct DevLattice {
 // list (forward launch); of the list itself (adjoint); of the root's cells
 // (kRootList).  32 target cells per item: the
 // cells of one parity class (px, py, pz) with z-index 2 (2 half + q) + pz,
-// q in {0, 1}.
+// q in {0, 1}.  Grouped items (list kGroupList): y = level | group << 8 |
+// list << 12, z = k0 | k1 << 16 (a range of list positions, each lane's
+// clipped to its own list), w = index of the group's 32 cells in grp_cells.
 __host__ __device__ inline int item_level(int4 it) { return it.y & 0xff; }
 __host__ __device__ inline int item_parity(int4 it) { return (it.y >> 8) & 7; }
 __host__ __device__ inline int item_half(int4 it) { return (it.y >> 11) & 1; }

@@ -195,15 +195,56 @@ __device__ __forceinline__ int issue32(const DevTree& t, WarpStage32& ws, int q,
     return sleaf ? 1 : 2;
 }
 
+// Node-local target cell (i, j, k) of a lane: from the item's parity class
+// and half, or from its group's cell list (grouped items).
+__device__ __forceinline__ void item_cell(const DevPlan& p, const int4 it, int lane, int& i, int& j,
+                                          int& k) {
+    if (item_list(it) == kGroupList) {
+        const int c = __ldg(p.grp_cells + it.w + lane);
+        i = c & 7;
+        j = (c >> 3) & 7;
+        k = c >> 6;
+    } else {
+        const int par = item_parity(it), half = item_half(it);
+        i = 2 * (lane & 3) + (par & 1);
+        j = 2 * ((lane >> 2) & 3) + ((par >> 1) & 1);
+        k = 2 * (2 * half + (lane >> 4)) + (par >> 2);
+    }
+}
+
+// Grouped items (level >= 1): moves q, this lane's position in the list of
+// its own parity class, to its next pair in [q, qend) and returns the pair's
+// kind (2: a leaf source, 3: an interior source; 0: no pair left), with the
+// source's node and node-local cell.  An interior target pairs with every
+// leaf source and with the far interior ones (near interior pairs descend to
+// the next level); a leaf target only with interior sources (leaf-leaf
+// pairs are the lattice kernel's).
+template <bool FULL>
+__device__ __forceinline__ int next_grouped(const DevPlan& p, const int* s_nb, const int* s_lf, int base,
+                                            int qend, int i, int j, int k, int& q, int& nb, int& lc) {
+    for (; q < qend; q++) {
+        const int e = __ldg(p.entries + base + q);
+        const int sx = i + entry_dx(e), sy = j + entry_dy(e), sz = k + entry_dz(e);
+        const int slot = ((sx >> 3) + 1) + 3 * ((sy >> 3) + 1) + 9 * ((sz >> 3) + 1);
+        const int n = s_nb[slot];
+        if (n < 0) continue;  // outside the domain, or covered by a coarser leaf
+        const bool sleaf = s_lf[slot] != 0;
+        if (FULL ? (!sleaf && entry_near(e)) : sleaf) continue;
+        nb = n;
+        lc = (sx & 7) + 8 * (sy & 7) + 64 * (sz & 7);
+        return sleaf ? 2 : 3;
+    }
+    return 0;
+}
+
 template <class T, bool FULL, bool AM>
 __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, const int4 it,
                                          const int lane, const int* s_nb, const int* s_lf,
                                          const LevelScales& sc, WarpStage32* ws) {
     const int node = it.x;
-    const int L = item_level(it), par = item_parity(it), half = item_half(it);
-    const int i = 2 * (lane & 3) + (par & 1);
-    const int j = 2 * ((lane >> 2) & 3) + ((par >> 1) & 1);
-    const int k = 2 * (2 * half + (lane >> 4)) + (par >> 2);
+    const int L = item_level(it);
+    int i, j, k;
+    item_cell(p, it, lane, i, j, k);
     const long long N = t.n_cells;
     const long long cell = (long long)node * kCells + i + 8 * j + 64 * k;
     T ma, dax, day, daz;
@@ -252,6 +293,35 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
             for (int a = 0; a < 3; a++) atomicAdd(loc + (20 + a) * N + cell, scaled(A.S[a] - P[a], sa));
         }
     };
+    // One pair with a source of kind 2 (a leaf cell) or 3 (an interior cell)
+    // in cell src, stencil entry ent.  With multi (some lane of the warp has
+    // an interior source) a leaf source takes the multipole formula with
+    // zero moments: the same sums, in the warp's single pass.
+    auto pair_at = [&](int kind, bool multi, long long src, int ent) {
+        T m, bx, by, bz, ox, oy, oz;
+        load_head(t, src, m, bx, by, bz);
+        load_off(p, ent, ox, oy, oz);
+        // R' = X_A - X_B in cell units: the source sits at offset d from the target
+        const T x = (dax - bx) - ox;
+        const T y = (day - by) - oy;
+        const T z = (daz - bz) - oz;
+        if (!multi) {
+            m2l_pair<T, FULL, false, AM>(x, y, z, m, nullptr, nullptr, nullptr, A);
+            return;
+        }
+        T b2[6], b3[10], bt[4];
+        if (kind == 3) {
+            load_tail(t, src, b2, b3, bt);
+        } else {
+#pragma unroll
+            for (int r = 0; r < 6; r++) b2[r] = T(0.0);
+#pragma unroll
+            for (int r = 0; r < 10; r++) b3[r] = T(0.0);
+#pragma unroll
+            for (int r = 0; r < 4; r++) bt[r] = T(0.0);
+        }
+        m2l_pair<T, FULL, true, AM>(x, y, z, m, b2, b3, bt, A);
+    };
     if (FULL && item_list(it) == kRootList) {
         // the interior root: sources are the root's own cells [z, w), the
         // same cell for every lane (a broadcast load); a pair is far iff
@@ -292,17 +362,22 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
                     issue32<FULL>(t, *ws, q + 1, q0, q1, i, j, k, lane, s_nb, s_lf, st ^ 1, d_next);
                 cp_async_commit();
                 cp_async_wait1();  // this lane's copies of pair q are done
+                // leaf sources of a warp that also holds interior ones take the
+                // multipole formula with zero moments, in the same pass
+                const bool multi = __any_sync(0xffffffffu, kind == 2);
                 if (kind) {
                     const float4 h = ws->rec[st][0][lane];
                     // R' = X_A - X_B in cell units: the source sits at offset d
                     const float x = (dax - h.y) - d.x;
                     const float y = (day - h.z) - d.y;
                     const float z = (daz - h.w) - d.z;
-                    if (kind == 1) {
+                    if (!multi) {
                         m2l_pair<float, FULL, false, AM>(x, y, z, h.x, nullptr, nullptr, nullptr, A);
                     } else {
-                        const float4 v1 = ws->rec[st][1][lane], v2 = ws->rec[st][2][lane],
-                                     v3 = ws->rec[st][3][lane], v4 = ws->rec[st][4][lane];
+                        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                        const bool lf = kind == 1;
+                        const float4 v1 = lf ? z4 : ws->rec[st][1][lane], v2 = lf ? z4 : ws->rec[st][2][lane],
+                                     v3 = lf ? z4 : ws->rec[st][3][lane], v4 = lf ? z4 : ws->rec[st][4][lane];
                         const float b2[6] = {v1.x, v1.y, v1.z, v1.w, v2.x, v2.y};
                         const float b3[10] = {v2.z, v2.w, v3.x, v3.y, v3.z, v3.w, v4.x, v4.y, v4.z, v4.w};
                         const float bt[4] = {b3[0] + b3[3] + b3[5], b3[1] + b3[6] + b3[8],
@@ -322,6 +397,22 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
             cp_async_wait0();
             __syncwarp();  // the stage and entry buffers are reused by the next item
         }
+    } else if (std::is_same<T, double>::value && item_list(it) == kGroupList) {
+        // grouped item: every lane walks its own list and computes its pairs
+        // one after another; the warp runs while any lane has a pair left
+        const int par = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
+        const int base = __ldg(p.list_first + par);
+        const int qend = min(it.z >> 16, __ldg(p.list_len + par));
+        int q = it.z & 0xffff;
+#pragma unroll 1
+        for (;;) {
+            int nb = 0, lc = 0;
+            const int kind = next_grouped<FULL>(p, s_nb, s_lf, base, qend, i, j, k, q, nb, lc);
+            if (!__any_sync(0xffffffffu, kind != 0)) break;
+            const bool multi = __any_sync(0xffffffffu, kind == 3);
+            if (kind != 0) pair_at(kind, multi, (long long)nb * kCells + lc, base + q);
+            q++;
+        }
     } else {
     const int base = p.list_first[item_list(it)];
 #pragma unroll 1
@@ -332,11 +423,23 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
         const int sx = i + dx, sy = j + dy, sz = k + dz;
         const int slot = ((sx >> 3) + 1) + 3 * ((sy >> 3) + 1) + 9 * ((sz >> 3) + 1);
         const int nb = s_nb[slot];
-        if (nb < 0) continue;  // outside the domain, or covered by a coarser leaf
         const bool sleaf = s_lf[slot] != 0;
+        // 0: no pair (outside the domain, covered by a coarser leaf, a
+        // leaf-leaf pair of level >= 1 for the lattice kernel, or a near
+        // pair of two interior cells resolved at the next level); 1: two
+        // point masses of a leaf root; 2: a leaf source; 3: an interior one
+        int kind = 0;
+        if (nb >= 0) {
+            if (!FULL && sleaf) kind = L > 0 ? 0 : 1;
+            else if (!(FULL && !sleaf && entry_near(e))) kind = sleaf ? 2 : 3;
+        }
+        // where the warp holds both leaf and interior sources, the leaf ones
+        // take the multipole formula with zero moments (the same sums) rather
+        // than a second, divergent pass
+        const bool multi = __any_sync(0xffffffffu, kind == 3);
+        if (kind == 0) continue;
         const long long sc = (long long)nb * kCells + (sx & 7) + 8 * (sy & 7) + 64 * (sz & 7);
-        if (!FULL && sleaf) {
-            if (L > 0) continue;  // leaf-leaf pairs of level >= 1: lattice kernel
+        if (kind == 1) {
             // two point masses on the lattice (a leaf root)
             if (sizeof(T) == 4 && entry_near(e)) {
                 double a, b, c, d;
@@ -358,21 +461,7 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
             }
             continue;
         }
-        if (FULL && !sleaf && entry_near(e)) continue;  // resolved at the next level
-        T m, bx, by, bz, ox, oy, oz;
-        load_head(t, sc, m, bx, by, bz);
-        load_off(p, base + q, ox, oy, oz);
-        // R' = X_A - X_B in cell units: the source sits at offset d from the target
-        const T x = (dax - bx) - ox;
-        const T y = (day - by) - oy;
-        const T z = (daz - bz) - oz;
-        if (sleaf) {
-            m2l_pair<T, FULL, false, AM>(x, y, z, m, nullptr, nullptr, nullptr, A);
-        } else {
-            T b2[6], b3[10], bt[4];
-            load_tail(t, sc, b2, b3, bt);
-            m2l_pair<T, FULL, true, AM>(x, y, z, m, b2, b3, bt, A);
-        }
+        pair_at(kind, multi, sc, base + q);
     }
     }
     flush();
@@ -388,10 +477,9 @@ __device__ __forceinline__ void run_item_split(const DevTree& t, const DevPlan& 
                                                const int lane, const int* s_nb, const int* s_lf,
                                                const LevelScales& sc) {
     const int node = it.x;
-    const int L = item_level(it), par = item_parity(it), half = item_half(it);
-    const int i = 2 * (lane & 3) + (par & 1);
-    const int j = 2 * ((lane >> 2) & 3) + ((par >> 1) & 1);
-    const int k = 2 * (2 * half + (lane >> 4)) + (par >> 2);
+    const int L = item_level(it);
+    int i, j, k;
+    item_cell(p, it, lane, i, j, k);
     const long long N = t.n_cells;
     const long long cell = (long long)node * kCells + i + 8 * j + 64 * k;
     double ma, dax, day, daz;
@@ -416,6 +504,40 @@ __device__ __forceinline__ void run_item_split(const DevTree& t, const DevPlan& 
             }
         }
     };
+    // A pair through a stencil entry (kinds and multi as in run_item): R in
+    // FP64 from the FP64 records, and in FP32 from the FP32 ones for the
+    // multipole part.
+    auto pair_at = [&](int kind, bool multi, long long src, int ent) {
+        double m, bx, by, bz, ox, oy, oz;
+        load_head(t, src, m, bx, by, bz);
+        load_off(p, ent, ox, oy, oz);
+        const double x = (dax - bx) - ox, y = (day - by) - oy, z = (daz - bz) - oz;
+        if (!multi) {
+            m2l_pair_split<double, float, FULL, false, AM>(x, y, z, m, 0.f, 0.f, 0.f, nullptr, nullptr,
+                                                           nullptr, A);
+            return;
+        }
+        float mf, bxf, byf, bzf, oxf, oyf, ozf;
+        load_head(t, src, mf, bxf, byf, bzf);
+        load_off(p, ent, oxf, oyf, ozf);
+        const float xf = (daxf - bxf) - oxf, yf = (dayf - byf) - oyf, zf = (dazf - bzf) - ozf;
+        float b2[6], b3[10], bt[4];
+        if (kind == 3) {
+            load_tail(t, src, b2, b3, bt);
+        } else {
+#pragma unroll
+            for (int r = 0; r < 6; r++) b2[r] = 0.f;
+#pragma unroll
+            for (int r = 0; r < 10; r++) b3[r] = 0.f;
+#pragma unroll
+            for (int r = 0; r < 4; r++) bt[r] = 0.f;
+        }
+        m2l_pair_split<double, float, FULL, true, AM>(x, y, z, m, xf, yf, zf, b2, b3, bt, A);
+        if (++since == kFlush32) {
+            flush_split(A);
+            since = 0;
+        }
+    };
     if (FULL && item_list(it) == kRootList) {
         // the interior root: sources are the root's own cells [z, w)
         const int root = it.x;
@@ -435,6 +557,21 @@ __device__ __forceinline__ void run_item_split(const DevTree& t, const DevPlan& 
                         zf = (dazf - bzf) - (float)dz;
             pair(x, y, z, m, xf, yf, zf, src, false);
         }
+    } else if (item_list(it) == kGroupList) {
+        // grouped item: every lane walks its own list (see run_item)
+        const int par = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
+        const int base = __ldg(p.list_first + par);
+        const int qend = min(it.z >> 16, __ldg(p.list_len + par));
+        int q = it.z & 0xffff;
+#pragma unroll 1
+        for (;;) {
+            int nb = 0, lc = 0;
+            const int kind = next_grouped<FULL>(p, s_nb, s_lf, base, qend, i, j, k, q, nb, lc);
+            if (!__any_sync(0xffffffffu, kind != 0)) break;
+            const bool multi = __any_sync(0xffffffffu, kind == 3);
+            if (kind != 0) pair_at(kind, multi, (long long)nb * kCells + lc, base + q);
+            q++;
+        }
     } else {
         const int base = p.list_first[item_list(it)];
 #pragma unroll 1
@@ -445,11 +582,20 @@ __device__ __forceinline__ void run_item_split(const DevTree& t, const DevPlan& 
             const int sx = i + dx, sy = j + dy, sz = k + dz;
             const int slot = ((sx >> 3) + 1) + 3 * ((sy >> 3) + 1) + 9 * ((sz >> 3) + 1);
             const int nb = s_nb[slot];
-            if (nb < 0) continue;  // outside the domain, or covered by a coarser leaf
             const bool sleaf = s_lf[slot] != 0;
+            // pair kinds as in run_item: 0 none, 1 point masses of a leaf
+            // root, 2 leaf source, 3 interior source
+            int kind = 0;
+            if (nb >= 0) {
+                if (!FULL && sleaf) kind = L > 0 ? 0 : 1;
+                else if (!(FULL && !sleaf && entry_near(e))) kind = sleaf ? 2 : 3;
+            }
+            // leaf sources of a warp that also holds interior ones take the
+            // multipole formula with zero moments, in the same pass
+            const bool multi = __any_sync(0xffffffffu, kind == 3);
+            if (kind == 0) continue;
             const long long src = (long long)nb * kCells + (sx & 7) + 8 * (sy & 7) + 64 * (sz & 7);
-            if (!FULL && sleaf) {
-                if (L > 0) continue;  // leaf-leaf pairs of level >= 1: lattice kernel
+            if (kind == 1) {
                 // two point masses on the lattice (a leaf root), FP64
                 double a, b, c, d;
                 tab_of(p, base + q, a, b, c, d);
@@ -460,21 +606,7 @@ __device__ __forceinline__ void run_item_split(const DevTree& t, const DevPlan& 
                 A.L1[2] = fma(m, d, A.L1[2]);
                 continue;
             }
-            if (FULL && !sleaf && entry_near(e)) continue;  // resolved at the next level
-            double m, bx, by, bz, ox, oy, oz;
-            load_head(t, src, m, bx, by, bz);
-            load_off(p, base + q, ox, oy, oz);
-            const double x = (dax - bx) - ox, y = (day - by) - oy, z = (daz - bz) - oz;
-            float xf = 0.f, yf = 0.f, zf = 0.f;
-            if (!sleaf) {
-                float mf, bxf, byf, bzf, oxf, oyf, ozf;
-                load_head(t, src, mf, bxf, byf, bzf);
-                load_off(p, base + q, oxf, oyf, ozf);
-                xf = (daxf - bxf) - oxf;
-                yf = (dayf - byf) - oyf;
-                zf = (dazf - bzf) - ozf;
-            }
-            pair(x, y, z, m, xf, yf, zf, src, sleaf);
+            pair_at(kind, multi, src, base + q);
         }
     }
     flush_split(A);
@@ -599,12 +731,18 @@ void launch_interact(const DevTree& t, const DevPlan& p, int precision, double G
                      int ctas, int warps_per_cta, cudaStream_t s) {
     if (warps_per_cta > 4) warps_per_cta = 4;
     const LevelScales sc = level_scales(t.inv_side8, G);
+    // the FP64 and FP32-bulk forms take the grouped items where the plan has them
+    DevPlan g = p;
+    if (p.items_grp) {
+        g.items = p.items_grp;
+        g.n_items = p.n_items_grp;
+    }
     if (precision == kPrecWide)
         k_interact<float><<<ctas, 32 * warps_per_cta, warps_per_cta * sizeof(WarpStage32), s>>>(t, p, sc, am);
     else if (precision == kPrecBulk)
-        k_interact_split<<<ctas, 32 * warps_per_cta, 0, s>>>(t, p, sc, am);
+        k_interact_split<<<ctas, 32 * warps_per_cta, 0, s>>>(t, g, sc, am);
     else
-        k_interact<double><<<ctas, 32 * warps_per_cta, 0, s>>>(t, p, sc, am);
+        k_interact<double><<<ctas, 32 * warps_per_cta, 0, s>>>(t, g, sc, am);
 }
 
 }  // namespace otfmm

@@ -317,10 +317,77 @@ uint32_t slot_mask(int par, int half, int e) {
 // iterations.  With `all` (the adjoint's items), every node gets items over
 // its whole list, leaf nodes of level >= 1 without interior neighbours one
 // item per parity half (their pairs are all lattice pairs).
+// For every cell of a node and neighbour slot s, the numbers of far and near
+// entries of the cell's parity list whose source lies in slot s:
+// out[(c * 27 + s) * 2 + near].
+std::vector<int> slot_counts(const HostPlan& p) {
+    std::vector<int> cnt((size_t)kCells * 27 * 2, 0);
+    for (int c = 0; c < kCells; c++) {
+        const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
+        const int par = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
+        for (int q = 0; q < p.list_len[par]; q++) {
+            const int e = p.entries[p.list_first[par] + q];
+            const int sx = i + entry_dx(e), sy = j + entry_dy(e), sz = k + entry_dz(e);
+            const int slot = ((sx >> 3) + 1) + 3 * ((sy >> 3) + 1) + 9 * ((sz >> 3) + 1);
+            cnt[((size_t)c * 27 + slot) * 2 + entry_near(e)]++;
+        }
+    }
+    return cnt;
+}
+
+// Grouped items of node v (level >= 1, interior or a leaf bordering interior
+// cells): the pairs of each cell counted per neighbour slot by the rules of
+// the general kernel (an interior target pairs with every leaf source and
+// with the far interior ones; a leaf target with every interior source), the
+// cells sorted by their counts, 16 groups of 32 (groups without pairs
+// dropped), each chunked over the list positions.
+void grouped_items(const HostTree& t, const HostPlan& p, const std::vector<int>& cnt, int v,
+                   uint32_t exist, uint32_t leafm, int chunk, std::vector<Item>& items,
+                   std::vector<int64_t>& cost, std::vector<uint16_t>& cells) {
+    const int L = t.node_level[v];
+    const bool tl = t.node_leaf[v] >= 0;
+    int count[kCells];
+    for (int c = 0; c < kCells; c++) {
+        int n = 0;
+        for (int s = 0; s < 27; s++) {
+            if (!((exist >> s) & 1)) continue;
+            const bool sl = (leafm >> s) & 1;
+            const int nf = cnt[((size_t)c * 27 + s) * 2], nn = cnt[((size_t)c * 27 + s) * 2 + 1];
+            if (tl) n += sl ? 0 : nf + nn;
+            else n += sl ? nf + nn : nf;
+        }
+        count[c] = n;
+    }
+    int order[kCells];
+    for (int c = 0; c < kCells; c++) order[c] = c;
+    std::stable_sort(order, order + kCells, [&](int a, int b) { return count[a] > count[b]; });
+    int len = 0;
+    for (int par = 0; par < 8; par++) len = std::max(len, p.list_len[par]);
+    const int step = std::max(1, chunk);
+    for (int g = 0; g < kCells / 32; g++) {
+        const int mx = count[order[32 * g]];
+        if (mx == 0) break;  // sorted: the remaining groups have no pairs either
+        const int off = (int)cells.size();
+        for (int l = 0; l < 32; l++) cells.push_back((uint16_t)order[32 * g + l]);
+        for (int k0 = 0; k0 < len; k0 += step) {
+            const int k1 = std::min(len, k0 + step);
+            items.push_back({v, L | (g << 8) | (kGroupList << 12), k0 | (k1 << 16), off});
+            // the busiest lane's pairs in the range, weighted by the pair cost
+            cost.push_back((int64_t)mx * (k1 - k0) * (tl ? 6 : 9) / len + 1);
+        }
+    }
+}
+
 std::vector<Item> make_items(const HostTree& t, int chunk, const HostPlan& p, bool all,
-                             std::vector<int>* lattice_nodes, std::vector<int>* kept) {
+                             std::vector<int>* lattice_nodes, std::vector<int>* kept,
+                             std::vector<Item>* grouped = nullptr,
+                             std::vector<uint16_t>* grp_cells = nullptr) {
     std::vector<Item> items;
     std::vector<int64_t> cost;
+    std::vector<Item> gitems;
+    std::vector<int64_t> gcost;
+    std::vector<int> cnt;
+    if (grouped) cnt = slot_counts(p);
     // slot masks per list, parity and half (list 8: the leaf root)
     std::vector<uint32_t> masks[kNumLists][8][2];
     auto masks_of = [&](int list, int par, int half) -> const std::vector<uint32_t>& {
@@ -347,6 +414,9 @@ std::vector<Item> make_items(const HostTree& t, int chunk, const HostPlan& p, bo
         if (tl && L > 0 && lattice_nodes) lattice_nodes->push_back(v);
         if (lattice_only && !all) continue;
         const bool root_cells = L == 0 && !tl && !all;  // an interior root, forward launch
+        const size_t n_before = items.size();
+        if (grouped && L > 0)
+            grouped_items(t, p, cnt, v, exist, leafm, chunk, gitems, gcost, *grp_cells);
         for (int par = 0; par < 8; par++) {
             int list = root_cells ? kRootList : (L == 0 ? 8 : par);
             int len = root_cells ? kCells : p.list_len[list];
@@ -373,14 +443,24 @@ std::vector<Item> make_items(const HostTree& t, int chunk, const HostPlan& p, bo
                 }
             }
         }
+        if (grouped && L == 0)
+            for (size_t n = n_before; n < items.size(); n++) {
+                gitems.push_back(items[n]);
+                // the same scale as the grouped items' costs (pairs x weight)
+                gcost.push_back(cost[n] * (tl ? 6 : 9) / (tl ? 4 : 24) + 1);
+            }
     }
     // longest items first; ties keep the breadth-first node order
-    std::vector<int> order(items.size());
-    for (size_t i = 0; i < order.size(); i++) order[i] = (int)i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-    std::vector<Item> sorted(items.size());
-    for (size_t i = 0; i < order.size(); i++) sorted[i] = items[order[i]];
-    return sorted;
+    auto by_cost = [](std::vector<Item>& it, const std::vector<int64_t>& c) {
+        std::vector<int> order(it.size());
+        for (size_t i = 0; i < order.size(); i++) order[i] = (int)i;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return c[a] > c[b]; });
+        std::vector<Item> sorted(it.size());
+        for (size_t i = 0; i < order.size(); i++) sorted[i] = it[order[i]];
+        return sorted;
+    };
+    if (grouped) *grouped = by_cost(gitems, gcost);
+    return by_cost(items, cost);
 }
 
 }  // namespace
@@ -389,7 +469,9 @@ void build_items(const HostTree& t, int chunk, HostPlan& p) {
     p.chunk = chunk;
     p.lattice_nodes.clear();
     p.item_entries.clear();
-    p.items = make_items(t, chunk, p, false, &p.lattice_nodes, &p.item_entries);
+    p.grp_cells.clear();
+    p.items = make_items(t, chunk, p, false, &p.lattice_nodes, &p.item_entries, &p.items_grp,
+                         &p.grp_cells);
     p.items_adj = make_items(t, chunk, p, true, nullptr, nullptr);
 }
 

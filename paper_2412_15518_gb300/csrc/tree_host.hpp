@@ -99,6 +99,9 @@ struct HostPlan {
     std::vector<Item> items;          // ranges over item_entries (kRootList: over root cells)
     std::vector<int> item_entries;    // list positions kept per node and target group
     std::vector<Item> items_adj;      // every node, ranges over the lists themselves
+    std::vector<Item> items_grp;      // the forward items with the nodes of level >= 1
+                                      // as grouped items (kGroupList)
+    std::vector<uint16_t> grp_cells;  // 32 node-local cells per group
     int64_t n_m2l = 0, n_p2p = 0, n_seam = 0, n_lattice = 0;
     int64_t n_class[PairClasses] = {0, 0, 0, 0, 0};
     double flops_am = 0.0, flops_noam = 0.0;  // one interaction launch
@@ -118,6 +121,9 @@ int build_stencil(const HostTree& t, double theta, HostPlan& p);
 // interior cells), and a leaf root; the leaf-leaf pairs of leaf nodes of
 // level >= 1 go to the lattice kernel (lattice_nodes).  The adjoint's items
 // (items_adj) cover every node and use the stencil lists at every level.
+// items_grp holds the same work with the targets of each node of level >= 1
+// regrouped: its 512 cells sorted by their number of pairs and taken 32 at a
+// time (grp_cells), so that the lanes of a warp have nearly equal work.
 void build_items(const HostTree& t, int chunk, HostPlan& p);
 
 }  // namespace otfmm
