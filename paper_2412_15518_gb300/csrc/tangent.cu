@@ -16,6 +16,7 @@
 #include "tangent.hpp"
 
 #include "lattice.hpp"
+#include "items.cuh"
 #include "pair_formula.cuh"
 
 namespace otfmm {
@@ -215,10 +216,9 @@ __device__ __forceinline__ void tan_item(const DevTree& t, const TanArrays& a, c
                                          const int4 it, const int lane, const int* s_nb, const int* s_lf,
                                          const LevelScales& sc) {
     const int node = it.x;
-    const int L = item_level(it), par = item_parity(it), half = item_half(it);
-    const int i = 2 * (lane & 3) + (par & 1);
-    const int j = 2 * ((lane >> 2) & 3) + ((par >> 1) & 1);
-    const int k = 2 * (2 * half + (lane >> 4)) + (par >> 2);
+    const int L = item_level(it);
+    int i, j, k;
+    item_cell(p, it, lane, i, j, k);
     const long long N = t.n_cells;
     const long long cell = (long long)node * kCells + i + 8 * j + 64 * k;
     Dual ma, dax, day, daz;
@@ -234,6 +234,31 @@ __device__ __forceinline__ void tan_item(const DevTree& t, const TanArrays& a, c
             m2l_pair<Dual, FULL, true, AM>(x, y, z, m, b2, b3, bt, A);
         }
     };
+    // A pair through stencil entry ent with a source of kind 2 (leaf) or 3
+    // (interior); with multi, leaf sources take the multipole formula with
+    // zero moments (the same sums, one pass for the warp).
+    auto pair_at = [&](int kind, bool multi, long long src, int ent) {
+        Dual m, bx, by, bz;
+        head_d(t, a, src, m, bx, by, bz);
+        const double2 o0 = __ldg(p.off64 + 2 * ent), o1 = __ldg(p.off64 + 2 * ent + 1);
+        const Dual x = (dax - bx) - Dual(o0.x), y = (day - by) - Dual(o0.y), z = (daz - bz) - Dual(o1.x);
+        if (!multi) {
+            m2l_pair<Dual, FULL, false, AM>(x, y, z, m, nullptr, nullptr, nullptr, A);
+            return;
+        }
+        Dual b2[6], b3[10], bt[4];
+        if (kind == 3) {
+            tail_d(t, a, src, b2, b3, bt);
+        } else {
+#pragma unroll
+            for (int r = 0; r < 6; r++) b2[r] = Dual(0.0);
+#pragma unroll
+            for (int r = 0; r < 10; r++) b3[r] = Dual(0.0);
+#pragma unroll
+            for (int r = 0; r < 4; r++) bt[r] = Dual(0.0);
+        }
+        m2l_pair<Dual, FULL, true, AM>(x, y, z, m, b2, b3, bt, A);
+    };
     if (FULL && item_list(it) == kRootList) {
         const int root = it.x;
 #pragma unroll 1
@@ -247,6 +272,21 @@ __device__ __forceinline__ void tan_item(const DevTree& t, const TanArrays& a, c
             pair((dax - bx) - Dual((double)dx), (day - by) - Dual((double)dy), (daz - bz) - Dual((double)dz),
                  m, src, false);
         }
+    } else if (item_list(it) == kGroupList) {
+        // grouped item: every lane walks its own list (as in the FP64 kernel)
+        const int par = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
+        const int base = __ldg(p.list_first + par);
+        const int qend = min(it.z >> 16, __ldg(p.list_len + par));
+        int q = it.z & 0xffff;
+#pragma unroll 1
+        for (;;) {
+            int nb = 0, lc = 0;
+            const int kind = next_grouped<FULL>(p, s_nb, s_lf, base, qend, i, j, k, q, nb, lc);
+            if (!__any_sync(0xffffffffu, kind != 0)) break;
+            const bool multi = __any_sync(0xffffffffu, kind == 3);
+            if (kind != 0) pair_at(kind, multi, (long long)nb * kCells + lc, base + q);
+            q++;
+        }
     } else {
         const int base = p.list_first[item_list(it)];
 #pragma unroll 1
@@ -257,11 +297,18 @@ __device__ __forceinline__ void tan_item(const DevTree& t, const TanArrays& a, c
             const int sx = i + dx, sy = j + dy, sz = k + dz;
             const int slot = ((sx >> 3) + 1) + 3 * ((sy >> 3) + 1) + 9 * ((sz >> 3) + 1);
             const int nb = s_nb[slot];
-            if (nb < 0) continue;
             const bool sleaf = s_lf[slot] != 0;
+            // pair kinds as in the FP64 kernel: 0 none, 1 point masses of a
+            // leaf root, 2 leaf source, 3 interior source
+            int kind = 0;
+            if (nb >= 0) {
+                if (!FULL && sleaf) kind = L > 0 ? 0 : 1;
+                else if (!(FULL && !sleaf && entry_near(e))) kind = sleaf ? 2 : 3;
+            }
+            const bool multi = __any_sync(0xffffffffu, kind == 3);
+            if (kind == 0) continue;
             const long long src = (long long)nb * kCells + (sx & 7) + 8 * (sy & 7) + 64 * (sz & 7);
-            if (!FULL && sleaf) {
-                if (L > 0) continue;  // leaf-leaf pairs of level >= 1: lattice kernel
+            if (kind == 1) {
                 // two point masses on the lattice (a leaf root): fixed coefficients
                 const double2 k0 = __ldg(p.tab64 + 2 * (base + q)), k1 = __ldg(p.tab64 + 2 * (base + q) + 1);
                 const Dual m = at(t.mom64, a.mom_d, src);
@@ -271,11 +318,7 @@ __device__ __forceinline__ void tan_item(const DevTree& t, const TanArrays& a, c
                 A.L1[2] = fma_(m, Dual(k1.y), A.L1[2]);
                 continue;
             }
-            if (FULL && !sleaf && entry_near(e)) continue;
-            Dual m, bx, by, bz;
-            head_d(t, a, src, m, bx, by, bz);
-            const double2 o0 = __ldg(p.off64 + 2 * (base + q)), o1 = __ldg(p.off64 + 2 * (base + q) + 1);
-            pair((dax - bx) - Dual(o0.x), (day - by) - Dual(o0.y), (daz - bz) - Dual(o1.x), m, src, sleaf);
+            pair_at(kind, multi, src, base + q);
         }
     }
     const double* sl = sc.s64[L];
@@ -462,7 +505,12 @@ void launch_tangent(const DevTree& t, const TanArrays& a, const int* leaf_node, 
     DevLattice lp2 = lp;
     lp2.counter = lp.counter + 1;  // the second pair of node counters
     launch_lattice(td, p, lp2, kPrecFP64, G, 0, s);
-    k_tan_interact<<<ctas, 128, 0, s>>>(t, a, p, sc, am);
+    DevPlan pg = p;  // the grouped items where the plan has them
+    if (p.items_grp) {
+        pg.items = p.items_grp;
+        pg.n_items = p.n_items_grp;
+    }
+    k_tan_interact<<<ctas, 128, 0, s>>>(t, a, pg, sc, am);
     for (int L = 0; L < n_levels; L++) {
         const int count = level_first[L + 1] - level_first[L];
         if (count > 0)
