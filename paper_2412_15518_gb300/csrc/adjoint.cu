@@ -21,6 +21,7 @@
 //   mombar [20][cells]  dJ/dm, dJ/dX(3), dJ/dM2(6), dJ/dM3(10) (symmetric)
 #include "adjoint.hpp"
 #include "adjoint_pair.cuh"
+#include "items.cuh"
 
 namespace otfmm {
 
@@ -187,7 +188,37 @@ __global__ void __launch_bounds__(32) k_l2l_reverse(DevTree t, int first, double
     }
 }
 
-// M2L / near-pair reverse: persistent over the forward's work items.
+// Grouped reverse items (interior cells of level >= 1): moves q, this lane's
+// position in the list of its own parity class, to its next partner in
+// [q, qend) that the pass reverses -- pass 1 a leaf partner (this cell is the
+// source of the leaf's expansion), pass 2 a leaf partner or a far interior
+// one (this cell is the target) -- and returns 2 for a leaf partner, 3 for an
+// interior one, 0 when none is left; e = the entry, nb/lc = the partner's
+// node and node-local cell.
+template <int PASS>
+__device__ __forceinline__ int next_partner(const DevPlan& p, const int* s_nb, const int* s_lf, int base,
+                                            int qend, int i, int j, int k, int& q, int& e, int& nb,
+                                            int& lc) {
+    for (; q < qend; q++) {
+        const int en = __ldg(p.entries + base + q);
+        const int sx = i + entry_dx(en), sy = j + entry_dy(en), sz = k + entry_dz(en);
+        const int slot = ((sx >> 3) + 1) + 3 * ((sy >> 3) + 1) + 9 * ((sz >> 3) + 1);
+        const int n = s_nb[slot];
+        if (n < 0) continue;
+        const bool pleaf = s_lf[slot] != 0;
+        if (PASS == 1 ? !pleaf : (!pleaf && entry_near(en))) continue;
+        e = en;
+        nb = n;
+        lc = (sx & 7) + 8 * (sy & 7) + 64 * (sz & 7);
+        return pleaf ? 2 : 3;
+    }
+    return 0;
+}
+
+// M2L / near-pair reverse: persistent over the reverse work items.  A
+// parity-class item runs both passes for its 32 cells; a grouped item (32
+// interior cells of one node sorted by their numbers of partners) runs one,
+// every lane walking its own list.
 __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const double* locbar,
                                                      double* mombar, double G, int am) {
     __shared__ int s_nb[4][28];
@@ -209,11 +240,24 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
         __syncwarp();
         const int node = it.x;
         const bool cleaf = t.node_leaf[node] >= 0;
-        const int L = item_level(it), par = item_parity(it), half = item_half(it);
-        const int i = 2 * (lane & 3) + (par & 1);
-        const int j = 2 * ((lane >> 2) & 3) + ((par >> 1) & 1);
-        const int k = 2 * (2 * half + (lane >> 4)) + (par >> 2);
+        const int L = item_level(it);
+        const bool grp = item_list(it) == kGroupList;
+        const int passes = grp ? (it.y >> 16) & 3 : 3;  // bit 0: pass 1, bit 1: pass 2
+        int i, j, k;
+        item_cell(p, it, lane, i, j, k);
         const long long cell = (long long)node * kCells + i + 8 * j + 64 * k;
+        // the list and its range: a grouped item's lane walks its own parity list
+        int base, q0, q1;
+        if (grp) {
+            const int par = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
+            base = __ldg(p.list_first + par);
+            q0 = it.z & 0xffff;
+            q1 = min(it.z >> 16, __ldg(p.list_len + par));
+        } else {
+            base = p.list_first[item_list(it)];
+            q0 = it.z;
+            q1 = it.w;
+        }
         const double h = t.size / (double)(8 << L);
         const double h2 = h * h, h3 = h2 * h;
         // own moments (physical) and own expansion adjoints
@@ -234,89 +278,95 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
         PairAdjOut acc;
         adj_zero(acc);
         double lat0 = 0.0, lat1 = 0.0;   // lattice pairs: dJ/dm of this leaf cell (h, h^2 parts)
-        const int base = p.list_first[item_list(it)];
         // Two passes over the partners, each holding only what its role needs;
         // every directed pair is reversed once.  Pass 1: this cell as the
         // source of a leaf partner's expansion (R = X_P - X_C), and the
         // transposed lattice pairs of a leaf cell.  A pair with an interior
         // target is reversed whole in that target's pass 2, which sends the
         // source-side adjoints here with atomics.
-#pragma unroll 1
-        for (int q = it.z; q < it.w; q++) {
-            const int e = __ldg(p.entries + base + q);
-            const int dx = entry_dx(e), dy = entry_dy(e), dz = entry_dz(e);
-            const int sx = i + dx, sy = j + dy, sz = k + dz;
-            const int slot = ((sx >> 3) + 1) + 3 * ((sy >> 3) + 1) + 9 * ((sz >> 3) + 1);
-            const int nb = s_nb[w][slot];
-            if (nb < 0) continue;
-            const bool pleaf = s_lf[w][slot] != 0;
-            const long long pc = (long long)nb * kCells + (sx & 7) + 8 * (sy & 7) + 64 * (sz & 7);
-            if (cleaf && pleaf) {
-                // transposed lattice pair: this cell is the source of P's point-mass pair
-                const double2 t0 = __ldg(p.tab64 + 2 * (base + q)), t1 = __ldg(p.tab64 + 2 * (base + q) + 1);
-                lat0 = fma(locbar[pc], t0.x, lat0);
-                lat1 = fma(locbar[N + pc], t0.y, fma(locbar[2 * N + pc], t1.x, fma(locbar[3 * N + pc], t1.y, lat1)));
-                continue;
-            }
-            if (!pleaf) continue;  // an interior target: its own pass 2
+        auto rev1 = [&](int e, long long pc) {
             const double mP = t.mom64[pc];
-            const double R[3] = {h * ((double)dx + t.mom64[N + pc] - dC[0]),
-                                 h * ((double)dy + t.mom64[2 * N + pc] - dC[1]),
-                                 h * ((double)dz + t.mom64[3 * N + pc] - dC[2])};
+            const double R[3] = {h * ((double)entry_dx(e) + t.mom64[N + pc] - dC[0]),
+                                 h * ((double)entry_dy(e) + t.mom64[2 * N + pc] - dC[1]),
+                                 h * ((double)entry_dz(e) + t.mom64[3 * N + pc] - dC[2])};
+            // a leaf partner: no octupole, and only its L0/L1 adjoints exist
             double M3P[10], EP[20], aP[3];
 #pragma unroll
-            for (int r = 0; r < 10; r++) M3P[r] = pleaf ? 0.0 : h3 * t.mom64[(10 + r) * N + pc];
+            for (int r = 0; r < 10; r++) M3P[r] = 0.0;
 #pragma unroll
-            for (int r = 0; r < 20; r++) EP[r] = (pleaf && r >= 4) ? 0.0 : locbar[r * N + pc];
+            for (int r = 0; r < 20; r++) EP[r] = r >= 4 ? 0.0 : locbar[r * N + pc];
 #pragma unroll
             for (int r = 0; r < 3; r++) aP[r] = locbar[(20 + r) * N + pc];
             // the R-gradient of this pair moves this cell's centre of mass (a
             // leaf partner's centre is fixed)
             m2l_pair_reverse<true, false>(R, G, am, mC, M2C, M3C, !cleaf, mP, M3P, false, EP[0], EP + 1,
                                           EP + 4, EP + 10, aP, !cleaf, -1.0, acc.R, acc);
-        }
-        // this cell's source-side adjoints so far; acc's source fields then
-        // carry one pair's partner adjoints at a time in pass 2
-        const double hi = 1.0 / h;
-        atomicAdd(mombar + cell, acc.mB - G * (lat0 * hi - lat1 * hi * hi));
-        acc.mB = 0.0;
-        if (!cleaf) {
-#pragma unroll
-            for (int r = 0; r < 6; r++) {
-                atomicAdd(mombar + (4 + r) * N + cell, acc.M2B[r]);
-                acc.M2B[r] = 0.0;
+        };
+        if (passes & 1) {
+            if (grp) {
+#pragma unroll 1
+                for (int q = q0;;) {
+                    int e = 0, nb = 0, lc = 0;
+                    const int kind = next_partner<1>(p, s_nb[w], s_lf[w], base, q1, i, j, k, q, e, nb, lc);
+                    if (!__any_sync(0xffffffffu, kind != 0)) break;
+                    if (kind != 0) rev1(e, (long long)nb * kCells + lc);
+                    q++;
+                }
+            } else {
+#pragma unroll 1
+                for (int q = q0; q < q1; q++) {
+                    const int e = __ldg(p.entries + base + q);
+                    const int sx = i + entry_dx(e), sy = j + entry_dy(e), sz = k + entry_dz(e);
+                    const int slot = ((sx >> 3) + 1) + 3 * ((sy >> 3) + 1) + 9 * ((sz >> 3) + 1);
+                    const int nb = s_nb[w][slot];
+                    if (nb < 0) continue;
+                    const bool pleaf = s_lf[w][slot] != 0;
+                    const long long pc = (long long)nb * kCells + (sx & 7) + 8 * (sy & 7) + 64 * (sz & 7);
+                    if (cleaf && pleaf) {
+                        // transposed lattice pair: this cell is the source of P's point-mass pair
+                        const double2 t0 = __ldg(p.tab64 + 2 * (base + q)), t1 = __ldg(p.tab64 + 2 * (base + q) + 1);
+                        lat0 = fma(locbar[pc], t0.x, lat0);
+                        lat1 = fma(locbar[N + pc], t0.y,
+                                   fma(locbar[2 * N + pc], t1.x, fma(locbar[3 * N + pc], t1.y, lat1)));
+                        continue;
+                    }
+                    if (!pleaf) continue;  // an interior target: its own pass 2
+                    rev1(e, pc);
+                }
             }
+            // this cell's source-side adjoints of pass 1; acc's source fields
+            // then carry one pair's partner adjoints at a time in pass 2
+            const double hi = 1.0 / h;
+            atomicAdd(mombar + cell, acc.mB - G * (lat0 * hi - lat1 * hi * hi));
+            acc.mB = 0.0;
+            if (!cleaf) {
 #pragma unroll
-            for (int r = 0; r < 10; r++) {
-                atomicAdd(mombar + (10 + r) * N + cell, acc.M3B[r]);
-                acc.M3B[r] = 0.0;
+                for (int r = 0; r < 6; r++) {
+                    atomicAdd(mombar + (4 + r) * N + cell, acc.M2B[r]);
+                    acc.M2B[r] = 0.0;
+                }
+#pragma unroll
+                for (int r = 0; r < 10; r++) {
+                    atomicAdd(mombar + (10 + r) * N + cell, acc.M3B[r]);
+                    acc.M3B[r] = 0.0;
+                }
             }
         }
         // Pass 2 (interior cells): this cell as the target of its partners
         // (R = X_C - X_P), each pair reversed whole: the correction's mass
         // ratio and the pair's R-gradient for this cell, the partner's
         // source-side adjoints and its part of the R-gradient by atomics.
-        if (!cleaf) {
+        if (!cleaf && (passes & 2)) {
             double EC[20], aC[3];
 #pragma unroll
             for (int r = 0; r < 20; r++) EC[r] = locbar[r * N + cell];
 #pragma unroll
             for (int r = 0; r < 3; r++) aC[r] = locbar[(20 + r) * N + cell];
-#pragma unroll 1
-            for (int q = it.z; q < it.w; q++) {
-                const int e = __ldg(p.entries + base + q);
-                const int dx = entry_dx(e), dy = entry_dy(e), dz = entry_dz(e);
-                const int sx = i + dx, sy = j + dy, sz = k + dz;
-                const int slot = ((sx >> 3) + 1) + 3 * ((sy >> 3) + 1) + 9 * ((sz >> 3) + 1);
-                const int nb = s_nb[w][slot];
-                if (nb < 0) continue;
-                const bool pleaf = s_lf[w][slot] != 0;
-                if (!pleaf && entry_near(e)) continue;
-                const long long pc = (long long)nb * kCells + (sx & 7) + 8 * (sy & 7) + 64 * (sz & 7);
+            auto rev2 = [&](int e, bool pleaf, long long pc) {
                 const double mP = t.mom64[pc];
-                const double Rn[3] = {h * (dC[0] - (double)dx - t.mom64[N + pc]),
-                                      h * (dC[1] - (double)dy - t.mom64[2 * N + pc]),
-                                      h * (dC[2] - (double)dz - t.mom64[3 * N + pc])};
+                const double Rn[3] = {h * (dC[0] - (double)entry_dx(e) - t.mom64[N + pc]),
+                                      h * (dC[1] - (double)entry_dy(e) - t.mom64[2 * N + pc]),
+                                      h * (dC[2] - (double)entry_dz(e) - t.mom64[3 * N + pc])};
                 double M2P[6], M3P[10];
 #pragma unroll
                 for (int r = 0; r < 6; r++) M2P[r] = pleaf ? 0.0 : h2 * t.mom64[(4 + r) * N + pc];
@@ -348,22 +398,46 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
 #pragma unroll
                     for (int s = 0; s < 3; s++) atomicAdd(mombar + (1 + s) * N + pc, -gR[s]);
                 }
+            };
+            if (grp) {
+#pragma unroll 1
+                for (int q = q0;;) {
+                    int e = 0, nb = 0, lc = 0;
+                    const int kind = next_partner<2>(p, s_nb[w], s_lf[w], base, q1, i, j, k, q, e, nb, lc);
+                    if (!__any_sync(0xffffffffu, kind != 0)) break;
+                    if (kind != 0) rev2(e, kind == 2, (long long)nb * kCells + lc);
+                    q++;
+                }
+            } else {
+#pragma unroll 1
+                for (int q = q0; q < q1; q++) {
+                    const int e = __ldg(p.entries + base + q);
+                    const int sx = i + entry_dx(e), sy = j + entry_dy(e), sz = k + entry_dz(e);
+                    const int slot = ((sx >> 3) + 1) + 3 * ((sy >> 3) + 1) + 9 * ((sz >> 3) + 1);
+                    const int nb = s_nb[w][slot];
+                    if (nb < 0) continue;
+                    const bool pleaf = s_lf[w][slot] != 0;
+                    if (!pleaf && entry_near(e)) continue;
+                    rev2(e, pleaf, (long long)nb * kCells + (sx & 7) + 8 * (sy & 7) + 64 * (sz & 7));
+                }
             }
         }
-        // this cell's target-side adjoints (the correction's mass ratio) and
-        // centre-of-mass adjoint
+        // this cell's target-side adjoints (the correction's mass ratio, after
+        // pass 2) and centre-of-mass adjoint (both passes)
         if (!cleaf) {
-            if (am && mC != 0.0) {
-                double aC[3];
+            if (passes & 2) {
+                if (am && mC != 0.0) {
+                    double aC[3];
 #pragma unroll
-                for (int r = 0; r < 3; r++) aC[r] = locbar[(20 + r) * N + cell];
-                reverse_target_finish(acc, aC, (G / 6.0) / mC);
+                    for (int r = 0; r < 3; r++) aC[r] = locbar[(20 + r) * N + cell];
+                    reverse_target_finish(acc, aC, (G / 6.0) / mC);
+                }
+                atomicAdd(mombar + cell, acc.mA);
+#pragma unroll
+                for (int r = 0; r < 10; r++) atomicAdd(mombar + (10 + r) * N + cell, acc.M3A[r]);
             }
-            atomicAdd(mombar + cell, acc.mA);
 #pragma unroll
             for (int s = 0; s < 3; s++) atomicAdd(mombar + (1 + s) * N + cell, acc.R[s]);
-#pragma unroll
-            for (int r = 0; r < 10; r++) atomicAdd(mombar + (10 + r) * N + cell, acc.M3A[r]);
         }
         __syncwarp();
     }

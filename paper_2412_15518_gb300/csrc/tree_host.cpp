@@ -335,14 +335,20 @@ std::vector<int> slot_counts(const HostPlan& p) {
     return cnt;
 }
 
-// Grouped items of node v (level >= 1, interior or a leaf bordering interior
-// cells): the pairs of each cell counted per neighbour slot by the rules of
-// the general kernel (an interior target pairs with every leaf source and
-// with the far interior ones; a leaf target with every interior source), the
-// cells sorted by their counts, 16 groups of 32 (groups without pairs
-// dropped), each chunked over the list positions.
+// Which pairs of a cell of node v a grouped item walks, by neighbour slot
+// (the general kernel's rules): kForward, an interior target pairs with every
+// leaf source and with the far interior ones, a leaf target with every
+// interior source; kReverse1, the adjoint's pass 1 of an interior cell, its
+// leaf partners; kReverse2, its pass 2, the forward rule of an interior
+// target.
+enum { kForward = 0, kReverse1 = 1, kReverse2 = 2 };
+
+// Groups of node v (level >= 1) for one rule: the pairs of each cell counted
+// per neighbour slot, the cells sorted by their counts, 16 groups of 32
+// (groups without pairs dropped), each chunked over the list positions; y
+// carries pass << 16 (0 for the forward items).
 void grouped_items(const HostTree& t, const HostPlan& p, const std::vector<int>& cnt, int v,
-                   uint32_t exist, uint32_t leafm, int chunk, std::vector<Item>& items,
+                   uint32_t exist, uint32_t leafm, int chunk, int rule, std::vector<Item>& items,
                    std::vector<int64_t>& cost, std::vector<uint16_t>& cells) {
     const int L = t.node_level[v];
     const bool tl = t.node_leaf[v] >= 0;
@@ -353,7 +359,8 @@ void grouped_items(const HostTree& t, const HostPlan& p, const std::vector<int>&
             if (!((exist >> s) & 1)) continue;
             const bool sl = (leafm >> s) & 1;
             const int nf = cnt[((size_t)c * 27 + s) * 2], nn = cnt[((size_t)c * 27 + s) * 2 + 1];
-            if (tl) n += sl ? 0 : nf + nn;
+            if (rule == kReverse1) n += sl ? nf + nn : 0;
+            else if (tl) n += sl ? 0 : nf + nn;
             else n += sl ? nf + nn : nf;
         }
         count[c] = n;
@@ -364,6 +371,9 @@ void grouped_items(const HostTree& t, const HostPlan& p, const std::vector<int>&
     int len = 0;
     for (int par = 0; par < 8; par++) len = std::max(len, p.list_len[par]);
     const int step = std::max(1, chunk);
+    // pair weights on the scale of the parity-class items' costs
+    const int weight = rule == kReverse1 ? 20 : (rule == kReverse2 ? 24 : (tl ? 6 : 9));
+    const int pass = rule == kForward ? 0 : rule;
     for (int g = 0; g < kCells / 32; g++) {
         const int mx = count[order[32 * g]];
         if (mx == 0) break;  // sorted: the remaining groups have no pairs either
@@ -371,9 +381,9 @@ void grouped_items(const HostTree& t, const HostPlan& p, const std::vector<int>&
         for (int l = 0; l < 32; l++) cells.push_back((uint16_t)order[32 * g + l]);
         for (int k0 = 0; k0 < len; k0 += step) {
             const int k1 = std::min(len, k0 + step);
-            items.push_back({v, L | (g << 8) | (kGroupList << 12), k0 | (k1 << 16), off});
+            items.push_back({v, L | (g << 8) | (kGroupList << 12) | (pass << 16), k0 | (k1 << 16), off});
             // the busiest lane's pairs in the range, weighted by the pair cost
-            cost.push_back((int64_t)mx * (k1 - k0) * (tl ? 6 : 9) / len + 1);
+            cost.push_back((int64_t)mx * (k1 - k0) * weight / len + 1);
         }
     }
 }
@@ -387,7 +397,7 @@ std::vector<Item> make_items(const HostTree& t, int chunk, const HostPlan& p, bo
     std::vector<Item> gitems;
     std::vector<int64_t> gcost;
     std::vector<int> cnt;
-    if (grouped) cnt = slot_counts(p);
+    if (grouped || (all && grp_cells)) cnt = slot_counts(p);
     // slot masks per list, parity and half (list 8: the leaf root)
     std::vector<uint32_t> masks[kNumLists][8][2];
     auto masks_of = [&](int list, int par, int half) -> const std::vector<uint32_t>& {
@@ -416,7 +426,13 @@ std::vector<Item> make_items(const HostTree& t, int chunk, const HostPlan& p, bo
         const bool root_cells = L == 0 && !tl && !all;  // an interior root, forward launch
         const size_t n_before = items.size();
         if (grouped && L > 0)
-            grouped_items(t, p, cnt, v, exist, leafm, chunk, gitems, gcost, *grp_cells);
+            grouped_items(t, p, cnt, v, exist, leafm, chunk, kForward, gitems, gcost, *grp_cells);
+        if (all && grp_cells && L > 0 && !tl) {
+            // the adjoint: an interior cell's two passes as grouped items
+            grouped_items(t, p, cnt, v, exist, leafm, chunk, kReverse1, items, cost, *grp_cells);
+            grouped_items(t, p, cnt, v, exist, leafm, chunk, kReverse2, items, cost, *grp_cells);
+            continue;
+        }
         for (int par = 0; par < 8; par++) {
             int list = root_cells ? kRootList : (L == 0 ? 8 : par);
             int len = root_cells ? kCells : p.list_len[list];
@@ -472,7 +488,7 @@ void build_items(const HostTree& t, int chunk, HostPlan& p) {
     p.grp_cells.clear();
     p.items = make_items(t, chunk, p, false, &p.lattice_nodes, &p.item_entries, &p.items_grp,
                          &p.grp_cells);
-    p.items_adj = make_items(t, chunk, p, true, nullptr, nullptr);
+    p.items_adj = make_items(t, chunk, p, true, nullptr, nullptr, nullptr, &p.grp_cells);
 }
 
 }  // namespace otfmm

@@ -3,7 +3,9 @@
 // the FP64 and FP32-bulk forms (cells of a node regrouped by their pair
 // counts, each lane walking its own parity list) must enumerate exactly the
 // pairs of the parity-class items (32 cells of one parity class over the
-// kept list positions), and every index they produce must stay in bounds.
+// kept list positions); the adjoint's grouped items of its two passes must
+// enumerate exactly the partners each pass reverses; and every index they
+// produce must stay in bounds.
 //
 // Usage: items_check <leaves.bin> <theta> <chunk>; leaves.bin holds int32
 // (L, ix, iy, iz) rows.  Prints "pairs <n> grouped_items <m> bad <b>" and
@@ -114,6 +116,64 @@ int main(int argc, char** argv) {
             for (int lane = 0; lane < 32; lane++)
                 if (!seen.insert({it.x, p.grp_cells[it.w + lane]}).second) bad++;
     if (a != b) bad++;
-    std::printf("pairs %zu grouped_items %d bad %d\n", a.size(), grouped, bad);
+    // The adjoint's items: interior nodes of level >= 1 as grouped items of
+    // pass 1 (leaf partners) and pass 2 (leaf partners and far interior
+    // ones) over their cells' whole parity lists; every other node keeps
+    // parity-class items running both passes.
+    std::multiset<Pair> r_want, r_got;
+    for (int v = 0; v < t.n_nodes(); v++) {
+        if (t.node_level[v] < 1 || t.node_leaf[v] >= 0) continue;
+        for (int c = 0; c < kCells; c++) {
+            const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
+            const int par = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
+            for (int q = 0; q < p.list_len[par]; q++) {
+                const int ent = p.list_first[par] + q, e = p.entries[ent];
+                const int sx = i + entry_dx(e), sy = j + entry_dy(e), sz = k + entry_dz(e);
+                const int nb = t.nbr[(size_t)v * 27 + ((sx >> 3) + 1) + 3 * ((sy >> 3) + 1) + 9 * ((sz >> 3) + 1)];
+                if (nb < 0) continue;
+                const bool pleaf = t.node_leaf[nb] >= 0;
+                if (pleaf) r_want.insert(Pair(v, c, ent, 1));
+                if (pleaf || !entry_near(e)) r_want.insert(Pair(v, c, ent, 2));
+            }
+        }
+    }
+    for (const Item& it : p.items_adj) {
+        const int v = it.x, list = (it.y >> 12) & 15;
+        if (list != kGroupList) {
+            if (t.node_level[v] >= 1 && t.node_leaf[v] < 0) bad++;  // interior nodes are grouped
+            continue;
+        }
+        const int pass = (it.y >> 16) & 3, k0 = it.z & 0xffff, k1 = it.z >> 16;
+        if ((pass != 1 && pass != 2) || t.node_leaf[v] >= 0 || it.w < 0 ||
+            (size_t)it.w + 32 > p.grp_cells.size()) {
+            bad++;
+            continue;
+        }
+        for (int lane = 0; lane < 32; lane++) {
+            const int c = p.grp_cells[it.w + lane];
+            if (c >= kCells) {
+                bad++;
+                continue;
+            }
+            const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
+            const int par = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
+            const int qend = k1 < p.list_len[par] ? k1 : p.list_len[par];
+            for (int q = k0; q < qend; q++) {
+                const int ent = p.list_first[par] + q, e = p.entries[ent];
+                const int sx = i + entry_dx(e), sy = j + entry_dy(e), sz = k + entry_dz(e);
+                if (sx < -8 || sx >= 16 || sy < -8 || sy >= 16 || sz < -8 || sz >= 16) {
+                    bad++;
+                    continue;
+                }
+                const int nb = t.nbr[(size_t)v * 27 + ((sx >> 3) + 1) + 3 * ((sy >> 3) + 1) + 9 * ((sz >> 3) + 1)];
+                if (nb < 0) continue;
+                const bool pleaf = t.node_leaf[nb] >= 0;
+                if (pass == 1 ? pleaf : (pleaf || !entry_near(e))) r_got.insert(Pair(v, c, ent, pass));
+            }
+        }
+    }
+    if (r_want != r_got) bad++;
+    std::printf("pairs %zu grouped_items %d reverse_pairs %zu bad %d\n", a.size(), grouped, r_want.size(),
+                bad);
     return bad ? 1 : 0;
 }
