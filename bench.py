@@ -91,6 +91,9 @@ def parse():
                          "markdown table and one JSON object per row")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the autotuner (default: tune the persistent launch before timing)")
+    ap.add_argument("--hydro-only", type=int, default=None, metavar="LEVEL",
+                    help="time only the hydro companions (PPM values and the right-hand side) on a "
+                         "uniform tree of this level and print them as one JSON object")
     return ap.parse_args()
 
 
@@ -480,6 +483,7 @@ def run_ours(args):
         if args.workload != "binary_l3":
             extra["binary_l3"] = companion_workload("binary_l3", flush, not args.no_autotune, peaks)
         extra["ppm_reconstruction"] = ppm_companion(flush, peaks)
+        extra["hydro_rhs"] = hydro_companion(flush, peaks)
         extra["cpu_baseline"] = cpu_baseline(leaves, rho_np)
     # library kernels of one solve: leaf moments; per parent level the M2M
     # kernel for cells with interior children and/or the one for cells with
@@ -591,6 +595,63 @@ def ppm_companion(flush, peaks, level=4, steps=20):
                          "fp64_ops_per_launch": ops, "fp64_ops_per_cell_field_line": 25},
             "hbm": {"achieved_gbs": nbytes / (med / 1e3) / 1e9, "peak_gbs": hbm, "peak_source": src,
                     "frac": nbytes / (med / 1e3) / 1e9 / hbm, "bytes_per_launch": nbytes}}
+
+
+# FP64 operations of the hydro right-hand side (hydro.cu), counted from its
+# code: per face point 83 (two states' Euler fluxes and wave speeds, 23 each
+# with the reciprocal and the square root as one operation; the Rusanov flux,
+# 27; the weighted sum, 10), per cell 44 (divergence 30, scale 5, source 9);
+# a leaf computes 3 x 9 x 8 x 8 faces of 9 points.
+HYDRO_OPS_PER_POINT = 83
+HYDRO_OPS_PER_CELL = 44
+
+
+def hydro_companion(flush, peaks, level=4, steps=20):
+    """The hydro solver's right-hand side dU/dt on a uniform tree
+    (8^level leaf sub-grids) with the rotating binary's five conserved fields
+    and the gravity solve's acceleration: PPM values, face fluxes and the
+    gravity source in one call.  Median time and the FP64 roofline of the
+    whole call (the PPM kernel's and the flux kernel's operations against the
+    measured FP64 instruction rate, the FMA peak / 2)."""
+    import torch
+    from paper_2412_15518_gb300 import fmm, inputs
+    leaves = inputs.uniform_leaves(level)
+    u = torch.from_numpy(inputs.hydro_fields(leaves)).cuda()
+    tree = fmm.Tree(leaves)
+    phi, g = tree.solve(u[:, 0].contiguous())
+    out = torch.empty_like(u)
+    for _ in range(3):
+        fmm.ot_hydro_rhs(tree.handle, u, g, 5.0 / 3.0, out)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fmm.ot_hydro_rhs(tree.handle, u, g, 5.0 / 3.0, out)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    med = statistics.median(ms)
+    n_leaf = leaves.shape[0]
+    cells = n_leaf * 512
+    ops_ppm = cells * 5 * 13 * 25
+    ops_flux = n_leaf * 3 * 576 * 9 * HYDRO_OPS_PER_POINT + cells * HYDRO_OPS_PER_CELL
+    gops = (ops_ppm + ops_flux) / (med / 1e3) / 1e12
+    peak_ops = peaks["fp64_tflops"] / 2.0
+    tree.close()
+    del u, out, phi, g
+    return {"workload": f"uniform level-{level} octree ({n_leaf} leaf sub-grids, {cells} cells), "
+                        "5 conserved fields of the rotating binary, g from the gravity solve",
+            "ms_per_launch": med, "cells_per_s": cells / (med / 1e3),
+            "roofline": {"bound": "alu", "achieved": gops, "peak": peak_ops, "unit": "T FP64 ops/s",
+                         "frac": gops / peak_ops,
+                         "peak_source": "measured FP64 FMA rate (ot_alu_peaks) / 2, one FP64 operation "
+                                        "per lane per issue slot",
+                         "fp64_ops_per_launch": ops_ppm + ops_flux, "ppm_ops": ops_ppm,
+                         "flux_ops": ops_flux}}
 
 
 def companion_workload(name, flush, autotune, peaks):
@@ -786,6 +847,13 @@ def main():
         run_reference(args)
     elif args.table:
         run_table(args)
+    elif args.hydro_only is not None:
+        import torch
+        from paper_2412_15518_gb300 import fmm
+        peaks = fmm.ot_alu_peaks(0, 3)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        print(json.dumps({"ppm_reconstruction": ppm_companion(flush, peaks, args.hydro_only, args.steps),
+                          "hydro_rhs": hydro_companion(flush, peaks, args.hydro_only, args.steps)}))
     else:
         run_ours(args)
 

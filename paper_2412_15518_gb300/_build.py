@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libotfmm.so")
 SOURCES = ["tree_host.cpp", "flops.cpp", "capi.cpp", "moments.cu", "interact.cu", "downward.cu",
-           "static_solve.cu", "adjoint.cu", "lattice.cu", "peaks.cu", "tangent.cu", "ppm.cu"]
+           "static_solve.cu", "adjoint.cu", "lattice.cu", "peaks.cu", "tangent.cu", "ppm.cu",
+           "hydro.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -74,6 +74,7 @@ _lib.ot_solve_gravity_static.argtypes = [ctypes.POINTER(ot_tree_desc), _P, _P, _
                                          ctypes.POINTER(ot_solve_opts), _P]
 _lib.ot_solve_gravity_tangent.argtypes = [_P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(ot_solve_opts), _P]
 _lib.ot_ppm_reconstruct.argtypes = [_P, _P, ctypes.c_int, _P, _P]
+_lib.ot_hydro_rhs.argtypes = [_P, _P, _P, ctypes.c_double, _P, _P]
 _lib.ot_get_moments.argtypes = [_P, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int32), _P]
 _lib.ot_set_launch_shape.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
 _lib.ot_alu_peaks.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -87,7 +88,7 @@ EXPORTS = ["ot_build_tree", "ot_compute_moments", "ot_solve_gravity", "ot_solve_
            "ot_gravity_backward", "ot_autotune", "ot_last_solve_times", "ot_tree_info",
            "ot_destroy_tree", "ot_error_string", "ot_solve_gravity_static", "ot_get_moments",
            "ot_set_launch_shape", "ot_alu_peaks", "ot_solve_gravity_tangent",
-           "ot_ppm_reconstruct"]
+           "ot_ppm_reconstruct", "ot_hydro_rhs"]
 
 
 class OTError(RuntimeError):
@@ -169,6 +170,11 @@ def ot_solve_gravity_tangent(tree, rho, rho_dot, phi, g, phi_dot, g_dot,
                                          _ptr(phi_dot), _ptr(g_dot),
                                          ctypes.byref(opts) if opts is not None else None,
                                          _stream(stream)), "ot_solve_gravity_tangent")
+
+
+def ot_hydro_rhs(tree, u, g, gamma, dudt, stream=None):
+    _check(_lib.ot_hydro_rhs(_P(tree), _ptr(u), _ptr(g), float(gamma), _ptr(dudt), _stream(stream)),
+           "ot_hydro_rhs")
 
 
 def ot_ppm_reconstruct(tree, u, out, stream=None):
@@ -313,6 +319,14 @@ class Tree:
         cell averages u [n_leaf, n_fields, 512] (leaves all at one level)."""
         out = torch.empty((u.shape[0], u.shape[1], 26, 512), dtype=torch.float64, device=u.device)
         ot_ppm_reconstruct(self.handle, u, out, stream)
+        return out
+
+    def hydro_rhs(self, u, g=None, gamma=5.0 / 3.0, stream=None):
+        """dU/dt [n_leaf, 5, 512] of the conserved fields u [n_leaf, 5, 512]
+        (rho, s, E; leaves all at one level) with the gravitational
+        acceleration g [n_leaf, 3, 512] or None."""
+        out = torch.empty_like(u)
+        ot_hydro_rhs(self.handle, u, g, gamma, out, stream)
         return out
 
     def compute_moments(self, rho, stream=None):

@@ -1,0 +1,160 @@
+"""GPU hydro right-hand side (ot_hydro_rhs) against the oracle
+(oracle/hydro.py), element by element.
+
+Both sides evaluate the same formulas operation by operation in FP64
+without fused multiply-adds (PPM values, Rusanov fluxes, Simpson face rule,
+divergence, gravity source), so the limiter and the wave-speed maxima take
+the same branches and the rates agree bit for bit: the comparison is exact
+equality.  At the bench's size (uniform level 4, 2.1M cells), where the
+oracle would hold several GB of directional values, the tests check what
+holds at any size: a uniform state feels the gravity source only, and a
+linear state in uniform motion changes at its closed-form rate.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import hydro as H
+from paper_2412_15518_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+GAMMA = 5.0 / 3.0
+
+
+@pytest.fixture(scope="module")
+def fmm():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2412_15518_gb300 import fmm as F
+    return F
+
+
+def rand_g(lv, seed):
+    return np.random.default_rng(seed).standard_normal((lv.shape[0], 3, 512))
+
+
+CASES = {
+    # uniform level 1, shuffled leaf order, the binary's fields, gravity
+    "l1_hydro_g": lambda: (lambda lv: (lv, I.hydro_fields(lv, seed=3), rand_g(lv, 4)))(
+        I.uniform_leaves(1, seed=2)),
+    # uniform level 2, no gravity
+    "l2_hydro": lambda: (lambda lv: (lv, I.hydro_fields(lv, seed=1), None))(I.uniform_leaves(2)),
+    # uniform level 3 (262,144 cells), gravity
+    "l3_hydro_g": lambda: (lambda lv: (lv, I.hydro_fields(lv, seed=2), rand_g(lv, 5)))(
+        I.uniform_leaves(3, seed=5)),
+    # a lone root leaf: every face of the domain is transmissive
+    "root_g": lambda: (np.array([[0, 0, 0, 0]], np.int32),
+                       I.hydro_fields(np.array([[0, 0, 0, 0]], np.int32), seed=6),
+                       rand_g(np.array([[0, 0, 0, 0]], np.int32), 7)),
+}
+
+
+def gpu_rhs(fmm, lv, u, g, gamma=GAMMA, size=1.0):
+    tree = fmm.Tree(lv, size=size)
+    ug = torch.from_numpy(np.ascontiguousarray(u)).cuda()
+    gg = None if g is None else torch.from_numpy(np.ascontiguousarray(g)).cuda()
+    out = tree.hydro_rhs(ug, gg, gamma)
+    torch.cuda.synchronize()
+    res = out.cpu().numpy()
+    tree.close()
+    return res
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_hydro_rhs_matches_oracle_bit_for_bit(fmm, case):
+    lv, u, g = CASES[case]()
+    got = gpu_rhs(fmm, lv, u, g)
+    want = H.rhs(lv, u, g, GAMMA)
+    diff = int((got != want).sum())
+    print(f"hydro {case}: {got.size} values, {diff} differ, max |diff| {np.abs(got - want).max():.2e}")
+    assert np.isfinite(got).all()
+    assert diff == 0
+
+
+def test_hydro_rhs_other_gamma_and_domain_size(fmm):
+    lv = I.uniform_leaves(1)
+    u = I.hydro_fields(lv, seed=8)
+    g = rand_g(lv, 9)
+    got = gpu_rhs(fmm, lv, u, g, gamma=1.4, size=3.0)
+    want = H.rhs(lv, u, g, 1.4, size=3.0)
+    assert int((got != want).sum()) == 0
+
+
+def test_hydro_rhs_with_the_gravity_solve(fmm):
+    """The two workloads coupled: g from the GPU gravity solve of the same
+    density, both sides fed the same g."""
+    lv = I.uniform_leaves(2)
+    u = I.hydro_fields(lv, seed=10)
+    tree = fmm.Tree(lv)
+    ug = torch.from_numpy(u).cuda()
+    rho = ug[:, 0].contiguous()
+    phi, g = tree.solve(rho)
+    out = tree.hydro_rhs(ug, g, GAMMA)
+    torch.cuda.synchronize()
+    got, gn = out.cpu().numpy(), g.cpu().numpy()
+    tree.close()
+    want = H.rhs(lv, u, gn, GAMMA)
+    assert int((got != want).sum()) == 0
+
+
+def test_level4_uniform_state_feels_the_source_only(fmm):
+    lv = I.uniform_leaves(4)
+    vel = (0.3, -0.2, 0.7)
+    rho, p = 1.3, 0.8
+    E = p / (GAMMA - 1.0) + 0.5 * rho * sum(v * v for v in vel)
+    u = np.empty((lv.shape[0], 5, 512))
+    for f, val in enumerate([rho, rho * vel[0], rho * vel[1], rho * vel[2], E]):
+        u[:, f] = val
+    g = rand_g(lv, 11)
+    got = gpu_rhs(fmm, lv, u, g)
+    assert np.all(got[:, 0] == 0.0)
+    for b in range(3):
+        assert np.all(got[:, 1 + b] == rho * g[:, b])
+    assert np.allclose(got[:, 4], rho * (vel[0] * g[:, 0] + vel[1] * g[:, 1] + vel[2] * g[:, 2]),
+                       rtol=1e-14, atol=1e-15)
+
+
+def test_level4_linear_state_advects_at_the_closed_form_rate(fmm):
+    lv = I.uniform_leaves(4)
+    n, h = 128, 1.0 / 128
+    b = np.array([0.0011, -0.0007, 0.0005])
+    vel = (0.4, -0.3, 0.25)
+    c = np.arange(8)
+    kk, jj, ii = np.meshgrid(c, c, c, indexing="ij")
+    u = np.empty((lv.shape[0], 5, 512))
+    for m, (_, ix, iy, iz) in enumerate(lv):
+        rho = 1.0 + b[0] * (8 * ix + ii) + b[1] * (8 * iy + jj) + b[2] * (8 * iz + kk)
+        rho = rho.reshape(-1)
+        u[m] = [rho, rho * vel[0], rho * vel[1], rho * vel[2],
+                0.9 / (GAMMA - 1.0) + 0.5 * rho * sum(v * v for v in vel)]
+    got = gpu_rhs(fmm, lv, u, None)
+    vb = (vel[0] * b[0] + vel[1] * b[1] + vel[2] * b[2]) / h
+    v2 = sum(v * v for v in vel)
+    want = [-vb] + [-vel[a] * vb for a in range(3)] + [-0.5 * v2 * vb]
+    # interior cells: three cells from the domain boundary
+    lo = np.asarray(lv)[:, 1:4] * 8
+    glob = np.stack([lo[:, 0:1] + ii.reshape(1, -1), lo[:, 1:2] + jj.reshape(1, -1),
+                     lo[:, 2:3] + kk.reshape(1, -1)])
+    inner = np.all((glob >= 3) & (glob < n - 3), axis=0)
+    for f in range(5):
+        assert np.abs(got[:, f][inner] - want[f]).max() < 1e-9, f
+
+
+def test_hydro_rhs_rejects_mixed_levels_and_bad_gamma(fmm):
+    lv = I.amr_leaves(3, 2e-4, I.BINARY)
+    tree = fmm.Tree(lv)
+    u = torch.ones((lv.shape[0], 5, 512), dtype=torch.float64, device="cuda")
+    out = torch.empty_like(u)
+    with pytest.raises(fmm.OTError) as e:
+        fmm.ot_hydro_rhs(tree.handle, u, None, GAMMA, out)
+    assert e.value.code == -1
+    tree.close()
+    lv = I.uniform_leaves(1)
+    tree = fmm.Tree(lv)
+    u = torch.ones((lv.shape[0], 5, 512), dtype=torch.float64, device="cuda")
+    out = torch.empty_like(u)
+    for bad in (1.0, 0.5, float("nan"), float("inf")):
+        with pytest.raises(fmm.OTError) as e:
+            fmm.ot_hydro_rhs(tree.handle, u, None, bad, out)
+        assert e.value.code == -1
+    tree.close()
