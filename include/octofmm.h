@@ -240,22 +240,27 @@ int ot_ppm_reconstruct(ot_tree* tree, const double* u, int n_fields, double* out
 /* Right-hand side of the hydro solver, dU/dt of the conserved fields
  * U = (rho, s_x, s_y, s_z, E) of an ideal gas with adiabatic index gamma
  * (Sec. 2: finite-volume hydrodynamics with PPM values at all 26 directions
- * of a cell; Sec. 4.3.1: the hydro solver runs beside the gravity solve in
- * every Runge-Kutta stage).  The PPM values of the five fields
- * (ot_ppm_reconstruct) give, on each face, the states at its centre, edge
- * midpoints and corners; the face flux is the 2-D Simpson rule (weights
- * (1, 4, 1) x (1, 4, 1) / 36) of the local Lax-Friedrichs (Rusanov) flux
- * F* = (F(U_L) + F(U_R)) / 2 - a (U_R - U_L) / 2, a the larger of
- * |v_a| + sqrt(max(gamma p / rho, 0)) of the two states, p = (gamma - 1)
- * (E - s.s / (2 rho)); a face on the domain boundary takes the inside state
- * on both sides (transmissive); dU/dt = sum over axes of (F_low - F_high) / h
- * + (0, rho g, s.g).  The tree's leaves must all be at one level
- * (OT_ERR_INVALID_ARG otherwise, or for gamma <= 1 or not finite).
- * u: device float64 [n_leaf][5][512]; g: device float64 [n_leaf][3][512]
- * (e.g. the gravity solve's output) or NULL for no gravity; dudt: device
- * float64 [n_leaf][5][512].  The first call allocates the workspace of the
- * PPM values (130 doubles per cell).  FP64, written so that every operation
- * matches a plain FP64 evaluation of the same formulas (no fused
+ * of a cell; Sec. 3: mass, momentum and energy conserved across refinement
+ * jumps by matching the fluxes there; Sec. 4.3.1: the hydro solver runs
+ * beside the gravity solve in every Runge-Kutta stage).  Every leaf sees 3
+ * ghost layers at its own level (the same-level cells; across a refinement
+ * jump the mean of the 8 finer cells or the coarser cell's average; indices
+ * clamped into the domain); PPM (Colella & Woodward 1984) gives the states
+ * at the centre, edge midpoints and corners of each face; the face flux is
+ * the 2-D Simpson rule (weights (1, 4, 1) x (1, 4, 1) / 36) of the local
+ * Lax-Friedrichs (Rusanov) flux F* = (F(U_L) + F(U_R)) / 2 - a (U_R - U_L) / 2,
+ * a the larger of |v_a| + sqrt(max(gamma p / rho, 0)) of the two states,
+ * p = (gamma - 1) (E - s.s / (2 rho)); a face on the domain boundary takes
+ * the inside state on both sides (transmissive); a face next to a finer
+ * region takes the mean of the 4 finer faces' fluxes (flux matching);
+ * dU/dt = sum over axes of (F_low - F_high) / h + (0, rho g, s.g).
+ * OT_ERR_INVALID_ARG for gamma <= 1 or not finite.  u: device float64
+ * [n_leaf][5][512]; g: device float64 [n_leaf][3][512] (e.g. the gravity
+ * solve's output) or NULL for no gravity; dudt: device float64
+ * [n_leaf][5][512].  The first call allocates the workspace (the PPM values
+ * of the cells and of the ghost cells next to the faces, and the face
+ * fluxes: about 181 doubles per cell).  FP64, written so that every
+ * operation matches a plain FP64 evaluation of the same formulas (no fused
  * multiply-adds). */
 int ot_hydro_rhs(ot_tree* tree, const double* u, const double* g, double gamma, double* dudt, void* stream);
 

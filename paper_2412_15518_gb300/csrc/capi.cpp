@@ -95,9 +95,9 @@ struct ot_tree {
     double* d_mom_d = nullptr;
     double* d_rec_d = nullptr;
     double* d_loc_d = nullptr;
-    // hydro workspace: the PPM values of the five conserved fields
-    // (allocated by the first ot_hydro_rhs call)
-    double* d_hydro_v = nullptr;
+    // hydro workspace: the PPM values of the five conserved fields and the
+    // face fluxes (allocated by the first ot_hydro_rhs call)
+    double* d_hydro_work = nullptr;
     // staging of the host-buffer solve
     double *d_rho_in = nullptr, *d_phi_out = nullptr, *d_g_out = nullptr;
     // tuning of the persistent launch
@@ -545,7 +545,7 @@ void ot_destroy_tree(ot_tree* t) {
                         t->d_status, t->d_entries, t->d_tab64, t->d_tab32, t->d_list_first,
                         t->d_list_len, t->d_items, t->d_counter, t->d_rho_in, t->d_phi_out,
                         t->d_hoff_far, t->d_hoff_near, t->d_lattice_nodes, t->d_items_adj, t->d_item_entries,
-                        t->d_off64, t->d_off32, t->d_items_grp, t->d_grp_cells, t->d_hydro_v,
+                        t->d_off64, t->d_off32, t->d_items_grp, t->d_grp_cells, t->d_hydro_work,
                         t->d_g_out, t->d_locbar, t->d_mombar, t->d_mom_d, t->d_rec_d, t->d_loc_d};
         for (void* p : ptrs)
             if (p) cudaFree(p);
@@ -717,18 +717,16 @@ int ot_ppm_reconstruct(ot_tree* t, const double* u, int n_fields, double* out, v
 int ot_hydro_rhs(ot_tree* t, const double* u, const double* g, double gamma, double* dudt, void* stream) {
     if (!t) return OT_ERR_BAD_POINTER;
     if (t->device < 0 || !(gamma > 1.0) || !std::isfinite(gamma)) return OT_ERR_INVALID_ARG;
-    const HostTree& h = t->h;
-    const int L = h.n_levels - 1;
-    if (h.leaf_nodes_at(L) != h.n_leaf) return OT_ERR_INVALID_ARG;  // all leaves at one level
     DeviceGuard guard(t->device);
     TRY(check_dev_ptr(t, u));
     TRY(check_dev_ptr(t, dudt));
     if (g) TRY(check_dev_ptr(t, g));
-    if (!t->d_hydro_v) TRY(dalloc(t, &t->d_hydro_v, (size_t)h.n_leaf * 5 * 26 * kCells));
+    size_t own, ghost, faces;
+    const size_t n = hydro_workspace_doubles(t->h.n_leaf, &own, &ghost, &faces);
+    if (!t->d_hydro_work) TRY(dalloc(t, &t->d_hydro_work, n));
     cudaStream_t s = (cudaStream_t)stream;
     t->last_stream = s;
-    launch_ppm(dev_tree(t), t->d_leaf_node, u, 5, 8 << L, t->d_hydro_v, s);
-    launch_hydro_rhs(dev_tree(t), t->d_leaf_node, t->d_hydro_v, u, g, gamma, h.size / (double)(8 << L), dudt, s);
+    launch_hydro_rhs(dev_tree(t), t->d_leaf_node, u, g, gamma, t->d_hydro_work, dudt, s);
     TRYC(cudaGetLastError());
     return OT_OK;
 }

@@ -1,5 +1,6 @@
-"""GPU hydro right-hand side (ot_hydro_rhs) against the oracle
-(oracle/hydro.py), element by element.
+"""GPU hydro right-hand side (ot_hydro_rhs) against the oracles
+(oracle/hydro.py on uniform trees, oracle/hydro_amr.py on adaptive ones),
+element by element.
 
 Both sides evaluate the same formulas operation by operation in FP64
 without fused multiply-adds (PPM values, Rusanov fluxes, Simpson face rule,
@@ -15,6 +16,7 @@ import pytest
 import torch
 
 from oracle import hydro as H
+from oracle import hydro_amr as A
 from paper_2412_15518_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -140,15 +142,51 @@ def test_level4_linear_state_advects_at_the_closed_form_rate(fmm):
         assert np.abs(got[:, f][inner] - want[f]).max() < 1e-9, f
 
 
-def test_hydro_rhs_rejects_mixed_levels_and_bad_gamma(fmm):
-    lv = I.amr_leaves(3, 2e-4, I.BINARY)
+AMR_CASES = {
+    # levels 1-2 and 1-3 refined on the binary: coarse-fine faces, restriction
+    # and injection in the halos, flux matching
+    "binary_l1_l2_g": lambda: (lambda lv: (lv, I.hydro_fields(lv, seed=12), rand_g(lv, 13)))(
+        I.amr_leaves(2, 5e-4, I.BINARY, lmin=1)),
+    "binary_l1_l3": lambda: (lambda lv: (lv, I.hydro_fields(lv, seed=14), None))(
+        I.amr_leaves(3, 2e-4, I.BINARY)),
+    "sphere_l2_l3_g": lambda: (lambda lv: (lv, I.hydro_fields(lv, I.SPHERE, seed=15), rand_g(lv, 16)))(
+        I.amr_leaves(3, 1e-3, I.SPHERE, lmin=1)),
+}
+
+
+@pytest.mark.parametrize("case", sorted(AMR_CASES))
+def test_hydro_rhs_on_adaptive_trees_matches_oracle_bit_for_bit(fmm, case):
+    lv, u, g = AMR_CASES[case]()
+    assert len(set(np.asarray(lv)[:, 0].tolist())) >= 2
     tree = fmm.Tree(lv)
-    u = torch.ones((lv.shape[0], 5, 512), dtype=torch.float64, device="cuda")
-    out = torch.empty_like(u)
-    with pytest.raises(fmm.OTError) as e:
-        fmm.ot_hydro_rhs(tree.handle, u, None, GAMMA, out)
-    assert e.value.code == -1
+    ug = torch.from_numpy(np.ascontiguousarray(u)).cuda()
+    gg = None if g is None else torch.from_numpy(np.ascontiguousarray(g)).cuda()
+    out = tree.hydro_rhs(ug, gg, GAMMA)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    assert tree.info()["device_status"] == 0
     tree.close()
+    want = A.rhs(lv, u, g, GAMMA)
+    diff = int((got != want).sum())
+    print(f"hydro amr {case}: {got.size} values, {diff} differ, max |diff| {np.abs(got - want).max():.2e}")
+    assert np.isfinite(got).all()
+    assert diff == 0
+
+
+def test_hydro_rhs_on_an_adaptive_tree_with_the_gravity_solve(fmm):
+    lv = I.amr_leaves(3, 2e-4, I.BINARY)
+    u = I.hydro_fields(lv, seed=17)
+    tree = fmm.Tree(lv)
+    ug = torch.from_numpy(u).cuda()
+    phi, g = tree.solve(ug[:, 0].contiguous())
+    out = tree.hydro_rhs(ug, g, GAMMA)
+    torch.cuda.synchronize()
+    got, gn = out.cpu().numpy(), g.cpu().numpy()
+    tree.close()
+    assert int((got != A.rhs(lv, u, gn, GAMMA)).sum()) == 0
+
+
+def test_hydro_rhs_rejects_bad_gamma(fmm):
     lv = I.uniform_leaves(1)
     tree = fmm.Tree(lv)
     u = torch.ones((lv.shape[0], 5, 512), dtype=torch.float64, device="cuda")
