@@ -240,7 +240,7 @@ int ot_ppm_reconstruct(ot_tree* tree, const double* u, int n_fields, double* out
 /* Right-hand side of the hydro solver, dU/dt of the conserved fields
  * U = (rho, s_x, s_y, s_z, E) of an ideal gas with adiabatic index gamma
  * (Sec. 2: finite-volume hydrodynamics with PPM values at all 26 directions
- * of a cell; Sec. 3: mass, momentum and energy conserved across refinement
+ * of a cell; Sec. 4.3.1: mass, momentum and energy conserved across refinement
  * jumps by matching the fluxes there; Sec. 4.3.1: the hydro solver runs
  * beside the gravity solve in every Runge-Kutta stage).  Every leaf sees 3
  * ghost layers at its own level (the same-level cells; across a refinement

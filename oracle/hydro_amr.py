@@ -1,6 +1,6 @@
 """Oracle of the hydro right-hand side on an adaptive octree of 8^3
 sub-grids (arXiv 2412.15518, Sec. 2: finite-volume hydrodynamics with PPM
-values at all 26 directions of a cell; Sec. 3: Octo-Tiger conserves mass,
+values at all 26 directions of a cell; Sec. 4.3.1: Octo-Tiger conserves mass,
 momentum and energy across jumps in refinement level by matching the fluxes
 there; Sec. 4.3.2: the octree of sub-grids with ghost layers).
 

@@ -2,7 +2,7 @@
 // the conserved fields U = (rho, s, E) of an ideal gas from the finite-volume
 // fluxes through every cell face and the gravity source (Sec. 2: Octo-Tiger's
 // finite-volume hydrodynamics with PPM values at all 26 directions of a cell;
-// Sec. 3: mass, momentum and energy conserved across jumps in refinement level
+// Sec. 4.3.1: mass, momentum and energy conserved across jumps in refinement level
 // by matching the fluxes there; Sec. 4.3.1: the hydro solver beside the
 // gravity solve in every Runge-Kutta stage).
 //
