@@ -484,6 +484,7 @@ def run_ours(args):
             extra["binary_l3"] = companion_workload("binary_l3", flush, not args.no_autotune, peaks)
         extra["ppm_reconstruction"] = ppm_companion(flush, peaks)
         extra["hydro_rhs"] = hydro_companion(flush, peaks)
+        extra["hydro_rhs_workload_tree"] = hydro_tree_companion(tree, leaves, args.workload, flush, peaks)
         extra["cpu_baseline"] = cpu_baseline(leaves, rho_np)
     # library kernels of one solve: leaf moments; per parent level the M2M
     # kernel for cells with interior children and/or the one for cells with
@@ -652,6 +653,59 @@ def hydro_companion(flush, peaks, level=4, steps=20):
                                         "per lane per issue slot",
                          "fp64_ops_per_launch": ops_ppm + ops_flux, "ppm_ops": ops_ppm,
                          "flux_ops": ops_flux}}
+
+
+def hydro_tree_companion(tree, leaves, name, flush, peaks, steps=5):
+    """The hydro right-hand side on the workload's own tree (adaptive for the
+    AMR workloads: halos across refinement jumps, flux matching), with the
+    workload's density plus the rotating binary's momentum and energy, and g
+    from an FP64 gravity solve of that density: median time, the same
+    operation count as hydro_companion (the leaves' own cells), and the
+    volume-weighted totals of the rates against their magnitudes (what the
+    fluxes move between cells cancels; the rest is the gravity source and
+    the domain boundary)."""
+    import torch
+    from paper_2412_15518_gb300 import fmm, inputs
+    u = torch.from_numpy(inputs.hydro_fields(leaves, inputs.WORKLOAD_STARS[name])).cuda()
+    phi, g = tree.solve(u[:, 0].contiguous())
+    out = torch.empty_like(u)
+    for _ in range(2):
+        fmm.ot_hydro_rhs(tree.handle, u, g, 5.0 / 3.0, out)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fmm.ot_hydro_rhs(tree.handle, u, g, 5.0 / 3.0, out)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    med = statistics.median(ms)
+    n_leaf = leaves.shape[0]
+    cells = n_leaf * 512
+    ops = cells * 5 * 13 * 25 + n_leaf * 3 * 576 * 9 * HYDRO_OPS_PER_POINT + cells * HYDRO_OPS_PER_CELL
+    gops = ops / (med / 1e3) / 1e12
+    peak_ops = peaks["fp64_tflops"] / 2.0
+    # mass rate without gravity: fluxes only, so its total is the domain
+    # boundary's (the bench's trees span the unit cube)
+    fmm.ot_hydro_rhs(tree.handle, u, None, 5.0 / 3.0, out)
+    status = tree.info()["device_status"]
+    h = 1.0 / (8.0 * 2.0 ** torch.from_numpy(leaves[:, 0].astype("float64")).cuda())
+    w = (h ** 3)[:, None]
+    mass_rate = out[:, 0]
+    res = {"workload": f"{name}'s tree ({n_leaf} leaf sub-grids, {cells} cells, levels "
+                       f"{int(leaves[:, 0].min())}-{int(leaves[:, 0].max())}), the workload's density, "
+                       "5 conserved fields, g from the FP64 gravity solve",
+           "ms_per_launch": med, "cells_per_s": cells / (med / 1e3),
+           "roofline": {"bound": "alu", "achieved": gops, "peak": peak_ops, "unit": "T FP64 ops/s",
+                        "frac": gops / peak_ops, "fp64_ops_per_launch": ops},
+           "mass_rate_total_over_magnitude": float((mass_rate * w).sum() / (mass_rate.abs() * w).sum()),
+           "device_status": status}
+    del u, out, phi, g
+    return res
 
 
 def companion_workload(name, flush, autotune, peaks):

@@ -211,6 +211,11 @@ WORKLOADS = {
     "binary_amr8": "AMR octree to level 8, mass ratio 0.7 binary, ~40,000 leaves (~20M cells)",
 }
 
+# the stars of each workload's density (hydro_fields builds the workload's
+# density with them, plus momentum and energy)
+WORKLOAD_STARS = {"sphere_l1": SPHERE, "binary_l3": BINARY, "binary_amr6": BINARY,
+                  "binary_amr8": BINARY_Q07}
+
 AMR6_MTHR = 1e-5
 AMR8_MTHR = 1e-6
 

@@ -196,3 +196,40 @@ def test_hydro_rhs_rejects_bad_gamma(fmm):
             fmm.ot_hydro_rhs(tree.handle, u, None, bad, out)
         assert e.value.code == -1
     tree.close()
+
+
+def test_level8_adaptive_tree_properties(fmm):
+    """At the bench's adaptive size (the level-8 binary's tree, 22.1M cells,
+    levels 3-8): a uniform state is steady across every refinement jump, and
+    a compact perturbation of a gas at rest conserves the totals of mass,
+    momentum and energy (the fluxes matched at every jump); the device
+    status word stays clear."""
+    lv, _ = I.workload("binary_amr8")
+    lv = np.asarray(lv)
+    tree = fmm.Tree(lv)
+    x = torch.from_numpy(I.cell_centres(lv)).cuda()                  # [n, 512, 3]
+    u = torch.empty((lv.shape[0], 5, 512), dtype=torch.float64, device="cuda")
+    vel = (0.3, -0.2, 0.7)
+    u[:, 0] = 1.3
+    for b in range(3):
+        u[:, 1 + b] = 1.3 * vel[b]
+    u[:, 4] = 0.8 / (GAMMA - 1.0) + 0.5 * 1.3 * sum(v * v for v in vel)
+    d = tree.hydro_rhs(u, None, GAMMA)
+    torch.cuda.synchronize()
+    assert float(d.abs().max()) < 1e-8
+    r2 = ((x[..., 0] - 0.45) ** 2 + (x[..., 1] - 0.5) ** 2 + (x[..., 2] - 0.52) ** 2) / 0.0625
+    bump = torch.clamp(1.0 - r2, min=0.0) ** 4
+    u[:, 0] = 1.0 + 0.5 * bump
+    u[:, 1] = 0.3 * bump * (x[..., 1] - 0.5)
+    u[:, 2] = -0.2 * bump * (x[..., 0] - 0.45)
+    u[:, 3] = 0.1 * bump
+    u[:, 4] = 1.5 + 0.8 * bump
+    d = tree.hydro_rhs(u, None, GAMMA)
+    torch.cuda.synchronize()
+    h = 1.0 / (8.0 * 2.0 ** torch.from_numpy(lv[:, 0].astype(np.float64)).cuda())
+    w = (h ** 3)[:, None, None]
+    total = (d * w).sum(dim=(0, 2))
+    scale = (d.abs() * w).sum(dim=(0, 2))
+    assert bool((total.abs() < 1e-11 * scale).all()), (total / scale).tolist()
+    assert tree.info()["device_status"] == 0
+    tree.close()
