@@ -188,9 +188,12 @@ int ot_compute_moments(ot_tree* tree, const double* rho, void* stream);
 int ot_solve_gravity(ot_tree* tree, const double* rho, double* phi, double* g,
                      const ot_solve_opts* opts, void* stream);
 
-/* Same as ot_solve_gravity with HOST buffers (pageable or pinned):
- * copies rho in, solves, copies phi and g out, all on `stream`; the outputs
- * are valid after the stream is synchronised. */
+/* Same as ot_solve_gravity with HOST buffers, all on `stream`; the outputs
+ * are valid after the stream is synchronised.  Page-locked (pinned) buffers,
+ * which the device can address, are read and written by the solve's own
+ * kernels across the host link (no staging copies; a CUDA graph per buffer
+ * set, as for device buffers); pageable buffers are copied in to and out of
+ * device staging buffers around the solve.  Buffers must be 8-byte aligned. */
 int ot_solve_gravity_host(ot_tree* tree, const double* rho_host, double* phi_host,
                           double* g_host, const ot_solve_opts* opts, void* stream);
 

@@ -593,6 +593,24 @@ int ot_solve_gravity_host(ot_tree* t, const double* rho_host, double* phi_host, 
     DeviceGuard guard(t->device);
     TRY(ensure_plan(t, o.theta));
     cudaStream_t s = (cudaStream_t)stream;
+    t->last_stream = s;
+    // page-locked host buffers are mapped into the device's address space: the
+    // solve then reads the densities and writes phi and g across the host link
+    // inside its own kernels, overlapped with the computation, with no
+    // staging copies; other host memory goes through the device buffers
+    auto mapped = [](const void* p, void** dp) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        if (a.type != cudaMemoryTypeHost || !a.devicePointer || (((uintptr_t)a.devicePointer) & 7)) return false;
+        *dp = a.devicePointer;
+        return true;
+    };
+    void *dr = nullptr, *dphi = nullptr, *dg = nullptr;
+    if (mapped(rho_host, &dr) && mapped(phi_host, &dphi) && mapped(g_host, &dg))
+        return solve_graph(t, (const double*)dr, (double*)dphi, (double*)dg, o, s);
     const size_t n = (size_t)t->h.n_leaf * kCells;
     TRYC(cudaMemcpyAsync(t->d_rho_in, rho_host, n * sizeof(double), cudaMemcpyHostToDevice, s));
     TRY(solve_graph(t, t->d_rho_in, t->d_phi_out, t->d_g_out, o, s));

@@ -262,10 +262,32 @@ def test_graph_replay_and_host_buffers(fmm):
     hr = torch.from_numpy(rho2).pin_memory()
     hp = torch.empty((lv.shape[0], 512), dtype=torch.float64).pin_memory()
     hg = torch.empty((lv.shape[0], 3, 512), dtype=torch.float64).pin_memory()
-    tree.solve_host(hr, hp, hg)
+    tree.solve_host(hr, hp, hg)    # pinned: read and written by the kernels
     torch.cuda.synchronize()
     assert rel(hp.numpy(), phi_o) < TOL64
     assert rel(hg.numpy(), g_o) < TOL64
+    # the same pinned buffers with new contents replay their graph
+    hr.copy_(torch.from_numpy(rho))
+    tree.solve_host(hr, hp, hg)
+    torch.cuda.synchronize()
+    phi_r, g_r = O.solve(lv, rho)
+    assert rel(hp.numpy(), phi_r) < TOL64
+    assert rel(hg.numpy(), g_r) < TOL64
+    # pageable buffers: staged through device copies; and the self term,
+    # which reads the densities again in the evaluation
+    pr = np.ascontiguousarray(rho2)
+    pp = np.empty((lv.shape[0], 512))
+    pg = np.empty((lv.shape[0], 3, 512))
+    tree.solve_host(pr, pp, pg)
+    torch.cuda.synchronize()
+    assert rel(pp, phi_o) < TOL64
+    assert rel(pg, g_o) < TOL64
+    hr.copy_(torch.from_numpy(rho2))
+    tree.solve_host(hr, hp, hg, self_term=True)
+    torch.cuda.synchronize()
+    phi_s, g_s = O.solve(lv, rho2, self_term=True)
+    assert rel(hp.numpy(), phi_s) < TOL64
+    assert rel(hg.numpy(), g_s) < TOL64
     tree.close()
 
 
