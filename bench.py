@@ -485,6 +485,7 @@ def run_ours(args):
         extra["ppm_reconstruction"] = ppm_companion(flush, peaks)
         extra["hydro_rhs"] = hydro_companion(flush, peaks)
         extra["hydro_rhs_workload_tree"] = hydro_tree_companion(tree, leaves, args.workload, flush, peaks)
+        extra["rk3_step_workload_tree"] = step_companion(tree, leaves, args.workload, flush)
         extra["cpu_baseline"] = cpu_baseline(leaves, rho_np)
     # library kernels of one solve: leaf moments; per parent level the M2M
     # kernel for cells with interior children and/or the one for cells with
@@ -706,6 +707,40 @@ def hydro_tree_companion(tree, leaves, name, flush, peaks, steps=5):
            "device_status": status}
     del u, out, phi, g
     return res
+
+
+def step_companion(tree, leaves, name, flush, steps=2):
+    """One coupled time step on the workload's own tree, on the device: the
+    third-order Runge-Kutta scheme, each of its 3 stages a gravity solve of
+    the stage's density (FP64) and the hydro right-hand side, with the
+    combinations between them (ot_hydro_rk3_step).  Median time per step."""
+    import torch
+    from paper_2412_15518_gb300 import fmm, inputs
+    u0 = torch.from_numpy(inputs.hydro_fields(leaves, inputs.WORKLOAD_STARS[name])).cuda()
+    u = u0.clone()
+    fmm.ot_hydro_rk3_step(tree.handle, u, 1e-5, 5.0 / 3.0, 1)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ms = []
+    for _ in range(steps):
+        u.copy_(u0)
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fmm.ot_hydro_rk3_step(tree.handle, u, 1e-5, 5.0 / 3.0, 1)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    med = statistics.median(ms)
+    cells = leaves.shape[0] * 512
+    status = tree.info()["device_status"]
+    del u, u0
+    return {"workload": f"{name}'s tree ({cells} cells), the workload's density plus the rotating "
+                        "binary's momentum and energy, dt = 1e-5",
+            "ms_per_step": med, "cell_updates_per_s": cells / (med / 1e3),
+            "includes": "3 stages x (FP64 gravity solve of the stage density + hydro right-hand side "
+                        "+ Runge-Kutta combination)", "device_status": status}
 
 
 def companion_workload(name, flush, autotune, peaks):

@@ -267,6 +267,23 @@ int ot_ppm_reconstruct(ot_tree* tree, const double* u, int n_fields, double* out
  * multiply-adds). */
 int ot_hydro_rhs(ot_tree* tree, const double* u, const double* g, double gamma, double* dudt, void* stream);
 
+/* One time step of the coupled hydro-gravity system, on the device (Sec.
+ * 4.3.1: a third-order Runge-Kutta scheme whose every stage runs the hydro
+ * solver and the FMM gravity solve; the paper names GPU-resident data as the
+ * next step, Sec. 5.5 and Sec. 6).  The scheme is the strong-stability-
+ * preserving third-order method of Shu & Osher (1988): U1 = U0 + dt L(U0),
+ * U2 = 3/4 U0 + 1/4 (U1 + dt L(U1)), U3 = 1/3 U0 + 2/3 (U2 + dt L(U2)),
+ * each combination in that order, where L is ot_hydro_rhs with, when
+ * gravity is 1, the acceleration of one ot_solve_gravity of the stage's own
+ * density U[:, 0] (opts: that solve's options, NULL for the defaults;
+ * gravity 0: no gravity, opts unused).  u: device float64 [n_leaf][5][512],
+ * U^n in, U^(n+1) out.  dt: finite.  OT_ERR_INVALID_ARG for a bad gamma, dt,
+ * gravity flag or solve option.  The first call allocates 20 doubles per
+ * cell besides ot_hydro_rhs's workspace; the gravity solves replay one CUDA
+ * graph. */
+int ot_hydro_rk3_step(ot_tree* tree, double* u, double dt, double gamma, int gravity,
+                      const ot_solve_opts* opts, void* stream);
+
 /* Chooses the persistent launch's stencil-chunk length and the CTAs per SM
  * of the general kernel (and, wide FP32 form, of the lattice kernels) for
  * this plan: every candidate is timed as the whole solve graph it would run,

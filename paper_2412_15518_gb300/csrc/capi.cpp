@@ -98,6 +98,9 @@ struct ot_tree {
     // hydro workspace: the PPM values of the five conserved fields and the
     // face fluxes (allocated by the first ot_hydro_rhs call)
     double* d_hydro_work = nullptr;
+    // time-step workspace: U0, the stage state, dU/dt, and the stage's
+    // density, phi and g (allocated by the first ot_hydro_rk3_step call)
+    double* d_step = nullptr;
     // staging of the host-buffer solve
     double *d_rho_in = nullptr, *d_phi_out = nullptr, *d_g_out = nullptr;
     // tuning of the persistent launch
@@ -545,7 +548,7 @@ void ot_destroy_tree(ot_tree* t) {
                         t->d_status, t->d_entries, t->d_tab64, t->d_tab32, t->d_list_first,
                         t->d_list_len, t->d_items, t->d_counter, t->d_rho_in, t->d_phi_out,
                         t->d_hoff_far, t->d_hoff_near, t->d_lattice_nodes, t->d_items_adj, t->d_item_entries,
-                        t->d_off64, t->d_off32, t->d_items_grp, t->d_grp_cells, t->d_hydro_work,
+                        t->d_off64, t->d_off32, t->d_items_grp, t->d_grp_cells, t->d_hydro_work, t->d_step,
                         t->d_g_out, t->d_locbar, t->d_mombar, t->d_mom_d, t->d_rec_d, t->d_loc_d};
         for (void* p : ptrs)
             if (p) cudaFree(p);
@@ -745,6 +748,47 @@ int ot_hydro_rhs(ot_tree* t, const double* u, const double* g, double gamma, dou
     cudaStream_t s = (cudaStream_t)stream;
     t->last_stream = s;
     launch_hydro_rhs(dev_tree(t), t->d_leaf_node, u, g, gamma, t->d_hydro_work, dudt, s);
+    TRYC(cudaGetLastError());
+    return OT_OK;
+}
+
+int ot_hydro_rk3_step(ot_tree* t, double* u, double dt, double gamma, int gravity, const ot_solve_opts* opts,
+                      void* stream) {
+    if (!t) return OT_ERR_BAD_POINTER;
+    if (t->device < 0 || !(gamma > 1.0) || !std::isfinite(gamma) || !std::isfinite(dt) ||
+        (gravity != 0 && gravity != 1))
+        return OT_ERR_INVALID_ARG;
+    ot_solve_opts o;
+    fill_opts(opts, o);
+    if (gravity) TRY(check_opts(o));
+    DeviceGuard guard(t->device);
+    TRY(check_dev_ptr(t, u));
+    if (gravity) TRY(ensure_plan(t, o.theta));
+    const int nl = t->h.n_leaf;
+    const size_t nc = (size_t)nl * kCells;
+    size_t own, ghost, faces;
+    const size_t nw = hydro_workspace_doubles(nl, &own, &ghost, &faces);
+    if (!t->d_hydro_work) TRY(dalloc(t, &t->d_hydro_work, nw));
+    if (!t->d_step) TRY(dalloc(t, &t->d_step, 20 * nc));
+    double* U0 = t->d_step;        // [n_leaf][5][512]
+    double* Us = U0 + 5 * nc;      // the stage state
+    double* L = Us + 5 * nc;       // its dU/dt
+    double* rho = L + 5 * nc;      // [n_leaf][512]
+    double* phi = rho + nc;        // [n_leaf][512]
+    double* g = phi + nc;          // [n_leaf][3][512]
+    cudaStream_t s = (cudaStream_t)stream;
+    t->last_stream = s;
+    TRYC(cudaMemcpyAsync(U0, u, 5 * nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    const DevTree d = dev_tree(t);
+    for (int stage = 1; stage <= 3; stage++) {
+        const double* U = stage == 1 ? U0 : Us;
+        if (gravity) {
+            launch_stage_density(U, rho, nl, s);
+            TRY(solve_graph(t, rho, phi, g, o, s));
+        }
+        launch_hydro_rhs(d, t->d_leaf_node, U, gravity ? g : nullptr, gamma, t->d_hydro_work, L, s);
+        launch_rk3_combine(U0, Us, L, dt, stage, stage == 3 ? u : Us, nl, s);
+    }
     TRYC(cudaGetLastError());
     return OT_OK;
 }

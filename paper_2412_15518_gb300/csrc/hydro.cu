@@ -449,7 +449,41 @@ __global__ void __launch_bounds__(256) k_hydro_assemble(DevTree t, const int* __
         for (int f = 0; f < kNF; f++) out[((long long)leaf * kNF + f) * kCells + cell] = r[f];
     }
 }
+// The density of the stage's state, rho[leaf][c] = U[leaf][0][c], for its
+// gravity solve.
+__global__ void k_stage_density(const double* __restrict__ U, double* __restrict__ rho, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) rho[i] = U[(i / kCells) * kNF * kCells + (i % kCells)];
+}
+
+// One combination of the third-order strong-stability-preserving Runge-Kutta
+// scheme (Shu & Osher 1988), in the order written: stage 1
+// out = U0 + dt L; stage 2 out = 3/4 U0 + 1/4 (Uc + dt L); stage 3
+// out = 1/3 U0 + 2/3 (Uc + dt L).
+__global__ void k_rk3_combine(const double* __restrict__ U0, const double* Uc, const double* __restrict__ L,
+                              double dt, int stage, double* out, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double dl = __dmul_rn(dt, L[i]);
+    double v;
+    if (stage == 1) v = __dadd_rn(U0[i], dl);
+    else if (stage == 2) v = __dadd_rn(__dmul_rn(0.75, U0[i]), __dmul_rn(0.25, __dadd_rn(Uc[i], dl)));
+    else v = __dadd_rn(__dmul_rn(1.0 / 3.0, U0[i]), __dmul_rn(2.0 / 3.0, __dadd_rn(Uc[i], dl)));
+    out[i] = v;
+}
+
 }  // namespace
+
+void launch_stage_density(const double* U, double* rho, int n_leaf, cudaStream_t s) {
+    const long long n = (long long)n_leaf * kCells;
+    if (n > 0) k_stage_density<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(U, rho, n);
+}
+
+void launch_rk3_combine(const double* U0, const double* Uc, const double* L, double dt, int stage, double* out,
+                        int n_leaf, cudaStream_t s) {
+    const long long n = (long long)n_leaf * kNF * kCells;
+    if (n > 0) k_rk3_combine<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(U0, Uc, L, dt, stage, out, n);
+}
 
 size_t hydro_workspace_doubles(int n_leaf, size_t* own, size_t* ghost, size_t* faces) {
     *own = (size_t)n_leaf * kNF * 26 * kCells;

@@ -75,6 +75,8 @@ _lib.ot_solve_gravity_static.argtypes = [ctypes.POINTER(ot_tree_desc), _P, _P, _
 _lib.ot_solve_gravity_tangent.argtypes = [_P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(ot_solve_opts), _P]
 _lib.ot_ppm_reconstruct.argtypes = [_P, _P, ctypes.c_int, _P, _P]
 _lib.ot_hydro_rhs.argtypes = [_P, _P, _P, ctypes.c_double, _P, _P]
+_lib.ot_hydro_rk3_step.argtypes = [_P, _P, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                   ctypes.POINTER(ot_solve_opts), _P]
 _lib.ot_get_moments.argtypes = [_P, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int32), _P]
 _lib.ot_set_launch_shape.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
 _lib.ot_alu_peaks.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -88,7 +90,7 @@ EXPORTS = ["ot_build_tree", "ot_compute_moments", "ot_solve_gravity", "ot_solve_
            "ot_gravity_backward", "ot_autotune", "ot_last_solve_times", "ot_tree_info",
            "ot_destroy_tree", "ot_error_string", "ot_solve_gravity_static", "ot_get_moments",
            "ot_set_launch_shape", "ot_alu_peaks", "ot_solve_gravity_tangent",
-           "ot_ppm_reconstruct", "ot_hydro_rhs"]
+           "ot_ppm_reconstruct", "ot_hydro_rhs", "ot_hydro_rk3_step"]
 
 
 class OTError(RuntimeError):
@@ -175,6 +177,12 @@ def ot_solve_gravity_tangent(tree, rho, rho_dot, phi, g, phi_dot, g_dot,
 def ot_hydro_rhs(tree, u, g, gamma, dudt, stream=None):
     _check(_lib.ot_hydro_rhs(_P(tree), _ptr(u), _ptr(g), float(gamma), _ptr(dudt), _stream(stream)),
            "ot_hydro_rhs")
+
+
+def ot_hydro_rk3_step(tree, u, dt, gamma, gravity, opts=None, stream=None):
+    o = ctypes.byref(opts) if opts is not None else None
+    _check(_lib.ot_hydro_rk3_step(_P(tree), _ptr(u), float(dt), float(gamma), int(gravity), o,
+                                  _stream(stream)), "ot_hydro_rk3_step")
 
 
 def ot_ppm_reconstruct(tree, u, out, stream=None):
@@ -328,6 +336,13 @@ class Tree:
         out = torch.empty_like(u)
         ot_hydro_rhs(self.handle, u, g, gamma, out, stream)
         return out
+
+    def hydro_step(self, u, dt, gamma=5.0 / 3.0, gravity=True, stream=None, **opts):
+        """One third-order Runge-Kutta step of the conserved fields u
+        [n_leaf, 5, 512] in place, each stage with the gravity solve of its
+        own density (gravity=True) or without gravity."""
+        ot_hydro_rk3_step(self.handle, u, dt, gamma, 1 if gravity else 0, make_opts(**opts), stream)
+        return u
 
     def compute_moments(self, rho, stream=None):
         ot_compute_moments(self.handle, rho, stream)
