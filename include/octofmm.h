@@ -270,7 +270,7 @@ int ot_hydro_rhs(ot_tree* tree, const double* u, const double* g, double gamma, 
 /* One time step of the coupled hydro-gravity system, on the device (Sec.
  * 4.3.1: a third-order Runge-Kutta scheme whose every stage runs the hydro
  * solver and the FMM gravity solve; the paper names GPU-resident data as the
- * next step, Sec. 5.5 and Sec. 6).  The scheme is the strong-stability-
+ * next step, Sec. 5.5 and Sec. 8).  The scheme is the strong-stability-
  * preserving third-order method of Shu & Osher (1988): U1 = U0 + dt L(U0),
  * U2 = 3/4 U0 + 1/4 (U1 + dt L(U1)), U3 = 1/3 U0 + 2/3 (U2 + dt L(U2)),
  * each combination in that order, where L is ot_hydro_rhs with, when
