@@ -142,8 +142,12 @@ typedef struct {
     int32_t tuned_lattice_ctas_per_sm;         /* wide FP32 form: persistent CTAs per
                                                   SM of each lattice kernel (0: one
                                                   CTA per leaf node)                 */
-    int32_t device_status;                     /* latched device error, 0 = none;
-                                                  reading it clears it              */
+    int32_t device_status;                     /* latched device errors, 0 = none;
+                                                  reading it clears it.  Bits: 1 a
+                                                  tree lookup a valid tree cannot
+                                                  produce, 2 a work item longer than
+                                                  a kernel stages, 4 a hydro state
+                                                  with a density <= 0 (or NaN)      */
     int64_t workspace_bytes;                   /* device memory held by the tree    */
     double flops_bulk64;                       /* FP32-bulk form, one interaction
                                                   launch with the correction: FP64
@@ -257,7 +261,10 @@ int ot_ppm_reconstruct(ot_tree* tree, const double* u, int n_fields, double* out
  * the inside state on both sides (transmissive); a face next to a finer
  * region takes the mean of the 4 finer faces' fluxes (flux matching);
  * dU/dt = sum over axes of (F_low - F_high) / h + (0, rho g, s.g).
- * OT_ERR_INVALID_ARG for gamma <= 1 or not finite.  u: device float64
+ * OT_ERR_INVALID_ARG for gamma <= 1 or not finite.  A face state whose
+ * density is not positive (a non-physical state) is latched in the device
+ * status word (bit 4), which ot_tree_info reports as OT_ERR_DEVICE_STATUS;
+ * the rates are then not finite.  u: device float64
  * [n_leaf][5][512]; g: device float64 [n_leaf][3][512] (e.g. the gravity
  * solve's output) or NULL for no gravity; dudt: device float64
  * [n_leaf][5][512].  The first call allocates the workspace (the PPM values

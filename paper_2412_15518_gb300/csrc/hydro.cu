@@ -265,7 +265,7 @@ __device__ __forceinline__ int face_index(int fa, const int* c) {
 template <int A>
 __device__ __forceinline__ void leaf_faces(const double* __restrict__ Vown, const double* __restrict__ Vgh,
                                            int leaf, bool lo_bd, bool hi_bd, double gamma, double gm1,
-                                           double* __restrict__ F) {
+                                           double* __restrict__ F, int* status) {
     constexpr int T1 = (A + 1) % 3, T2 = (A + 2) % 3;
     constexpr int kStA = A == 0 ? 1 : (A == 1 ? 8 : 64);
     for (int idx = threadIdx.x; idx < kFaces; idx += blockDim.x) {
@@ -315,6 +315,8 @@ __device__ __forceinline__ void leaf_faces(const double* __restrict__ Vown, cons
             if (fa == 8 && hi_bd)
 #pragma unroll
                 for (int f = 0; f < kNF; f++) UR[f] = UL[f];
+            // a non-physical state is reported, not hidden (its rates are not finite)
+            if (!(UL[0] > 0.0) || !(UR[0] > 0.0)) atomicOr(status, kStatusBadDensity);
             double FL[kNF], FR[kNF];
             const double cl = state_flux<A>(UL, gamma, gm1, FL);
             const double cr = state_flux<A>(UR, gamma, gm1, FR);
@@ -343,9 +345,9 @@ __global__ void __launch_bounds__(256) k_hydro_faces(DevTree t, const int* __res
     const int top = (1 << t.node_level[node]) - 1;
     const int* xyz = t.node_xyz + 3 * node;
     const double gm1 = __dsub_rn(gamma, 1.0);
-    leaf_faces<0>(Vown, Vgh, leaf, xyz[0] == 0, xyz[0] == top, gamma, gm1, F);
-    leaf_faces<1>(Vown, Vgh, leaf, xyz[1] == 0, xyz[1] == top, gamma, gm1, F);
-    leaf_faces<2>(Vown, Vgh, leaf, xyz[2] == 0, xyz[2] == top, gamma, gm1, F);
+    leaf_faces<0>(Vown, Vgh, leaf, xyz[0] == 0, xyz[0] == top, gamma, gm1, F, t.status);
+    leaf_faces<1>(Vown, Vgh, leaf, xyz[1] == 0, xyz[1] == top, gamma, gm1, F, t.status);
+    leaf_faces<2>(Vown, Vgh, leaf, xyz[2] == 0, xyz[2] == top, gamma, gm1, F, t.status);
 }
 
 // d += F_low - F_high along A for the cell c of the leaf; a boundary face

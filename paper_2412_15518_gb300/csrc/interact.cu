@@ -690,7 +690,8 @@ void launch_interact(const DevTree& t, const DevPlan& p, int precision, double G
                      int ctas, int warps_per_cta, cudaStream_t s) {
     if (warps_per_cta > 4) warps_per_cta = 4;
     const LevelScales sc = level_scales(t.inv_side8, G);
-    // the FP64 and FP32-bulk forms take the grouped items where the plan has them
+    // the FP64 and FP32-bulk forms take the grouped items where the plan has
+    // them; the wide FP32 form's staged loop keeps the parity-class items
     DevPlan g = p;
     if (p.items_grp) {
         g.items = p.items_grp;

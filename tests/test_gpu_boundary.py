@@ -112,9 +112,9 @@ def test_fixed_launch_shape_keeps_parity(fmm):
 
 def test_device_status_latch_reports_an_over_long_item_once(fmm):
     """Items of up to 1000 stencil entries at theta = 0.35 (lists of about 700
-    entries at levels >= 1): the FP64 kernel handles them, the wide FP32
-    kernel (264 staged entries) skips them and latches the status word;
-    ot_tree_info reports that once and clears it."""
+    entries at levels >= 1): the FP64 and FP32-bulk kernels (grouped items)
+    handle them, the wide FP32 kernel (264 staged entries) skips them and
+    latches the status word; ot_tree_info reports that once and clears it."""
     lv = I.uniform_leaves(2)
     rho = I.density(lv, I.BINARY, seed=2)
     theta = 0.35
@@ -122,10 +122,12 @@ def test_device_status_latch_reports_an_over_long_item_once(fmm):
     r = torch.from_numpy(rho).cuda()
     phi_o, g_o = O.solve(lv, rho, theta=theta)
     tree.set_launch_shape(1000, 4)
-    phi, g = tree.solve(r, theta=theta)
-    torch.cuda.synchronize()
-    assert rel(phi.cpu().numpy(), phi_o) < 1e-12
-    assert tree.info()["device_status"] == 0
+    for prec, tol in ((fmm.OT_PRECISION_FP64, 1e-12), (fmm.OT_PRECISION_FP32_BULK, 1e-8)):
+        phi, g = tree.solve(r, theta=theta, precision=prec)
+        torch.cuda.synchronize()
+        assert rel(phi.cpu().numpy(), phi_o) < tol
+        assert rel(g.cpu().numpy(), g_o) < tol
+        assert tree.info()["device_status"] == 0
     tree.solve(r, theta=theta, precision=fmm.OT_PRECISION_FP32_WIDE)
     with pytest.raises(fmm.OTError) as e:
         tree.info()
@@ -136,6 +138,29 @@ def test_device_status_latch_reports_an_over_long_item_once(fmm):
     torch.cuda.synchronize()
     assert rel(phi.cpu().numpy(), phi_o) < 1e-6
     assert rel(g.cpu().numpy(), g_o) < 1e-6
+    assert tree.info()["device_status"] == 0
+    tree.close()
+
+
+def test_device_status_latch_reports_a_non_physical_state_once(fmm):
+    """A hydro state with a zero density in one cell: the faces kernel
+    latches bit 4 of the status word; ot_tree_info reports it once as
+    OT_ERR_DEVICE_STATUS and clears it; a physical state then leaves it
+    clear."""
+    lv = I.uniform_leaves(1)
+    u = torch.from_numpy(I.hydro_fields(lv, seed=3)).cuda()
+    tree = fmm.Tree(lv)
+    bad = u.clone()
+    bad[2, 0, 100] = 0.0
+    tree.hydro_rhs(bad)
+    torch.cuda.synchronize()
+    with pytest.raises(fmm.OTError) as e:
+        tree.info()
+    assert e.value.code == -8                       # OT_ERR_DEVICE_STATUS
+    assert tree.info()["device_status"] == 0        # reported once, then cleared
+    d = tree.hydro_rhs(u)
+    torch.cuda.synchronize()
+    assert bool(torch.isfinite(d).all())
     assert tree.info()["device_status"] == 0
     tree.close()
 
