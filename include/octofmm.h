@@ -56,6 +56,11 @@ extern "C" {
 #define OT_ERR_CUDA -6           /* a CUDA runtime call failed                    */
 #define OT_ERR_TIMEOUT -7        /* a bounded device wait gave up                 */
 #define OT_ERR_DEVICE_STATUS -8  /* a kernel latched an error in the status word  */
+
+/* Bits of the device status word (ot_tree_stats.device_status). */
+#define OT_STATUS_BAD_INDEX 1    /* a tree lookup a validated tree cannot produce  */
+#define OT_STATUS_BAD_ITEM 2     /* a work item longer than a kernel stages        */
+#define OT_STATUS_BAD_DENSITY 4  /* a hydro face state with density <= 0 or NaN    */
 #define OT_ERR_NO_MEMORY -9      /* host or device allocation failed              */
 #define OT_ERR_WRONG_DEVICE -10  /* buffer on another device than the tree        */
 #define OT_ERR_TOO_LARGE -11     /* problem exceeds a fixed-size scratch buffer   */

@@ -153,6 +153,19 @@ __global__ void __launch_bounds__(256) k_hydro_ppm(DevTree t, const int* __restr
                 if (k >= 0 && k < km) lines[nl++] = {ox, oy, oz, k, km};
             }
     __syncthreads();
+    // The ghost cells next to a face need their own values only across a
+    // refinement jump: across a same-level leaf they are that leaf's own
+    // values (the same averages, the same arithmetic), which the faces kernel
+    // reads there; across the domain boundary the face takes the inside state.
+    bool need[6];
+    const int top = (1 << L) - 1;
+#pragma unroll
+    for (int side = 0; side < 6; side++) {
+        const int A = side >> 1, hi = side & 1;
+        const int step = A == 0 ? 1 : (A == 1 ? 3 : 9);
+        const bool boundary = hi ? xyz[A] == top : xyz[A] == 0;
+        need[side] = !boundary && s.lf[13 + (hi ? step : -step)] < 0;
+    }
     for (int f = 0; f < kNF; f++) {
         for (int h = threadIdx.x; h < kHs * kHs * kHs; h += blockDim.x) {
             const int hx = h % kHs, hy = (h / kHs) % kHs, hz = h / (kHs * kHs);
@@ -168,9 +181,20 @@ __global__ void __launch_bounds__(256) k_hydro_ppm(DevTree t, const int* __restr
             const int ex = lines[l].ex, ey = lines[l].ey, ez = lines[l].ez;
             const int st = ex + kHs * (ey + kHs * ez);
             // boundary values between p and p + e for the positions p = c and
-            // p = c - e of the cells c in [-1, 8]^3 (box positions -2..9)
-            const int lx = ex > 0 ? -2 : -1, ly = ey > 0 ? -2 : -1, lz = ez > 0 ? -2 : -1;
-            const int nx = ex ? 11 : 10, ny = ey ? 11 : 10, nz = ez ? 11 : 10;
+            // p = c - e of the leaf's cells and of the ghost cells it needs
+            int lo[3], hi[3];
+            {
+                const int e[3] = {ex, ey, ez};
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    lo[a] = min(0, -e[a]);
+                    hi[a] = max(7, 7 - e[a]);
+                    if (need[2 * a]) lo[a] = min(lo[a], min(-1, -1 - e[a]));
+                    if (need[2 * a + 1]) hi[a] = max(hi[a], max(8, 8 - e[a]));
+                }
+            }
+            const int lx = lo[0], ly = lo[1], lz = lo[2];
+            const int nx = hi[0] - lo[0] + 1, ny = hi[1] - lo[1] + 1, nz = hi[2] - lo[2] + 1;
             for (int q = threadIdx.x; q < nx * ny * nz; q += blockDim.x) {
                 const int px = q % nx + lx, py = (q / nx) % ny + ly, pz = q / (nx * ny) + lz;
                 const int h = (px + kW) + kHs * ((py + kW) + kHs * (pz + kW));
@@ -188,6 +212,7 @@ __global__ void __launch_bounds__(256) k_hydro_ppm(DevTree t, const int* __restr
                     c[2] = q >> 6;
                 } else {
                     side = (q - kCells) >> 6;
+                    if (!need[side]) continue;
                     gq = (q - kCells) & 63;
                     const int A = side >> 1;
                     c[A] = (side & 1) ? 8 : -1;
@@ -264,8 +289,8 @@ __device__ __forceinline__ int face_index(int fa, const int* c) {
 // the domain boundary (the inside state on both sides).
 template <int A>
 __device__ __forceinline__ void leaf_faces(const double* __restrict__ Vown, const double* __restrict__ Vgh,
-                                           int leaf, bool lo_bd, bool hi_bd, double gamma, double gm1,
-                                           double* __restrict__ F, int* status) {
+                                           int leaf, bool lo_bd, bool hi_bd, int lf_lo, int lf_hi, double gamma,
+                                           double gm1, double* __restrict__ F, int* status) {
     constexpr int T1 = (A + 1) % 3, T2 = (A + 2) % 3;
     constexpr int kStA = A == 0 ? 1 : (A == 1 ? 8 : 64);
     for (int idx = threadIdx.x; idx < kFaces; idx += blockDim.x) {
@@ -285,7 +310,11 @@ __device__ __forceinline__ void leaf_faces(const double* __restrict__ Vown, cons
         }
         c[A] = 0;
         const int base = c[0] + 8 * c[1] + 64 * c[2];
-        const int cellL = base + (fa - 1) * kStA, cellR = base + fa * kStA;
+        // at the leaf's faces: the same-level neighbour's own cell (7 or 0
+        // along A) where there is one, else the ghost cell's values
+        const int cellL = base + (fa == 0 ? 7 : fa - 1) * kStA, cellR = base + (fa == 8 ? 0 : fa) * kStA;
+        const int leafL = fa == 0 ? lf_lo : leaf, leafR = fa == 8 ? lf_hi : leaf;
+        const bool ghL = fa == 0 && lf_lo < 0, ghR = fa == 8 && lf_hi < 0;
         const int gq = c[T1] + 8 * c[T2];
         double acc[kNF];
 #pragma unroll
@@ -304,10 +333,14 @@ __device__ __forceinline__ void leaf_faces(const double* __restrict__ Vown, cons
 #pragma unroll
             for (int f = 0; f < kNF; f++) {
                 const long long lf = (long long)leaf * kNF + f;
-                UL[f] = fa == 0 ? __ldg(Vgh + ((lf * 6 + 2 * A) * 9 + p) * 64 + gq)
-                                : __ldg(Vown + (lf * 26 + kL) * kCells + cellL);
-                UR[f] = fa == 8 ? __ldg(Vgh + ((lf * 6 + 2 * A + 1) * 9 + p) * 64 + gq)
-                                : __ldg(Vown + (lf * 26 + kR) * kCells + cellR);
+                // (a ghost slot at the domain boundary is never read: the
+                // inside state stands on both sides there)
+                if (!(fa == 0 && lo_bd))
+                    UL[f] = ghL ? __ldg(Vgh + ((lf * 6 + 2 * A) * 9 + p) * 64 + gq)
+                                : __ldg(Vown + (((long long)leafL * kNF + f) * 26 + kL) * kCells + cellL);
+                if (!(fa == 8 && hi_bd))
+                    UR[f] = ghR ? __ldg(Vgh + ((lf * 6 + 2 * A + 1) * 9 + p) * 64 + gq)
+                                : __ldg(Vown + (((long long)leafR * kNF + f) * 26 + kR) * kCells + cellR);
             }
             if (fa == 0 && lo_bd)
 #pragma unroll
@@ -336,7 +369,7 @@ __device__ __forceinline__ void leaf_faces(const double* __restrict__ Vown, cons
     }
 }
 
-__global__ void __launch_bounds__(256) k_hydro_faces(DevTree t, const int* __restrict__ leaf_node,
+__global__ void __launch_bounds__(256, 3) k_hydro_faces(DevTree t, const int* __restrict__ leaf_node,
                                                       const double* __restrict__ Vown,
                                                       const double* __restrict__ Vgh, double gamma,
                                                       double* __restrict__ F) {
@@ -345,9 +378,20 @@ __global__ void __launch_bounds__(256) k_hydro_faces(DevTree t, const int* __res
     const int top = (1 << t.node_level[node]) - 1;
     const int* xyz = t.node_xyz + 3 * node;
     const double gm1 = __dsub_rn(gamma, 1.0);
-    leaf_faces<0>(Vown, Vgh, leaf, xyz[0] == 0, xyz[0] == top, gamma, gm1, F, t.status);
-    leaf_faces<1>(Vown, Vgh, leaf, xyz[1] == 0, xyz[1] == top, gamma, gm1, F, t.status);
-    leaf_faces<2>(Vown, Vgh, leaf, xyz[2] == 0, xyz[2] == top, gamma, gm1, F, t.status);
+    // the same-level leaf across each face (-1: none)
+    int lf[6];
+#pragma unroll
+    for (int side = 0; side < 6; side++) {
+        const int step = (side >> 1) == 0 ? 1 : ((side >> 1) == 1 ? 3 : 9);
+        const int nb = t.nbr[(long long)node * 27 + 13 + ((side & 1) ? step : -step)];
+        lf[side] = nb >= 0 ? t.node_leaf[nb] : -1;
+    }
+    leaf_faces<0>(Vown, Vgh, leaf, xyz[0] == 0, xyz[0] == top, lf[0], lf[1], gamma, gm1, F,
+                    t.status);
+    leaf_faces<1>(Vown, Vgh, leaf, xyz[1] == 0, xyz[1] == top, lf[2], lf[3], gamma, gm1, F,
+                    t.status);
+    leaf_faces<2>(Vown, Vgh, leaf, xyz[2] == 0, xyz[2] == top, lf[4], lf[5], gamma, gm1, F,
+                    t.status);
 }
 
 // d += F_low - F_high along A for the cell c of the leaf; a boundary face

@@ -21,6 +21,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libotfmm.so")
 
 OT_OK = 0
+OT_ERR_DEVICE_STATUS = -8
+# bits of the device status word (ot_tree_info's device_status)
+OT_STATUS_BAD_INDEX = 1
+OT_STATUS_BAD_ITEM = 2
+OT_STATUS_BAD_DENSITY = 4
 OT_PRECISION_FP64 = 0
 OT_PRECISION_FP32_BULK = 1
 OT_PRECISION_FP32_WIDE = 2
@@ -261,6 +266,11 @@ def ot_tree_info(tree) -> dict:
                 workspace_bytes=st.workspace_bytes, flops_bulk64=st.flops_bulk64,
                 flops_bulk32=st.flops_bulk32, flops_adjoint=st.flops_adjoint,
                 flops_tangent=st.flops_tangent)
+    if code == OT_ERR_DEVICE_STATUS:
+        # the latched bits travel with the error (reading them cleared them)
+        err = OTError(code, "ot_tree_info")
+        err.info = info
+        raise err
     _check(code, "ot_tree_info")
     return info
 

@@ -33,9 +33,19 @@ def gpu_step(fmm, lv, u, dt, gravity):
     ug = torch.from_numpy(np.ascontiguousarray(u)).cuda()
     tree.hydro_step(ug, dt, GAMMA, gravity=gravity)
     torch.cuda.synchronize()
-    status = tree.info()["device_status"]
+    try:
+        status = tree.info()["device_status"]
+    except fmm.OTError as e:
+        status = e.info["device_status"]
     tree.close()
     return ug.cpu().numpy(), status
+
+
+def only_density_bit(fmm, status):
+    """The binary's 1e-10 atmosphere next to the stars drives some stage
+    densities below zero (this scheme has no positivity fix): the density
+    bit may be set, nothing else."""
+    return status & ~fmm.OT_STATUS_BAD_DENSITY == 0
 
 
 CASES = {
@@ -51,7 +61,7 @@ def test_step_without_gravity_matches_oracle_bit_for_bit(fmm, case):
     lv, u = CASES[case]()
     got, status = gpu_step(fmm, lv, u, 1e-3, False)
     want = S.rk3_step(lv, u, 1e-3, GAMMA, gravity=False)
-    assert status == 0
+    assert only_density_bit(fmm, status)
     diff = int((got != want).sum())
     print(f"step {case}: {got.size} values, {diff} differ")
     assert diff == 0
@@ -63,7 +73,7 @@ def test_step_with_gravity_matches_oracle(fmm, case):
     lv, u = CASES[case]()
     got, status = gpu_step(fmm, lv, u, 1e-3, True)
     want = S.rk3_step(lv, u, 1e-3, GAMMA, gravity=True)
-    assert status == 0
+    assert only_density_bit(fmm, status)
     scale = np.abs(want).max(axis=(0, 2))
     err = np.abs(got - want).max(axis=(0, 2)) / scale
     print(f"step with gravity {case}: relative error per field {err}")
@@ -71,6 +81,19 @@ def test_step_with_gravity_matches_oracle(fmm, case):
     # gravity does act on the step
     nograv = S.rk3_step(lv, u, 1e-3, GAMMA, gravity=False)
     assert np.abs(want - nograv).max() > 1e-9 * np.abs(want).max()
+
+
+def test_positive_state_keeps_the_status_word_clear(fmm):
+    """A blob in a uniform gas (no near vacuum): every stage state stays
+    physical and the status word stays clear."""
+    lv = I.amr_leaves(2, 5e-4, I.BINARY, lmin=1)
+    x = I.cell_centres(lv)
+    r2 = ((x[..., 0] - 0.45) ** 2 + (x[..., 1] - 0.5) ** 2 + (x[..., 2] - 0.52) ** 2) / 0.0625
+    b = np.maximum(1.0 - r2, 0.0) ** 4
+    u = np.stack([1.0 + 0.5 * b, 0.3 * b, -0.2 * b, 0.1 * b, 1.5 + 0.8 * b], axis=1)
+    got, status = gpu_step(fmm, lv, u, 1e-3, True)
+    assert status == 0
+    assert np.abs(got - S.rk3_step(lv, u, 1e-3, GAMMA, gravity=True)).max() < 1e-9 * np.abs(u).max()
 
 
 def test_step_rejects_bad_arguments(fmm):
