@@ -216,7 +216,9 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
     // with the level's factors in the accumulators' type.
     auto flush = [&]() {
         const T* sl = scales_of(sc, L, T(0));
-        const T s1 = sl[0], s2 = sl[1], s3 = sl[2], s4 = sl[3];
+        // (the L2, L3 and correction sums are held without their radial
+        // constants kAccL2, kAccL3, kAccCor)
+        const T s1 = sl[0], s2 = sl[1], s3 = sl[2] * T(kAccL2), s4 = sl[3] * T(kAccL3);
         double* loc = t.loc;
         if (sizeof(T) == 4 && L == 0 && !FULL) {
             // a leaf root: its near pairs were summed in FP64
@@ -241,7 +243,7 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
         if (AM) {
             // a_c = -(G/6) h^-2 (S - P), P from A4 and the target's octupole
             // per unit mass (loaded here, not held across the pair loop)
-            const T sa = sl[4];
+            const T sa = sl[4] * T(kAccCor);
             T P[3] = {T(0.0), T(0.0), T(0.0)};
             if (FULL) {
                 T a3[10], ta[3];

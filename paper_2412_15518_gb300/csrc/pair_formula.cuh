@@ -26,6 +26,12 @@
 // side h (R' = R / h, M2' = M2 / h^2, M3' = M3 / h^3) and without the -G
 // factor; the caller scales L^(n) by -G h^-(n+1) and the correction sums S
 // and P by -(G/6) h^-2 once per target.
+//
+// The radial factors are formed as the plain chain g_k = 1/r^(2k+1)
+// (f_k = (-1)^k (2k-1)!! g_k): the constants of the monopole sums L2, L3 and
+// A4 and of the correction sum S are left out of the per-pair work and
+// applied once per target with the level's scale factors (kAccL2, kAccL3,
+// kAccCor below).
 #pragma once
 
 #include "common.cuh"
@@ -33,11 +39,18 @@
 namespace otfmm {
 
 template <class T> struct Acc {
-    T L0, L1[3], L2[6], L3[10];
-    T S[3];   // correction sum of the source octupoles
-    T A4[15]; // sum m_B f4 R^4 of interior targets (xxxx xxxy xxxz xxyy xxyz xxzz xyyy
-              // xyyz xyzz xzzz yyyy yyyz yyzz yzzz zzzz)
+    T L0, L1[3];
+    T L2[6];  // sum m g2 R R = L2 / kAccL2 (before finish_acc)
+    T L3[10]; // sum m g3 R R R = L3 / kAccL3 (before finish_acc)
+    T S[3];   // correction sum of the source octupoles / kAccCor
+    T A4[15]; // sum m_B g4 R^4 = sum m_B f4 R^4 / kAccCor of interior targets (xxxx
+              // xxxy xxxz xxyy xxyz xxzz xyyy xyyz xyzz xzzz yyyy yyyz yyzz yzzz zzzz)
 };
+// The constants left out of the sums: f2 = 3 g2, f3 = -15 g3, f4 = 105 g4.
+// finish_acc and correction_target are linear, so they act on the sums as
+// held; the flush multiplies the level's scale of L2 by kAccL2, of L3 by
+// kAccL3 and of the correction (S - P) by kAccCor.
+constexpr double kAccL2 = 3.0, kAccL3 = -15.0, kAccCor = 105.0;
 // The Kronecker parts of L2 and L3 are not accumulated: D2 and D3 are
 // traceless, so per pair sum m f1 = -trace(m f2 R R) / 3 and
 // sum m f2 R = -trace(m f3 R R R) / 5; finish_acc restores them from the
@@ -146,28 +159,29 @@ __host__ __device__ __forceinline__ void correction_target(const Acc<T>& A, cons
 template <class T, bool TGT_FULL, bool SRC_MULTI, bool AM>
 __host__ __device__ __forceinline__ void m2l_pair(T x, T y, T z, T m, const T* b2, const T* b3,
                                                   const T* bt, Acc<T>& A) {
+    constexpr bool kHigh = TGT_FULL || SRC_MULTI;  // needs g2 and g3
     const T r2 = fma_(x, x, fma_(y, y, z * z));
-    const T f0 = rsqrt_(r2);
-    const T ri2 = f0 * f0;
-    const T f1 = -(f0 * ri2);
-    const T f2 = f1 * (T(-3.0) * ri2);
-    const T f3 = f2 * (T(-5.0) * ri2);
-    const T c1 = m * f1;
-    T f4 = T(0.0);
-    if (AM) f4 = f3 * (T(-7.0) * ri2);
-    const T xx = x * x, yy = y * y, zz = z * z;
-    const T xy = x * y, xz = x * z, yz = y * z;
-    T xy2 = T(0.0), xz2 = T(0.0), yz2 = T(0.0), u = T(0.0), w = T(0.0);
-    if (SRC_MULTI) {
-        xy2 = xy + xy;
-        xz2 = xz + xz;
-        yz2 = yz + yz;
+    const T g0 = rsqrt_(r2);
+    const T ri2 = g0 * g0;
+    const T g1 = g0 * ri2;
+    T g2 = T(0.0), g3 = T(0.0), g4 = T(0.0);
+    if (kHigh) {
+        g2 = g1 * ri2;
+        g3 = g2 * ri2;
     }
-    if (AM) {
-        u = T(3.0) * f3;
-        w = T(3.0) * f2;
+    if (kHigh && AM) g4 = g3 * ri2;
+    const T c1 = m * g1;  // -m f1
+    T xx = T(0.0), yy = T(0.0), zz = T(0.0), xy = T(0.0), xz = T(0.0), yz = T(0.0);
+    if (kHigh) {
+        xx = x * x;
+        yy = y * y;
+        zz = z * z;
+        xy = x * y;
+        xz = x * z;
+        yz = y * z;
     }
     if (SRC_MULTI) {
+        const T xy2 = xy + xy, xz2 = xz + xz, yz2 = yz + yz;
         const T Mx = fma_(b2[0], x, fma_(b2[1], y, b2[2] * z));
         const T My = fma_(b2[1], x, fma_(b2[3], y, b2[4] * z));
         const T Mz = fma_(b2[2], x, fma_(b2[4], y, b2[5] * z));
@@ -177,36 +191,41 @@ __host__ __device__ __forceinline__ void m2l_pair(T x, T y, T z, T m, const T* b
         contract_rr(b3, xx, yy, zz, xy2, xz2, yz2, qx, qy, qz);
         const T q3 = fma_(x, qx, fma_(y, qy, z * qz));
         const T Rt = fma_(x, bt[0], fma_(y, bt[1], z * bt[2]));
-        const T h2 = T(0.5) * f2;
+        const T h2 = T(1.5) * g2;  // f2 / 2
         // L0 += m f0 + (f2 xMx + f1 tr) / 2 - (f3 q3 + 3 f2 Rt) / 6
-        A.L0 = fma_(m, f0, fma_(T(0.5) * f1, tr, fma_(h2, xMx - Rt, fma_(T(-1.0 / 6.0) * f3, q3, A.L0))));
+        //     = m g0 - g1 tr / 2 + (3/2) g2 (xMx - Rt) + (5/2) g3 q3
+        A.L0 = fma_(m, g0, fma_(T(-0.5) * g1, tr, fma_(h2, xMx - Rt, fma_(T(2.5) * g3, q3, A.L0))));
         // L1 += R (m f1 + (f3 xMx + f2 tr) / 2) + f2 M2 R
-        const T g1 = fma_(T(0.5) * f3, xMx, fma_(h2, tr, c1));
-        A.L1[0] = fma_(g1, x, fma_(f2, Mx, A.L1[0]));
-        A.L1[1] = fma_(g1, y, fma_(f2, My, A.L1[1]));
-        A.L1[2] = fma_(g1, z, fma_(f2, Mz, A.L1[2]));
+        //     = R (-m g1 - (15/2) g3 xMx + (3/2) g2 tr) + 3 g2 M2 R
+        const T e = fma_(T(-7.5) * g3, xMx, fma_(h2, tr, -c1));
+        const T d2 = h2 + h2;
+        A.L1[0] = fma_(e, x, fma_(d2, Mx, A.L1[0]));
+        A.L1[1] = fma_(e, y, fma_(d2, My, A.L1[1]));
+        A.L1[2] = fma_(e, z, fma_(d2, Mz, A.L1[2]));
         if (AM) {
-            // S += f4 R q3 + 3 f3 (q2 + R Rt) + 3 f2 t = R k + u q2 + w t
-            const T k = fma_(u, Rt, f4 * q3);
+            // S += f4 R q3 + 3 f3 (q2 + R Rt) + 3 f2 t, held / 105:
+            //    R (g4 q3 - (3/7) g3 Rt) - (3/7) g3 q2 + (3/35) g2 t = R k + u q2 + w t
+            const T u = T(-3.0 / 7.0) * g3, w = T(3.0 / 35.0) * g2;
+            const T k = fma_(u, Rt, g4 * q3);
             A.S[0] = fma_(k, x, fma_(u, qx, fma_(w, bt[0], A.S[0])));
             A.S[1] = fma_(k, y, fma_(u, qy, fma_(w, bt[1], A.S[1])));
             A.S[2] = fma_(k, z, fma_(u, qz, fma_(w, bt[2], A.S[2])));
         }
     } else {
-        A.L0 = fma_(m, f0, A.L0);
-        A.L1[0] = fma_(c1, x, A.L1[0]);
-        A.L1[1] = fma_(c1, y, A.L1[1]);
-        A.L1[2] = fma_(c1, z, A.L1[2]);
+        A.L0 = fma_(m, g0, A.L0);
+        A.L1[0] = fma_(-c1, x, A.L1[0]);
+        A.L1[1] = fma_(-c1, y, A.L1[1]);
+        A.L1[2] = fma_(-c1, z, A.L1[2]);
     }
     if (TGT_FULL) {
-        const T s2 = m * f2;
+        const T s2 = m * g2;
         A.L2[0] = fma_(s2, xx, A.L2[0]);
         A.L2[1] = fma_(s2, xy, A.L2[1]);
         A.L2[2] = fma_(s2, xz, A.L2[2]);
         A.L2[3] = fma_(s2, yy, A.L2[3]);
         A.L2[4] = fma_(s2, yz, A.L2[4]);
         A.L2[5] = fma_(s2, zz, A.L2[5]);
-        const T s3 = m * f3;
+        const T s3 = m * g3;
         const T tx3 = s3 * x, ty3 = s3 * y, tz3 = s3 * z;
         A.L3[0] = fma_(tx3, xx, A.L3[0]);
         A.L3[1] = fma_(tx3, xy, A.L3[1]);
@@ -219,23 +238,25 @@ __host__ __device__ __forceinline__ void m2l_pair(T x, T y, T z, T m, const T* b
         A.L3[8] = fma_(ty3, zz, A.L3[8]);
         A.L3[9] = fma_(tz3, zz, A.L3[9]);
         if (AM) {
-            // A4 += m f4 R^4 (the target octupole is contracted once per target)
-            const T s4 = m * f4;
-            const T txx = s4 * xx, txy = s4 * xy, txz = s4 * xz, tyy = s4 * yy, tyz = s4 * yz, tzz = s4 * zz;
+            // A4 += m g4 R^4 (the target octupole is contracted once per
+            // target): every quartic monomial is a square's multiple times a
+            // quadratic one
+            const T s4 = m * g4;
+            const T txx = s4 * xx, tyy = s4 * yy, tzz = s4 * zz;
             A.A4[0] = fma_(txx, xx, A.A4[0]);
             A.A4[1] = fma_(txx, xy, A.A4[1]);
             A.A4[2] = fma_(txx, xz, A.A4[2]);
             A.A4[3] = fma_(txx, yy, A.A4[3]);
             A.A4[4] = fma_(txx, yz, A.A4[4]);
             A.A4[5] = fma_(txx, zz, A.A4[5]);
-            A.A4[6] = fma_(txy, yy, A.A4[6]);
-            A.A4[7] = fma_(txy, yz, A.A4[7]);
-            A.A4[8] = fma_(txy, zz, A.A4[8]);
-            A.A4[9] = fma_(txz, zz, A.A4[9]);
+            A.A4[6] = fma_(tyy, xy, A.A4[6]);
+            A.A4[7] = fma_(tyy, xz, A.A4[7]);
+            A.A4[8] = fma_(tzz, xy, A.A4[8]);
+            A.A4[9] = fma_(tzz, xz, A.A4[9]);
             A.A4[10] = fma_(tyy, yy, A.A4[10]);
             A.A4[11] = fma_(tyy, yz, A.A4[11]);
             A.A4[12] = fma_(tyy, zz, A.A4[12]);
-            A.A4[13] = fma_(tyz, zz, A.A4[13]);
+            A.A4[13] = fma_(tzz, yz, A.A4[13]);
             A.A4[14] = fma_(tzz, zz, A.A4[14]);
         }
     }
@@ -380,21 +401,21 @@ __host__ __device__ __forceinline__ void m2l_pair_split(D x, D y, D z, D m, F xf
         A.L3[9] = fma_(-tz3, zz, A.L3[9]);
         if (AM) {
             const D w4 = w3 * ri2;
-            const D txx = w4 * xx, txy = w4 * xy, txz = w4 * xz, tyy = w4 * yy, tyz = w4 * yz, tzz = w4 * zz;
+            const D txx = w4 * xx, tyy = w4 * yy, tzz = w4 * zz;
             A.A4[0] = fma_(txx, xx, A.A4[0]);
             A.A4[1] = fma_(txx, xy, A.A4[1]);
             A.A4[2] = fma_(txx, xz, A.A4[2]);
             A.A4[3] = fma_(txx, yy, A.A4[3]);
             A.A4[4] = fma_(txx, yz, A.A4[4]);
             A.A4[5] = fma_(txx, zz, A.A4[5]);
-            A.A4[6] = fma_(txy, yy, A.A4[6]);
-            A.A4[7] = fma_(txy, yz, A.A4[7]);
-            A.A4[8] = fma_(txy, zz, A.A4[8]);
-            A.A4[9] = fma_(txz, zz, A.A4[9]);
+            A.A4[6] = fma_(tyy, xy, A.A4[6]);
+            A.A4[7] = fma_(tyy, xz, A.A4[7]);
+            A.A4[8] = fma_(tzz, xy, A.A4[8]);
+            A.A4[9] = fma_(tzz, xz, A.A4[9]);
             A.A4[10] = fma_(tyy, yy, A.A4[10]);
             A.A4[11] = fma_(tyy, yz, A.A4[11]);
             A.A4[12] = fma_(tyy, zz, A.A4[12]);
-            A.A4[13] = fma_(tyz, zz, A.A4[13]);
+            A.A4[13] = fma_(tzz, yz, A.A4[13]);
             A.A4[14] = fma_(tzz, zz, A.A4[14]);
         }
     }

@@ -328,9 +328,9 @@ __device__ __forceinline__ void tan_item(const DevTree& t, const TanArrays& a, c
     if (FULL) {
         finish_acc(A);
 #pragma unroll
-        for (int r = 0; r < 6; r++) add_d(t, a, (4 + r) * N + cell, A.L2[r], sl[2]);
+        for (int r = 0; r < 6; r++) add_d(t, a, (4 + r) * N + cell, A.L2[r], kAccL2 * sl[2]);
 #pragma unroll
-        for (int r = 0; r < 10; r++) add_d(t, a, (10 + r) * N + cell, A.L3[r], sl[3]);
+        for (int r = 0; r < 10; r++) add_d(t, a, (10 + r) * N + cell, A.L3[r], kAccL3 * sl[3]);
     }
     if (AM) {
         Dual P[3] = {Dual(0.0), Dual(0.0), Dual(0.0)};
@@ -347,7 +347,7 @@ __device__ __forceinline__ void tan_item(const DevTree& t, const TanArrays& a, c
             correction_target(A, a3, ta, P);
         }
 #pragma unroll
-        for (int r = 0; r < 3; r++) add_d(t, a, (20 + r) * N + cell, A.S[r] - P[r], sl[4]);
+        for (int r = 0; r < 3; r++) add_d(t, a, (20 + r) * N + cell, A.S[r] - P[r], kAccCor * sl[4]);
     }
 }
 

@@ -97,11 +97,13 @@ int main() {
             trace3(a3, ta);
             correction_target(A, a3, ta, P);
         }
+        // the sums are held without their radial constants
         std::printf("%.17g", -G * A.L0);
         for (double v : A.L1) std::printf(" %.17g", -G * v);
-        for (double v : A.L2) std::printf(" %.17g", -G * v);
-        for (double v : A.L3) std::printf(" %.17g", -G * v);
-        for (int i = 0; i < 3; i++) std::printf(" %.17g", am ? -(G / 6.0) * (A.S[i] - P[i]) : 0.0);
+        for (double v : A.L2) std::printf(" %.17g", -G * kAccL2 * v);
+        for (double v : A.L3) std::printf(" %.17g", -G * kAccL3 * v);
+        for (int i = 0; i < 3; i++)
+            std::printf(" %.17g", am ? -(G / 6.0) * kAccCor * (A.S[i] - P[i]) : 0.0);
         // reverse of the same pair, both roles and the R-gradient
         PairAdjOut o;
         adj_zero(o);
