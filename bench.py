@@ -57,10 +57,10 @@ L2_FLUSH_BYTES = 256 << 20
 # captures of the interaction kernels summarised in profiles/ (per launch;
 # binary_amr8 from its full-size one-pass capture).  A workload or form
 # without a capture of the current kernels reports null.
-TRAFFIC_BYTES = {("binary_l3", "fp64"): 14.39e6 + 10.64e6,
-                 ("binary_l3", "fp32_bulk"): 17.39e6 + 10.65e6,
-                 ("binary_l3", "fp32_wide"): 13.47e6 + 10.66e6 + 9.56e6,
-                 ("binary_amr8", "fp64"): 5.37e9 + 1.54e9 + 0.914e9 + 0.654e9,
+TRAFFIC_BYTES = {("binary_l3", "fp64"): 14.56e6 + 10.64e6,
+                 ("binary_l3", "fp32_bulk"): 17.39e6 + 10.64e6,
+                 ("binary_l3", "fp32_wide"): 13.49e6 + 10.66e6 + 9.56e6,
+                 ("binary_amr8", "fp64"): 5.35e9 + 1.53e9 + 0.911e9 + 0.653e9,
                  ("binary_amr8", "fp32_bulk"): 6.56e9 + 1.51e9 + 0.912e9 + 0.653e9}
 
 WORKLOAD_TEXT = {

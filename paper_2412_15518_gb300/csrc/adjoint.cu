@@ -258,17 +258,23 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
             q0 = it.z;
             q1 = it.w;
         }
+        // The pairs run in cell units (R, M2, M3 of this level) with the
+        // adjoints pre-scaled by -G h^-(n+1) (E_n) and -(G/6) h^-2 (a); their
+        // moment and centre-of-mass adjoints come out physical through the
+        // factors h^-2, h^-3 and h^-1 (m2l_pair_reverse).
         const double h = t.size / (double)(8 << L);
-        const double h2 = h * h, h3 = h2 * h;
-        // own moments (physical) and own expansion adjoints
+        const double hi = 1.0 / h, hi2 = hi * hi, hi3 = hi2 * hi;
+        const double sE0 = -G * hi, sE1 = sE0 * hi, sE2 = sE1 * hi, sE3 = sE2 * hi;
+        const double sA = (-G / 6.0) * hi2;
+        // own moments (cell units) and own expansion adjoints
         const double mC = t.mom64[cell];
         const double dC[3] = {t.mom64[N + cell], t.mom64[2 * N + cell], t.mom64[3 * N + cell]};
         double M2C[6], M3C[10];
         if (!cleaf) {
 #pragma unroll
-            for (int r = 0; r < 6; r++) M2C[r] = h2 * t.mom64[(4 + r) * N + cell];
+            for (int r = 0; r < 6; r++) M2C[r] = t.mom64[(4 + r) * N + cell];
 #pragma unroll
-            for (int r = 0; r < 10; r++) M3C[r] = h3 * t.mom64[(10 + r) * N + cell];
+            for (int r = 0; r < 10; r++) M3C[r] = t.mom64[(10 + r) * N + cell];
         } else {
 #pragma unroll
             for (int r = 0; r < 6; r++) M2C[r] = 0.0;
@@ -285,22 +291,21 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
         // target is reversed whole in that target's pass 2, which sends the
         // source-side adjoints here with atomics.
         auto rev1 = [&](int e, long long pc) {
-            const double mP = t.mom64[pc];
-            const double R[3] = {h * ((double)entry_dx(e) + t.mom64[N + pc] - dC[0]),
-                                 h * ((double)entry_dy(e) + t.mom64[2 * N + pc] - dC[1]),
-                                 h * ((double)entry_dz(e) + t.mom64[3 * N + pc] - dC[2])};
+            const double R[3] = {(double)entry_dx(e) + t.mom64[N + pc] - dC[0],
+                                 (double)entry_dy(e) + t.mom64[2 * N + pc] - dC[1],
+                                 (double)entry_dz(e) + t.mom64[3 * N + pc] - dC[2]};
             // a leaf partner: no octupole, and only its L0/L1 adjoints exist
-            double M3P[10], EP[20], aP[3];
+            const double e0 = sE0 * locbar[pc];
+            double e1[3], aP[3];
 #pragma unroll
-            for (int r = 0; r < 10; r++) M3P[r] = 0.0;
-#pragma unroll
-            for (int r = 0; r < 20; r++) EP[r] = r >= 4 ? 0.0 : locbar[r * N + pc];
-#pragma unroll
-            for (int r = 0; r < 3; r++) aP[r] = locbar[(20 + r) * N + pc];
+            for (int r = 0; r < 3; r++) {
+                e1[r] = sE1 * locbar[(1 + r) * N + pc];
+                aP[r] = sA * locbar[(20 + r) * N + pc];
+            }
             // the R-gradient of this pair moves this cell's centre of mass (a
-            // leaf partner's centre is fixed)
-            m2l_pair_reverse<true, false>(R, G, am, mC, M2C, M3C, !cleaf, mP, M3P, false, EP[0], EP + 1,
-                                          EP + 4, EP + 10, aP, !cleaf, -1.0, acc.R, acc);
+            // leaf partner's centre is fixed): R = X_P - X_C
+            m2l_pair_reverse<true, false, false, double>(R, mC, M2C, M3C, !cleaf, false, 0.0, M3C, e0, e1, nullptr,
+                                                 nullptr, am, aP, !cleaf, hi2, hi3, -hi, acc.R, acc);
         };
         if (passes & 1) {
             if (grp) {
@@ -336,8 +341,7 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
             }
             // this cell's source-side adjoints of pass 1; acc's source fields
             // then carry one pair's partner adjoints at a time in pass 2
-            const double hi = 1.0 / h;
-            atomicAdd(mombar + cell, acc.mB - G * (lat0 * hi - lat1 * hi * hi));
+            atomicAdd(mombar + cell, acc.mB - G * (lat0 * hi - lat1 * hi2));
             acc.mB = 0.0;
             if (!cleaf) {
 #pragma unroll
@@ -359,22 +363,26 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
         if (!cleaf && (passes & 2)) {
             double EC[20], aC[3];
 #pragma unroll
-            for (int r = 0; r < 20; r++) EC[r] = locbar[r * N + cell];
+            for (int r = 0; r < 20; r++)
+                EC[r] = (r == 0 ? sE0 : (r < 4 ? sE1 : (r < 10 ? sE2 : sE3))) * locbar[r * N + cell];
 #pragma unroll
-            for (int r = 0; r < 3; r++) aC[r] = locbar[(20 + r) * N + cell];
+            for (int r = 0; r < 3; r++) aC[r] = sA * locbar[(20 + r) * N + cell];
+            // the correction's mass-ratio term (a target of non-zero mass)
+            const bool useA = am && mC != 0.0;
+            const double iA = useA ? 1.0 / mC : 0.0;
             auto rev2 = [&](int e, bool pleaf, long long pc) {
                 const double mP = t.mom64[pc];
-                const double Rn[3] = {h * (dC[0] - (double)entry_dx(e) - t.mom64[N + pc]),
-                                      h * (dC[1] - (double)entry_dy(e) - t.mom64[2 * N + pc]),
-                                      h * (dC[2] - (double)entry_dz(e) - t.mom64[3 * N + pc])};
+                const double Rn[3] = {dC[0] - (double)entry_dx(e) - t.mom64[N + pc],
+                                      dC[1] - (double)entry_dy(e) - t.mom64[2 * N + pc],
+                                      dC[2] - (double)entry_dz(e) - t.mom64[3 * N + pc]};
                 double M2P[6], M3P[10];
 #pragma unroll
-                for (int r = 0; r < 6; r++) M2P[r] = pleaf ? 0.0 : h2 * t.mom64[(4 + r) * N + pc];
+                for (int r = 0; r < 6; r++) M2P[r] = pleaf ? 0.0 : t.mom64[(4 + r) * N + pc];
 #pragma unroll
-                for (int r = 0; r < 10; r++) M3P[r] = pleaf ? 0.0 : h3 * t.mom64[(10 + r) * N + pc];
+                for (int r = 0; r < 10; r++) M3P[r] = pleaf ? 0.0 : t.mom64[(10 + r) * N + pc];
                 double gR[3] = {0.0, 0.0, 0.0};
-                m2l_pair_reverse<true, true>(Rn, G, am, mP, M2P, M3P, !pleaf, mC, M3C, true, EC[0], EC + 1,
-                                             EC + 4, EC + 10, aC, true, 1.0, gR, acc);
+                m2l_pair_reverse<true, true, true>(Rn, mP, M2P, M3P, !pleaf, useA, iA, M3C, EC[0], EC + 1,
+                                                   EC + 4, EC + 10, am, aC, true, hi2, hi3, hi, gR, acc);
                 // the partner's source-side adjoints of this pair
                 atomicAdd(mombar + pc, acc.mB);
                 acc.mB = 0.0;
@@ -427,10 +435,11 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
         if (!cleaf) {
             if (passes & 2) {
                 if (am && mC != 0.0) {
+                    // dJ/dM3_A = -(1 / m_A) h^-3 al . sum_B m_B D4(R'_B), al = -(G/6) h^-2 a
                     double aC[3];
 #pragma unroll
-                    for (int r = 0; r < 3; r++) aC[r] = locbar[(20 + r) * N + cell];
-                    reverse_target_finish(acc, aC, (G / 6.0) / mC);
+                    for (int r = 0; r < 3; r++) aC[r] = sA * locbar[(20 + r) * N + cell];
+                    reverse_target_finish(acc, aC, -hi3 / mC);
                 }
                 atomicAdd(mombar + cell, acc.mA);
 #pragma unroll

@@ -23,6 +23,8 @@
 // unrolled, so nothing is indexed at run time.
 #pragma once
 
+#include "pair_formula.cuh"
+
 namespace otfmm {
 
 template <class T> struct PairAdjOutT {
@@ -154,156 +156,234 @@ __device__ __forceinline__ double rsqrt_adj(double a) { return rsqrt(a); }
 inline double rsqrt_adj(double a) { return 1.0 / sqrt(a); }
 #endif
 
-// Reverse of one pair, added into out.  SRC: source-moment adjoints (mB
-// always; M2B, M3B when the source is an interior cell).  TGT: the
-// target-side mass-ratio adjoints (interior targets only).  want_R: dJ/dR,
-// added to gR times sR (+1 for the target's centre of mass, -1 for the
-// source's).
-template <bool SRC, bool TGT, class T>
+// Reverse of one pair, added into out, without the -G factors and in the
+// caller's units.  By homogeneity the pair's physical expansion is
+// -G h^-(n+1) times its value from R' = R / h, M2' = M2 / h^2, M3' = M3 / h^3
+// (and the correction -(G/6) h^-2 times D4(R') : Q'), so the caller passes R
+// and the moments in cell units and the adjoints pre-scaled,
+//   e0 = -G h^-1 E0, e1 = -G h^-2 E1, e2 = -G h^-3 E2, e3 = -G h^-4 E3,
+//   al = -(G/6) h^-2 a,
+// and receives dJ/dm_B and dJ/dm_A in physical units, dJ/dM2_B, dJ/dM3_B and
+// dJ/dR times oM2, oM3 and oR (h^-2, h^-3 and +-h^-1 give physical adjoints,
+// the sign that of the centre of mass that R moves).  With h = 1 and G
+// folded into the adjoints this is the physical pair.
+//   SRC: the source's adjoints (m_B; M2_B, M3_B for an interior source,
+//        multiB), added to out.mB, out.M2B, out.M3B;
+//   TGT: the target side of the correction's mass ratio (useA: an interior
+//        target of mass m_A = 1 / iA != 0, octupole M3A): out.mA and the
+//        quartic sum out.A4 = sum_B m_B f4 R^4 (reverse_target_finish);
+//   EFULL: the target has E2 and E3 adjoints (an interior target; a leaf
+//        target's are zero and skipped);
+//   want_R: dJ/dR into gR.
+template <bool SRC, bool TGT, bool EFULL, class T>
 __host__ __device__ __forceinline__ void m2l_pair_reverse(
-    const T* Rv, T G, int am,
-    T mB, const T* M2B, const T* M3B, bool multiB,   // source moments
-    T mA, const T* M3A, bool multiA,                      // target moments (ratio)
-    T E0, const T* E1, const T* E2, const T* E3, const T* ac,
-    bool want_R, T sR, T* gR, PairAdjOutT<T>& out) {
-    RMono<T> m;
-    r_mono(Rv[0], Rv[1], Rv[2], m);
-    const T x = m.x, y = m.y, z = m.z;
+    const T* Rv, T mB, const T* M2B, const T* M3B, bool multiB, bool useA, T iA, const T* M3A, T e0,
+    const T* e1, const T* e2, const T* e3, bool am, const T* al, bool want_R, T oM2, T oM3, T oR,
+    T* gR, PairAdjOutT<T>& out) {
+    const T x = Rv[0], y = Rv[1], z = Rv[2];
     const T R[3] = {x, y, z};
-    const T f0 = rsqrt_adj(m.xx + m.yy + m.zz);
+    const T xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z;
+    const T xy2 = xy + xy, xz2 = xz + xz, yz2 = yz + yz;
+    const T f0 = rsqrt_adj(xx + yy + zz);
     const T ri2 = f0 * f0;
-    const T f1 = -f0 * ri2;
-    const T f2 = -3.0 * f1 * ri2;
-    const T f3 = -5.0 * f2 * ri2;
-    const T f4 = -7.0 * f3 * ri2;
-    const T f5 = -9.0 * f4 * ri2;
-    const T k6 = G / 6.0;
-    // the target's M3 enters only through the correction's mass-ratio term,
-    // which is taken as zero (and has no derivative) for a target of zero mass
-    const bool useA = am && multiA && mA != 0.0;
-    const T iA = useA ? 1.0 / mA : 0.0;
-    const T ratio = mB * iA;
-    const T zero3[3] = {0.0, 0.0, 0.0};
-    const T* a = am ? ac : zero3;
-    const T aR = a[0] * x + a[1] * y + a[2] * z;
+    const T f1 = -(f0 * ri2);
+    const T f2 = f1 * (T(-3.0) * ri2);
+    const T f3 = f2 * (T(-5.0) * ri2);
+    const T f4 = f3 * (T(-7.0) * ri2);
+    const T zero3[3] = {T(0.0), T(0.0), T(0.0)};
+    const T* a = am ? al : zero3;
+    const T aR = fma_(a[0], x, fma_(a[1], y, a[2] * z));
+    const T e1R = fma_(e1[0], x, fma_(e1[1], y, e1[2] * z));
 
-    // contractions of the adjoints with R
-    const T E1R = E1[0] * x + E1[1] * y + E1[2] * z;
-    T E2R[3];
-    sym2_vec(E2, R, E2R);
-    const T RE2R = E2R[0] * x + E2R[1] * y + E2R[2] * z;
-    const T trE2 = E2[0] + E2[3] + E2[5];
-    S4Parts<T> e3;
-    s4_parts(E3, m, e3);
-    // s4a = a . (D4 : M3_A) (the ratio part of the correction)
-    T s4a = 0.0;
-    S4Parts<T> qa;
+    // the interior target's E2 and E3 with R: e2R = E2 R, Re2R = R.E2.R,
+    // q2e = E3 : R R, q3e = R.q2e, te = the trace vector of E3, Rte = R.te;
+    // sum1 = e1R + tr E2 and sum2 = Re2R + 3 Rte recur below
+    T e2R[3] = {T(0.0), T(0.0), T(0.0)}, q2e[3] = {T(0.0), T(0.0), T(0.0)};
+    T te[3] = {T(0.0), T(0.0), T(0.0)}, q3e = T(0.0), sum1 = e1R, sum2 = T(0.0);
+    if (EFULL) {
+        e2R[0] = fma_(e2[0], x, fma_(e2[1], y, e2[2] * z));
+        e2R[1] = fma_(e2[1], x, fma_(e2[3], y, e2[4] * z));
+        e2R[2] = fma_(e2[2], x, fma_(e2[4], y, e2[5] * z));
+        const T Re2R = fma_(x, e2R[0], fma_(y, e2R[1], z * e2R[2]));
+        sum1 = e1R + (e2[0] + e2[3] + e2[5]);
+        contract_rr(e3, xx, yy, zz, xy2, xz2, yz2, q2e[0], q2e[1], q2e[2]);
+        q3e = fma_(x, q2e[0], fma_(y, q2e[1], z * q2e[2]));
+        sym3_trace(e3, te);
+        sum2 = fma_(T(3.0), fma_(x, te[0], fma_(y, te[1], z * te[2])), Re2R);
+    }
+    // the target octupole's parts (the correction's ratio term) and
+    // s4a = a . (D4 : M3A)
+    T q2a[3] = {T(0.0), T(0.0), T(0.0)}, ta[3] = {T(0.0), T(0.0), T(0.0)};
+    T q3a = T(0.0), Rta = T(0.0), s4a = T(0.0);
+    const T f4aR = f4 * aR;
     if (useA) {
-        s4_parts(M3A, m, qa);
-        s4a = f4 * aR * qa.q3 + 3.0 * f3 * (a[0] * qa.q2[0] + a[1] * qa.q2[1] + a[2] * qa.q2[2] + aR * qa.Rt) +
-              3.0 * f2 * (a[0] * qa.t[0] + a[1] * qa.t[1] + a[2] * qa.t[2]);
+        contract_rr(M3A, xx, yy, zz, xy2, xz2, yz2, q2a[0], q2a[1], q2a[2]);
+        q3a = fma_(x, q2a[0], fma_(y, q2a[1], z * q2a[2]));
+        sym3_trace(M3A, ta);
+        Rta = fma_(x, ta[0], fma_(y, ta[1], z * ta[2]));
+        const T aq2a = fma_(a[0], q2a[0], fma_(a[1], q2a[1], a[2] * q2a[2]));
+        const T ata = fma_(a[0], ta[0], fma_(a[1], ta[1], a[2] * ta[2]));
+        s4a = fma_(f4aR, q3a, T(3.0) * fma_(f3, fma_(aR, Rta, aq2a), f2 * ata));
     }
 
     if (SRC) {
-        // dJ/dm_B
-        const T v = E0 * f0 + f1 * (E1R + trE2) + f2 * RE2R + f3 * e3.q3 + 3.0 * f2 * e3.Rt;
-        out.mB += -G * v + k6 * iA * s4a;
+        // dJ/dm_B = e0 D0 + e1.D1 + e2:D2 + e3:D3 - a.(D4:M3A) / m_A
+        T v = fma_(f1, sum1, e0 * f0);
+        if (EFULL) v = fma_(f2, sum2, fma_(f3, q3e, v));
+        if (useA) v = fma_(-iA, s4a, v);
+        out.mB += v;
         if (multiB) {
-            // dJ/dM2_B = -G [E0 D2 / 2 + (E1 . D3) / 2]
-            const T c2 = -0.5 * G * (E0 * f2 + f3 * E1R);
-            const T c1 = -0.5 * G * (E0 * f1 + f2 * E1R);
-            const T c3 = -0.5 * G * f2;
-            out.M2B[0] += c2 * m.xx + c1 + c3 * (2.0 * E1[0] * x);
-            out.M2B[1] += c2 * m.xy + c3 * (E1[0] * y + E1[1] * x);
-            out.M2B[2] += c2 * m.xz + c3 * (E1[0] * z + E1[2] * x);
-            out.M2B[3] += c2 * m.yy + c1 + c3 * (2.0 * E1[1] * y);
-            out.M2B[4] += c2 * m.yz + c3 * (E1[1] * z + E1[2] * y);
-            out.M2B[5] += c2 * m.zz + c1 + c3 * (2.0 * E1[2] * z);
-            // dJ/dM3_B = (G/6) E0 D3 - (G/6) a . D4
-            add_rank3(out.M3B, m, a, k6 * (E0 * f3 - f4 * aR), -k6 * f3, k6 * (E0 * f2 - f3 * aR),
-                      -k6 * f2);
+            // dJ/dM2_B = [e0 D2 + e1 . D3] / 2
+            //   = [(e0 f2 + f3 e1R) R R + (e0 f1 + f2 e1R) I + f2 (e1 R + R e1)] / 2
+            const T h = T(0.5) * oM2;
+            const T c2 = h * fma_(e0, f2, f3 * e1R);
+            const T c1 = h * fma_(e0, f1, f2 * e1R);
+            const T c3 = h * f2;
+            const T ex = c3 * e1[0], ey = c3 * e1[1], ez = c3 * e1[2];
+            out.M2B[0] = fma_(c2, xx, fma_(ex + ex, x, out.M2B[0] + c1));
+            out.M2B[1] = fma_(c2, xy, fma_(ex, y, fma_(ey, x, out.M2B[1])));
+            out.M2B[2] = fma_(c2, xz, fma_(ex, z, fma_(ez, x, out.M2B[2])));
+            out.M2B[3] = fma_(c2, yy, fma_(ey + ey, y, out.M2B[3] + c1));
+            out.M2B[4] = fma_(c2, yz, fma_(ey, z, fma_(ez, y, out.M2B[4])));
+            out.M2B[5] = fma_(c2, zz, fma_(ez + ez, z, out.M2B[5] + c1));
+            // dJ/dM3_B = -e0 D3 / 6 + a . D4
+            //   = k4 RRR + k3 (aRR) + k3r (IR) + k2 (Ia), with
+            // (aRR)_jkl = a_j R_k R_l + a_k R_j R_l + a_l R_j R_k, (IR)_jkl =
+            // d_jk R_l + d_jl R_k + d_kl R_j and (Ia) likewise with a
+            const T e6 = T(-1.0 / 6.0) * e0;
+            const T k4 = oM3 * fma_(e6, f3, f4aR);
+            const T k3r = oM3 * fma_(f3, aR, e6 * f2);
+            const T k3 = oM3 * f3, k2 = oM3 * f2;
+            const T ax = k3 * a[0], ay = k3 * a[1], az = k3 * a[2];
+            const T bx = k2 * a[0], by = k2 * a[1], bz = k2 * a[2];
+            const T kx = k4 * x, ky = k4 * y, kz = k4 * z;
+            T* o = out.M3B;
+            o[0] = fma_(kx, xx, fma_(T(3.0), fma_(ax, xx, fma_(k3r, x, bx)), o[0]));   // xxx
+            o[1] = fma_(kx, xy, fma_(ax, xy2, fma_(ay, xx, fma_(k3r, y, by + o[1])))); // xxy
+            o[2] = fma_(kx, xz, fma_(ax, xz2, fma_(az, xx, fma_(k3r, z, bz + o[2])))); // xxz
+            o[3] = fma_(kx, yy, fma_(ax, yy, fma_(ay, xy2, fma_(k3r, x, bx + o[3])))); // xyy
+            o[4] = fma_(kx, yz, fma_(ax, yz, fma_(ay, xz, fma_(az, xy, o[4]))));       // xyz
+            o[5] = fma_(kx, zz, fma_(ax, zz, fma_(az, xz2, fma_(k3r, x, bx + o[5])))); // xzz
+            o[6] = fma_(ky, yy, fma_(T(3.0), fma_(ay, yy, fma_(k3r, y, by)), o[6]));   // yyy
+            o[7] = fma_(ky, yz, fma_(ay, yz2, fma_(az, yy, fma_(k3r, z, bz + o[7])))); // yyz
+            o[8] = fma_(ky, zz, fma_(ay, zz, fma_(az, yz2, fma_(k3r, y, by + o[8])))); // yzz
+            o[9] = fma_(kz, zz, fma_(T(3.0), fma_(az, zz, fma_(k3r, z, bz)), o[9]));   // zzz
         }
     }
     if (TGT && useA) {
-        // the ratio term -(m_B / m_A) M3_A: dJ/dm_A here; dJ/dM3_A =
-        // (G/6) / m_A a . sum_B m_B D4(R_B) from the partners' quartic sum,
-        // contracted once per target (reverse_target_finish)
+        // the ratio term -(m_B / m_A) M3A: dJ/dm_A = m_B / m_A^2 a.(D4:M3A)
+        // here; dJ/dM3_A = -(1 / m_A) a . sum_B m_B D4(R_B) once per target
+        // from the partners' quartic sum (reverse_target_finish), whose
+        // monomials are multiples of m_B f4 x^2, y^2, z^2
         const T s4 = mB * f4;
-        const T txx = s4 * m.xx, txy = s4 * m.xy, txz = s4 * m.xz, tyy = s4 * m.yy, tyz = s4 * m.yz,
-                tzz = s4 * m.zz;
-        out.A4[0] += txx * m.xx;
-        out.A4[1] += txx * m.xy;
-        out.A4[2] += txx * m.xz;
-        out.A4[3] += txx * m.yy;
-        out.A4[4] += txx * m.yz;
-        out.A4[5] += txx * m.zz;
-        out.A4[6] += txy * m.yy;
-        out.A4[7] += txy * m.yz;
-        out.A4[8] += txy * m.zz;
-        out.A4[9] += txz * m.zz;
-        out.A4[10] += tyy * m.yy;
-        out.A4[11] += tyy * m.yz;
-        out.A4[12] += tyy * m.zz;
-        out.A4[13] += tyz * m.zz;
-        out.A4[14] += tzz * m.zz;
-        out.mA += -k6 * s4a * mB * iA * iA;
+        const T txx = s4 * xx, tyy = s4 * yy, tzz = s4 * zz;
+        out.A4[0] = fma_(txx, xx, out.A4[0]);
+        out.A4[1] = fma_(txx, xy, out.A4[1]);
+        out.A4[2] = fma_(txx, xz, out.A4[2]);
+        out.A4[3] = fma_(txx, yy, out.A4[3]);
+        out.A4[4] = fma_(txx, yz, out.A4[4]);
+        out.A4[5] = fma_(txx, zz, out.A4[5]);
+        out.A4[6] = fma_(tyy, xy, out.A4[6]);
+        out.A4[7] = fma_(tyy, xz, out.A4[7]);
+        out.A4[8] = fma_(tzz, xy, out.A4[8]);
+        out.A4[9] = fma_(tzz, xz, out.A4[9]);
+        out.A4[10] = fma_(tyy, yy, out.A4[10]);
+        out.A4[11] = fma_(tyy, yz, out.A4[11]);
+        out.A4[12] = fma_(tyy, zz, out.A4[12]);
+        out.A4[13] = fma_(tzz, yz, out.A4[13]);
+        out.A4[14] = fma_(tzz, zz, out.A4[14]);
+        out.mA = fma_(mB * (iA * iA), s4a, out.mA);
     }
-    S4Parts<T> m3;  // the partner's octupole parts (interior partners)
-    if (want_R) {
-        // mB E0 D0 + mB E1.D1 + mB E2:D2 + mB E3:D3
-        const T cR = mB * (E0 * f1 + f2 * (E1R + trE2) + f3 * RE2R + f4 * e3.q3 + 3.0 * f3 * e3.Rt);
-        T g[3];
+    if (!want_R) return;
+    // dJ/dR: the monopole part mB (e0 D1 + e1.D2 + e2:D3 + e3:D4)
+    T g[3];
+    {
+        const T a1 = mB * f1;
+        if (EFULL) {
+            const T cR = mB * fma_(e0, f1, fma_(f2, sum1, fma_(f3, sum2, f4 * q3e)));
+            const T a2 = mB * f2, a3 = T(3.0) * (mB * f3);
+#pragma unroll
+            for (int p = 0; p < 3; p++)
+                g[p] = fma_(cR, R[p], fma_(a1, e1[p], fma_(a2, fma_(T(2.0), e2R[p], T(3.0) * te[p]),
+                                                            a3 * q2e[p])));
+        } else {
+            const T cR = mB * fma_(e0, f1, f2 * e1R);
+#pragma unroll
+            for (int p = 0; p < 3; p++) g[p] = fma_(cR, R[p], a1 * e1[p]);
+        }
+    }
+    // the source octupole's parts (interior sources)
+    T q2b[3] = {T(0.0), T(0.0), T(0.0)}, tb[3] = {T(0.0), T(0.0), T(0.0)}, q3b = T(0.0), Rtb = T(0.0);
+    if (multiB) {
+        // e0 (M2:D2 / 2 - M3:D3 / 6) + e1 . (D3 : M2) / 2
+        T MR[3], ME1[3];
+        MR[0] = fma_(M2B[0], x, fma_(M2B[1], y, M2B[2] * z));
+        MR[1] = fma_(M2B[1], x, fma_(M2B[3], y, M2B[4] * z));
+        MR[2] = fma_(M2B[2], x, fma_(M2B[4], y, M2B[5] * z));
+        ME1[0] = fma_(M2B[0], e1[0], fma_(M2B[1], e1[1], M2B[2] * e1[2]));
+        ME1[1] = fma_(M2B[1], e1[0], fma_(M2B[3], e1[1], M2B[4] * e1[2]));
+        ME1[2] = fma_(M2B[2], e1[0], fma_(M2B[4], e1[1], M2B[5] * e1[2]));
+        const T xMx = fma_(x, MR[0], fma_(y, MR[1], z * MR[2]));
+        const T trM = M2B[0] + M2B[3] + M2B[5];
+        const T E1MR = fma_(e1[0], MR[0], fma_(e1[1], MR[1], e1[2] * MR[2]));
+        contract_rr(M3B, xx, yy, zz, xy2, xz2, yz2, q2b[0], q2b[1], q2b[2]);
+        q3b = fma_(x, q2b[0], fma_(y, q2b[1], z * q2b[2]));
+        sym3_trace(M3B, tb);
+        Rtb = fma_(x, tb[0], fma_(y, tb[1], z * tb[2]));
+        const T he0 = T(0.5) * e0;
+        const T A2 = fma_(f3, xMx, f2 * trM);  // f3 xMx + f2 trM
+        const T B2 = fma_(f4, xMx, f3 * trM);  // f4 xMx + f3 trM
+        // R_p: e0 [(f3 xMx + f2 trM) / 2 - f4 q3 / 6 - f3 Rt / 2]
+        //      + e1R (f4 xMx + f3 trM) / 2 + f3 e1.M2 R
+        const T cr = fma_(he0, fma_(-f3, Rtb, fma_(T(-1.0 / 3.0) * f4, q3b, A2)),
+                          fma_(T(0.5) * e1R, B2, f3 * E1MR));
+        const T cmr = fma_(e0, f2, f3 * e1R);
+        const T cq2 = -(he0 * f3), ct = -(he0 * f2), ce1 = T(0.5) * A2;
 #pragma unroll
         for (int p = 0; p < 3; p++)
-            g[p] = cR * R[p] + mB * (f1 * E1[p] + 2.0 * f2 * E2R[p] + 3.0 * f3 * e3.q2[p] + 3.0 * f2 * e3.t[p]);
-        if (multiB) {
-            // E0 M2:D2 / 2 - E0 M3:D3 / 6 + E1 . (D3 : M2) / 2
-            T MR[3], ME1[3];
-            sym2_vec(M2B, R, MR);
-            sym2_vec(M2B, E1, ME1);
-            const T xMx = MR[0] * x + MR[1] * y + MR[2] * z;
-            const T trM = M2B[0] + M2B[3] + M2B[5];
-            const T E1MR = E1[0] * MR[0] + E1[1] * MR[1] + E1[2] * MR[2];
-            s4_parts(M3B, m, m3);
-            const T cr = 0.5 * E0 * (f3 * xMx + f2 * trM) - (1.0 / 6.0) * E0 * f4 * m3.q3 -
-                              0.5 * E0 * f3 * m3.Rt + 0.5 * f4 * E1R * xMx + 0.5 * f3 * (2.0 * E1MR + E1R * trM);
-            const T cmr = E0 * f2 + f3 * E1R;
-            const T cq2 = -0.5 * E0 * f3, ct = -0.5 * E0 * f2;
-            const T ce1 = 0.5 * (f3 * xMx + f2 * trM);
+            g[p] = fma_(cr, R[p], fma_(cmr, MR[p], fma_(cq2, q2b[p], fma_(ct, tb[p], fma_(ce1, e1[p],
+                                                                                     fma_(f2, ME1[p], g[p]))))));
+    }
+    if (am && (multiB || useA)) {
+        // a . grad_R (D4 : Q), Q = M3_B - (m_B / m_A) M3A: the parts of Q are
+        // those of the two octupoles combined
+        T q2[3], tq[3], Q[10], q3 = q3b, Rt = Rtb;
 #pragma unroll
-            for (int p = 0; p < 3; p++)
-                g[p] += cr * R[p] + cmr * MR[p] + cq2 * m3.q2[p] + ct * m3.t[p] + ce1 * E1[p] + f2 * ME1[p];
+        for (int p = 0; p < 3; p++) {
+            q2[p] = q2b[p];
+            tq[p] = tb[p];
         }
 #pragma unroll
-        for (int p = 0; p < 3; p++) gR[p] += -sR * G * g[p];
-        if (am && (multiB || useA)) {
-            // a . (D4 : Q), Q = M3_B - ratio M3_A
-            T Q[10];
-#pragma unroll
-            for (int n = 0; n < 10; n++) Q[n] = (multiB ? M3B[n] : 0.0) - (useA ? ratio * M3A[n] : 0.0);
-            // the parts of Q are linear in Q: from the octupoles' own parts
-            S4Parts<T> q;
-            const T rq = useA ? ratio : T(0.0);
+        for (int n = 0; n < 10; n++) Q[n] = M3B[n];
+        if (useA) {
+            const T rq = mB * iA;
 #pragma unroll
             for (int p = 0; p < 3; p++) {
-                q.q2[p] = (multiB ? m3.q2[p] : T(0.0)) - (useA ? rq * qa.q2[p] : T(0.0));
-                q.t[p] = (multiB ? m3.t[p] : T(0.0)) - (useA ? rq * qa.t[p] : T(0.0));
+                q2[p] = fma_(-rq, q2a[p], q2[p]);
+                tq[p] = fma_(-rq, ta[p], tq[p]);
             }
-            q.q3 = (multiB ? m3.q3 : T(0.0)) - (useA ? rq * qa.q3 : T(0.0));
-            q.Rt = (multiB ? m3.Rt : T(0.0)) - (useA ? rq * qa.Rt : T(0.0));
-            T u[3];  // u_p = Q_pik a_i R_k
-            sym3_contract(Q, a[0] * x, a[1] * y, a[2] * z, a[0] * y + a[1] * x, a[0] * z + a[2] * x,
-                          a[1] * z + a[2] * y, u);
-            const T aq2 = a[0] * q.q2[0] + a[1] * q.q2[1] + a[2] * q.q2[2];
-            const T at = a[0] * q.t[0] + a[1] * q.t[1] + a[2] * q.t[2];
-            const T cv = f5 * aR * q.q3 + 3.0 * f4 * aq2 + 3.0 * f4 * aR * q.Rt + 3.0 * f3 * at;
-            const T ca = f4 * q.q3 + 3.0 * f3 * q.Rt;
+            q3 = fma_(-rq, q3a, q3);
+            Rt = fma_(-rq, Rta, Rt);
 #pragma unroll
-            for (int p = 0; p < 3; p++)
-                gR[p] += -sR * k6 * (cv * R[p] + ca * a[p] + 3.0 * f4 * aR * q.q2[p] + 6.0 * f3 * u[p] +
-                                        3.0 * f3 * aR * q.t[p]);
+            for (int n = 0; n < 10; n++) Q[n] = fma_(-rq, M3A[n], Q[n]);
         }
+        T u[3];  // u_p = Q_pik a_i R_k
+        sym3_contract(Q, a[0] * x, a[1] * y, a[2] * z, fma_(a[0], y, a[1] * x), fma_(a[0], z, a[2] * x),
+                      fma_(a[1], z, a[2] * y), u);
+        const T aq2 = fma_(a[0], q2[0], fma_(a[1], q2[1], a[2] * q2[2]));
+        const T at = fma_(a[0], tq[0], fma_(a[1], tq[1], a[2] * tq[2]));
+        const T f5 = f4 * (T(-9.0) * ri2);
+        const T F3 = T(3.0) * f3;
+        // R_p: f5 aR q3 + 3 f4 (a.q2 + aR Rt) + 3 f3 a.t; a_p: f4 q3 + 3 f3 Rt
+        const T cv = fma_(f5 * aR, q3, fma_(T(3.0) * f4, fma_(aR, Rt, aq2), F3 * at));
+        const T ca = fma_(f4, q3, F3 * Rt);
+        const T cq = T(3.0) * f4aR, cu = F3 + F3, ctq = F3 * aR;
+#pragma unroll
+        for (int p = 0; p < 3; p++)
+            g[p] = fma_(cv, R[p], fma_(ca, a[p], fma_(cq, q2[p], fma_(cu, u[p], fma_(ctq, tq[p], g[p])))));
     }
+#pragma unroll
+    for (int p = 0; p < 3; p++) gR[p] = fma_(oR, g[p], gR[p]);
 }
 
 

@@ -135,23 +135,26 @@ void pair_flops_split(double f64[PairClasses], double f32[PairClasses]) {
 // The reverse of one directed pair, as the adjoint kernel runs it (with the
 // correction): a pair with a leaf target in its interior source's pass
 // (source adjoints and the R-gradient), a pair with an interior target whole
-// in the target's pass; R formed from the offsets and the centres (9 flops).
-template <bool SRC, bool TGT> static double count_reverse(bool multiB, bool multiA) {
+// in the target's pass; R formed from the offsets and the centres in cell
+// units (6 flops).
+template <bool TGT_INTERIOR> static double count_reverse(bool multiB) {
     g_flops = 0;
     CountT R[3], M2B[6], M3B[10], M3A[10], E1[3], E2[6], E3[10], ac[3], gR[3];
-    CountT G, mB, mA, E0, sR;
+    CountT mB, iA, E0, oM2, oM3, oR;
     PairAdjOutT<CountT> o;
-    m2l_pair_reverse<SRC, TGT>(R, G, 1, mB, M2B, M3B, multiB, mA, M3A, multiA, E0, E1, E2, E3, ac, true,
-                               sR, gR, o);
-    return (double)g_flops + 9.0;
+    // an interior target (pass 2) keeps the correction's mass ratio; a leaf
+    // target (pass 1) has no E2, E3 or octupole
+    m2l_pair_reverse<true, TGT_INTERIOR, TGT_INTERIOR>(R, mB, M2B, M3B, multiB, TGT_INTERIOR, iA, M3A, E0, E1,
+                                                       E2, E3, true, ac, true, oM2, oM3, oR, gR, o);
+    return (double)g_flops + 6.0;
 }
 
 void pair_flops_adjoint(double out[PairClasses]) {
     // leaf-leaf pairs: the lattice table transposed, 4 fma
     out[kLatticeFar] = out[kNearP2P] = 8.0;
-    out[kM2P] = count_reverse<true, false>(true, false);
-    out[kP2M] = count_reverse<true, true>(false, true);
-    out[kMM] = count_reverse<true, true>(true, true);
+    out[kM2P] = count_reverse<false>(true);
+    out[kP2M] = count_reverse<true>(false);
+    out[kMM] = count_reverse<true>(true);
 }
 
 void pair_flops(double out[PairClasses][2]) {

@@ -14,7 +14,10 @@
 // then the same expansion from the FP32-bulk form's split pair
 // (m2l_pair_split) twice: with both scalars double (the split's algebra),
 // and with the FP32 part in float (R, M2, M3 rounded to float as the FP32
-// records hold them).
+// records hold them); then the reverse again in cell units of side 0.37 (as
+// the adjoint kernel runs it), in physical units; then the reverse for a
+// leaf target (no E2, E3 or octupole): dJ/dmB, dJ/dM2B[6], dJ/dM3B[10],
+// dJ/dR[3].
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -70,6 +73,44 @@ static void split_out(int am, double G, const double* R, double mA, const double
     for (int i = 0; i < 3; i++) std::printf(" %.17g", am ? -(G / 6.0) * (A.S[i] - P[i]) : 0.0);
 }
 
+// The reverse pair with an interior target (both roles and the R-gradient)
+// in cell units of side h, its outputs printed in physical units: dJ/dmB,
+// dJ/dM2B, dJ/dM3B, dJ/dmA, dJ/dM3A, dJ/dR.
+static void reverse_out(int am, double G, double h, const double* R, double mA, const double* M3A,
+                        double mB, const double* M2B, const double* M3B, double E0, const double* E1,
+                        const double* E2, const double* E3, const double* a) {
+    const double hi = 1.0 / h;
+    double Rc[3], M2c[6], M3Bc[10], M3Ac[10], e1[3], e2[6], e3[10], al[3];
+    for (int r = 0; r < 3; r++) {
+        Rc[r] = R[r] * hi;
+        e1[r] = -G * hi * hi * E1[r];
+        al[r] = (-G / 6.0) * hi * hi * a[r];
+    }
+    for (int r = 0; r < 6; r++) {
+        M2c[r] = M2B[r] * hi * hi;
+        e2[r] = -G * hi * hi * hi * E2[r];
+    }
+    for (int r = 0; r < 10; r++) {
+        M3Bc[r] = M3B[r] * hi * hi * hi;
+        M3Ac[r] = M3A[r] * hi * hi * hi;
+        e3[r] = -G * hi * hi * hi * hi * E3[r];
+    }
+    const bool useA = am && mA != 0.0;
+    const double iA = useA ? 1.0 / mA : 0.0;
+    PairAdjOut o;
+    adj_zero(o);
+    double gR[3] = {0.0, 0.0, 0.0};
+    m2l_pair_reverse<true, true, true>(Rc, mB, M2c, M3Bc, true, useA, iA, M3Ac, -G * hi * E0, e1, e2, e3,
+                                       am != 0, al, true, hi * hi, hi * hi * hi, hi, gR, o);
+    if (useA) reverse_target_finish(o, al, -hi * hi * hi / mA);
+    std::printf(" %.17g", o.mB);
+    for (double v : o.M2B) std::printf(" %.17g", v);
+    for (double v : o.M3B) std::printf(" %.17g", v);
+    std::printf(" %.17g", o.mA);
+    for (double v : o.M3A) std::printf(" %.17g", v);
+    for (double v : gR) std::printf(" %.17g", v);
+}
+
 int main() {
     int am;
     double G;
@@ -104,21 +145,33 @@ int main() {
         for (double v : A.L3) std::printf(" %.17g", -G * kAccL3 * v);
         for (int i = 0; i < 3; i++)
             std::printf(" %.17g", am ? -(G / 6.0) * kAccCor * (A.S[i] - P[i]) : 0.0);
-        // reverse of the same pair, both roles and the R-gradient
-        PairAdjOut o;
-        adj_zero(o);
-        double gR[3] = {0.0, 0.0, 0.0};
-        m2l_pair_reverse<true, true>(R, G, am, mB, M2B, M3B, true, mA, M3A, true, E0, E1, E2, E3, a, true,
-                                     1.0, gR, o);
-        if (am && mA != 0.0) reverse_target_finish(o, a, (G / 6.0) / mA);
-        std::printf(" %.17g", o.mB);
-        for (double v : o.M2B) std::printf(" %.17g", v);
-        for (double v : o.M3B) std::printf(" %.17g", v);
-        std::printf(" %.17g", o.mA);
-        for (double v : o.M3A) std::printf(" %.17g", v);
-        for (double v : gR) std::printf(" %.17g", v);
+        // reverse of the same pair, both roles and the R-gradient, as the
+        // adjoint kernel's pass 2 runs it (an interior target): physical
+        // units are cell units with h = 1, the adjoints pre-scaled by -G and
+        // -G/6
+        reverse_out(am, G, 1.0, R, mA, M3A, mB, M2B, M3B, E0, E1, E2, E3, a);
         split_out<double>(am, G, R, mA, M3A, mB, M2B, M3B, bt);
         split_out<float>(am, G, R, mA, M3A, mB, M2B, M3B, bt);
+        // the same in the kernel's cell units (side h = 0.37): R, M2, M3
+        // divided by h, h^2, h^3, the adjoints scaled by h^-(n+1) and h^-2,
+        // the moment and R adjoints brought back by h^-2, h^-3, h^-1
+        reverse_out(am, G, 0.37, R, mA, M3A, mB, M2B, M3B, E0, E1, E2, E3, a);
+        // a leaf target (pass 1): no E2, E3, octupole or mass ratio
+        {
+            PairAdjOut o;
+            adj_zero(o);
+            double gR[3] = {0.0, 0.0, 0.0}, e1[3], al[3];
+            for (int r = 0; r < 3; r++) {
+                e1[r] = -G * E1[r];
+                al[r] = (-G / 6.0) * a[r];
+            }
+            m2l_pair_reverse<true, false, false, double>(R, mB, M2B, M3B, true, false, 0.0, M3A, -G * E0, e1, nullptr,
+                                                 nullptr, am != 0, al, true, 1.0, 1.0, 1.0, gR, o);
+            std::printf(" %.17g", o.mB);
+            for (double v : o.M2B) std::printf(" %.17g", v);
+            for (double v : o.M3B) std::printf(" %.17g", v);
+            for (double v : gR) std::printf(" %.17g", v);
+        }
         std::printf("\n");
     }
     return 0;

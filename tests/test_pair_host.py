@@ -136,7 +136,26 @@ def test_reverse_pair_matches_the_oracle(pair_check):
         # dJ/dmB, dJ/dM2B, dJ/dM3B, dJ/dmA, dJ/dM3A, dJ/dR (R = XA - XB)
         want = np.concatenate([[ob[0]], [obM2[i] for i in P2], [obM3[i] for i in P3], [oa[0]],
                                [oaM3[i] for i in P3], oa[1:4]])
-        r = h[23:54]
-        worst = max(worst, np.abs(r - want).max() / max(np.abs(oa).max(), np.abs(ob).max()))
+        scale = max(np.abs(oa).max(), np.abs(ob).max())
+        worst = max(worst, np.abs(h[23:54] - want).max() / scale)
+        # the kernel's cell units (R, M2, M3 over h, h^2, h^3; adjoints pre-scaled)
+        worst = max(worst, np.abs(h[100:131] - want).max() / scale)
         assert np.abs(oa[1:4] + ob[1:4]).max() <= 1e-12 * np.abs(oa[1:4]).max()  # R-gradient only
+    assert worst < 1e-13, worst
+
+
+def test_leaf_target_reverse_pair_matches_the_oracle(pair_check):
+    """The reverse pair for a leaf target (the adjoint kernel's pass 1, which
+    skips the target's E2, E3 and octupole): against the oracle's reverse with
+    those set to zero."""
+    cases = random_cases(40, 6)
+    worst = 0.0
+    for c, h in zip(cases, run(pair_check, cases)):
+        c0 = dict(c, M3A=np.zeros(10), E2=np.zeros(6), E3=np.zeros(10))
+        momA, momB = moments(c0)
+        Eb = np.concatenate([[c0["E0"]], c0["E1"], np.zeros(9 + 27), c0["a"]])
+        oa, ob = O.m2l_reverse(momA, momB, Eb, G=c["G"], am_correction=bool(c["am"]))
+        obM2, obM3 = ob[4:13].reshape(3, 3), ob[13:40].reshape(3, 3, 3)
+        want = np.concatenate([[ob[0]], [obM2[i] for i in P2], [obM3[i] for i in P3], oa[1:4]])
+        worst = max(worst, np.abs(h[131:151] - want).max() / max(np.abs(oa).max(), np.abs(ob).max()))
     assert worst < 1e-13, worst
