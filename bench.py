@@ -604,7 +604,14 @@ def ppm_companion(flush, peaks, level=4, steps=20):
 # with the reciprocal and the square root as one operation; the Rusanov flux,
 # 27; the weighted sum, 10), per cell 44 (divergence 30, scale 5, source 9);
 # a leaf computes 3 x 9 x 8 x 8 faces of 9 points.
-HYDRO_OPS_PER_POINT = 83
+# FP64 operations of the hydro right-hand side, the correctly rounded
+# reciprocal and square root counted as one each: per face point the two
+# states' fluxes from their primitives (7 each), the Rusanov flux (27) and the
+# weighted sum (10); per own cell and direction the state's primitives (16,
+# formed once); per cell the divergence, scale and source (44).  The ghost
+# states' primitives at refinement jumps are not counted.
+HYDRO_OPS_PER_POINT = 51
+HYDRO_OPS_PER_STATE = 16
 HYDRO_OPS_PER_CELL = 44
 
 
@@ -640,7 +647,8 @@ def hydro_companion(flush, peaks, level=4, steps=20):
     n_leaf = leaves.shape[0]
     cells = n_leaf * 512
     ops_ppm = cells * 5 * 13 * 25
-    ops_flux = n_leaf * 3 * 576 * 9 * HYDRO_OPS_PER_POINT + cells * HYDRO_OPS_PER_CELL
+    ops_flux = (n_leaf * 3 * 576 * 9 * HYDRO_OPS_PER_POINT + cells * 26 * HYDRO_OPS_PER_STATE
+                + cells * HYDRO_OPS_PER_CELL)
     gops = (ops_ppm + ops_flux) / (med / 1e3) / 1e12
     peak_ops = peaks["fp64_tflops"] / 2.0
     tree.close()
@@ -687,7 +695,8 @@ def hydro_tree_companion(tree, leaves, name, flush, peaks, steps=5):
     med = statistics.median(ms)
     n_leaf = leaves.shape[0]
     cells = n_leaf * 512
-    ops = cells * 5 * 13 * 25 + n_leaf * 3 * 576 * 9 * HYDRO_OPS_PER_POINT + cells * HYDRO_OPS_PER_CELL
+    ops = (cells * 5 * 13 * 25 + n_leaf * 3 * 576 * 9 * HYDRO_OPS_PER_POINT + cells * 26 * HYDRO_OPS_PER_STATE
+           + cells * HYDRO_OPS_PER_CELL)
     gops = ops / (med / 1e3) / 1e12
     peak_ops = peaks["fp64_tflops"] / 2.0
     # mass rate without gravity: fluxes only, so its total is the domain

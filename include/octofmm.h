@@ -273,8 +273,9 @@ int ot_ppm_reconstruct(ot_tree* tree, const double* u, int n_fields, double* out
  * [n_leaf][5][512]; g: device float64 [n_leaf][3][512] (e.g. the gravity
  * solve's output) or NULL for no gravity; dudt: device float64
  * [n_leaf][5][512].  The first call allocates the workspace (the PPM values
- * of the cells and of the ghost cells next to the faces, and the face
- * fluxes: about 181 doubles per cell).  FP64, written so that every
+ * of the cells and their primitive variables, the PPM values of the ghost
+ * cells next to the faces, and the face fluxes: about 311 doubles per
+ * cell).  FP64, written so that every
  * operation matches a plain FP64 evaluation of the same formulas (no fused
  * multiply-adds). */
 int ot_hydro_rhs(ot_tree* tree, const double* u, const double* g, double gamma, double* dudt, void* stream);

@@ -256,24 +256,53 @@ __global__ void __launch_bounds__(256) k_hydro_ppm(DevTree t, const int* __restr
     }
 }
 
-// Euler flux along axis A of the state U and its wave speed |v_A| + c.
-template <int A>
-__device__ __forceinline__ double state_flux(const double* U, double gamma, double gm1, double* F) {
+// The primitive variables of a state U: P = (v_x, v_y, v_z, p, c), c the
+// sound speed, each operation correctly rounded (as the oracle evaluates it).
+__device__ __forceinline__ void state_prims(const double* U, double gamma, double gm1, double* P) {
     const double rinv = __drcp_rn(U[0]);
     const double vx = __dmul_rn(U[1], rinv), vy = __dmul_rn(U[2], rinv), vz = __dmul_rn(U[3], rinv);
     const double ke = __dmul_rn(0.5, __dadd_rn(__dadd_rn(__dmul_rn(U[1], vx), __dmul_rn(U[2], vy)),
                                                __dmul_rn(U[3], vz)));
     const double p = __dmul_rn(gm1, __dsub_rn(U[4], ke));
-    const double c = __dsqrt_rn(fmax(__dmul_rn(__dmul_rn(gamma, p), rinv), 0.0));
+    P[0] = vx;
+    P[1] = vy;
+    P[2] = vz;
+    P[3] = p;
+    P[4] = __dsqrt_rn(fmax(__dmul_rn(__dmul_rn(gamma, p), rinv), 0.0));
+}
+
+// Euler flux along axis A of the state U with primitives P, and its wave
+// speed |v_A| + c.
+template <int A>
+__device__ __forceinline__ double prim_flux(const double* U, const double* P, double* F) {
     const double s = U[1 + A];
-    const double v = A == 0 ? vx : (A == 1 ? vy : vz);
+    const double v = P[A];
     F[0] = s;
-    F[1] = __dmul_rn(s, vx);
-    F[2] = __dmul_rn(s, vy);
-    F[3] = __dmul_rn(s, vz);
-    F[4] = __dmul_rn(__dadd_rn(U[4], p), v);
-    F[1 + A] = __dadd_rn(F[1 + A], p);
-    return __dadd_rn(fabs(v), c);
+    F[1] = __dmul_rn(s, P[0]);
+    F[2] = __dmul_rn(s, P[1]);
+    F[3] = __dmul_rn(s, P[2]);
+    F[4] = __dmul_rn(__dadd_rn(U[4], P[3]), v);
+    F[1 + A] = __dadd_rn(F[1 + A], P[3]);
+    return __dadd_rn(fabs(v), P[4]);
+}
+
+// The primitives of every PPM value of the leaves' own cells, Vprim
+// [n_leaf][5][26][512] beside Vown (component j of P for direction k of cell
+// c at ((leaf 5 + j) 26 + k) 512 + c): each state's reciprocal and square root
+// once, where the faces along the three axes use a corner value three times
+// and an edge value twice.
+__global__ void __launch_bounds__(256) k_hydro_prims(const double* __restrict__ Vown, double gamma,
+                                                      double* __restrict__ Vprim) {
+    const long long base = (long long)blockIdx.x * kNF * 26 * kCells;
+    const double gm1 = __dsub_rn(gamma, 1.0);
+    for (int idx = threadIdx.x; idx < 26 * kCells; idx += blockDim.x) {
+        double U[kNF], P[kNF];
+#pragma unroll
+        for (int f = 0; f < kNF; f++) U[f] = __ldg(Vown + base + (long long)f * 26 * kCells + idx);
+        state_prims(U, gamma, gm1, P);
+#pragma unroll
+        for (int f = 0; f < kNF; f++) Vprim[base + (long long)f * 26 * kCells + idx] = P[f];
+    }
 }
 
 // Index of the face fa (0..8) along A of the cell coordinates c across A in
@@ -288,9 +317,10 @@ __device__ __forceinline__ int face_index(int fa, const int* c) {
 // at fa = 0 and 8; lo_bd / hi_bd: the leaf's low / high face along A lies on
 // the domain boundary (the inside state on both sides).
 template <int A>
-__device__ __forceinline__ void leaf_faces(const double* __restrict__ Vown, const double* __restrict__ Vgh,
-                                           int leaf, bool lo_bd, bool hi_bd, int lf_lo, int lf_hi, double gamma,
-                                           double gm1, double* __restrict__ F, int* status) {
+__device__ __forceinline__ void leaf_faces(const double* __restrict__ Vown, const double* __restrict__ Vprim,
+                                           const double* __restrict__ Vgh, int leaf, bool lo_bd, bool hi_bd,
+                                           int lf_lo, int lf_hi, double gamma, double gm1,
+                                           double* __restrict__ F, int* status) {
     constexpr int T1 = (A + 1) % 3, T2 = (A + 2) % 3;
     constexpr int kStA = A == 0 ? 1 : (A == 1 ? 8 : 64);
     for (int idx = threadIdx.x; idx < kFaces; idx += blockDim.x) {
@@ -329,30 +359,53 @@ __device__ __forceinline__ void leaf_faces(const double* __restrict__ Vown, cons
             const int kL = dir_index(o[0], o[1], o[2]);
             o[A] = -1;
             const int kR = dir_index(o[0], o[1], o[2]);
-            double UL[kNF], UR[kNF];
+            // the states and their primitives: an own or same-level value's
+            // from Vprim, a ghost value's formed here
+            double UL[kNF], UR[kNF], PL[kNF], PR[kNF];
+            const bool inL = !(fa == 0 && lo_bd), inR = !(fa == 8 && hi_bd);
 #pragma unroll
             for (int f = 0; f < kNF; f++) {
                 const long long lf = (long long)leaf * kNF + f;
                 // (a ghost slot at the domain boundary is never read: the
                 // inside state stands on both sides there)
-                if (!(fa == 0 && lo_bd))
-                    UL[f] = ghL ? __ldg(Vgh + ((lf * 6 + 2 * A) * 9 + p) * 64 + gq)
-                                : __ldg(Vown + (((long long)leafL * kNF + f) * 26 + kL) * kCells + cellL);
-                if (!(fa == 8 && hi_bd))
-                    UR[f] = ghR ? __ldg(Vgh + ((lf * 6 + 2 * A + 1) * 9 + p) * 64 + gq)
-                                : __ldg(Vown + (((long long)leafR * kNF + f) * 26 + kR) * kCells + cellR);
+                if (inL) {
+                    if (ghL) {
+                        UL[f] = __ldg(Vgh + ((lf * 6 + 2 * A) * 9 + p) * 64 + gq);
+                    } else {
+                        const long long o = (((long long)leafL * kNF + f) * 26 + kL) * kCells + cellL;
+                        UL[f] = __ldg(Vown + o);
+                        PL[f] = __ldg(Vprim + o);
+                    }
+                }
+                if (inR) {
+                    if (ghR) {
+                        UR[f] = __ldg(Vgh + ((lf * 6 + 2 * A + 1) * 9 + p) * 64 + gq);
+                    } else {
+                        const long long o = (((long long)leafR * kNF + f) * 26 + kR) * kCells + cellR;
+                        UR[f] = __ldg(Vown + o);
+                        PR[f] = __ldg(Vprim + o);
+                    }
+                }
             }
-            if (fa == 0 && lo_bd)
+            if (inL && ghL) state_prims(UL, gamma, gm1, PL);
+            if (inR && ghR) state_prims(UR, gamma, gm1, PR);
+            if (!inL)
 #pragma unroll
-                for (int f = 0; f < kNF; f++) UL[f] = UR[f];
-            if (fa == 8 && hi_bd)
+                for (int f = 0; f < kNF; f++) {
+                    UL[f] = UR[f];
+                    PL[f] = PR[f];
+                }
+            if (!inR)
 #pragma unroll
-                for (int f = 0; f < kNF; f++) UR[f] = UL[f];
+                for (int f = 0; f < kNF; f++) {
+                    UR[f] = UL[f];
+                    PR[f] = PL[f];
+                }
             // a non-physical state is reported, not hidden (its rates are not finite)
             if (!(UL[0] > 0.0) || !(UR[0] > 0.0)) atomicOr(status, kStatusBadDensity);
             double FL[kNF], FR[kNF];
-            const double cl = state_flux<A>(UL, gamma, gm1, FL);
-            const double cr = state_flux<A>(UR, gamma, gm1, FR);
+            const double cl = prim_flux<A>(UL, PL, FL);
+            const double cr = prim_flux<A>(UR, PR, FR);
             const double half_a = __dmul_rn(0.5, fmax(cl, cr));
             // Simpson weights (1, 4, 1) x (1, 4, 1) / 36: centre, edges, corners
             const double w = p == 4 ? (4.0 * 4.0) / 36.0 : ((p & 1) ? (4.0 * 1.0) / 36.0 : (1.0 * 1.0) / 36.0);
@@ -371,6 +424,7 @@ __device__ __forceinline__ void leaf_faces(const double* __restrict__ Vown, cons
 
 __global__ void __launch_bounds__(256, 3) k_hydro_faces(DevTree t, const int* __restrict__ leaf_node,
                                                       const double* __restrict__ Vown,
+                                                      const double* __restrict__ Vprim,
                                                       const double* __restrict__ Vgh, double gamma,
                                                       double* __restrict__ F) {
     const int leaf = blockIdx.x;
@@ -386,11 +440,11 @@ __global__ void __launch_bounds__(256, 3) k_hydro_faces(DevTree t, const int* __
         const int nb = t.nbr[(long long)node * 27 + 13 + ((side & 1) ? step : -step)];
         lf[side] = nb >= 0 ? t.node_leaf[nb] : -1;
     }
-    leaf_faces<0>(Vown, Vgh, leaf, xyz[0] == 0, xyz[0] == top, lf[0], lf[1], gamma, gm1, F,
+    leaf_faces<0>(Vown, Vprim, Vgh, leaf, xyz[0] == 0, xyz[0] == top, lf[0], lf[1], gamma, gm1, F,
                     t.status);
-    leaf_faces<1>(Vown, Vgh, leaf, xyz[1] == 0, xyz[1] == top, lf[2], lf[3], gamma, gm1, F,
+    leaf_faces<1>(Vown, Vprim, Vgh, leaf, xyz[1] == 0, xyz[1] == top, lf[2], lf[3], gamma, gm1, F,
                     t.status);
-    leaf_faces<2>(Vown, Vgh, leaf, xyz[2] == 0, xyz[2] == top, lf[4], lf[5], gamma, gm1, F,
+    leaf_faces<2>(Vown, Vprim, Vgh, leaf, xyz[2] == 0, xyz[2] == top, lf[4], lf[5], gamma, gm1, F,
                     t.status);
 }
 
@@ -532,7 +586,7 @@ void launch_rk3_combine(const double* U0, const double* Uc, const double* L, dou
 }
 
 size_t hydro_workspace_doubles(int n_leaf, size_t* own, size_t* ghost, size_t* faces) {
-    *own = (size_t)n_leaf * kNF * 26 * kCells;
+    *own = 2 * (size_t)n_leaf * kNF * 26 * kCells;  // the PPM values, then their primitives
     *ghost = (size_t)n_leaf * kNF * kGhost;
     *faces = (size_t)n_leaf * 3 * kFaces * kNF;
     return *own + *ghost + *faces;
@@ -544,12 +598,14 @@ void launch_hydro_rhs(const DevTree& t, const int* leaf_node, const double* u, c
     size_t own, ghost, faces;
     hydro_workspace_doubles(t.n_leaf, &own, &ghost, &faces);
     double* Vown = work;
+    double* Vprim = work + own / 2;
     double* Vgh = work + own;
     double* F = Vgh + ghost;
     HydroLevels lv;
     for (int L = 0; L < kMaxLevels; L++) lv.hinv[L] = 1.0 / (t.size / (double)(8 << L));
     k_hydro_ppm<<<t.n_leaf, 256, 0, s>>>(t, leaf_node, u, Vown, Vgh);
-    k_hydro_faces<<<t.n_leaf, 256, 0, s>>>(t, leaf_node, Vown, Vgh, gamma, F);
+    k_hydro_prims<<<t.n_leaf, 256, 0, s>>>(Vown, gamma, Vprim);
+    k_hydro_faces<<<t.n_leaf, 256, 0, s>>>(t, leaf_node, Vown, Vprim, Vgh, gamma, F);
     k_hydro_assemble<<<t.n_leaf, 256, 0, s>>>(t, leaf_node, F, u, g, lv, dudt);
 }
 

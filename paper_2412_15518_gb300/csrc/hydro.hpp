@@ -10,8 +10,9 @@
 namespace otfmm {
 
 // Doubles of the hydro workspace of a tree with n_leaf leaves: the PPM values
-// of the leaves' cells (own), of the ghost cells next to their faces (ghost)
-// and the fluxes of their faces (faces); returns the sum.
+// of the leaves' cells and their primitive variables (own), the PPM values
+// of the ghost cells next to their faces (ghost) and the fluxes of their
+// faces (faces); returns the sum.
 size_t hydro_workspace_doubles(int n_leaf, size_t* own, size_t* ghost, size_t* faces);
 
 // u: device [n_leaf][5][512] cell averages of a 2:1-balanced tree; g: device
