@@ -242,7 +242,10 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
         const bool cleaf = t.node_leaf[node] >= 0;
         const int L = item_level(it);
         const bool grp = item_list(it) == kGroupList;
-        const int passes = grp ? (it.y >> 16) & 3 : 3;  // bit 0: pass 1, bit 1: pass 2
+        // an interior root's items range over its own 512 cells as partners
+        // (all interior: pass 2 only)
+        const bool rootc = item_list(it) == kRootList;
+        const int passes = grp ? (it.y >> 16) & 3 : (rootc ? 2 : 3);  // bit 0: pass 1, bit 1: pass 2
         int i, j, k;
         item_cell(p, it, lane, i, j, k);
         const long long cell = (long long)node * kCells + i + 8 * j + 64 * k;
@@ -254,7 +257,7 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
             q0 = it.z & 0xffff;
             q1 = min(it.z >> 16, __ldg(p.list_len + par));
         } else {
-            base = p.list_first[item_list(it)];
+            base = rootc ? 0 : p.list_first[item_list(it)];
             q0 = it.z;
             q1 = it.w;
         }
@@ -269,7 +272,7 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
         // own moments (cell units) and own expansion adjoints
         const double mC = t.mom64[cell];
         const double dC[3] = {t.mom64[N + cell], t.mom64[2 * N + cell], t.mom64[3 * N + cell]};
-        double M2C[6], M3C[10];
+        double M2C[6], M3C[10], btC[4];  // btC: M3's trace vector, trace of M2
         if (!cleaf) {
 #pragma unroll
             for (int r = 0; r < 6; r++) M2C[r] = t.mom64[(4 + r) * N + cell];
@@ -281,6 +284,8 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
 #pragma unroll
             for (int r = 0; r < 10; r++) M3C[r] = 0.0;
         }
+        sym3_trace(M3C, btC);
+        btC[3] = M2C[0] + M2C[3] + M2C[5];
         PairAdjOut acc;
         adj_zero(acc);
         double lat0 = 0.0, lat1 = 0.0;   // lattice pairs: dJ/dm of this leaf cell (h, h^2 parts)
@@ -302,10 +307,14 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
                 e1[r] = sE1 * locbar[(1 + r) * N + pc];
                 aP[r] = sA * locbar[(20 + r) * N + pc];
             }
+            RevTarget<double> tg;
+            reverse_target_prep<false>(e0, (const double*)nullptr, (const double*)nullptr, false, 0.0,
+                                       (const double*)nullptr, aP, tg);
             // the R-gradient of this pair moves this cell's centre of mass (a
             // leaf partner's centre is fixed): R = X_P - X_C
-            m2l_pair_reverse<true, false, false, double>(R, mC, M2C, M3C, !cleaf, false, 0.0, M3C, e0, e1, nullptr,
-                                                 nullptr, am, aP, !cleaf, hi2, hi3, -hi, acc.R, acc);
+            m2l_pair_reverse<true, false, false, double>(R, mC, M2C, M3C, btC, !cleaf, false, 0.0, M3C, e0, e1,
+                                                         nullptr, nullptr, tg, am, aP, !cleaf, hi2, hi3, -hi,
+                                                         acc.R, acc);
         };
         if (passes & 1) {
             if (grp) {
@@ -370,19 +379,29 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
             // the correction's mass-ratio term (a target of non-zero mass)
             const bool useA = am && mC != 0.0;
             const double iA = useA ? 1.0 / mC : 0.0;
-            auto rev2 = [&](int e, bool pleaf, long long pc) {
-                const double mP = t.mom64[pc];
-                const double Rn[3] = {dC[0] - (double)entry_dx(e) - t.mom64[N + pc],
-                                      dC[1] - (double)entry_dy(e) - t.mom64[2 * N + pc],
-                                      dC[2] - (double)entry_dz(e) - t.mom64[3 * N + pc]};
-                double M2P[6], M3P[10];
+            RevTarget<double> tg;
+            reverse_target_prep<true>(EC[0], EC + 4, EC + 10, useA, iA, M3C, aC, tg);
+            auto rev2 = [&](int dx, int dy, int dz, bool pleaf, long long pc) {
+                // the partner's record: m, its centre-of-mass offset, and for
+                // an interior partner M2, M3 and their traces (16-byte loads)
+                const double2* pr = reinterpret_cast<const double2*>(t.rec64 + pc * kRec);
+                const double2 h0 = __ldg(pr), h1 = __ldg(pr + 1);
+                const double mP = h0.x;
+                const double Rn[3] = {dC[0] - (double)dx - h0.y, dC[1] - (double)dy - h1.x,
+                                      dC[2] - (double)dz - h1.y};
+                double V[20];
 #pragma unroll
-                for (int r = 0; r < 6; r++) M2P[r] = pleaf ? 0.0 : t.mom64[(4 + r) * N + pc];
-#pragma unroll
-                for (int r = 0; r < 10; r++) M3P[r] = pleaf ? 0.0 : t.mom64[(10 + r) * N + pc];
+                for (int r = 0; r < 10; r++) {
+                    const double2 v = pleaf ? make_double2(0.0, 0.0) : __ldg(pr + 2 + r);
+                    V[2 * r] = v.x;
+                    V[2 * r + 1] = v.y;
+                }
+                const double* M2P = V;
+                const double* M3P = V + 6;
+                const double* btP = V + 16;
                 double gR[3] = {0.0, 0.0, 0.0};
-                m2l_pair_reverse<true, true, true>(Rn, mP, M2P, M3P, !pleaf, useA, iA, M3C, EC[0], EC + 1,
-                                                   EC + 4, EC + 10, am, aC, true, hi2, hi3, hi, gR, acc);
+                m2l_pair_reverse<true, true, true>(Rn, mP, M2P, M3P, btP, !pleaf, useA, iA, M3C, EC[0], EC + 1,
+                                                   EC + 4, EC + 10, tg, am, aC, true, hi2, hi3, hi, gR, acc);
                 // the partner's source-side adjoints of this pair
                 atomicAdd(mombar + pc, acc.mB);
                 acc.mB = 0.0;
@@ -407,13 +426,22 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
                     for (int s = 0; s < 3; s++) atomicAdd(mombar + (1 + s) * N + pc, -gR[s]);
                 }
             };
-            if (grp) {
+            if (rootc) {
+                // the same partner cell for every lane (a broadcast load); a
+                // pair is far iff |d|^2 > near_d2 (near ones descend)
+#pragma unroll 1
+                for (int sc = q0; sc < q1; sc++) {
+                    const int dx = (sc & 7) - i, dy = ((sc >> 3) & 7) - j, dz = (sc >> 6) - k;
+                    if (dx * dx + dy * dy + dz * dz <= p.near_d2) continue;
+                    rev2(dx, dy, dz, false, (long long)node * kCells + sc);
+                }
+            } else if (grp) {
 #pragma unroll 1
                 for (int q = q0;;) {
                     int e = 0, nb = 0, lc = 0;
                     const int kind = next_partner<2>(p, s_nb[w], s_lf[w], base, q1, i, j, k, q, e, nb, lc);
                     if (!__any_sync(0xffffffffu, kind != 0)) break;
-                    if (kind != 0) rev2(e, kind == 2, (long long)nb * kCells + lc);
+                    if (kind != 0) rev2(entry_dx(e), entry_dy(e), entry_dz(e), kind == 2, (long long)nb * kCells + lc);
                     q++;
                 }
             } else {
@@ -426,7 +454,8 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
                     if (nb < 0) continue;
                     const bool pleaf = s_lf[w][slot] != 0;
                     if (!pleaf && entry_near(e)) continue;
-                    rev2(e, pleaf, (long long)nb * kCells + (sx & 7) + 8 * (sy & 7) + 64 * (sz & 7));
+                    rev2(entry_dx(e), entry_dy(e), entry_dz(e), pleaf,
+                         (long long)nb * kCells + (sx & 7) + 8 * (sy & 7) + 64 * (sz & 7));
                 }
             }
         }

@@ -51,6 +51,17 @@ template <class T> __host__ __device__ __forceinline__ void adj_zero(PairAdjOutT
     for (int i = 0; i < 15; i++) o.A4[i] = 0.0;
 }
 
+// What the reverse pair needs of its target that does not depend on the
+// partner, formed once per target (reverse_target_prep) instead of per pair:
+// e0 / 2 and -e0 / 6; for an interior target (EFULL) the trace of E2 and
+// three times the trace vector of E3 (E3_ijj); for the correction's mass
+// ratio (useA) the trace vector of M3A, a . that vector and 1 / m_A^2.
+template <class T> struct RevTarget {
+    T he0, e6;
+    T trE2, te3[3];
+    T ta[3], ata, iA2;
+};
+
 // Symmetric rank-2 (packed xx xy xz yy yz zz) times vector.
 template <class T>
 __host__ __device__ __forceinline__ void sym2_vec(const T* S, const T* v, T* o) {
@@ -94,6 +105,34 @@ __host__ __device__ __forceinline__ void sym3_trace(const T* c, T* t) {
     t[0] = c[0] + c[3] + c[5];
     t[1] = c[1] + c[6] + c[8];
     t[2] = c[2] + c[7] + c[9];
+}
+
+template <bool EFULL, class T>
+__host__ __device__ __forceinline__ void reverse_target_prep(T e0, const T* e2, const T* e3, bool useA,
+                                                             T iA, const T* M3A, const T* a,
+                                                             RevTarget<T>& tg) {
+    tg.he0 = T(0.5) * e0;
+    tg.e6 = T(-1.0 / 6.0) * e0;
+    tg.trE2 = T(0.0);
+    tg.ata = T(0.0);
+    tg.iA2 = T(0.0);
+#pragma unroll
+    for (int p = 0; p < 3; p++) {
+        tg.te3[p] = T(0.0);
+        tg.ta[p] = T(0.0);
+    }
+    if (EFULL) {
+        tg.trE2 = e2[0] + e2[3] + e2[5];
+        T te[3];
+        sym3_trace(e3, te);
+#pragma unroll
+        for (int p = 0; p < 3; p++) tg.te3[p] = T(3.0) * te[p];
+    }
+    if (useA) {
+        sym3_trace(M3A, tg.ta);
+        tg.ata = fma_(a[0], tg.ta[0], fma_(a[1], tg.ta[1], a[2] * tg.ta[2]));
+        tg.iA2 = iA * iA;
+    }
 }
 
 // The pieces of a . (D4 : T) for a symmetric rank-3 T: q2 = T:RR, q3 = R.q2,
@@ -168,18 +207,21 @@ inline double rsqrt_adj(double a) { return 1.0 / sqrt(a); }
 // the sign that of the centre of mass that R moves).  With h = 1 and G
 // folded into the adjoints this is the physical pair.
 //   SRC: the source's adjoints (m_B; M2_B, M3_B for an interior source,
-//        multiB), added to out.mB, out.M2B, out.M3B;
+//        multiB, whose trace vector M3_B,ijj and trace of M2_B come in btB),
+//        added to out.mB, out.M2B, out.M3B;
 //   TGT: the target side of the correction's mass ratio (useA: an interior
 //        target of mass m_A = 1 / iA != 0, octupole M3A): out.mA and the
 //        quartic sum out.A4 = sum_B m_B f4 R^4 (reverse_target_finish);
 //   EFULL: the target has E2 and E3 adjoints (an interior target; a leaf
 //        target's are zero and skipped);
 //   want_R: dJ/dR into gR.
+// tg holds the target's partner-independent parts (reverse_target_prep with
+// the same e0, e2, e3, useA, iA, M3A and al).
 template <bool SRC, bool TGT, bool EFULL, class T>
 __host__ __device__ __forceinline__ void m2l_pair_reverse(
-    const T* Rv, T mB, const T* M2B, const T* M3B, bool multiB, bool useA, T iA, const T* M3A, T e0,
-    const T* e1, const T* e2, const T* e3, bool am, const T* al, bool want_R, T oM2, T oM3, T oR,
-    T* gR, PairAdjOutT<T>& out) {
+    const T* Rv, T mB, const T* M2B, const T* M3B, const T* btB, bool multiB, bool useA, T iA,
+    const T* M3A, T e0, const T* e1, const T* e2, const T* e3, const RevTarget<T>& tg, bool am,
+    const T* al, bool want_R, T oM2, T oM3, T oR, T* gR, PairAdjOutT<T>& out) {
     const T x = Rv[0], y = Rv[1], z = Rv[2];
     const T R[3] = {x, y, z};
     const T xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z;
@@ -196,34 +238,32 @@ __host__ __device__ __forceinline__ void m2l_pair_reverse(
     const T e1R = fma_(e1[0], x, fma_(e1[1], y, e1[2] * z));
 
     // the interior target's E2 and E3 with R: e2R = E2 R, Re2R = R.E2.R,
-    // q2e = E3 : R R, q3e = R.q2e, te = the trace vector of E3, Rte = R.te;
-    // sum1 = e1R + tr E2 and sum2 = Re2R + 3 Rte recur below
+    // q2e = E3 : R R, q3e = R.q2e, te = the trace vector of E3 (3 te in
+    // tg.te3), Rte = R.te; sum1 = e1R + tr E2 and sum2 = Re2R + 3 Rte recur
+    // below
     T e2R[3] = {T(0.0), T(0.0), T(0.0)}, q2e[3] = {T(0.0), T(0.0), T(0.0)};
-    T te[3] = {T(0.0), T(0.0), T(0.0)}, q3e = T(0.0), sum1 = e1R, sum2 = T(0.0);
+    T q3e = T(0.0), sum1 = e1R, sum2 = T(0.0);
     if (EFULL) {
         e2R[0] = fma_(e2[0], x, fma_(e2[1], y, e2[2] * z));
         e2R[1] = fma_(e2[1], x, fma_(e2[3], y, e2[4] * z));
         e2R[2] = fma_(e2[2], x, fma_(e2[4], y, e2[5] * z));
         const T Re2R = fma_(x, e2R[0], fma_(y, e2R[1], z * e2R[2]));
-        sum1 = e1R + (e2[0] + e2[3] + e2[5]);
+        sum1 = e1R + tg.trE2;
         contract_rr(e3, xx, yy, zz, xy2, xz2, yz2, q2e[0], q2e[1], q2e[2]);
         q3e = fma_(x, q2e[0], fma_(y, q2e[1], z * q2e[2]));
-        sym3_trace(e3, te);
-        sum2 = fma_(T(3.0), fma_(x, te[0], fma_(y, te[1], z * te[2])), Re2R);
+        sum2 = fma_(x, tg.te3[0], fma_(y, tg.te3[1], fma_(z, tg.te3[2], Re2R)));
     }
     // the target octupole's parts (the correction's ratio term) and
     // s4a = a . (D4 : M3A)
-    T q2a[3] = {T(0.0), T(0.0), T(0.0)}, ta[3] = {T(0.0), T(0.0), T(0.0)};
+    T q2a[3] = {T(0.0), T(0.0), T(0.0)};
     T q3a = T(0.0), Rta = T(0.0), s4a = T(0.0);
     const T f4aR = f4 * aR;
     if (useA) {
         contract_rr(M3A, xx, yy, zz, xy2, xz2, yz2, q2a[0], q2a[1], q2a[2]);
         q3a = fma_(x, q2a[0], fma_(y, q2a[1], z * q2a[2]));
-        sym3_trace(M3A, ta);
-        Rta = fma_(x, ta[0], fma_(y, ta[1], z * ta[2]));
+        Rta = fma_(x, tg.ta[0], fma_(y, tg.ta[1], z * tg.ta[2]));
         const T aq2a = fma_(a[0], q2a[0], fma_(a[1], q2a[1], a[2] * q2a[2]));
-        const T ata = fma_(a[0], ta[0], fma_(a[1], ta[1], a[2] * ta[2]));
-        s4a = fma_(f4aR, q3a, T(3.0) * fma_(f3, fma_(aR, Rta, aq2a), f2 * ata));
+        s4a = fma_(f4aR, q3a, T(3.0) * fma_(f3, fma_(aR, Rta, aq2a), f2 * tg.ata));
     }
 
     if (SRC) {
@@ -250,9 +290,8 @@ __host__ __device__ __forceinline__ void m2l_pair_reverse(
             //   = k4 RRR + k3 (aRR) + k3r (IR) + k2 (Ia), with
             // (aRR)_jkl = a_j R_k R_l + a_k R_j R_l + a_l R_j R_k, (IR)_jkl =
             // d_jk R_l + d_jl R_k + d_kl R_j and (Ia) likewise with a
-            const T e6 = T(-1.0 / 6.0) * e0;
-            const T k4 = oM3 * fma_(e6, f3, f4aR);
-            const T k3r = oM3 * fma_(f3, aR, e6 * f2);
+            const T k4 = oM3 * fma_(tg.e6, f3, f4aR);
+            const T k3r = oM3 * fma_(f3, aR, tg.e6 * f2);
             const T k3 = oM3 * f3, k2 = oM3 * f2;
             const T ax = k3 * a[0], ay = k3 * a[1], az = k3 * a[2];
             const T bx = k2 * a[0], by = k2 * a[1], bz = k2 * a[2];
@@ -292,7 +331,7 @@ __host__ __device__ __forceinline__ void m2l_pair_reverse(
         out.A4[12] = fma_(tyy, zz, out.A4[12]);
         out.A4[13] = fma_(tzz, yz, out.A4[13]);
         out.A4[14] = fma_(tzz, zz, out.A4[14]);
-        out.mA = fma_(mB * (iA * iA), s4a, out.mA);
+        out.mA = fma_(mB * tg.iA2, s4a, out.mA);
     }
     if (!want_R) return;
     // dJ/dR: the monopole part mB (e0 D1 + e1.D2 + e2:D3 + e3:D4)
@@ -304,7 +343,7 @@ __host__ __device__ __forceinline__ void m2l_pair_reverse(
             const T a2 = mB * f2, a3 = T(3.0) * (mB * f3);
 #pragma unroll
             for (int p = 0; p < 3; p++)
-                g[p] = fma_(cR, R[p], fma_(a1, e1[p], fma_(a2, fma_(T(2.0), e2R[p], T(3.0) * te[p]),
+                g[p] = fma_(cR, R[p], fma_(a1, e1[p], fma_(a2, fma_(T(2.0), e2R[p], tg.te3[p]),
                                                             a3 * q2e[p])));
         } else {
             const T cR = mB * fma_(e0, f1, f2 * e1R);
@@ -312,8 +351,10 @@ __host__ __device__ __forceinline__ void m2l_pair_reverse(
             for (int p = 0; p < 3; p++) g[p] = fma_(cR, R[p], a1 * e1[p]);
         }
     }
-    // the source octupole's parts (interior sources)
-    T q2b[3] = {T(0.0), T(0.0), T(0.0)}, tb[3] = {T(0.0), T(0.0), T(0.0)}, q3b = T(0.0), Rtb = T(0.0);
+    // the source octupole's parts (interior sources; its trace vector tb
+    // comes in btB)
+    T q2b[3] = {T(0.0), T(0.0), T(0.0)}, q3b = T(0.0), Rtb = T(0.0);
+    const T* tb = btB;
     if (multiB) {
         // e0 (M2:D2 / 2 - M3:D3 / 6) + e1 . (D3 : M2) / 2
         T MR[3], ME1[3];
@@ -324,13 +365,12 @@ __host__ __device__ __forceinline__ void m2l_pair_reverse(
         ME1[1] = fma_(M2B[1], e1[0], fma_(M2B[3], e1[1], M2B[4] * e1[2]));
         ME1[2] = fma_(M2B[2], e1[0], fma_(M2B[4], e1[1], M2B[5] * e1[2]));
         const T xMx = fma_(x, MR[0], fma_(y, MR[1], z * MR[2]));
-        const T trM = M2B[0] + M2B[3] + M2B[5];
+        const T trM = btB[3];
         const T E1MR = fma_(e1[0], MR[0], fma_(e1[1], MR[1], e1[2] * MR[2]));
         contract_rr(M3B, xx, yy, zz, xy2, xz2, yz2, q2b[0], q2b[1], q2b[2]);
         q3b = fma_(x, q2b[0], fma_(y, q2b[1], z * q2b[2]));
-        sym3_trace(M3B, tb);
         Rtb = fma_(x, tb[0], fma_(y, tb[1], z * tb[2]));
-        const T he0 = T(0.5) * e0;
+        const T he0 = tg.he0;
         const T A2 = fma_(f3, xMx, f2 * trM);  // f3 xMx + f2 trM
         const T B2 = fma_(f4, xMx, f3 * trM);  // f4 xMx + f3 trM
         // R_p: e0 [(f3 xMx + f2 trM) / 2 - f4 q3 / 6 - f3 Rt / 2]
@@ -351,7 +391,7 @@ __host__ __device__ __forceinline__ void m2l_pair_reverse(
 #pragma unroll
         for (int p = 0; p < 3; p++) {
             q2[p] = q2b[p];
-            tq[p] = tb[p];
+            tq[p] = multiB ? tb[p] : T(0.0);
         }
 #pragma unroll
         for (int n = 0; n < 10; n++) Q[n] = M3B[n];
@@ -360,7 +400,7 @@ __host__ __device__ __forceinline__ void m2l_pair_reverse(
 #pragma unroll
             for (int p = 0; p < 3; p++) {
                 q2[p] = fma_(-rq, q2a[p], q2[p]);
-                tq[p] = fma_(-rq, ta[p], tq[p]);
+                tq[p] = fma_(-rq, tg.ta[p], tq[p]);
             }
             q3 = fma_(-rq, q3a, q3);
             Rt = fma_(-rq, Rta, Rt);

@@ -137,15 +137,21 @@ void pair_flops_split(double f64[PairClasses], double f32[PairClasses]) {
 // (source adjoints and the R-gradient), a pair with an interior target whole
 // in the target's pass; R formed from the offsets and the centres in cell
 // units (6 flops).
+// The target's partner-independent parts (reverse_target_prep) are formed
+// once per interior target and not counted; a leaf target's (e0 / 2, -e0 / 6)
+// are formed per pair and counted.
 template <bool TGT_INTERIOR> static double count_reverse(bool multiB) {
-    g_flops = 0;
-    CountT R[3], M2B[6], M3B[10], M3A[10], E1[3], E2[6], E3[10], ac[3], gR[3];
+    CountT R[3], M2B[6], M3B[10], btB[4], M3A[10], E1[3], E2[6], E3[10], ac[3], gR[3];
     CountT mB, iA, E0, oM2, oM3, oR;
     PairAdjOutT<CountT> o;
+    RevTarget<CountT> tg;
+    g_flops = 0;
+    reverse_target_prep<TGT_INTERIOR>(E0, E2, E3, TGT_INTERIOR, iA, M3A, ac, tg);
+    if (TGT_INTERIOR) g_flops = 0;
     // an interior target (pass 2) keeps the correction's mass ratio; a leaf
     // target (pass 1) has no E2, E3 or octupole
-    m2l_pair_reverse<true, TGT_INTERIOR, TGT_INTERIOR>(R, mB, M2B, M3B, multiB, TGT_INTERIOR, iA, M3A, E0, E1,
-                                                       E2, E3, true, ac, true, oM2, oM3, oR, gR, o);
+    m2l_pair_reverse<true, TGT_INTERIOR, TGT_INTERIOR>(R, mB, M2B, M3B, btB, multiB, TGT_INTERIOR, iA, M3A, E0,
+                                                       E1, E2, E3, tg, true, ac, true, oM2, oM3, oR, gR, o);
     return (double)g_flops + 6.0;
 }
 

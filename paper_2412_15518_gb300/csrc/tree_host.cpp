@@ -316,7 +316,8 @@ uint32_t slot_mask(int par, int half, int e) {
 // domain boundaries and the descending near pairs of interior cells cost no
 // iterations.  With `all` (the adjoint's items), every node gets items over
 // its whole list, leaf nodes of level >= 1 without interior neighbours one
-// item per parity half (their pairs are all lattice pairs).
+// item per parity half (their pairs are all lattice pairs), and an interior
+// root items over its own 512 cells as partners (as the forward's).
 // For every cell of a node and neighbour slot s, the numbers of far and near
 // entries of the cell's parity list whose source lies in slot s:
 // out[(c * 27 + s) * 2 + near].
@@ -423,7 +424,7 @@ std::vector<Item> make_items(const HostTree& t, int chunk, const HostPlan& p, bo
         bool lattice_only = tl && L > 0 && !seam;
         if (tl && L > 0 && lattice_nodes) lattice_nodes->push_back(v);
         if (lattice_only && !all) continue;
-        const bool root_cells = L == 0 && !tl && !all;  // an interior root, forward launch
+        const bool root_cells = L == 0 && !tl;  // an interior root: its own cells as sources
         const size_t n_before = items.size();
         if (grouped && L > 0)
             grouped_items(t, p, cnt, v, exist, leafm, chunk, kForward, gitems, gcost, *grp_cells);

@@ -3,9 +3,10 @@
 // the FP64 and FP32-bulk forms (cells of a node regrouped by their pair
 // counts, each lane walking its own parity list) must enumerate exactly the
 // pairs of the parity-class items (32 cells of one parity class over the
-// kept list positions); the adjoint's grouped items of its two passes must
-// enumerate exactly the partners each pass reverses; and every index they
-// produce must stay in bounds.
+// kept list positions); the adjoint's grouped items of its two passes, and
+// its items of an interior root over the root's own cells, must enumerate
+// exactly the partners each pass reverses; and every index they produce
+// must stay in bounds.
 //
 // Usage: items_check <leaves.bin> <theta> <chunk>; leaves.bin holds int32
 // (L, ix, iy, iz) rows.  Prints "pairs <n> grouped_items <m> bad <b>" and
@@ -118,10 +119,18 @@ int main(int argc, char** argv) {
     if (a != b) bad++;
     // The adjoint's items: interior nodes of level >= 1 as grouped items of
     // pass 1 (leaf partners) and pass 2 (leaf partners and far interior
-    // ones) over their cells' whole parity lists; every other node keeps
-    // parity-class items running both passes.
+    // ones) over their cells' whole parity lists; an interior root as items
+    // over its own cells (pass 2 with the far ones, |d|^2 > near_d2); every
+    // other node keeps parity-class items running both passes.
     std::multiset<Pair> r_want, r_got;
     for (int v = 0; v < t.n_nodes(); v++) {
+        if (t.node_level[v] == 0 && t.node_leaf[v] < 0)
+            for (int c = 0; c < kCells; c++)
+                for (int sc = 0; sc < kCells; sc++) {
+                    const int dx = (sc & 7) - (c & 7), dy = ((sc >> 3) & 7) - ((c >> 3) & 7),
+                              dz = (sc >> 6) - (c >> 6);
+                    if (dx * dx + dy * dy + dz * dz > p.near_d2) r_want.insert(Pair(v, c, -1 - sc, 2));
+                }
         if (t.node_level[v] < 1 || t.node_leaf[v] >= 0) continue;
         for (int c = 0; c < kCells; c++) {
             const int i = c & 7, j = (c >> 3) & 7, k = c >> 6;
@@ -139,7 +148,26 @@ int main(int argc, char** argv) {
     }
     for (const Item& it : p.items_adj) {
         const int v = it.x, list = (it.y >> 12) & 15;
+        if (list == kRootList) {
+            // cells [z, w) of the interior root as the partners of the 32
+            // cells of one parity class and half
+            if (t.node_level[v] != 0 || t.node_leaf[v] >= 0 || it.z < 0 || it.w > kCells || it.z >= it.w) {
+                bad++;
+                continue;
+            }
+            const int par = (it.y >> 8) & 7, half = (it.y >> 11) & 1;
+            for (int lane = 0; lane < 32; lane++) {
+                const int i = 2 * (lane & 3) + (par & 1), j = 2 * ((lane >> 2) & 3) + ((par >> 1) & 1);
+                const int k = 2 * (2 * half + (lane >> 4)) + (par >> 2);
+                for (int sc = it.z; sc < it.w; sc++) {
+                    const int dx = (sc & 7) - i, dy = ((sc >> 3) & 7) - j, dz = (sc >> 6) - k;
+                    if (dx * dx + dy * dy + dz * dz > p.near_d2) r_got.insert(Pair(v, i + 8 * j + 64 * k, -1 - sc, 2));
+                }
+            }
+            continue;
+        }
         if (list != kGroupList) {
+            if (t.node_level[v] == 0 && t.node_leaf[v] < 0) bad++;  // the interior root's items are kRootList
             if (t.node_level[v] >= 1 && t.node_leaf[v] < 0) bad++;  // interior nodes are grouped
             continue;
         }

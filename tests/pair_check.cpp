@@ -99,9 +99,13 @@ static void reverse_out(int am, double G, double h, const double* R, double mA, 
     const double iA = useA ? 1.0 / mA : 0.0;
     PairAdjOut o;
     adj_zero(o);
-    double gR[3] = {0.0, 0.0, 0.0};
-    m2l_pair_reverse<true, true, true>(Rc, mB, M2c, M3Bc, true, useA, iA, M3Ac, -G * hi * E0, e1, e2, e3,
-                                       am != 0, al, true, hi * hi, hi * hi * hi, hi, gR, o);
+    double gR[3] = {0.0, 0.0, 0.0}, btB[4];
+    trace3(M3Bc, btB);
+    btB[3] = M2c[0] + M2c[3] + M2c[5];
+    RevTarget<double> tg;
+    reverse_target_prep<true>(-G * hi * E0, e2, e3, useA, iA, M3Ac, al, tg);
+    m2l_pair_reverse<true, true, true>(Rc, mB, M2c, M3Bc, btB, true, useA, iA, M3Ac, -G * hi * E0, e1, e2, e3,
+                                       tg, am != 0, al, true, hi * hi, hi * hi * hi, hi, gR, o);
     if (useA) reverse_target_finish(o, al, -hi * hi * hi / mA);
     std::printf(" %.17g", o.mB);
     for (double v : o.M2B) std::printf(" %.17g", v);
@@ -160,13 +164,19 @@ int main() {
         {
             PairAdjOut o;
             adj_zero(o);
-            double gR[3] = {0.0, 0.0, 0.0}, e1[3], al[3];
+            double gR[3] = {0.0, 0.0, 0.0}, e1[3], al[3], btB[4];
             for (int r = 0; r < 3; r++) {
                 e1[r] = -G * E1[r];
                 al[r] = (-G / 6.0) * a[r];
             }
-            m2l_pair_reverse<true, false, false, double>(R, mB, M2B, M3B, true, false, 0.0, M3A, -G * E0, e1, nullptr,
-                                                 nullptr, am != 0, al, true, 1.0, 1.0, 1.0, gR, o);
+            trace3(M3B, btB);
+            btB[3] = M2B[0] + M2B[3] + M2B[5];
+            RevTarget<double> tg;
+            reverse_target_prep<false>(-G * E0, (const double*)nullptr, (const double*)nullptr, false, 0.0,
+                                       (const double*)nullptr, al, tg);
+            m2l_pair_reverse<true, false, false, double>(R, mB, M2B, M3B, btB, true, false, 0.0, M3A, -G * E0, e1,
+                                                         nullptr, nullptr, tg, am != 0, al, true, 1.0, 1.0, 1.0,
+                                                         gR, o);
             std::printf(" %.17g", o.mB);
             for (double v : o.M2B) std::printf(" %.17g", v);
             for (double v : o.M3B) std::printf(" %.17g", v);
