@@ -463,16 +463,21 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
         // pass 2) and centre-of-mass adjoint (both passes)
         if (!cleaf) {
             if (passes & 2) {
-                if (am && mC != 0.0) {
-                    // dJ/dM3_A = -(1 / m_A) h^-3 al . sum_B m_B D4(R'_B), al = -(G/6) h^-2 a
+                // the octupole's adjoint once per target, in the item that
+                // starts its pass-2 range: dJ/dM3_A = -(1 / m_A) h^-3 al .
+                // sum_B m_B D4(R'_B), al = -(G/6) h^-2 a, from the quartic sum
+                // of all its pairs that the forward pass kept
+                if (am && mC != 0.0 && q0 == 0) {
                     double aC[3];
 #pragma unroll
                     for (int r = 0; r < 3; r++) aC[r] = sA * locbar[(20 + r) * N + cell];
+#pragma unroll
+                    for (int r = 0; r < 15; r++) acc.A4[r] = p.a4_out[r * N + cell];
                     reverse_target_finish(acc, aC, -hi3 / mC);
+#pragma unroll
+                    for (int r = 0; r < 10; r++) atomicAdd(mombar + (10 + r) * N + cell, acc.M3A[r]);
                 }
                 atomicAdd(mombar + cell, acc.mA);
-#pragma unroll
-                for (int r = 0; r < 10; r++) atomicAdd(mombar + (10 + r) * N + cell, acc.M3A[r]);
             }
 #pragma unroll
             for (int s = 0; s < 3; s++) atomicAdd(mombar + (1 + s) * N + cell, acc.R[s]);

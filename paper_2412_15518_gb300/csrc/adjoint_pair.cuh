@@ -31,7 +31,8 @@ template <class T> struct PairAdjOutT {
     T mB, M2B[6], M3B[10];
     T mA, M3A[10];
     T R[3];
-    T A4[15];  // target side: sum over partners of m_B f4 R^4 (reverse_target_finish)
+    T A4[15];  // target side: sum over partners of m_B f4 R^4 (reverse_target_quartic;
+               // reverse_target_finish)
 };
 using PairAdjOut = PairAdjOutT<double>;
 
@@ -210,8 +211,9 @@ inline double rsqrt_adj(double a) { return 1.0 / sqrt(a); }
 //        multiB, whose trace vector M3_B,ijj and trace of M2_B come in btB),
 //        added to out.mB, out.M2B, out.M3B;
 //   TGT: the target side of the correction's mass ratio (useA: an interior
-//        target of mass m_A = 1 / iA != 0, octupole M3A): out.mA and the
-//        quartic sum out.A4 = sum_B m_B f4 R^4 (reverse_target_finish);
+//        target of mass m_A = 1 / iA != 0, octupole M3A): out.mA; the
+//        quartic sum out.A4 = sum_B m_B f4 R^4 that reverse_target_finish
+//        needs is the forward pair's own (reverse_target_quartic);
 //   EFULL: the target has E2 and E3 adjoints (an interior target; a leaf
 //        target's are zero and skipped);
 //   want_R: dJ/dR into gR.
@@ -312,25 +314,7 @@ __host__ __device__ __forceinline__ void m2l_pair_reverse(
     if (TGT && useA) {
         // the ratio term -(m_B / m_A) M3A: dJ/dm_A = m_B / m_A^2 a.(D4:M3A)
         // here; dJ/dM3_A = -(1 / m_A) a . sum_B m_B D4(R_B) once per target
-        // from the partners' quartic sum (reverse_target_finish), whose
-        // monomials are multiples of m_B f4 x^2, y^2, z^2
-        const T s4 = mB * f4;
-        const T txx = s4 * xx, tyy = s4 * yy, tzz = s4 * zz;
-        out.A4[0] = fma_(txx, xx, out.A4[0]);
-        out.A4[1] = fma_(txx, xy, out.A4[1]);
-        out.A4[2] = fma_(txx, xz, out.A4[2]);
-        out.A4[3] = fma_(txx, yy, out.A4[3]);
-        out.A4[4] = fma_(txx, yz, out.A4[4]);
-        out.A4[5] = fma_(txx, zz, out.A4[5]);
-        out.A4[6] = fma_(tyy, xy, out.A4[6]);
-        out.A4[7] = fma_(tyy, xz, out.A4[7]);
-        out.A4[8] = fma_(tzz, xy, out.A4[8]);
-        out.A4[9] = fma_(tzz, xz, out.A4[9]);
-        out.A4[10] = fma_(tyy, yy, out.A4[10]);
-        out.A4[11] = fma_(tyy, yz, out.A4[11]);
-        out.A4[12] = fma_(tyy, zz, out.A4[12]);
-        out.A4[13] = fma_(tzz, yz, out.A4[13]);
-        out.A4[14] = fma_(tzz, zz, out.A4[14]);
+        // (reverse_target_finish)
         out.mA = fma_(mB * tg.iA2, s4a, out.mA);
     }
     if (!want_R) return;
@@ -427,8 +411,38 @@ __host__ __device__ __forceinline__ void m2l_pair_reverse(
 }
 
 
-// dJ/dM3_A of a target from the quartic sum A4 = sum_B m_B f4 R^4 that the
-// target's pairs accumulated: dJ/dM3_A = (G/6) / m_A a . sum_B m_B D4(R_B),
+// The target's quartic sum A4 += m_B f4 R^4 of one pair (R from the target):
+// the forward pair's own sum (pair_formula.cuh, Acc::A4 times kAccCor), which
+// the adjoint's forward pass keeps per interior target; every quartic
+// monomial is a square's multiple times a quadratic one.
+template <class T>
+__host__ __device__ __forceinline__ void reverse_target_quartic(const T* Rv, T mB, PairAdjOutT<T>& out) {
+    const T x = Rv[0], y = Rv[1], z = Rv[2];
+    const T xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z;
+    const T f0 = rsqrt_adj(xx + yy + zz);
+    const T ri2 = f0 * f0;
+    const T f4 = T(105.0) * (f0 * ri2 * ri2 * ri2 * ri2);
+    const T s4 = mB * f4;
+    const T txx = s4 * xx, tyy = s4 * yy, tzz = s4 * zz;
+    out.A4[0] = fma_(txx, xx, out.A4[0]);
+    out.A4[1] = fma_(txx, xy, out.A4[1]);
+    out.A4[2] = fma_(txx, xz, out.A4[2]);
+    out.A4[3] = fma_(txx, yy, out.A4[3]);
+    out.A4[4] = fma_(txx, yz, out.A4[4]);
+    out.A4[5] = fma_(txx, zz, out.A4[5]);
+    out.A4[6] = fma_(tyy, xy, out.A4[6]);
+    out.A4[7] = fma_(tyy, xz, out.A4[7]);
+    out.A4[8] = fma_(tzz, xy, out.A4[8]);
+    out.A4[9] = fma_(tzz, xz, out.A4[9]);
+    out.A4[10] = fma_(tyy, yy, out.A4[10]);
+    out.A4[11] = fma_(tyy, yz, out.A4[11]);
+    out.A4[12] = fma_(tyy, zz, out.A4[12]);
+    out.A4[13] = fma_(tzz, yz, out.A4[13]);
+    out.A4[14] = fma_(tzz, zz, out.A4[14]);
+}
+
+// dJ/dM3_A of a target from the quartic sum A4 = sum_B m_B f4 R^4 over the
+// target's pairs: dJ/dM3_A = (G/6) / m_A a . sum_B m_B D4(R_B),
 // where sum m D4 = A4 + sym(delta Q) + c0 sym(delta delta) with Q = sum m f3
 // R R = -tr(A4) / 7 and c0 = sum m f2 = -tr(Q) / 5 (D4 is traceless); so per
 // packed jkl: (a.A4)_jkl + a_j Q_kl + a_k Q_jl + a_l Q_jk + delta_jk (Q a)_l

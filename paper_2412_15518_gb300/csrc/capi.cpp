@@ -91,6 +91,7 @@ struct ot_tree {
     // adjoint workspace (allocated by the first backward call)
     double* d_locbar = nullptr;
     double* d_mombar = nullptr;
+    double* d_a4 = nullptr;  // [15][cells] interior targets' quartic sums (forward part)
     // tangent workspace (allocated by the first tangent call)
     double* d_mom_d = nullptr;
     double* d_rec_d = nullptr;
@@ -549,7 +550,7 @@ void ot_destroy_tree(ot_tree* t) {
                         t->d_list_len, t->d_items, t->d_counter, t->d_rho_in, t->d_phi_out,
                         t->d_hoff_far, t->d_hoff_near, t->d_lattice_nodes, t->d_items_adj, t->d_item_entries,
                         t->d_off64, t->d_off32, t->d_items_grp, t->d_grp_cells, t->d_hydro_work, t->d_step,
-                        t->d_g_out, t->d_locbar, t->d_mombar, t->d_mom_d, t->d_rec_d, t->d_loc_d};
+                        t->d_g_out, t->d_locbar, t->d_mombar, t->d_a4, t->d_mom_d, t->d_rec_d, t->d_loc_d};
         for (void* p : ptrs)
             if (p) cudaFree(p);
     }
@@ -640,20 +641,25 @@ int ot_gravity_backward(ot_tree* t, const double* rho, const double* w1, const d
     const size_t cells = (size_t)t->h.n_nodes() * kCells;
     if (!t->d_locbar) TRY(dalloc(t, &t->d_locbar, kLoc * cells));
     if (!t->d_mombar) TRY(dalloc(t, &t->d_mombar, kMom * cells));
+    if (!t->d_a4) TRY(dalloc(t, &t->d_a4, 15 * cells));
     cudaStream_t s = (cudaStream_t)stream;
     t->last_stream = s;
     // forward pass: the moments, and the complete expansions of the interior
     // cells (the reverse L2L needs them for the derivative of each shift with
     // respect to the centres of mass).  The leaf cells' expansions are never
     // read by the reverse sweep, so the lattice pairs, the pairs with a leaf
-    // target and the leaf evaluation are left out.
+    // target and the leaf evaluation are left out.  The interior targets'
+    // quartic sums of the correction (sum_B m_B f4 R^4) are kept for the
+    // reverse pass, which needs them for the target octupole's adjoint.
     DevTree d = dev_tree(t);
     const HostTree& h = t->h;
     enqueue_moments(t, rho, o.precision, s);
     TRYC(cudaMemsetAsync(t->d_counter, 0, 4 * sizeof(int), s));
+    TRYC(cudaMemsetAsync(t->d_a4, 0, sizeof(double) * 15 * cells, s));
     {
         DevPlan pf = dev_plan(t);
         pf.interior_only = 1;
+        pf.a4_out = t->d_a4;
         launch_interact(d, pf, o.precision, o.G, o.am_correction ? 1 : 0,
                         std::max(1, t->num_sms * t->ctas_per_sm), t->warps_per_cta, s);
     }
@@ -673,6 +679,7 @@ int ot_gravity_backward(ot_tree* t, const double* rho, const double* w1, const d
     pa.items = t->d_items_adj;
     pa.item_entries = nullptr;  // the adjoint's items range over the lists
     pa.n_items = (int)t->plan.items_adj.size();
+    pa.a4_out = t->d_a4;  // read here: the forward part's quartic sums
     launch_m2l_reverse(d, pa, t->d_locbar, t->d_mombar, o.G, o.am_correction ? 1 : 0,
                        std::max(1, t->num_sms * 4), s);
     for (int L = 0; L + 1 < h.n_levels; L++)

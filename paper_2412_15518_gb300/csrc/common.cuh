@@ -179,6 +179,10 @@ struct DevPlan {
     int near_d2;                // largest |d|^2 (cell units) of a near pair
     int interior_only;          // 1: skip the items of leaf targets (the adjoint's
                                 // forward pass needs only interior expansions)
+    double* a4_out;             // null, or [15][n_cells]: the FP64 general kernel
+                                // adds each interior target's quartic sum
+                                // sum_B m_B f4 R'^4 (cell units, packed as Acc::A4)
+                                // here, which the adjoint's reverse pass reads
 };
 
 // List id of the items of an interior root: their range runs over the

@@ -249,6 +249,13 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
                 T a3[10], ta[3];
                 load_octupole_per_mass(t, cell, a3, ta);
                 correction_target(A, a3, ta, P);
+                if constexpr (std::is_same<T, double>::value) {
+                    // the adjoint's forward pass keeps the quartic sum
+                    if (p.a4_out)
+#pragma unroll
+                        for (int r = 0; r < 15; r++)
+                            atomicAdd(p.a4_out + r * N + cell, A.A4[r] * kAccCor);
+                }
             }
 #pragma unroll
             for (int a = 0; a < 3; a++) atomicAdd(loc + (20 + a) * N + cell, scaled(A.S[a] - P[a], sa));

@@ -106,6 +106,9 @@ static void reverse_out(int am, double G, double h, const double* R, double mA, 
     reverse_target_prep<true>(-G * hi * E0, e2, e3, useA, iA, M3Ac, al, tg);
     m2l_pair_reverse<true, true, true>(Rc, mB, M2c, M3Bc, btB, true, useA, iA, M3Ac, -G * hi * E0, e1, e2, e3,
                                        tg, am != 0, al, true, hi * hi, hi * hi * hi, hi, gR, o);
+    // the quartic sum of the target's pairs (here one), which the kernel
+    // takes from the forward pass
+    reverse_target_quartic(Rc, mB, o);
     if (useA) reverse_target_finish(o, al, -hi * hi * hi / mA);
     std::printf(" %.17g", o.mB);
     for (double v : o.M2B) std::printf(" %.17g", v);
