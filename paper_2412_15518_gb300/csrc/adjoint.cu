@@ -215,6 +215,17 @@ __device__ __forceinline__ int next_partner(const DevPlan& p, const int* s_nb, c
     return 0;
 }
 
+// What a pass-2 target holds for all its pairs and reads once or twice per
+// pair: its E2, E3 and octupole, and its partner-independent parts.  Kept in
+// shared memory, one record per lane (37 doubles: consecutive lanes' records
+// start 2 banks apart, so a warp's access is conflict-free), which leaves the
+// registers to the pair itself.
+struct RevLane {
+    double e2[6], e3[10], m3[10];
+    RevTarget<double> tg;
+};
+static_assert(sizeof(RevLane) == 37 * sizeof(double), "odd record length in doubles");
+
 // M2L / near-pair reverse: persistent over the reverse work items.  A
 // parity-class item runs both passes for its 32 cells; a grouped item (32
 // interior cells of one node sorted by their numbers of partners) runs one,
@@ -223,8 +234,10 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
                                                      double* mombar, double G, int am) {
     __shared__ int s_nb[4][28];
     __shared__ int s_lf[4][28];
+    __shared__ RevLane s_rl[4][32];
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
+    RevLane& rl = s_rl[w][lane];
     const long long N = t.n_cells;
     for (;;) {
         int item = 0;
@@ -370,17 +383,22 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
         // ratio and the pair's R-gradient for this cell, the partner's
         // source-side adjoints and its part of the R-gradient by atomics.
         if (!cleaf && (passes & 2)) {
-            double EC[20], aC[3];
+            double EC[4], aC[3];
 #pragma unroll
-            for (int r = 0; r < 20; r++)
-                EC[r] = (r == 0 ? sE0 : (r < 4 ? sE1 : (r < 10 ? sE2 : sE3))) * locbar[r * N + cell];
+            for (int r = 0; r < 4; r++) EC[r] = (r == 0 ? sE0 : sE1) * locbar[r * N + cell];
+#pragma unroll
+            for (int r = 0; r < 6; r++) rl.e2[r] = sE2 * locbar[(4 + r) * N + cell];
+#pragma unroll
+            for (int r = 0; r < 10; r++) {
+                rl.e3[r] = sE3 * locbar[(10 + r) * N + cell];
+                rl.m3[r] = M3C[r];
+            }
 #pragma unroll
             for (int r = 0; r < 3; r++) aC[r] = sA * locbar[(20 + r) * N + cell];
             // the correction's mass-ratio term (a target of non-zero mass)
             const bool useA = am && mC != 0.0;
             const double iA = useA ? 1.0 / mC : 0.0;
-            RevTarget<double> tg;
-            reverse_target_prep<true>(EC[0], EC + 4, EC + 10, useA, iA, M3C, aC, tg);
+            reverse_target_prep<true>(EC[0], rl.e2, rl.e3, useA, iA, rl.m3, aC, rl.tg);
             auto rev2 = [&](int dx, int dy, int dz, bool pleaf, long long pc) {
                 // the partner's record: m, its centre-of-mass offset, and for
                 // an interior partner M2, M3 and their traces (16-byte loads)
@@ -400,8 +418,8 @@ __global__ void __launch_bounds__(128) k_m2l_reverse(DevTree t, DevPlan p, const
                 const double* M3P = V + 6;
                 const double* btP = V + 16;
                 double gR[3] = {0.0, 0.0, 0.0};
-                m2l_pair_reverse<true, true, true>(Rn, mP, M2P, M3P, btP, !pleaf, useA, iA, M3C, EC[0], EC + 1,
-                                                   EC + 4, EC + 10, tg, am, aC, true, hi2, hi3, hi, gR, acc);
+                m2l_pair_reverse<true, true, true>(Rn, mP, M2P, M3P, btP, !pleaf, useA, iA, rl.m3, EC[0], EC + 1,
+                                                   rl.e2, rl.e3, rl.tg, am, aC, true, hi2, hi3, hi, gR, acc);
                 // the partner's source-side adjoints of this pair
                 atomicAdd(mombar + pc, acc.mB);
                 acc.mB = 0.0;
