@@ -59,7 +59,8 @@ extern "C" {
 
 /* Bits of the device status word (ot_tree_stats.device_status). */
 #define OT_STATUS_BAD_INDEX 1    /* a tree lookup a validated tree cannot produce  */
-#define OT_STATUS_BAD_ITEM 2     /* a work item longer than a kernel stages        */
+#define OT_STATUS_BAD_ITEM 2     /* reserved: a work item longer than a kernel
+                                    stages (no kernel of this version latches it) */
 #define OT_STATUS_BAD_DENSITY 4  /* a hydro face state with density <= 0 or NaN    */
 #define OT_ERR_NO_MEMORY -9      /* host or device allocation failed              */
 #define OT_ERR_WRONG_DEVICE -10  /* buffer on another device than the tree        */
@@ -150,8 +151,10 @@ typedef struct {
     int32_t device_status;                     /* latched device errors, 0 = none;
                                                   reading it clears it.  Bits: 1 a
                                                   tree lookup a valid tree cannot
-                                                  produce, 2 a work item longer than
-                                                  a kernel stages, 4 a hydro state
+                                                  produce, 2 reserved (a work item
+                                                  longer than a kernel stages; no
+                                                  kernel of this version stages a
+                                                  bounded number), 4 a hydro state
                                                   with a density <= 0 (or NaN)      */
     int64_t workspace_bytes;                   /* device memory held by the tree    */
     double flops_bulk64;                       /* FP32-bulk form, one interaction
@@ -363,11 +366,9 @@ int ot_get_moments(ot_tree* tree, int level, double* out, int32_t* node_xyz, voi
  * stencil entries per work item (1 <= chunk <= 4096), ctas_per_sm = CTAs of
  * the general kernel per SM (1..16), lattice_ctas_per_sm = persistent CTAs
  * per SM of the wide FP32 form's lattice kernels (0 = one per leaf node,
- * 1..16).  The FP64 and FP32-bulk general kernels take items of any length;
- * the wide FP32 form stages at most 264 entries of an item: a longer item
- * is skipped by that kernel and latched in the device status word, which
- * ot_tree_info reports as OT_ERR_DEVICE_STATUS.  Rebuilds the work items
- * (host) and re-uploads them; the next solve captures a new graph. */
+ * 1..16).  The general kernels of every form take items of any length.
+ * Rebuilds the work items (host) and re-uploads them; the next solve
+ * captures a new graph. */
 int ot_set_launch_shape(ot_tree* tree, int chunk, int ctas_per_sm, int lattice_ctas_per_sm);
 
 /* Measures the CUDA-core arithmetic peaks of `device` with throughput

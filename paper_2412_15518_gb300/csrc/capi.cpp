@@ -815,15 +815,12 @@ int ot_autotune(ot_tree* t, const double* rho, double* phi, double* g, const ot_
     cudaEvent_t e0, e1;
     TRYC(cudaEventCreate(&e0));
     TRYC(cudaEventCreate(&e1));
-    // the wide FP32 form stages at most 264 entries per item and flushes
-    // its FP32 partial sums every 64 pairs anyway (their rounding error
-    // grows with the summation length), so longer items buy it nothing;
-    // the FP64 and FP32-bulk forms are FP64-pipe bound and tune like each other
+    // every form tries the same item lengths; the wide FP32 form (FP32
+    // general kernel beside two lattice kernels) also tries more general
+    // CTAs per SM and persistent lattice CTAs
     const bool bulk = o.precision == OT_PRECISION_FP32_WIDE;
-    const int chunks_fp64[] = {32, 64, 128, 263};
-    const int chunks_bulk[] = {32, 64};
-    const int* chunks = bulk ? chunks_bulk : chunks_fp64;
-    const int n_chunks = bulk ? 2 : 4;
+    const int chunks[] = {32, 64, 128, 263};
+    const int n_chunks = 4;
     // general CTAs per SM (at most 3 or 4 are resident, by registers; more
     // stay queued and start as others finish) and, for the bulk form, the
     // lattice kernels' persistent CTAs per SM (0: one per node)

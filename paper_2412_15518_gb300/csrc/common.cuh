@@ -45,8 +45,8 @@ constexpr int kPrecWide = 2;
 
 // Status word codes latched by kernels (never trapped).
 constexpr int kStatusBadIndex = 1;
-constexpr int kStatusBadItem = 2;
 constexpr int kStatusBadDensity = 4;  // a hydro face state with density <= 0 or NaN
+// (bit 2 is reserved: no kernel stages a bounded number of item entries)
 
 // Device view of a tree and its current plan; passed by value to kernels.
 struct DevTree {

@@ -152,54 +152,14 @@ __device__ __forceinline__ float small_int(int n, float) {
     return __int_as_float(0x4b000000 | n) - 8388608.0f;
 }
 
-// Per-warp shared staging of the FP32 loop: the item's stencil entries and
-// two stages of 32 source records (5 float4 each, component-major so that a
-// warp's 16-byte accesses are consecutive).
-constexpr int kMaxChunk = 264;
-constexpr int kFlush32 = 64;  // pairs per FP32 partial sum (a power of two)
-struct WarpStage32 {
-    int entries[kMaxChunk];
-    float4 rec[2][5][32];
-};
-
-// Small signed integer (|n| < 2^21) to float without a conversion
-// instruction: 2^23 + 2^21 + n is the float whose fraction bits are
-// 2^21 + n.
-__device__ __forceinline__ float small_sint(int n) {
-    return __int_as_float(0x4b000000 | (n + (1 << 21))) - 10485760.0f;
-}
-
-// Starts the copy of pair q's source into stage st and returns its kind:
-// 0 = no pair, 1 = leaf cell (monopole), 2 = interior cell (multipole); d
-// receives the entry's offset as floats.
-template <bool FULL>
-__device__ __forceinline__ int issue32(const DevTree& t, WarpStage32& ws, int q, int q0, int qend,
-                                       int i, int j, int k, int lane, const int* s_nb,
-                                       const int* s_lf, int st, float3& d) {
-    if (q >= qend) return 0;
-    const int e = ws.entries[q - q0];
-    const int dx = entry_dx(e), dy = entry_dy(e), dz = entry_dz(e);
-    d = make_float3(small_sint(dx), small_sint(dy), small_sint(dz));
-    const int sx = i + dx, sy = j + dy, sz = k + dz;
-    const int slot = ((sx >> 3) + 1) + 3 * ((sy >> 3) + 1) + 9 * ((sz >> 3) + 1);
-    const int nb = s_nb[slot];
-    if (nb < 0) return 0;  // outside the domain, or covered by a coarser leaf
-    const bool sleaf = s_lf[slot] != 0;
-    if (!FULL && sleaf) return 0;                   // leaf-leaf pairs of level >= 1: lattice kernel
-    if (FULL && !sleaf && entry_near(e)) return 0;  // resolved at the next level
-    const long long sc = (long long)nb * kCells + (sx & 7) + 8 * (sy & 7) + 64 * (sz & 7);
-    const float4* g = reinterpret_cast<const float4*>(t.mom32 + sc * kMom);
-    cp_async16(&ws.rec[st][0][lane], g);
-    if (!sleaf)
-#pragma unroll
-        for (int r = 1; r < 5; r++) cp_async16(&ws.rec[st][r][lane], g + r);
-    return sleaf ? 1 : 2;
-}
+// FP32 partial sums of the wide form span at most kFlush32 pairs of a lane:
+// their rounding error grows with the summation length.
+constexpr int kFlush32 = 64;
 
 template <class T, bool FULL, bool AM>
 __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, const int4 it,
                                          const int lane, const int* s_nb, const int* s_lf,
-                                         const LevelScales& sc, WarpStage32* ws) {
+                                         const LevelScales& sc) {
     const int node = it.x;
     const int L = item_level(it);
     int i, j, k;
@@ -311,74 +271,30 @@ __device__ __forceinline__ void run_item(const DevTree& t, const DevPlan& p, con
             const T z = (fk + daz) - (small_int(sz, T(0)) + bz);
             m2l_pair<T, FULL, true, AM>(x, y, z, m, b2, b3, bt, A);
         }
-    } else if (std::is_same<T, float>::value && L > 0) {
-        // FP32 form, levels >= 1: the next source's loads are issued before
-        // the current pair is computed, so their latency overlaps the math
-        if constexpr (std::is_same<T, float>::value) {
-            const int base = p.list_first[item_list(it)];
-            const int q0 = it.z, q1 = it.w;
-            for (int q = q0 + lane; q < q1; q += 32)
-                ws->entries[q - q0] = __ldg(p.entries + base + __ldg(p.item_entries + q));
-            __syncwarp();
-            float3 d = make_float3(0.f, 0.f, 0.f), d_next = d;
-            int kind = issue32<FULL>(t, *ws, q0, q0, q1, i, j, k, lane, s_nb, s_lf, 0, d);
-            cp_async_commit();
-#pragma unroll 1
-            for (int q = q0; q < q1; q++) {
-                const int st = (q - q0) & 1;
-                const int kind_next =
-                    issue32<FULL>(t, *ws, q + 1, q0, q1, i, j, k, lane, s_nb, s_lf, st ^ 1, d_next);
-                cp_async_commit();
-                cp_async_wait1();  // this lane's copies of pair q are done
-                // leaf sources of a warp that also holds interior ones take the
-                // multipole formula with zero moments, in the same pass
-                const bool multi = __any_sync(0xffffffffu, kind == 2);
-                if (kind) {
-                    const float4 h = ws->rec[st][0][lane];
-                    // R' = X_A - X_B in cell units: the source sits at offset d
-                    const float x = (dax - h.y) - d.x;
-                    const float y = (day - h.z) - d.y;
-                    const float z = (daz - h.w) - d.z;
-                    if (!multi) {
-                        m2l_pair<float, FULL, false, AM>(x, y, z, h.x, nullptr, nullptr, nullptr, A);
-                    } else {
-                        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                        const bool lf = kind == 1;
-                        const float4 v1 = lf ? z4 : ws->rec[st][1][lane], v2 = lf ? z4 : ws->rec[st][2][lane],
-                                     v3 = lf ? z4 : ws->rec[st][3][lane], v4 = lf ? z4 : ws->rec[st][4][lane];
-                        const float b2[6] = {v1.x, v1.y, v1.z, v1.w, v2.x, v2.y};
-                        const float b3[10] = {v2.z, v2.w, v3.x, v3.y, v3.z, v3.w, v4.x, v4.y, v4.z, v4.w};
-                        const float bt[4] = {b3[0] + b3[3] + b3[5], b3[1] + b3[6] + b3[8],
-                                             b3[2] + b3[7] + b3[9], b2[0] + b2[3] + b2[5]};
-                        m2l_pair<float, FULL, true, AM>(x, y, z, h.x, b2, b3, bt, A);
-                    }
-                }
-                kind = kind_next;
-                d = d_next;
-                // FP32 partial sums span at most kFlush32 pairs: their rounding
-                // error grows with the summation length
-                if (((q - q0) & (kFlush32 - 1)) == kFlush32 - 1 && q + 1 < q1) {
-                    flush();
-                    acc_zero(A);
-                }
-            }
-            cp_async_wait0();
-            __syncwarp();  // the stage and entry buffers are reused by the next item
-        }
-    } else if (std::is_same<T, double>::value && item_list(it) == kGroupList) {
+    } else if (item_list(it) == kGroupList) {
         // grouped item: every lane walks its own list and computes its pairs
-        // one after another; the warp runs while any lane has a pair left
+        // one after another; the warp runs while any lane has a pair left.
+        // The wide FP32 form adds a lane's FP32 partial sums to the FP64
+        // expansion every kFlush32 pairs.
         const int par = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
         const int base = __ldg(p.list_first + par);
         const int qend = min(it.z >> 16, __ldg(p.list_len + par));
         int q = it.z & 0xffff;
+        int since = 0;
 #pragma unroll 1
         for (;;) {
             int nb = 0, lc = 0;
             const int kind = next_grouped<FULL>(p, s_nb, s_lf, base, qend, i, j, k, q, nb, lc);
             if (!__any_sync(0xffffffffu, kind != 0)) break;
             const bool multi = __any_sync(0xffffffffu, kind == 3);
-            if (kind != 0) pair_at(kind, multi, (long long)nb * kCells + lc, base + q);
+            if (kind != 0) {
+                pair_at(kind, multi, (long long)nb * kCells + lc, base + q);
+                if (sizeof(T) == 4 && ++since == kFlush32) {
+                    flush();
+                    acc_zero(A);
+                    since = 0;
+                }
+            }
             q++;
         }
     } else {
@@ -639,10 +555,8 @@ __global__ void __launch_bounds__(128, std::is_same<T, double>::value ? 3 : 1)
     k_interact(DevTree t, DevPlan p, LevelScales sc, int am) {
     __shared__ int s_nb[kMaxWarps][28];
     __shared__ int s_lf[kMaxWarps][28];
-    extern __shared__ __align__(16) unsigned char s_dyn[];  // FP32 form: one WarpStage32 per warp
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
-    WarpStage32* ws = std::is_same<T, float>::value ? reinterpret_cast<WarpStage32*>(s_dyn) + w : nullptr;
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(p.counter, 1);
@@ -655,20 +569,14 @@ __global__ void __launch_bounds__(128, std::is_same<T, double>::value ? 3 : 1)
             s_lf[w][lane] = nb >= 0 ? (t.node_leaf[nb] >= 0) : 0;
         }
         __syncwarp();
-        if (std::is_same<T, float>::value && item_level(it) > 0 && it.w - it.z > kMaxChunk &&
-            item_list(it) != kRootList) {
-            // longer than the staging buffer of the FP32 loop: latched and skipped
-            if (lane == 0) atomicOr(t.status, kStatusBadItem);
-            continue;
-        }
         const bool full = t.node_leaf[it.x] < 0;
         if (!full && p.interior_only) continue;
         if (full) {
-            if (am) run_item<T, true, true>(t, p, it, lane, s_nb[w], s_lf[w], sc, ws);
-            else run_item<T, true, false>(t, p, it, lane, s_nb[w], s_lf[w], sc, ws);
+            if (am) run_item<T, true, true>(t, p, it, lane, s_nb[w], s_lf[w], sc);
+            else run_item<T, true, false>(t, p, it, lane, s_nb[w], s_lf[w], sc);
         } else {
-            if (am) run_item<T, false, true>(t, p, it, lane, s_nb[w], s_lf[w], sc, ws);
-            else run_item<T, false, false>(t, p, it, lane, s_nb[w], s_lf[w], sc, ws);
+            if (am) run_item<T, false, true>(t, p, it, lane, s_nb[w], s_lf[w], sc);
+            else run_item<T, false, false>(t, p, it, lane, s_nb[w], s_lf[w], sc);
         }
         __syncwarp();
     }
@@ -699,15 +607,14 @@ void launch_interact(const DevTree& t, const DevPlan& p, int precision, double G
                      int ctas, int warps_per_cta, cudaStream_t s) {
     if (warps_per_cta > 4) warps_per_cta = 4;
     const LevelScales sc = level_scales(t.inv_side8, G);
-    // the FP64 and FP32-bulk forms take the grouped items where the plan has
-    // them; the wide FP32 form's staged loop keeps the parity-class items
+    // every form takes the grouped items where the plan has them
     DevPlan g = p;
     if (p.items_grp) {
         g.items = p.items_grp;
         g.n_items = p.n_items_grp;
     }
     if (precision == kPrecWide)
-        k_interact<float><<<ctas, 32 * warps_per_cta, warps_per_cta * sizeof(WarpStage32), s>>>(t, p, sc, am);
+        k_interact<float><<<ctas, 32 * warps_per_cta, 0, s>>>(t, g, sc, am);
     else if (precision == kPrecBulk)
         k_interact_split<<<ctas, 32 * warps_per_cta, 0, s>>>(t, g, sc, am);
     else

@@ -24,7 +24,7 @@ OT_OK = 0
 OT_ERR_DEVICE_STATUS = -8
 # bits of the device status word (ot_tree_info's device_status)
 OT_STATUS_BAD_INDEX = 1
-OT_STATUS_BAD_ITEM = 2
+OT_STATUS_BAD_ITEM = 2  # reserved: no kernel of this version latches it
 OT_STATUS_BAD_DENSITY = 4
 OT_PRECISION_FP64 = 0
 OT_PRECISION_FP32_BULK = 1

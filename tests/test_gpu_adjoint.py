@@ -68,6 +68,26 @@ def test_adjoint_matches_oracle(fmm, case, am):
     assert e < TOLG
 
 
+@pytest.mark.parametrize("theta,chunk", [(0.35, 17), (0.7, 263)])
+def test_adjoint_other_theta_and_launch_shapes(fmm, theta, chunk):
+    """Other opening angles (the interior root's partners are its cells with
+    |d|^2 > near_d2 of that angle) and work items whose ranges split a
+    target's partners over many items (chunk 17, where the target's octupole
+    adjoint is still formed once) or cover them in one (chunk 263)."""
+    lv, rho = CASES["amr_l3_seams"]()
+    w1, w2 = I.weights(lv.shape[0])
+    tree = fmm.Tree(lv)
+    tree.set_launch_shape(chunk, 4)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    g_gpu = tree.backward(d(rho), d(w1), d(w2), theta=theta).cpu().numpy()
+    assert tree.info()["device_status"] == 0
+    tree.close()
+    g_orc = O.gradient(lv, rho, w1, w2, theta=theta)
+    e = rel(g_gpu, g_orc)
+    print(f"theta={theta} chunk={chunk}: max rel err {e:.2e}")
+    assert e < TOLG
+
+
 def test_adjoint_self_term(fmm):
     lv, rho = CASES["sphere_l1_shuffled"]()
     w1, w2 = I.weights(lv.shape[0])

@@ -98,7 +98,8 @@ def test_fixed_launch_shape_keeps_parity(fmm):
         tree.set_launch_shape(chunk, cps)
         info = tree.info()
         assert info["tuned_chunk"] == chunk and info["tuned_ctas_per_sm"] == cps
-        for prec, tol in ((fmm.OT_PRECISION_FP64, 1e-12), (fmm.OT_PRECISION_FP32_BULK, 1e-6)):
+        for prec, tol in ((fmm.OT_PRECISION_FP64, 1e-12), (fmm.OT_PRECISION_FP32_BULK, 1e-6),
+                          (fmm.OT_PRECISION_FP32_WIDE, 1e-6)):
             phi, g = tree.solve(r, precision=prec)
             torch.cuda.synchronize()
             assert rel(phi.cpu().numpy(), phi_o) < tol, (chunk, prec)
@@ -110,35 +111,27 @@ def test_fixed_launch_shape_keeps_parity(fmm):
     tree.close()
 
 
-def test_device_status_latch_reports_an_over_long_item_once(fmm):
+def test_items_of_any_length_in_every_form(fmm):
     """Items of up to 1000 stencil entries at theta = 0.35 (lists of about 700
-    entries at levels >= 1): the FP64 and FP32-bulk kernels (grouped items)
-    handle them, the wide FP32 kernel (264 staged entries) skips them and
-    latches the status word; ot_tree_info reports that once and clears it."""
+    entries at levels >= 1): the general kernels of all three forms take them
+    (the wide FP32 form adds a lane's FP32 partial sums to the FP64 expansion
+    every 64 pairs, so its error does not grow with the item length), and the
+    device status word stays clear."""
     lv = I.uniform_leaves(2)
     rho = I.density(lv, I.BINARY, seed=2)
     theta = 0.35
     tree = fmm.Tree(lv)
     r = torch.from_numpy(rho).cuda()
     phi_o, g_o = O.solve(lv, rho, theta=theta)
-    tree.set_launch_shape(1000, 4)
-    for prec, tol in ((fmm.OT_PRECISION_FP64, 1e-12), (fmm.OT_PRECISION_FP32_BULK, 1e-8)):
-        phi, g = tree.solve(r, theta=theta, precision=prec)
-        torch.cuda.synchronize()
-        assert rel(phi.cpu().numpy(), phi_o) < tol
-        assert rel(g.cpu().numpy(), g_o) < tol
-        assert tree.info()["device_status"] == 0
-    tree.solve(r, theta=theta, precision=fmm.OT_PRECISION_FP32_WIDE)
-    with pytest.raises(fmm.OTError) as e:
-        tree.info()
-    assert e.value.code == -8                       # OT_ERR_DEVICE_STATUS
-    assert tree.info()["device_status"] == 0        # reported once, then cleared
-    tree.set_launch_shape(64, 4)
-    phi, g = tree.solve(r, theta=theta, precision=fmm.OT_PRECISION_FP32_WIDE)
-    torch.cuda.synchronize()
-    assert rel(phi.cpu().numpy(), phi_o) < 1e-6
-    assert rel(g.cpu().numpy(), g_o) < 1e-6
-    assert tree.info()["device_status"] == 0
+    for chunk in (1000, 64):
+        tree.set_launch_shape(chunk, 4)
+        for prec, tol in ((fmm.OT_PRECISION_FP64, 1e-12), (fmm.OT_PRECISION_FP32_BULK, 1e-8),
+                          (fmm.OT_PRECISION_FP32_WIDE, 1e-6)):
+            phi, g = tree.solve(r, theta=theta, precision=prec)
+            torch.cuda.synchronize()
+            assert rel(phi.cpu().numpy(), phi_o) < tol, (chunk, prec)
+            assert rel(g.cpu().numpy(), g_o) < tol, (chunk, prec)
+            assert tree.info()["device_status"] == 0
     tree.close()
 
 
