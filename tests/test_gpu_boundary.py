@@ -8,10 +8,10 @@
   rounding relative to each group's natural scale: max m for m, the domain size for X, max m h^2 for
   M2 and max m h^3 for M3 (h = the level's cell side; |M2| <= 3/4 m h^2 and
   |M3| <= (3/4)^(3/2) m h^3 for points inside the cell): 1e-14.
-* ot_set_launch_shape: a fixed shape keeps parity; an item longer than the
-  wide FP32 form's staging buffer is skipped by that kernel and latched in
-  the device status word, which ot_tree_info reports once (a plan error made
-  on the host: nothing faults).
+* ot_set_launch_shape: a fixed shape keeps parity in every form, with items
+  of up to 1000 stencil entries; the device status word latches a
+  non-physical hydro state (made on the host: nothing faults), which
+  ot_tree_info reports once.
 * ot_alu_peaks: the measured CUDA-core peaks are positive and ordered.
 """
 import numpy as np
