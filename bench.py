@@ -57,11 +57,11 @@ L2_FLUSH_BYTES = 256 << 20
 # captures of the interaction kernels summarised in profiles/ (per launch;
 # binary_amr8 from its full-size one-pass capture).  A workload or form
 # without a capture of the current kernels reports null.
-TRAFFIC_BYTES = {("binary_l3", "fp64"): 14.56e6 + 10.64e6,
+TRAFFIC_BYTES = {("binary_l3", "fp64"): 14.44e6 + 10.64e6,
                  ("binary_l3", "fp32_bulk"): 17.39e6 + 10.64e6,
-                 ("binary_l3", "fp32_wide"): 13.49e6 + 10.66e6 + 9.56e6,
-                 ("binary_amr8", "fp64"): 5.35e9 + 1.53e9 + 0.911e9 + 0.653e9,
-                 ("binary_amr8", "fp32_bulk"): 6.56e9 + 1.51e9 + 0.912e9 + 0.653e9}
+                 ("binary_l3", "fp32_wide"): 12.54e6 + 10.66e6 + 9.56e6,
+                 ("binary_amr8", "fp64"): 5.360e9 + 1.536e9 + 0.911e9 + 0.653e9,
+                 ("binary_amr8", "fp32_bulk"): 6.558e9 + 1.513e9 + 0.912e9 + 0.653e9}
 
 WORKLOAD_TEXT = {
     "sphere_l1": "uniform level-1 octree, 8 leaves of 8^3 (4,096 cells), one polytrope",
