@@ -19,6 +19,9 @@
 //   locbar [23][cells]  E0, E1(3), E2(6), E3(10) symmetric adjoints of the
 //                       expansion, and the adjoint of a_c (3)
 //   mombar [20][cells]  dJ/dm, dJ/dX(3), dJ/dM2(6), dJ/dM3(10) (symmetric)
+//   a4     [15][cells]  the interior targets' quartic sums sum_B m_B f4 R^4
+//                       (cell units), added by the forward part's general
+//                       kernel (p.a4_out) and read here once per target
 #include "adjoint.hpp"
 #include "adjoint_pair.cuh"
 #include "items.cuh"
