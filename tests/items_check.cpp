@@ -5,14 +5,16 @@
 // pairs of the parity-class items (32 cells of one parity class over the
 // kept list positions); the adjoint's grouped items of its two passes, and
 // its items of an interior root over the root's own cells, must enumerate
-// exactly the partners each pass reverses; and every index they produce
-// must stay in bounds.
+// exactly the partners each pass reverses, with every interior target in
+// exactly one item that starts its pass-2 range; and every index they
+// produce must stay in bounds.
 //
 // Usage: items_check <leaves.bin> <theta> <chunk>; leaves.bin holds int32
 // (L, ix, iy, iz) rows.  Prints "pairs <n> grouped_items <m> bad <b>" and
 // exits 1 on any mismatch or out-of-bounds index.
 #include <cstdio>
 #include <cstdlib>
+#include <map>
 #include <set>
 #include <tuple>
 #include <vector>
@@ -201,6 +203,29 @@ int main(int argc, char** argv) {
         }
     }
     if (r_want != r_got) bad++;
+    // The reverse pass forms a target's octupole adjoint from the forward
+    // pass's quartic sum once, in the item that starts the target's pass-2
+    // range (range start 0): every interior target with a pass-2 partner lies
+    // in exactly one such item.
+    std::map<std::pair<int, int>, int> first;
+    for (const Item& it : p.items_adj) {
+        const int list = (it.y >> 12) & 15;
+        if (list == kRootList && it.z == 0) {
+            const int par = (it.y >> 8) & 7, half = (it.y >> 11) & 1;
+            for (int lane = 0; lane < 32; lane++) {
+                const int i = 2 * (lane & 3) + (par & 1), j = 2 * ((lane >> 2) & 3) + ((par >> 1) & 1);
+                const int k = 2 * (2 * half + (lane >> 4)) + (par >> 2);
+                first[{it.x, i + 8 * j + 64 * k}]++;
+            }
+        } else if (list == kGroupList && ((it.y >> 16) & 3) == 2 && (it.z & 0xffff) == 0) {
+            for (int lane = 0; lane < 32; lane++) first[{it.x, (int)p.grp_cells[it.w + lane]}]++;
+        }
+    }
+    std::set<std::pair<int, int>> targets;
+    for (const Pair& q : r_want)
+        if (std::get<3>(q) == 2) targets.insert({std::get<0>(q), std::get<1>(q)});
+    for (const auto& tc : targets)
+        if (first.count(tc) == 0 || first[tc] != 1) bad++;
     std::printf("pairs %zu grouped_items %d reverse_pairs %zu bad %d\n", a.size(), grouped, r_want.size(),
                 bad);
     return bad ? 1 : 0;

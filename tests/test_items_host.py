@@ -2,8 +2,10 @@
 the grouped items that the FP64 and FP32-bulk forms run (a node's cells
 regrouped by their numbers of pairs, every lane walking its own parity list)
 cover exactly the pairs of the parity-class items that the other kernels
-run, once each, and the adjoint's grouped items of its two passes the
-partners each pass reverses, with every index in bounds (items_check.cpp)."""
+run, once each, and the adjoint's items of its two passes the partners
+each pass reverses, every interior target in exactly one item that starts
+its pass-2 range (where its octupole adjoint is formed), with every index in
+bounds (items_check.cpp)."""
 import os
 import shutil
 import subprocess
