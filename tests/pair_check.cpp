@@ -75,10 +75,12 @@ static void split_out(int am, double G, const double* R, double mA, const double
 
 // The reverse pair with an interior target (both roles and the R-gradient)
 // in cell units of side h, its outputs printed in physical units: dJ/dmB,
-// dJ/dM2B, dJ/dM3B, dJ/dmA, dJ/dM3A, dJ/dR.
+// dJ/dM2B, dJ/dM3B, dJ/dmA, dJ/dM3A, dJ/dR.  The target's quartic sum comes
+// from reverse_target_quartic, or (from_forward, as the adjoint kernel takes
+// it) from the forward pair's own sum Acc::A4 times kAccCor.
 static void reverse_out(int am, double G, double h, const double* R, double mA, const double* M3A,
                         double mB, const double* M2B, const double* M3B, double E0, const double* E1,
-                        const double* E2, const double* E3, const double* a) {
+                        const double* E2, const double* E3, const double* a, bool from_forward) {
     const double hi = 1.0 / h;
     double Rc[3], M2c[6], M3Bc[10], M3Ac[10], e1[3], e2[6], e3[10], al[3];
     for (int r = 0; r < 3; r++) {
@@ -106,9 +108,18 @@ static void reverse_out(int am, double G, double h, const double* R, double mA, 
     reverse_target_prep<true>(-G * hi * E0, e2, e3, useA, iA, M3Ac, al, tg);
     m2l_pair_reverse<true, true, true>(Rc, mB, M2c, M3Bc, btB, true, useA, iA, M3Ac, -G * hi * E0, e1, e2, e3,
                                        tg, am != 0, al, true, hi * hi, hi * hi * hi, hi, gR, o);
-    // the quartic sum of the target's pairs (here one), which the kernel
-    // takes from the forward pass
-    reverse_target_quartic(Rc, mB, o);
+    // the quartic sum of the target's pairs (here one)
+    if (from_forward) {
+        Acc<double> F;
+        acc_zero(F);
+        double btc[4];
+        trace3(M3Bc, btc);
+        btc[3] = M2c[0] + M2c[3] + M2c[5];
+        m2l_pair<double, true, true, true>(Rc[0], Rc[1], Rc[2], mB, M2c, M3Bc, btc, F);
+        for (int r = 0; r < 15; r++) o.A4[r] = kAccCor * F.A4[r];
+    } else {
+        reverse_target_quartic(Rc, mB, o);
+    }
     if (useA) reverse_target_finish(o, al, -hi * hi * hi / mA);
     std::printf(" %.17g", o.mB);
     for (double v : o.M2B) std::printf(" %.17g", v);
@@ -156,13 +167,14 @@ int main() {
         // adjoint kernel's pass 2 runs it (an interior target): physical
         // units are cell units with h = 1, the adjoints pre-scaled by -G and
         // -G/6
-        reverse_out(am, G, 1.0, R, mA, M3A, mB, M2B, M3B, E0, E1, E2, E3, a);
+        reverse_out(am, G, 1.0, R, mA, M3A, mB, M2B, M3B, E0, E1, E2, E3, a, false);
         split_out<double>(am, G, R, mA, M3A, mB, M2B, M3B, bt);
         split_out<float>(am, G, R, mA, M3A, mB, M2B, M3B, bt);
         // the same in the kernel's cell units (side h = 0.37): R, M2, M3
         // divided by h, h^2, h^3, the adjoints scaled by h^-(n+1) and h^-2,
-        // the moment and R adjoints brought back by h^-2, h^-3, h^-1
-        reverse_out(am, G, 0.37, R, mA, M3A, mB, M2B, M3B, E0, E1, E2, E3, a);
+        // the moment and R adjoints brought back by h^-2, h^-3, h^-1, and the
+        // quartic sum from the forward pair, as the kernel takes it
+        reverse_out(am, G, 0.37, R, mA, M3A, mB, M2B, M3B, E0, E1, E2, E3, a, true);
         // a leaf target (pass 1): no E2, E3, octupole or mass ratio
         {
             PairAdjOut o;

@@ -6,7 +6,9 @@ exactly as the general kernel assembles it (the compact contractions of
 `pair_formula.cuh`, the Kronecker parts of L2 and L3 restored from the
 traces, the correction's target term from the quartic pair sum and the
 target's octupole per unit mass) and its reverse (`adjoint_pair.cuh`: both
-roles and the R-gradient).  The oracle forms every D tensor unpacked
+roles and the R-gradient; in the kernel's cell units the target's quartic
+sum is the forward pair's own, as the adjoint kernel takes it from the
+forward pass).  The oracle forms every D tensor unpacked
 (3^n entries) and sums plain index contractions.  Symmetric tensors travel
 packed; an adjoint's packed entry is the value at each of its positions.
 """
